@@ -1,0 +1,226 @@
+"""ctypes wrapper of the CPU oracle (oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg import this module; the library never does. The oracle
+states the method of "Fast Sparse Matrix Permutation for Mesh-Based Direct
+Solvers" (Algorithms 1-3) plainly and single-threaded, and shares no code with
+the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp into liboracle.so (g++, -O2, single-threaded)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER
+        i32p = P(ctypes.c_int32)
+        i64p = P(ctypes.c_int64)
+        L.oracle_graph_from_faces.restype = ctypes.c_int64
+        L.oracle_graph_from_faces.argtypes = [i32p, ctypes.c_int64, ctypes.c_int32, i32p, i32p, ctypes.c_int64]
+        L.oracle_graph_from_pattern.restype = ctypes.c_int64
+        L.oracle_graph_from_pattern.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, i32p, ctypes.c_int64]
+        L.oracle_seed_hash.restype = ctypes.c_uint64
+        L.oracle_seed_hash.argtypes = [ctypes.c_uint64, ctypes.c_int32]
+        L.oracle_seeds.restype = ctypes.c_int32
+        L.oracle_seeds.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, i32p]
+        L.oracle_voronoi.restype = None
+        L.oracle_voronoi.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p, i32p, i32p]
+        L.oracle_patches.restype = ctypes.c_int32
+        L.oracle_patches.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, i32p]
+        L.oracle_min_degree.restype = None
+        L.oracle_min_degree.argtypes = [i32p, i32p, ctypes.c_int32, i32p]
+        L.oracle_order.restype = ctypes.c_int32
+        L.oracle_order.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_void_p, i32p, i32p, i32p, i32p,
+                                   i32p, i32p, ctypes.c_int32, i32p, i64p]
+        L.oracle_symbolic.restype = None
+        L.oracle_symbolic.argtypes = [i32p, i32p, ctypes.c_int32, i32p, i32p, i32p, i64p, i64p]
+        L.oracle_dof_expand.restype = None
+        L.oracle_dof_expand.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i32p]
+        _lib = L
+    return _lib
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("patch_cap", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lloyd_rounds", ctypes.c_int32),
+                ("nd_level", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+
+
+def _p(a: np.ndarray, t=ctypes.c_int32):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+@dataclass
+class Graph:
+    rowptr: np.ndarray
+    col: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.rowptr.size - 1)
+
+    def neighbors(self, v: int) -> np.ndarray:
+        return self.col[self.rowptr[v]:self.rowptr[v + 1]]
+
+
+def graph_from_faces(faces: np.ndarray, n: int) -> Graph:
+    """Section 2: G = graph of A = (mesh Laplacian pattern) without diagonal."""
+    f = _i32(faces).reshape(-1, 3)
+    nnz = lib().oracle_graph_from_faces(_p(f), f.shape[0], n, None, None, 0)
+    if nnz < 0:
+        raise ValueError("face corner out of range")
+    rp = np.zeros(n + 1, np.int32)
+    col = np.zeros(max(nnz, 1), np.int32)
+    lib().oracle_graph_from_faces(_p(f), f.shape[0], n, _p(rp), _p(col), nnz)
+    return Graph(rp, col[:nnz])
+
+
+def graph_from_pattern(rowptr: np.ndarray, col: np.ndarray, b: int = 1) -> Graph:
+    """Vertex graph of a scalar or b x b block pattern (Section 6.5)."""
+    rp_in = _i32(rowptr); c_in = _i32(col) if len(col) else np.zeros(1, np.int32)
+    nrows = rp_in.size - 1
+    nnz = lib().oracle_graph_from_pattern(_p(rp_in), _p(c_in), nrows, b, None, None, 0)
+    if nnz == -2:
+        raise ValueError("pattern not structurally symmetric")
+    if nnz < 0:
+        raise ValueError("bad pattern")
+    n = nrows // b
+    rp = np.zeros(n + 1, np.int32)
+    out = np.zeros(max(nnz, 1), np.int32)
+    lib().oracle_graph_from_pattern(_p(rp_in), _p(c_in), nrows, b, _p(rp), _p(out), nnz)
+    return Graph(rp, out[:nnz])
+
+
+def _gp(g: Graph):
+    col = g.col if g.col.size else np.zeros(1, np.int32)
+    return _p(g.rowptr), _p(col), col
+
+
+def seed_hash(seed: int, v: int) -> int:
+    return int(lib().oracle_seed_hash(seed, v))
+
+
+def seeds(n: int, cap: int, seed: int) -> np.ndarray:
+    c = lib().oracle_seeds(n, cap, seed, None)
+    out = np.zeros(max(c, 1), np.int32)
+    lib().oracle_seeds(n, cap, seed, _p(out))
+    return out[:c]
+
+
+def voronoi(g: Graph, src, rank, group=None):
+    src = _i32(src); rank = _i32(rank)
+    d = np.zeros(g.n, np.int32); l = np.zeros(g.n, np.int32)
+    rp, cp, _keep = _gp(g)
+    gp = _p(_i32(group)) if group is not None else None
+    grp = _i32(group) if group is not None else None
+    lib().oracle_voronoi(rp, cp, g.n, src.size, _p(src), _p(rank), _p(grp) if grp is not None else None, _p(d), _p(l))
+    return d, l
+
+
+def patches(g: Graph, cap: int, seed: int = 0, lloyd_rounds: int = 2) -> tuple[np.ndarray, int]:
+    lab = np.zeros(g.n, np.int32)
+    rp, cp, _keep = _gp(g)
+    k = lib().oracle_patches(rp, cp, g.n, cap, seed, lloyd_rounds, _p(lab))
+    if k < 0:
+        raise ValueError("bad patch options")
+    return lab, int(k)
+
+
+def min_degree(g: Graph) -> np.ndarray:
+    o = np.zeros(max(g.n, 1), np.int32)
+    rp, cp, _keep = _gp(g)
+    lib().oracle_min_degree(rp, cp, g.n, _p(o))
+    return o[:g.n]
+
+
+@dataclass
+class Ordering:
+    k: int
+    depth: int
+    label: np.ndarray       # gmap: patch id per vertex
+    node_of: np.ndarray     # etree node per vertex
+    perm: np.ndarray        # perm[i] = original vertex at new position i
+    iperm: np.ndarray
+    node_begin: np.ndarray  # per tree node: first position in perm
+    node_size: np.ndarray   # per tree node: number of vertices
+    node_qsum: np.ndarray   # per bisected node: sum of quotient edge weights among its patches (-1 leaf)
+
+
+def order(g: Graph, cap: int, seed: int = 0, lloyd_rounds: int = 2, nd_level: int = 0,
+          schedule: int = 0) -> Ordering:
+    """Algorithm 1: patches -> patch-guided ND etree -> local orders -> perm."""
+    n = g.n
+    o = _Opts(cap, seed, lloyd_rounds, nd_level, schedule)
+    lab = np.zeros(max(n, 1), np.int32); nod = np.zeros(max(n, 1), np.int32)
+    perm = np.zeros(max(n, 1), np.int32); iperm = np.zeros(max(n, 1), np.int32)
+    tree_cap = 4 * max(n, 1) + 8
+    if nd_level > 0:
+        tree_cap = max(tree_cap, (1 << (nd_level + 1)))
+    nb = np.zeros(tree_cap, np.int32); ns = np.zeros(tree_cap, np.int32)
+    depth = np.zeros(1, np.int32)
+    qs = np.zeros(tree_cap, np.int64)
+    rp, cp, _keep = _gp(g)
+    k = lib().oracle_order(rp, cp, n, ctypes.byref(o), _p(lab), _p(nod), _p(perm), _p(iperm),
+                           _p(nb), _p(ns), tree_cap, _p(depth), _p(qs, ctypes.c_int64))
+    if k < 0:
+        raise ValueError(f"oracle_order failed ({k})")
+    D = int(depth[0])
+    nn = (1 << (D + 1)) - 1
+    return Ordering(int(k), D, lab[:n], nod[:n], perm[:n], iperm[:n], nb[:nn].copy(), ns[:nn].copy(),
+                    qs[:nn].copy())
+
+
+@dataclass
+class Symbolic:
+    parent: np.ndarray
+    colcount: np.ndarray
+    nnzL: int
+    flops: int
+
+
+def symbolic(g: Graph, perm: np.ndarray) -> Symbolic:
+    """Elimination tree and column counts of P (G + I) P^T."""
+    n = g.n
+    perm = _i32(perm) if n else np.zeros(1, np.int32)
+    par = np.zeros(max(n, 1), np.int32); cc = np.zeros(max(n, 1), np.int32)
+    nnz = np.zeros(1, np.int64); fl = np.zeros(1, np.int64)
+    rp, cp, _keep = _gp(g)
+    lib().oracle_symbolic(rp, cp, n, _p(perm), _p(par), _p(cc), _p(nnz, ctypes.c_int64), _p(fl, ctypes.c_int64))
+    return Symbolic(par[:n], cc[:n], int(nnz[0]), int(fl[0]))
+
+
+def dof_expand(b: int, perm, parent, colcount):
+    """Section 6.5: vertex ordering + symbolic results -> b DOFs per vertex."""
+    n = len(perm)
+    perm = _i32(perm); parent = _i32(parent); colcount = _i32(colcount)
+    pd = np.zeros(max(n * b, 1), np.int32); ad = np.zeros_like(pd); cd = np.zeros_like(pd)
+    lib().oracle_dof_expand(n, b, _p(perm), _p(parent), _p(colcount), _p(pd), _p(ad), _p(cd))
+    return pd[:n * b], ad[:n * b], cd[:n * b]

@@ -1,0 +1,681 @@
+// Oracle: a plain, slow, single-threaded CPU statement of the patch-guided
+// nested-dissection ordering of "Fast Sparse Matrix Permutation for Mesh-Based
+// Direct Solvers" (Algorithm 1 overview; Algorithm 2 GetSeparator; Algorithm 3
+// ComputePerm; Sections 4.1-4.3 and 5) together with the textbook symbolic
+// Cholesky quantities (elimination tree, column counts).
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the library links or calls this file;
+// only the tests, the smoke check and the benchmark's CPU-baseline leg do.
+// It shares no code, header, table or constant generator with the CUDA path.
+//
+// Where the paper leaves a choice open (its patcher, the METIS bisection and
+// node refinement, AMD) this file follows the deterministic readings of the
+// determinism contract, each restated at the function that implements it.
+// Readability over speed: plain std::vector / std::set / std::map, no
+// blocking, no fusion, no reordering beyond what a definition states.
+//
+// Parity status: every function below is pinned by a CPU test against
+// brute force, a closed form or an invariant, except where its header says
+// "parity unpinned".
+
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <vector>
+
+namespace {
+
+typedef std::vector<std::vector<int32_t>> Adj;   // sorted neighbour lists
+
+const int32_t INF = INT32_MAX;
+
+// SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the output for generator state `s` is the
+// finaliser applied to s + gamma.
+uint64_t splitmix64_at(uint64_t s) {
+  uint64_t z = s + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Contract R1: the seed hash h(v) = SplitMix64 at state seed*gamma + v.
+uint64_t seed_hash(uint64_t seed, int32_t v) {
+  return splitmix64_at(seed * 0x9E3779B97F4A7C15ULL + (uint64_t)(uint32_t)v);
+}
+
+// Contract R9: the tie-break hash of a vertex for separator refinement.
+uint32_t tie_hash(int32_t v) {
+  return (uint32_t)(splitmix64_at((uint64_t)(uint32_t)v) >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Section 2 / Section 4.1 step 2: G is the graph of A without its diagonal.
+// ---------------------------------------------------------------------------
+
+// Undirected simple graph of a face list: {a,b} is an edge iff a and b are
+// consecutive corners of some face and a != b.
+bool graph_from_faces(const int32_t* faces, int64_t nf, int32_t n, Adj& adj) {
+  adj.assign(n, {});
+  for (int64_t f = 0; f < nf; ++f) {
+    for (int c = 0; c < 3; ++c) {
+      int32_t a = faces[3 * f + c], b = faces[3 * f + (c + 1) % 3];
+      if (a < 0 || a >= n || b < 0 || b >= n) return false;
+      if (a == b) continue;
+      adj[a].push_back(b);
+      adj[b].push_back(a);
+    }
+  }
+  for (auto& r : adj) {
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+  }
+  return true;
+}
+
+// Graph of a (scalar or b x b block) symmetric pattern, Section 4.1 step 2 and
+// Section 6.5: each b x b block is merged into one vertex; vertices u != v are
+// adjacent iff some entry of block (u, v) is present. Returns 0 ok, -1 bad
+// index, -2 not structurally symmetric.
+int graph_from_pattern(const int32_t* rowptr, const int32_t* col, int32_t nrows, int32_t b, Adj& adj) {
+  if (b < 1 || nrows % b != 0) return -1;
+  int32_t n = nrows / b;
+  adj.assign(n, {});
+  for (int32_t i = 0; i < nrows; ++i)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      int32_t j = col[e];
+      if (j < 0 || j >= nrows) return -1;
+      if (i / b != j / b) adj[i / b].push_back(j / b);
+    }
+  for (auto& r : adj) {
+    std::sort(r.begin(), r.end());
+    r.erase(std::unique(r.begin(), r.end()), r.end());
+  }
+  for (int32_t u = 0; u < n; ++u)
+    for (int32_t v : adj[u])
+      if (!std::binary_search(adj[v].begin(), adj[v].end(), u)) return -2;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Section 4.1 step 1, GetPatches (Algorithm 1). The paper uses RXMesh's GPU
+// Lloyd patcher; the contract replaces it by seeded BFS Voronoi cells,
+// R Lloyd re-centring rounds and a hard size cap.
+// ---------------------------------------------------------------------------
+
+// Contract R2: multi-source BFS Voronoi labelling. dist(v) is the hop distance
+// to the nearest source along allowed edges; label(v) is the smallest rank
+// among the sources at that distance. An edge {u,v} is allowed iff group is
+// null or group[u] == group[v]. Stated level by level: a vertex first reached
+// at level d takes the minimum label over its neighbours at level d-1.
+// Vertices not reached keep dist INF / label -1.
+void voronoi(const Adj& adj, const std::vector<int32_t>& src, const std::vector<int32_t>& rank,
+             const int32_t* group, std::vector<int32_t>& dist, std::vector<int32_t>& label) {
+  std::vector<int32_t> frontier;
+  for (size_t i = 0; i < src.size(); ++i) {
+    dist[src[i]] = 0;
+    label[src[i]] = rank[i];
+    frontier.push_back(src[i]);
+  }
+  for (int32_t d = 0; !frontier.empty(); ++d) {
+    std::vector<int32_t> next;
+    for (int32_t u : frontier)
+      for (int32_t v : adj[u]) {
+        if (group && group[u] != group[v]) continue;
+        if (dist[v] == INF) {
+          dist[v] = d + 1;
+          label[v] = label[u];
+          next.push_back(v);
+        } else if (dist[v] == d + 1) {
+          label[v] = std::min(label[v], label[u]);
+        }
+      }
+    frontier.swap(next);
+  }
+}
+
+// Contract R1: v is a seed iff (h(v) >> 32) * n < k_target * 2^32 with
+// k_target = max(1, ceil(2n / cap)) (the paper's target patch size is read as
+// a mean of cap/2, Section 6). Seeds are ranked in increasing vertex id.
+void select_seeds(int32_t n, int32_t cap, uint64_t seed, std::vector<int32_t>& seeds) {
+  uint64_t kt = ((uint64_t)2 * (uint64_t)n + (uint64_t)cap - 1) / (uint64_t)cap;
+  if (kt < 1) kt = 1;
+  for (int32_t v = 0; v < n; ++v) {
+    uint64_t u = seed_hash(seed, v) >> 32;
+    if (u * (uint64_t)n < (kt << 32)) seeds.push_back(v);
+  }
+}
+
+struct Patching {
+  std::vector<int32_t> label;        // patch id (= rank) per vertex
+  std::vector<int32_t> seed_of;      // seed vertex per rank
+  int32_t k = 0;
+};
+
+// Full patching: seeds, Voronoi cells, unreached components, R Lloyd rounds,
+// cap splitting (contract R1-R5).
+Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_rounds) {
+  int32_t n = (int32_t)adj.size();
+  Patching P;
+  P.label.assign(n, -1);
+  std::vector<int32_t> dist(n, INF);
+  select_seeds(n, cap, seed, P.seed_of);
+  std::vector<int32_t> ranks(P.seed_of.size());
+  for (size_t r = 0; r < ranks.size(); ++r) ranks[r] = (int32_t)r;
+  voronoi(adj, P.seed_of, ranks, nullptr, dist, P.label);
+
+  // R3: each connected component that no seed reached gets its smallest
+  // vertex id as a new seed; new ranks follow in increasing vertex id.
+  {
+    std::vector<int32_t> extra;
+    std::vector<char> seen(n, 0);
+    for (int32_t v = 0; v < n; ++v) {
+      if (P.label[v] != -1 || seen[v]) continue;
+      extra.push_back(v);
+      std::vector<int32_t> stack = {v};
+      seen[v] = 1;
+      while (!stack.empty()) {
+        int32_t u = stack.back(); stack.pop_back();
+        for (int32_t w : adj[u]) if (!seen[w]) { seen[w] = 1; stack.push_back(w); }
+      }
+    }
+    if (!extra.empty()) {
+      std::vector<int32_t> xr;
+      for (int32_t v : extra) { xr.push_back((int32_t)P.seed_of.size()); P.seed_of.push_back(v); }
+      voronoi(adj, extra, xr, nullptr, dist, P.label);
+    }
+  }
+  P.k = (int32_t)P.seed_of.size();
+
+  // R4 Lloyd rounds: the new seed of a patch is its vertex farthest (in hops
+  // inside the patch) from the patch boundary, ties to the lowest id; a patch
+  // without boundary keeps its seed. Then every vertex is relabelled.
+  for (int32_t it = 0; it < lloyd_rounds; ++it) {
+    std::vector<int32_t> bsrc, bzero;
+    for (int32_t v = 0; v < n; ++v)
+      for (int32_t u : adj[v])
+        if (P.label[u] != P.label[v]) { bsrc.push_back(v); bzero.push_back(0); break; }
+    std::vector<int32_t> depth(n, INF), dummy(n, -1);
+    voronoi(adj, bsrc, bzero, P.label.data(), depth, dummy);
+    std::vector<int32_t> best(P.k, -1);
+    for (int32_t v = 0; v < n; ++v) {
+      if (depth[v] == INF) continue;
+      int32_t p = P.label[v];
+      if (best[p] == -1 || depth[v] > depth[best[p]] || (depth[v] == depth[best[p]] && v < best[p])) best[p] = v;
+    }
+    for (int32_t p = 0; p < P.k; ++p) if (best[p] != -1) P.seed_of[p] = best[p];
+    std::fill(P.label.begin(), P.label.end(), -1);
+    std::fill(dist.begin(), dist.end(), INF);
+    std::vector<int32_t> all(P.k);
+    for (int32_t p = 0; p < P.k; ++p) all[p] = p;
+    voronoi(adj, P.seed_of, all, nullptr, dist, P.label);
+  }
+
+  // R5 cap: while some patch is larger than cap, each such patch gets a second
+  // seed, its vertex farthest from its seed inside the patch (ties to the
+  // lowest id), ranked after all existing ranks in the order of the parent
+  // rank; then only that patch is relabelled from its two seeds.
+  for (;;) {
+    std::vector<int32_t> size(P.k, 0);
+    for (int32_t v = 0; v < n; ++v) size[P.label[v]]++;
+    std::vector<int32_t> over;
+    for (int32_t p = 0; p < P.k; ++p) if (size[p] > cap) over.push_back(p);
+    if (over.empty()) break;
+    std::vector<int32_t> old = P.label;
+    std::vector<int32_t> srcs, srank;
+    for (int32_t p : over) { srcs.push_back(P.seed_of[p]); srank.push_back(p); }
+    std::vector<int32_t> d(n, INF), dl(n, -1);
+    voronoi(adj, srcs, srank, old.data(), d, dl);
+    std::vector<int32_t> far(P.k, -1);
+    for (int32_t v = 0; v < n; ++v) {
+      if (d[v] == INF) continue;
+      int32_t p = old[v];
+      if (far[p] == -1 || d[v] > d[far[p]] || (d[v] == d[far[p]] && v < far[p])) far[p] = v;
+    }
+    std::vector<char> is_over(P.k, 0);
+    for (int32_t p : over) is_over[p] = 1;
+    std::vector<int32_t> s2, r2;
+    for (int32_t p : over) {       // increasing parent rank
+      int32_t r = (int32_t)P.seed_of.size();
+      P.seed_of.push_back(far[p]);
+      s2.push_back(P.seed_of[p]); r2.push_back(p);
+      s2.push_back(far[p]); r2.push_back(r);
+    }
+    for (int32_t v = 0; v < n; ++v) if (is_over[old[v]]) { P.label[v] = -1; dist[v] = INF; }
+    voronoi(adj, s2, r2, old.data(), dist, P.label);
+    P.k = (int32_t)P.seed_of.size();
+  }
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// Section 4.2 BuildEtree with Algorithm 2 GetSeparator, quotient graph built
+// once and updated by weight decrements (Section 5, "Quotient graph
+// computation").
+// ---------------------------------------------------------------------------
+
+struct NDTree {
+  int32_t D = 0;
+  std::vector<int32_t> node_of;        // tree node of every vertex
+};
+
+struct ND {
+  const Adj& adj;
+  const std::vector<int32_t>& patch;
+  int32_t D;
+  std::vector<int32_t> w;                        // R6 node weights
+  std::vector<std::map<int32_t, int32_t>> qw;    // R6 edge weights
+  std::vector<char> removed;
+  std::vector<int32_t> node_of;
+  // scratch, reset after each use so that a node costs O(its own size)
+  std::vector<char> here, released, newsep, inS, sideS, done;
+  std::vector<int32_t> cdeg;
+  std::map<int32_t, int64_t> qsum_at;     // node -> sum of w(p,q), p,q in S (trace)
+
+  ND(const Adj& a, const std::vector<int32_t>& p, int32_t k, int32_t d)
+      : adj(a), patch(p), D(d), w(k, 0), qw(k), removed(a.size(), 0), node_of(a.size(), -1),
+        here(a.size(), 0), released(a.size(), 0), newsep(a.size(), 0), inS(k, 0), sideS(k, 0),
+        done(k, 0), cdeg(a.size(), 0) {
+    // Quotient graph (Section 3 definition; Algorithm 2 step 1), built once.
+    for (size_t v = 0; v < adj.size(); ++v) {
+      w[patch[v]]++;
+      for (int32_t u : adj[v])
+        if (patch[u] != patch[v]) qw[patch[v]][patch[u]]++;
+    }
+  }
+
+  int32_t qdeg(int32_t p, const std::vector<char>& inS) const {
+    int32_t d = 0;
+    for (auto& e : qw[p]) if (e.second > 0 && inS[e.first]) ++d;
+    return d;
+  }
+
+  // BFS levels over the quotient subgraph on S from r (edges of weight > 0).
+  std::vector<std::vector<int32_t>> qbfs(int32_t r, const std::vector<char>& inS) const {
+    std::vector<std::vector<int32_t>> lv = {{r}};
+    std::set<int32_t> seen = {r};
+    while (true) {
+      std::vector<int32_t> nx;
+      for (int32_t p : lv.back())
+        for (auto& e : qw[p])
+          if (e.second > 0 && inS[e.first] && !seen.count(e.first)) { seen.insert(e.first); nx.push_back(e.first); }
+      if (nx.empty()) break;
+      lv.push_back(nx);
+    }
+    return lv;
+  }
+
+  // Contract R8, BiPartition (Algorithm 2 step 2; METIS in the paper): order S
+  // component by component (components by their smallest patch id); inside a
+  // component, r0 = min (degree, id), r1 = min (degree, id) on the last BFS
+  // level from r0, and the patches are ordered by (BFS level from r1, id).
+  // Left = the first ceil(|S|/2) patches of that order.
+  // Returns with sideS[p] set for p in S (0 left, 1 right); inS marks S.
+  void bipartition(const std::vector<int32_t>& S) {
+    for (int32_t p : S) { inS[p] = 1; sideS[p] = 0; done[p] = 0; }
+    std::vector<int32_t> order;
+    std::vector<int32_t> sorted = S;
+    std::sort(sorted.begin(), sorted.end());
+    for (int32_t c0 : sorted) {
+      if (done[c0]) continue;
+      auto comp_lv = qbfs(c0, inS);
+      int32_t r0 = -1, best = INT32_MAX;
+      for (auto& l : comp_lv) for (int32_t p : l) {
+        int32_t dg = qdeg(p, inS);
+        if (dg < best || (dg == best && p < r0)) { best = dg; r0 = p; }
+      }
+      auto lv0 = qbfs(r0, inS);
+      int32_t r1 = -1; best = INT32_MAX;
+      for (int32_t p : lv0.back()) {
+        int32_t dg = qdeg(p, inS);
+        if (dg < best || (dg == best && p < r1)) { best = dg; r1 = p; }
+      }
+      auto lv1 = qbfs(r1, inS);
+      for (auto& l : lv1) {
+        std::vector<int32_t> s = l;
+        std::sort(s.begin(), s.end());
+        for (int32_t p : s) { order.push_back(p); done[p] = 1; }
+      }
+    }
+    size_t nl = (order.size() + 1) / 2;
+    for (size_t i = nl; i < order.size(); ++i) sideS[order[i]] = 1;
+  }
+
+  void node(int32_t t, int32_t depth, std::vector<int32_t> S, const std::vector<int32_t>& verts) {
+    // Patches whose remaining weight is zero take no part (contract R7).
+    std::vector<int32_t> S2;
+    for (int32_t p : S) if (w[p] > 0) S2.push_back(p);
+    S.swap(S2);
+    if (depth == D || S.size() <= 1) {           // leaf: stores the remaining vertices
+      for (int32_t v : verts) node_of[v] = t;
+      return;
+    }
+    bipartition(S);
+    const std::vector<char>& side = sideS;
+    int64_t qs = 0;
+    for (int32_t p : S)
+      for (auto& e : qw[p]) if (inS[e.first]) qs += e.second;
+    qsum_at[t] = qs;
+    for (int32_t v : verts) here[v] = 1;
+
+    // Algorithm 2 step 3, SuperSeparator: remaining vertices of this node with
+    // a neighbour (also remaining here) on the other side.
+    std::vector<int32_t> super;
+    for (int32_t v : verts) {
+      for (int32_t u : adj[v])
+        if (here[u] && side[patch[u]] != side[patch[v]]) cdeg[v]++;
+      if (cdeg[v] > 0) super.push_back(v);
+    }
+    // Algorithm 2 step 4, RefineSeparator (contract R9; METIS node refinement
+    // in the paper): greedily release superset vertices back to their side in
+    // increasing (cdeg, tie_hash, id), a vertex being released iff none of its
+    // crossing neighbours was released before it. The separator is what stays:
+    // a minimal vertex cover of the crossing edges.
+    std::sort(super.begin(), super.end(), [&](int32_t a, int32_t b) {
+      if (cdeg[a] != cdeg[b]) return cdeg[a] < cdeg[b];
+      uint32_t ha = tie_hash(a), hb = tie_hash(b);
+      if (ha != hb) return ha < hb;
+      return a < b;
+    });
+    for (int32_t v : super) {
+      bool ok = true;
+      for (int32_t u : adj[v])
+        if (here[u] && side[patch[u]] != side[patch[v]] && released[u]) { ok = false; break; }
+      if (ok) released[v] = 1;
+    }
+    for (int32_t v : super) if (!released[v]) { newsep[v] = 1; node_of[v] = t; }
+
+    // Section 5: remove the separator's weight from the quotient graph: node
+    // weights lose the separator vertices, edge weights lose every G-edge
+    // between two remaining vertices of different patches that touches the
+    // separator (each such edge once).
+    for (int32_t v : verts) {
+      if (!newsep[v]) continue;
+      w[patch[v]]--;
+      for (int32_t u : adj[v]) {
+        if (!here[u] || patch[u] == patch[v]) continue;
+        if (newsep[u] && u < v) continue;        // counted from u
+        qw[patch[v]][patch[u]]--;
+        qw[patch[u]][patch[v]]--;
+      }
+    }
+    for (int32_t v : verts) if (newsep[v]) removed[v] = 1;
+
+    // Algorithm 2 step 5, LeftRight: children 2t+1 (left) and 2t+2 (right).
+    std::vector<int32_t> SL, SR, VL, VR;
+    for (int32_t p : S) (side[p] ? SR : SL).push_back(p);
+    for (int32_t v : verts) if (!newsep[v]) (side[patch[v]] ? VR : VL).push_back(v);
+    for (int32_t v : verts) { here[v] = 0; released[v] = 0; newsep[v] = 0; cdeg[v] = 0; }
+    for (int32_t p : S) inS[p] = 0;
+    node(2 * t + 1, depth + 1, SL, VL);
+    node(2 * t + 2, depth + 1, SR, VR);
+  }
+};
+
+int32_t ceil_log2(int64_t k) {
+  int32_t d = 0;
+  while (((int64_t)1 << d) < k) ++d;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 step 1, LocalOrder (AMD in the paper; contract R11 reads it as
+// exact minimum degree): repeatedly eliminate the vertex of smallest current
+// degree in the elimination graph, ties to the smallest original id, and make
+// its neighbours a clique.
+// ---------------------------------------------------------------------------
+std::vector<int32_t> min_degree(const Adj& adj, const std::vector<int32_t>& verts) {
+  std::map<int32_t, int32_t> loc;
+  for (size_t i = 0; i < verts.size(); ++i) loc[verts[i]] = (int32_t)i;
+  std::vector<std::set<int32_t>> g(verts.size());
+  for (size_t i = 0; i < verts.size(); ++i)
+    for (int32_t u : adj[verts[i]]) {
+      auto it = loc.find(u);
+      if (it != loc.end()) g[i].insert(it->second);
+    }
+  std::vector<char> alive(verts.size(), 1);
+  std::vector<int32_t> order;
+  for (size_t step = 0; step < verts.size(); ++step) {
+    int32_t p = -1;
+    for (size_t i = 0; i < verts.size(); ++i) {
+      if (!alive[i]) continue;
+      if (p == -1 || g[i].size() < g[p].size() ||
+          (g[i].size() == g[p].size() && verts[i] < verts[p])) p = (int32_t)i;
+    }
+    order.push_back(verts[p]);
+    alive[p] = 0;
+    std::vector<int32_t> nb(g[p].begin(), g[p].end());
+    for (int32_t a : nb) {
+      g[a].erase(p);
+      for (int32_t b : nb) if (b != a) g[a].insert(b);
+    }
+    g[p].clear();
+  }
+  return order;
+}
+
+// Algorithm 3 step 2 with the two schedules of Section 5: post-order (left
+// subtree, right subtree, node) or level order (deepest level first, nodes in
+// index order within a level).
+void concat_schedule(int32_t t, int32_t nnodes, const std::vector<std::vector<int32_t>>& local,
+                     std::vector<int32_t>& perm, std::vector<int32_t>& begin) {
+  if (t >= nnodes) return;
+  concat_schedule(2 * t + 1, nnodes, local, perm, begin);
+  concat_schedule(2 * t + 2, nnodes, local, perm, begin);
+  begin[t] = (int32_t)perm.size();
+  perm.insert(perm.end(), local[t].begin(), local[t].end());
+}
+
+// ---------------------------------------------------------------------------
+// Symbolic Cholesky of B = P (G + I) P^T (textbook: Liu 1990; George & Liu):
+// parent[j] = min{ i > j : L_ij != 0 } (-1 if none), colcount[j] = |{ i >= j :
+// L_ij != 0 }|. The etree follows from the definition via path-compressed
+// ancestors; row i of L is the union of the tree paths from each j < i with
+// B_ij != 0 up to i, which gives the column counts.
+// ---------------------------------------------------------------------------
+void symbolic(const Adj& adj, const int32_t* perm, std::vector<int32_t>& parent,
+              std::vector<int32_t>& colcount, int64_t& nnzL, int64_t& flops) {
+  int32_t n = (int32_t)adj.size();
+  std::vector<int32_t> iperm(n);
+  for (int32_t i = 0; i < n; ++i) iperm[perm[i]] = i;
+  parent.assign(n, -1);
+  std::vector<int32_t> anc(n, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    for (int32_t u : adj[perm[i]]) {
+      int32_t j = iperm[u];
+      if (j >= i) continue;
+      // climb from j to the root of its current subtree, pointing the path at i
+      while (j != -1 && j < i) {
+        int32_t nx = anc[j];
+        anc[j] = i;
+        if (nx == -1) parent[j] = i;
+        j = nx;
+      }
+    }
+  }
+  colcount.assign(n, 1);
+  std::vector<int32_t> mark(n, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    mark[i] = i;
+    for (int32_t u : adj[perm[i]]) {
+      int32_t j = iperm[u];
+      if (j >= i) continue;
+      while (mark[j] != i) { colcount[j]++; mark[j] = i; j = parent[j]; }
+    }
+  }
+  nnzL = 0; flops = 0;
+  for (int32_t j = 0; j < n; ++j) { nnzL += colcount[j]; flops += (int64_t)colcount[j] * colcount[j]; }
+}
+
+Adj adj_from_csr(const int32_t* rowptr, const int32_t* col, int32_t n) {
+  Adj a(n);
+  for (int32_t i = 0; i < n; ++i) a[i].assign(col + rowptr[i], col + rowptr[i + 1]);
+  return a;
+}
+
+int64_t adj_to_csr(const Adj& a, int32_t* rowptr, int32_t* col, int64_t cap) {
+  int64_t nnz = 0;
+  for (auto& r : a) nnz += (int64_t)r.size();
+  if (!rowptr) return nnz;
+  if (nnz > cap) return -3;
+  int64_t e = 0;
+  rowptr[0] = 0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    for (int32_t v : a[i]) col[e++] = v;
+    rowptr[i + 1] = (int32_t)e;
+  }
+  return nnz;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Flat C interface (ctypes) -- test infrastructure only.
+// ===========================================================================
+extern "C" {
+
+typedef struct {
+  int32_t patch_cap;
+  uint64_t seed;
+  int32_t lloyd_rounds;
+  int32_t nd_level;       // 0 = ceil(log2 k)
+  int32_t schedule;       // 0 post-order, 1 level order
+} oracle_opts;
+
+// Graph of a face list. With rowptr == NULL returns nnz (2E) only; else fills
+// rowptr[n+1], col[nnz]. Returns -1 for an out-of-range corner.
+int64_t oracle_graph_from_faces(const int32_t* faces, int64_t nf, int32_t n,
+                                int32_t* rowptr, int32_t* col, int64_t cap) {
+  Adj a;
+  if (!graph_from_faces(faces, nf, n, a)) return -1;
+  return adj_to_csr(a, rowptr, col, cap);
+}
+
+// Vertex graph of a scalar (b = 1) or block pattern. -1 bad input, -2 not
+// structurally symmetric.
+int64_t oracle_graph_from_pattern(const int32_t* rowptr, const int32_t* col, int32_t nrows, int32_t b,
+                                  int32_t* out_rowptr, int32_t* out_col, int64_t cap) {
+  Adj a;
+  int rc = graph_from_pattern(rowptr, col, nrows, b, a);
+  if (rc) return rc;
+  return adj_to_csr(a, out_rowptr, out_col, cap);
+}
+
+uint64_t oracle_seed_hash(uint64_t seed, int32_t v) { return seed_hash(seed, v); }
+
+// Seeds in rank order; returns the count (seeds may be NULL to count only).
+int32_t oracle_seeds(int32_t n, int32_t cap, uint64_t seed, int32_t* seeds) {
+  std::vector<int32_t> s;
+  select_seeds(n, cap, seed, s);
+  if (seeds) std::copy(s.begin(), s.end(), seeds);
+  return (int32_t)s.size();
+}
+
+// Voronoi labelling from explicit sources (group may be NULL).
+void oracle_voronoi(const int32_t* rowptr, const int32_t* col, int32_t n, int32_t nsrc,
+                    const int32_t* src, const int32_t* rank, const int32_t* group,
+                    int32_t* dist_out, int32_t* label_out) {
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> s(src, src + nsrc), r(rank, rank + nsrc), d(n, INF), l(n, -1);
+  voronoi(a, s, r, group, d, l);
+  for (int32_t v = 0; v < n; ++v) { dist_out[v] = d[v] == INF ? -1 : d[v]; label_out[v] = l[v]; }
+}
+
+// Patch labels (gmap); returns k.
+int32_t oracle_patches(const int32_t* rowptr, const int32_t* col, int32_t n, int32_t cap,
+                       uint64_t seed, int32_t lloyd_rounds, int32_t* label) {
+  if (cap < 1) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  Patching P = get_patches(a, cap, seed, lloyd_rounds);
+  std::copy(P.label.begin(), P.label.end(), label);
+  return P.k;
+}
+
+// Exact minimum-degree order of the whole graph.
+void oracle_min_degree(const int32_t* rowptr, const int32_t* col, int32_t n, int32_t* order) {
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> all(n);
+  for (int32_t i = 0; i < n; ++i) all[i] = i;
+  auto o = min_degree(a, all);
+  std::copy(o.begin(), o.end(), order);
+}
+
+// Algorithm 1: patches -> etree -> perm. Outputs (all caller-allocated):
+// label[n] (gmap), node_of[n], perm[n], iperm[n], node_begin/node_size
+// [tree_cap] (positions in perm per tree node), *depth_out. Returns k, or a
+// negative code: -1 bad options, -3 tree_cap too small.
+// node_qsum (nullable, [tree_cap]): for each bisected node, the sum of the
+// quotient edge weights w(p,q) over ordered pairs of its patches at the time
+// it is bisected; -1 for leaves and unused nodes.
+int32_t oracle_order(const int32_t* rowptr, const int32_t* col, int32_t n, const oracle_opts* o,
+                     int32_t* label, int32_t* node_of, int32_t* perm, int32_t* iperm,
+                     int32_t* node_begin, int32_t* node_size, int32_t tree_cap, int32_t* depth_out,
+                     int64_t* node_qsum) {
+  if (o->patch_cap < 1 || o->nd_level < 0 || o->lloyd_rounds < 0) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  Patching P = get_patches(a, o->patch_cap, o->seed, o->lloyd_rounds);
+  int32_t D = o->nd_level > 0 ? o->nd_level : ceil_log2(P.k);
+  int64_t nnodes = ((int64_t)1 << (D + 1)) - 1;
+  if (nnodes > tree_cap) return -3;
+  ND nd(a, P.label, P.k, D);
+  std::vector<int32_t> S(P.k), V(n);
+  for (int32_t p = 0; p < P.k; ++p) S[p] = p;
+  for (int32_t v = 0; v < n; ++v) V[v] = v;
+  nd.node(0, 0, S, V);
+
+  std::vector<std::vector<int32_t>> members(nnodes), local(nnodes);
+  for (int32_t v = 0; v < n; ++v) members[nd.node_of[v]].push_back(v);
+  for (int64_t t = 0; t < nnodes; ++t) local[t] = min_degree(a, members[t]);
+  std::vector<int32_t> pv, begin(nnodes, 0);
+  if (o->schedule == 0) {
+    concat_schedule(0, (int32_t)nnodes, local, pv, begin);
+  } else {
+    for (int32_t d = D; d >= 0; --d)
+      for (int64_t t = ((int64_t)1 << d) - 1; t < ((int64_t)1 << (d + 1)) - 1; ++t) {
+        begin[t] = (int32_t)pv.size();
+        pv.insert(pv.end(), local[t].begin(), local[t].end());
+      }
+  }
+  for (int32_t i = 0; i < n; ++i) { perm[i] = pv[i]; iperm[pv[i]] = i; }
+  std::copy(P.label.begin(), P.label.end(), label);
+  std::copy(nd.node_of.begin(), nd.node_of.end(), node_of);
+  for (int64_t t = 0; t < nnodes; ++t) { node_begin[t] = begin[t]; node_size[t] = (int32_t)members[t].size(); }
+  *depth_out = D;
+  if (node_qsum)
+    for (int64_t t = 0; t < nnodes; ++t) {
+      auto it = nd.qsum_at.find((int32_t)t);
+      node_qsum[t] = it == nd.qsum_at.end() ? -1 : it->second;
+    }
+  return P.k;
+}
+
+// Elimination tree and column counts of P (G + I) P^T.
+void oracle_symbolic(const int32_t* rowptr, const int32_t* col, int32_t n, const int32_t* perm,
+                     int32_t* parent, int32_t* colcount, int64_t* nnzL, int64_t* flops) {
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> p, c;
+  symbolic(a, perm, p, c, *nnzL, *flops);
+  std::copy(p.begin(), p.end(), parent);
+  std::copy(c.begin(), c.end(), colcount);
+}
+
+// Section 6.5: expand a vertex ordering and its symbolic results to b degrees
+// of freedom per vertex (vertex v owns unknowns b*v .. b*v+b-1). Every
+// vertex block is dense, so column b*j+c of L holds the rows b*j+c..b*j+b-1
+// of its own block and all b rows of each vertex below j in column j.
+void oracle_dof_expand(int32_t n, int32_t b, const int32_t* perm, const int32_t* parent,
+                       const int32_t* colcount, int32_t* perm_d, int32_t* parent_d, int32_t* colcount_d) {
+  for (int32_t k = 0; k < n; ++k)
+    for (int32_t c = 0; c < b; ++c) {
+      int64_t i = (int64_t)b * k + c;
+      perm_d[i] = b * perm[k] + c;
+      if (c < b - 1) parent_d[i] = (int32_t)(i + 1);
+      else parent_d[i] = parent[k] < 0 ? -1 : b * parent[k];
+      colcount_d[i] = b * colcount[k] - c;
+    }
+}
+
+}  // extern "C"
