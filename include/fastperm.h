@@ -1,0 +1,200 @@
+/*
+ * fastperm.h — C ABI of the B300 (sm_103a) fill-reducing permutation library.
+ *
+ * Computes the patch-guided nested-dissection ordering of "Fast Sparse Matrix
+ * Permutation for Mesh-Based Direct Solvers" (Algorithm 1: patches -> group
+ * map -> elimination tree -> permutation) for the matrix of a triangle mesh,
+ * plus the elimination tree and column counts of its Cholesky factor. Every
+ * step runs in the library's own CUDA kernels; the host code only sequences
+ * launches on the caller's stream.
+ *
+ * Conventions shared by all calls
+ *  - Pointers named d_* are device pointers (the current CUDA device), h_*
+ *    are host pointers. The caller owns every buffer it passes; the library
+ *    owns the handle and the workspace it allocates (stream-ordered, from a
+ *    library-private memory pool) and frees them in fp_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work of a handle is ordered on the stream given at creation. Calls
+ *    that return host values (h_*) synchronise that stream; the others do not
+ *    unless noted.
+ *  - perm[k] is the original vertex placed at new position k (Algorithm 3's
+ *    "Append" order); iperm[perm[k]] = k. Elimination-tree parents and column
+ *    counts are indexed by new position; a root has parent -1.
+ *  - Errors are returned as fp_status, never thrown. After FP_ERR_CUDA or
+ *    FP_ERR_TIMEOUT the handle is poisoned: further calls return
+ *    FP_ERR_STATE; fp_destroy still releases it. fp_last_error() gives a
+ *    message for the most recent failure.
+ *  - Not thread-safe per handle; distinct handles may be used concurrently.
+ */
+#ifndef FASTPERM_H
+#define FASTPERM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fp_handle fp_handle;
+
+typedef enum {
+  FP_OK = 0,
+  FP_ERR_INVALID_ARG = 1,    /* bad pointer, size, option or face index */
+  FP_ERR_NOT_SYMMETRIC = 2,  /* CSR pattern is not structurally symmetric */
+  FP_ERR_OUT_OF_MEMORY = 3,  /* device allocation failed */
+  FP_ERR_CUDA = 4,           /* a CUDA runtime call failed (handle poisoned) */
+  FP_ERR_TIMEOUT = 5,        /* a bounded device wait ran out (handle poisoned) */
+  FP_ERR_STATE = 6,          /* call order violated or handle poisoned */
+  FP_ERR_UNSUPPORTED = 7     /* input beyond a documented size limit */
+} fp_status;
+
+typedef struct {
+  int32_t patch_cap;       /* hard maximum patch size, >= 1 (default 512). The
+                              seeding targets a mean of cap/2 ("target patch
+                              size", Section 6). */
+  int32_t lloyd_rounds;    /* Lloyd re-centring rounds, >= 0 (default 2) */
+  uint64_t seed;           /* seeds the patch seeding hash (default 0) */
+  int32_t nd_level;        /* nested-dissection depth (Section 4.2); 0 = ceil(log2 k),
+                              which makes every leaf a single patch (default 0) */
+  int32_t schedule;        /* 0 = post-order, 1 = level order (Section 5) */
+  int32_t dof_per_vertex;  /* b >= 1: each vertex owns b consecutive unknowns
+                              (Section 6.5); perm/etree/colcount are then
+                              expanded to n*b entries (default 1) */
+  int32_t reserved;        /* must be 0 */
+} fp_options;
+
+/* Fills *opts with the defaults above. */
+void fp_default_options(fp_options* opts);
+
+/*
+ * Creates a handle from a triangle list (Section 2 / Section 4.1 step 2: G is
+ * the graph of A without its diagonal; for a mesh Laplacian it is the mesh
+ * adjacency). d_faces: int32 [n_faces][3] row-major, corners in
+ * [0, n_vertices); a face with repeated corners contributes only its distinct
+ * edges. Builds the symmetric, sorted, duplicate-free CSR of G on the device.
+ * Errors: FP_ERR_INVALID_ARG (NULL out/opts, n_vertices < 0, n_faces < 0,
+ * bad option, a corner out of range), FP_ERR_UNSUPPORTED (a vertex with more
+ * than 4096 incident face-edges, or more than 2^31-1 adjacency entries),
+ * FP_ERR_OUT_OF_MEMORY, FP_ERR_CUDA. Synchronises `stream` once (validation).
+ */
+fp_status fp_create_from_faces(const int32_t* d_faces, int64_t n_faces, int32_t n_vertices,
+                               const fp_options* opts, void* stream, fp_handle** out);
+
+/*
+ * Creates a handle from a CSR pattern of A (Section 4.1 step 2): d_rowptr
+ * [n_rows+1], d_col [rowptr[n_rows]] (int32, column order arbitrary,
+ * duplicates allowed, diagonal ignored). With opts->dof_per_vertex = b > 1 the
+ * pattern is the unknown-level pattern of n_rows = b*n unknowns and every
+ * b x b block is merged into one vertex (Section 6.5): vertices u != v are
+ * adjacent iff any entry of block (u, v) exists. The vertex graph must be
+ * structurally symmetric. Errors as fp_create_from_faces, plus
+ * FP_ERR_NOT_SYMMETRIC, and FP_ERR_INVALID_ARG if n_rows is not a multiple of
+ * b or an index is out of range. Synchronises `stream` once.
+ */
+fp_status fp_create_from_csr(const int32_t* d_rowptr, const int32_t* d_col, int32_t n_rows,
+                             const fp_options* opts, void* stream, fp_handle** out);
+
+/*
+ * Computes the permutation (Algorithm 1 steps 1-4: patching, patch-guided
+ * nested dissection over the quotient graph (Algorithm 2), local minimum-degree
+ * orderings and their concatenation (Algorithm 3)). d_perm, d_iperm: int32
+ * [n*b], caller-owned device buffers (either may be NULL to skip it).
+ * Synchronises `stream` (the number of patches decides the tree depth).
+ * Errors: FP_ERR_UNSUPPORTED (a tree node larger than 32768 vertices, which
+ * happens only with a small nd_level or a huge patch_cap), FP_ERR_OUT_OF_MEMORY,
+ * FP_ERR_CUDA, FP_ERR_STATE.
+ */
+fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm);
+
+/*
+ * Symbolic Cholesky of P (A) P^T for the last fp_permute: elimination-tree
+ * parent[j] = min{ i > j : L_ij != 0 } (-1 for a root) and colcount[j] =
+ * |{ i >= j : L_ij != 0 }|, both int32 [n*b] indexed by new position and
+ * expanded to DOFs when b > 1 (Section 6.5). h_nnzL = sum of colcount,
+ * h_flops = sum of colcount^2 (the O(sum d(i)^2) cost of Section 6.5); either
+ * host pointer may be NULL. Any device pointer may be NULL to skip it.
+ * Synchronises `stream`. Errors: FP_ERR_STATE (no fp_permute yet),
+ * FP_ERR_OUT_OF_MEMORY, FP_ERR_CUDA.
+ */
+fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL,
+                      int64_t* h_flops);
+
+/* Sizes of the handle: vertices n, DOFs per vertex b, nnz of G (2E). */
+fp_status fp_get_sizes(const fp_handle* h, int32_t* h_n, int32_t* h_dof, int64_t* h_nnz);
+
+/* Copies the CSR of the vertex graph G: d_rowptr [n+1], d_col [nnz]. */
+fp_status fp_get_graph(fp_handle* h, int32_t* d_rowptr, int32_t* d_col);
+
+/* After fp_permute: the group map (patch id per vertex, Section 4.1) into
+ * d_gmap [n] (may be NULL) and the number of patches into *h_k. */
+fp_status fp_get_patches(fp_handle* h, int32_t* d_gmap, int32_t* h_k);
+
+/*
+ * After fp_permute: the nested-dissection tree of Section 4.2 stored as a
+ * binary tree in a 1-D array (children of node t are 2t+1 and 2t+2).
+ * *h_depth = D; the tree has 2^(D+1)-1 nodes. d_node_begin / d_node_size
+ * [2^(D+1)-1]: first position in perm and vertex count of each node (vertex
+ * level, before DOF expansion). d_node_of [n]: the node of every vertex. Call
+ * first with only h_depth to size the buffers; any pointer may be NULL.
+ */
+fp_status fp_get_tree(fp_handle* h, int32_t* h_depth, int32_t* d_node_begin, int32_t* d_node_size,
+                      int32_t* d_node_of);
+
+/*
+ * One-shot host-buffer form (for callers without device buffers): copies
+ * h_faces to the device, runs create + permute + symbolic on `stream`, copies
+ * the results back and destroys the handle. h_perm/h_iperm/h_parent/
+ * h_colcount [n*b] may each be NULL. Returns the first failing status.
+ */
+fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n_vertices,
+                              const fp_options* opts, void* stream, int32_t* h_perm, int32_t* h_iperm,
+                              int32_t* h_parent, int32_t* h_colcount, int64_t* h_nnzL, int64_t* h_flops);
+
+/* Releases the handle and its workspace (stream-ordered). NULL is a no-op. */
+fp_status fp_destroy(fp_handle* h);
+
+/* Message of the last failure on h (or of the last failed create when h is
+ * NULL); never NULL. Valid until the next call on the same handle. */
+const char* fp_last_error(const fp_handle* h);
+
+/* Static name of a status code. */
+const char* fp_status_string(fp_status s);
+
+/* Number of kernel launches the library issued on this handle so far. */
+int64_t fp_launch_count(const fp_handle* h);
+
+/*
+ * Stage profiling (process-wide, off by default). While on, every handle
+ * records a CUDA event pair around each stage's launches on the stream the
+ * stage runs on; fp_profile_read() waits for those events and returns, per
+ * stage kind, the summed GPU milliseconds (ms[kind]) and the number of event
+ * pairs (launches[kind]); it returns FP_PROF_COUNT. Either output may be NULL;
+ * `cap` bounds how many kinds are written. fp_profile_reset() discards the
+ * totals. The paper reports the same breakdown (patching, separators, etree,
+ * local ordering) in its patch-size study (Section 6.6).
+ */
+typedef enum {
+  FP_PROF_GRAPH = 0,       /* a1 CSR assembly */
+  FP_PROF_PATCH_BFS,       /* a2 BFS searches (cooperative) */
+  FP_PROF_PATCH_OTHER,     /* a2 seeds, Lloyd picks, splits */
+  FP_PROF_QUOTIENT,        /* a3 quotient graph */
+  FP_PROF_ND_BISECT,       /* a4 bisection of the quotient graph */
+  FP_PROF_ND_SEPARATOR,    /* a4 superset, refinement, weight update */
+  FP_PROF_LAYOUT,          /* a6 tree layout and vertex lists */
+  FP_PROF_MD_SMALL,        /* a5 minimum degree, nodes <= 512 vertices */
+  FP_PROF_MD_MID,          /* a5 minimum degree, nodes <= 1344 vertices */
+  FP_PROF_MD_LARGE,        /* a5 minimum degree, larger nodes */
+  FP_PROF_PERM,            /* a6/a8 inverse permutation and DOF expansion */
+  FP_PROF_SYMBOLIC,        /* a7 etree and column counts */
+  FP_PROF_COUNT
+} fp_prof_kind;
+
+void fp_profiling(int on);
+int fp_profile_read(double* ms, int64_t* launches, int cap);
+void fp_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTPERM_H */

@@ -1,0 +1,239 @@
+"""Python binding of the fastperm C ABI (include/fastperm.h).
+
+Argument marshalling only: every function forwards to the function of the same
+name in libfastperm.so; PyTorch provides device memory and the CUDA stream.
+There is no fallback: if the shared library cannot be loaded (or built with
+nvcc), importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fastperm.h")
+
+FP_OK = 0
+STATUS = {0: "FP_OK", 1: "FP_ERR_INVALID_ARG", 2: "FP_ERR_NOT_SYMMETRIC", 3: "FP_ERR_OUT_OF_MEMORY",
+          4: "FP_ERR_CUDA", 5: "FP_ERR_TIMEOUT", 6: "FP_ERR_STATE", 7: "FP_ERR_UNSUPPORTED"}
+
+
+class FpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class fp_options(ctypes.Structure):
+    _fields_ = [("patch_cap", ctypes.c_int32), ("lloyd_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("nd_level", ctypes.c_int32), ("schedule", ctypes.c_int32), ("dof_per_vertex", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building in-tree if stale) libfastperm.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        P32, P64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+        opt = ctypes.POINTER(fp_options)
+        sig = {
+            "fp_default_options": (None, [opt]),
+            "fp_create_from_faces": (i32, [vp, i64, i32, opt, vp, ctypes.POINTER(vp)]),
+            "fp_create_from_csr": (i32, [vp, vp, i32, opt, vp, ctypes.POINTER(vp)]),
+            "fp_permute": (i32, [vp, vp, vp]),
+            "fp_symbolic": (i32, [vp, vp, vp, P64, P64]),
+            "fp_get_sizes": (i32, [vp, P32, P32, P64]),
+            "fp_get_graph": (i32, [vp, vp, vp]),
+            "fp_get_patches": (i32, [vp, vp, P32]),
+            "fp_get_tree": (i32, [vp, P32, vp, vp, vp]),
+            "fp_order_faces_host": (i32, [vp, i64, i32, opt, vp, vp, vp, vp, vp, P64, P64]),
+            "fp_destroy": (i32, [vp]),
+            "fp_last_error": (ctypes.c_char_p, [vp]),
+            "fp_status_string": (ctypes.c_char_p, [i32]),
+            "fp_launch_count": (i64, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+def _check(status: int, h=None):
+    if status != FP_OK:
+        raise FpError(status, lib().fp_last_error(h).decode())
+
+
+def fp_default_options(**kw) -> fp_options:
+    o = fp_options()
+    lib().fp_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def fp_create_from_faces(faces, n_vertices: int, opts: fp_options | None = None, stream=None):
+    """faces: int32 CUDA tensor [F, 3]. Returns an opaque handle (c_void_p)."""
+    opts = opts or fp_default_options()
+    h = ctypes.c_void_p()
+    nf = int(faces.shape[0]) if faces is not None else 0
+    _check(lib().fp_create_from_faces(_ptr(faces) if nf else None, nf, int(n_vertices), ctypes.byref(opts),
+                                      _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fp_create_from_csr(rowptr, col, n_rows: int, opts: fp_options | None = None, stream=None):
+    opts = opts or fp_default_options()
+    h = ctypes.c_void_p()
+    _check(lib().fp_create_from_csr(_ptr(rowptr), _ptr(col) if col is not None and col.numel() else None,
+                                    int(n_rows), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fp_permute(h, perm=None, iperm=None):
+    _check(lib().fp_permute(h, _ptr(perm), _ptr(iperm)), h)
+
+
+def fp_symbolic(h, parent=None, colcount=None) -> tuple[int, int]:
+    nnz, fl = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fp_symbolic(h, _ptr(parent), _ptr(colcount), ctypes.byref(nnz), ctypes.byref(fl)), h)
+    return nnz.value, fl.value
+
+
+def fp_get_sizes(h) -> tuple[int, int, int]:
+    n, b, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().fp_get_sizes(h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(nnz)), h)
+    return n.value, b.value, nnz.value
+
+
+def fp_get_graph(h, rowptr=None, col=None):
+    _check(lib().fp_get_graph(h, _ptr(rowptr), _ptr(col)), h)
+
+
+def fp_get_patches(h, gmap=None) -> int:
+    k = ctypes.c_int32()
+    _check(lib().fp_get_patches(h, _ptr(gmap), ctypes.byref(k)), h)
+    return k.value
+
+
+def fp_get_tree(h, node_begin=None, node_size=None, node_of=None) -> int:
+    d = ctypes.c_int32()
+    _check(lib().fp_get_tree(h, ctypes.byref(d), _ptr(node_begin), _ptr(node_size), _ptr(node_of)), h)
+    return d.value
+
+
+def fp_order_faces_host(faces, n_vertices: int, opts: fp_options | None = None, stream=None,
+                        perm=None, iperm=None, parent=None, colcount=None) -> tuple[int, int]:
+    """Host-buffer form: faces and outputs are CPU tensors (pinned for speed)."""
+    opts = opts or fp_default_options()
+    nnz, fl = ctypes.c_int64(), ctypes.c_int64()
+    nf = int(faces.shape[0])
+    _check(lib().fp_order_faces_host(_ptr(faces) if nf else None, nf, int(n_vertices), ctypes.byref(opts),
+                                     _stream(stream), _ptr(perm), _ptr(iperm), _ptr(parent), _ptr(colcount),
+                                     ctypes.byref(nnz), ctypes.byref(fl)))
+    return nnz.value, fl.value
+
+
+def fp_destroy(h):
+    if h:
+        lib().fp_destroy(h)
+
+
+def fp_last_error(h=None) -> str:
+    return lib().fp_last_error(h).decode()
+
+
+def fp_launch_count(h) -> int:
+    return int(lib().fp_launch_count(h))
+
+
+# ---- convenience wrapper ---------------------------------------------------------
+
+@dataclass
+class Result:
+    perm: object
+    iperm: object
+    parent: object
+    colcount: object
+    nnzL: int
+    flops: int
+    k: int
+    depth: int
+    gmap: object
+    node_of: object
+    node_begin: object
+    node_size: object
+    launches: int
+
+
+def order_faces(faces, n_vertices: int, stream=None, symbolic: bool = True, **opt) -> Result:
+    """Create + permute (+ symbolic) for a CUDA face tensor; returns every output
+    as CUDA tensors (perm/iperm/parent/colcount at DOF level, the rest at
+    vertex level)."""
+    import torch
+    o = fp_default_options(**opt)
+    h = fp_create_from_faces(faces, n_vertices, o, stream)
+    try:
+        return _run(h, n_vertices, o, stream, symbolic)
+    finally:
+        fp_destroy(h)
+
+
+def order_csr(rowptr, col, n_rows: int, stream=None, symbolic: bool = True, **opt) -> Result:
+    o = fp_default_options(**opt)
+    h = fp_create_from_csr(rowptr, col, n_rows, o, stream)
+    try:
+        return _run(h, n_rows // o.dof_per_vertex, o, stream, symbolic)
+    finally:
+        fp_destroy(h)
+
+
+def _run(h, n, o, stream, symbolic) -> Result:
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = n * o.dof_per_vertex
+    i32 = dict(dtype=torch.int32, device=dev)
+    perm = torch.empty(max(N, 1), **i32)
+    iperm = torch.empty(max(N, 1), **i32)
+    fp_permute(h, perm, iperm)
+    parent = colcount = None
+    nnz = fl = 0
+    if symbolic:
+        parent = torch.empty(max(N, 1), **i32)
+        colcount = torch.empty(max(N, 1), **i32)
+        nnz, fl = fp_symbolic(h, parent, colcount)
+        parent, colcount = parent[:N], colcount[:N]
+    depth = fp_get_tree(h)
+    nn = (1 << (depth + 1)) - 1
+    nb = torch.empty(nn, **i32)
+    ns = torch.empty(nn, **i32)
+    nod = torch.empty(max(n, 1), **i32)
+    fp_get_tree(h, nb, ns, nod)
+    gmap = torch.empty(max(n, 1), **i32)
+    k = fp_get_patches(h, gmap)
+    torch.cuda.current_stream().synchronize() if stream is None else torch.cuda.synchronize()
+    return Result(perm[:N], iperm[:N], parent, colcount, nnz, fl, k, depth, gmap[:n], nod[:n], nb, ns,
+                  fp_launch_count(h))

@@ -1,0 +1,413 @@
+// C ABI entry points (include/fastperm.h): argument checks, handle and
+// workspace management, and the order of the stages of Algorithm 1 on the
+// caller's stream. Device memory comes from a library-private stream-ordered
+// pool that keeps its reservation, so re-creating handles of similar size
+// costs no driver allocation after the first one.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "fp_internal.cuh"
+
+namespace fp {
+
+namespace {
+std::mutex g_mu;
+cudaMemPool_t g_pools[128];
+bool g_pool_ok[128];
+thread_local std::string g_create_err = "no error";
+
+// stage profiling state
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfRec { int kind; cudaEvent_t a, b; };
+std::vector<ProfRec> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_free;
+double g_prof_ms[FP_PROF_COUNT];
+int64_t g_prof_n[FP_PROF_COUNT];
+
+void prof_drain_locked() {
+  for (auto& r : g_prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess &&
+        r.kind >= 0 && r.kind < FP_PROF_COUNT) {
+      g_prof_ms[r.kind] += ms;
+      g_prof_n[r.kind] += 1;
+    }
+    cudaGetLastError();
+    g_prof_free.push_back(r.a);
+    g_prof_free.push_back(r.b);
+  }
+  g_prof_pending.clear();
+}
+}  // namespace
+
+bool profiling_on() { return g_prof_on; }
+
+cudaEvent_t prof_event() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_free.empty()) {
+    cudaEvent_t e = g_prof_free.back();
+    g_prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_record(int kind, cudaEvent_t a, cudaEvent_t b) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_pending.push_back({kind, a, b});
+  if (g_prof_pending.size() > 4096) prof_drain_locked();
+}
+
+cudaMemPool_t library_pool(int device) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (device < 0 || device >= 128) return nullptr;
+  if (!g_pool_ok[device]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&g_pools[device], &props) != cudaSuccess) return nullptr;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(g_pools[device], cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pool_ok[device] = true;
+  }
+  return g_pools[device];
+}
+
+void* dev_alloc(fp_handle* h, size_t bytes) {
+  void* p = nullptr;
+  cudaMemPool_t pool = library_pool(h->device);
+  if (!pool) return nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (cudaMallocFromPoolAsync(&p, bytes, pool, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  h->allocs.push_back(p);
+  return p;
+}
+
+void dev_free(fp_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it == h->allocs.end()) return;
+  h->allocs.erase(it);
+  cudaFreeAsync(p, h->stream);
+}
+
+fp_status fail(fp_handle* h, fp_status s, const std::string& msg) {
+  if (h) h->err = msg; else g_create_err = msg;
+  if (h && (s == FP_ERR_CUDA || s == FP_ERR_TIMEOUT)) h->poisoned = true;
+  return s;
+}
+
+fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FP_OK;
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(h, FP_ERR_OUT_OF_MEMORY, m);
+  return fail(h, FP_ERR_CUDA, m);
+}
+
+fp_status sync_status(fp_handle* h, int32_t* status_out) {
+  cudaError_t e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "stream");
+  *status_out = *h->h_status;
+  return FP_OK;
+}
+
+}  // namespace fp
+
+using namespace fp;
+
+namespace {
+
+fp_status validate_options(const fp_options* o) {
+  if (!o) return FP_ERR_INVALID_ARG;
+  if (o->patch_cap < 1 || o->lloyd_rounds < 0 || o->lloyd_rounds > 64 || o->nd_level < 0 || o->nd_level > 24 ||
+      (o->schedule != 0 && o->schedule != 1) || o->dof_per_vertex < 1 || o->reserved != 0)
+    return FP_ERR_INVALID_ARG;
+  return FP_OK;
+}
+
+fp_status new_handle(const fp_options* opts, void* stream, int32_t n, fp_handle** out) {
+  fp_handle* h = new fp_handle();
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)stream;
+  h->opt = *opts;
+  h->n = n;
+  h->b = opts->dof_per_vertex;
+  if (cudaMallocHost(&h->h_status, sizeof(int32_t)) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "pinned status word");
+  }
+  h->d_status = (int32_t*)dev_alloc(h, sizeof(int32_t));
+  if (!h->d_status) {
+    cudaFreeHost(h->h_status);
+    delete h;
+    return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "status word");
+  }
+  fill_i32(h, h->d_status, 0, 1);
+  *out = h;
+  return FP_OK;
+}
+
+fp_status finish_create(fp_handle* h, fp_status s, fp_handle** out) {
+  if (s == FP_OK) {
+    const int64_t n = h->n > 0 ? h->n : 1;
+    h->gmap = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    h->node_of = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    h->perm = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    h->iperm = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    if (!h->gmap || !h->node_of || !h->perm || !h->iperm) s = fail(h, FP_ERR_OUT_OF_MEMORY, "handle arrays");
+  }
+  if (s != FP_OK) {
+    g_create_err = h->err;
+    fp_destroy(h);
+    *out = nullptr;
+    return s;
+  }
+  *out = h;
+  return FP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fp_default_options(fp_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->patch_cap = 512;
+  o->lloyd_rounds = 2;
+  o->seed = 0;
+  o->nd_level = 0;
+  o->schedule = 0;
+  o->dof_per_vertex = 1;
+  o->reserved = 0;
+}
+
+fp_status fp_create_from_faces(const int32_t* d_faces, int64_t n_faces, int32_t n_vertices, const fp_options* opts,
+                               void* stream, fp_handle** out) {
+  if (!out) return fail(nullptr, FP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (validate_options(opts) != FP_OK) return fail(nullptr, FP_ERR_INVALID_ARG, "bad options");
+  if (n_vertices < 0 || n_faces < 0 || (n_faces > 0 && !d_faces))
+    return fail(nullptr, FP_ERR_INVALID_ARG, "bad sizes or NULL faces");
+  if ((int64_t)n_vertices * opts->dof_per_vertex > INT32_MAX)
+    return fail(nullptr, FP_ERR_UNSUPPORTED, "n * dof_per_vertex exceeds int32");
+  if (n_faces > INT32_MAX / 6) return fail(nullptr, FP_ERR_UNSUPPORTED, "too many faces");
+  fp_handle* h = nullptr;
+  FP_TRY(new_handle(opts, stream, n_vertices, &h));
+  fp_status s = build_graph_from_faces(h, d_faces, n_faces);
+  return finish_create(h, s, out);
+}
+
+fp_status fp_create_from_csr(const int32_t* d_rowptr, const int32_t* d_col, int32_t n_rows, const fp_options* opts,
+                             void* stream, fp_handle** out) {
+  if (!out) return fail(nullptr, FP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (validate_options(opts) != FP_OK) return fail(nullptr, FP_ERR_INVALID_ARG, "bad options");
+  if (n_rows < 0 || !d_rowptr || n_rows % opts->dof_per_vertex != 0)
+    return fail(nullptr, FP_ERR_INVALID_ARG, "bad n_rows or NULL rowptr");
+  fp_handle* h = nullptr;
+  FP_TRY(new_handle(opts, stream, n_rows / opts->dof_per_vertex, &h));
+  fp_status s = build_graph_from_csr(h, d_rowptr, d_col, n_rows);
+  return finish_create(h, s, out);
+}
+
+fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  h->permuted = false;
+  FP_TRY(run_patching(h));
+  FP_TRY(run_nested_dissection(h));
+  h->nnodes = ((int64_t)1 << (h->D + 1)) - 1;
+  if (h->nnodes > h->node_cap) {
+    dev_free(h, h->node_begin);
+    dev_free(h, h->node_size);
+    h->node_begin = (int32_t*)dev_alloc(h, sizeof(int32_t) * h->nnodes);
+    h->node_size = (int32_t*)dev_alloc(h, sizeof(int32_t) * h->nnodes);
+    if (!h->node_begin || !h->node_size) return fail(h, FP_ERR_OUT_OF_MEMORY, "tree arrays");
+    h->node_cap = h->nnodes;
+  }
+  FP_TRY(run_local_order(h));
+  const int64_t N = (int64_t)h->n * h->b;
+  if (N > 0) {
+    if (h->b == 1) {
+      if (d_perm) cudaMemcpyAsync(d_perm, h->perm, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, h->stream);
+      if (d_iperm) cudaMemcpyAsync(d_iperm, h->iperm, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      launch_dof_expand_perm(h, h->perm, d_perm, d_iperm);
+    }
+  }
+  FP_CHECK_LAUNCH(h, "permute outputs");
+  h->permuted = true;
+  return FP_OK;
+}
+
+fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL, int64_t* h_flops) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "fp_symbolic before fp_permute");
+  const int32_t n = h->n, b = h->b;
+  int32_t* par = (b == 1 && d_parent) ? d_parent : (int32_t*)dev_alloc(h, sizeof(int32_t) * (n > 0 ? n : 1));
+  int32_t* cc = (b == 1 && d_colcount) ? d_colcount : (int32_t*)dev_alloc(h, sizeof(int32_t) * (n > 0 ? n : 1));
+  if (!par || !cc) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic outputs");
+  int64_t nnz = 0, fl = 0;
+  FP_TRY(run_symbolic(h, par, cc, &nnz, &fl));
+  if (b > 1) {
+    launch_dof_expand_symbolic(h, par, cc, d_parent, d_colcount);
+    FP_CHECK_LAUNCH(h, "dof expansion");
+    const int64_t B = b;
+    const int64_t nnz_d = B * B * nnz - (int64_t)n * B * (B - 1) / 2;
+    const int64_t fl_d = B * B * B * fl - B * B * (B - 1) * nnz + (int64_t)n * (B - 1) * B * (2 * B - 1) / 6;
+    nnz = nnz_d;
+    fl = fl_d;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "symbolic sync");
+  }
+  if (par != d_parent) dev_free(h, par);
+  if (cc != d_colcount) dev_free(h, cc);
+  if (h_nnzL) *h_nnzL = nnz;
+  if (h_flops) *h_flops = fl;
+  return FP_OK;
+}
+
+fp_status fp_get_sizes(const fp_handle* h, int32_t* h_n, int32_t* h_dof, int64_t* h_nnz) {
+  if (!h) return FP_ERR_INVALID_ARG;
+  if (h_n) *h_n = h->n;
+  if (h_dof) *h_dof = h->b;
+  if (h_nnz) *h_nnz = h->nnz;
+  return FP_OK;
+}
+
+fp_status fp_get_graph(fp_handle* h, int32_t* d_rowptr, int32_t* d_col) {
+  if (!h) return FP_ERR_INVALID_ARG;
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned");
+  if (d_rowptr) cudaMemcpyAsync(d_rowptr, h->rowptr, sizeof(int32_t) * (h->n + 1), cudaMemcpyDeviceToDevice, h->stream);
+  if (d_col && h->nnz) cudaMemcpyAsync(d_col, h->col, sizeof(int32_t) * h->nnz, cudaMemcpyDeviceToDevice, h->stream);
+  FP_CHECK_LAUNCH(h, "get graph");
+  return FP_OK;
+}
+
+fp_status fp_get_patches(fp_handle* h, int32_t* d_gmap, int32_t* h_k) {
+  if (!h) return FP_ERR_INVALID_ARG;
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "no permutation yet");
+  if (d_gmap && h->n) cudaMemcpyAsync(d_gmap, h->gmap, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  if (h_k) *h_k = h->k;
+  FP_CHECK_LAUNCH(h, "get patches");
+  return FP_OK;
+}
+
+fp_status fp_get_tree(fp_handle* h, int32_t* h_depth, int32_t* d_node_begin, int32_t* d_node_size, int32_t* d_node_of) {
+  if (!h) return FP_ERR_INVALID_ARG;
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "no permutation yet");
+  if (h_depth) *h_depth = h->D;
+  if (d_node_begin) cudaMemcpyAsync(d_node_begin, h->node_begin, sizeof(int32_t) * h->nnodes, cudaMemcpyDeviceToDevice, h->stream);
+  if (d_node_size) cudaMemcpyAsync(d_node_size, h->node_size, sizeof(int32_t) * h->nnodes, cudaMemcpyDeviceToDevice, h->stream);
+  if (d_node_of && h->n) cudaMemcpyAsync(d_node_of, h->node_of, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  FP_CHECK_LAUNCH(h, "get tree");
+  return FP_OK;
+}
+
+fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n_vertices, const fp_options* opts,
+                              void* stream, int32_t* h_perm, int32_t* h_iperm, int32_t* h_parent, int32_t* h_colcount,
+                              int64_t* h_nnzL, int64_t* h_flops) {
+  if (validate_options(opts) != FP_OK || n_vertices < 0 || n_faces < 0 || (n_faces > 0 && !h_faces))
+    return fail(nullptr, FP_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = library_pool(dev);
+  const int64_t N = (int64_t)n_vertices * opts->dof_per_vertex;
+  int32_t* d_faces = nullptr;
+  int32_t* d_out = nullptr;
+  if (cudaMallocFromPoolAsync((void**)&d_faces, sizeof(int32_t) * 3 * (n_faces > 0 ? n_faces : 1), pool, s) != cudaSuccess ||
+      cudaMallocFromPoolAsync((void**)&d_out, sizeof(int32_t) * 4 * (N > 0 ? N : 1), pool, s) != cudaSuccess)
+    return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "staging buffers");
+  if (n_faces > 0) cudaMemcpyAsync(d_faces, h_faces, sizeof(int32_t) * 3 * n_faces, cudaMemcpyHostToDevice, s);
+  fp_handle* h = nullptr;
+  fp_status st = fp_create_from_faces(d_faces, n_faces, n_vertices, opts, stream, &h);
+  if (st == FP_OK) st = fp_permute(h, d_out, d_out + N);
+  int64_t nnz = 0, fl = 0;
+  if (st == FP_OK) st = fp_symbolic(h, d_out + 2 * N, d_out + 3 * N, &nnz, &fl);
+  if (st == FP_OK && N > 0) {
+    int32_t* hs[4] = {h_perm, h_iperm, h_parent, h_colcount};
+    for (int i = 0; i < 4; ++i)
+      if (hs[i]) cudaMemcpyAsync(hs[i], d_out + i * N, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s);
+  }
+  if (st != FP_OK && h) g_create_err = h->err;
+  fp_destroy(h);
+  cudaFreeAsync(d_faces, s);
+  cudaFreeAsync(d_out, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == FP_OK && e != cudaSuccess) return fail(nullptr, FP_ERR_CUDA, cudaGetErrorString(e));
+  if (h_nnzL) *h_nnzL = nnz;
+  if (h_flops) *h_flops = fl;
+  return st;
+}
+
+fp_status fp_destroy(fp_handle* h) {
+  if (!h) return FP_OK;
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+  h->allocs.clear();
+  if (h->h_status) {
+    cudaStreamSynchronize(h->stream);
+    cudaFreeHost(h->h_status);
+  }
+  delete h;
+  return FP_OK;
+}
+
+const char* fp_last_error(const fp_handle* h) {
+  if (h) return h->err.empty() ? "no error" : h->err.c_str();
+  return g_create_err.c_str();
+}
+
+const char* fp_status_string(fp_status s) {
+  switch (s) {
+    case FP_OK: return "FP_OK";
+    case FP_ERR_INVALID_ARG: return "FP_ERR_INVALID_ARG";
+    case FP_ERR_NOT_SYMMETRIC: return "FP_ERR_NOT_SYMMETRIC";
+    case FP_ERR_OUT_OF_MEMORY: return "FP_ERR_OUT_OF_MEMORY";
+    case FP_ERR_CUDA: return "FP_ERR_CUDA";
+    case FP_ERR_TIMEOUT: return "FP_ERR_TIMEOUT";
+    case FP_ERR_STATE: return "FP_ERR_STATE";
+    case FP_ERR_UNSUPPORTED: return "FP_ERR_UNSUPPORTED";
+  }
+  return "FP_ERR_UNKNOWN";
+}
+
+int64_t fp_launch_count(const fp_handle* h) { return h ? h->launches : 0; }
+
+void fp_profiling(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+
+int fp_profile_read(double* ms, int64_t* launches, int cap) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain_locked();
+  for (int i = 0; i < FP_PROF_COUNT && i < cap; ++i) {
+    if (ms) ms[i] = g_prof_ms[i];
+    if (launches) launches[i] = g_prof_n[i];
+  }
+  return FP_PROF_COUNT;
+}
+
+void fp_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_drain_locked();
+  for (int i = 0; i < FP_PROF_COUNT; ++i) { g_prof_ms[i] = 0.0; g_prof_n[i] = 0; }
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations of the fastperm CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fastperm.h"
+
+namespace fp {
+
+constexpr unsigned long long KEY_INF = ~0ull;
+constexpr int NUM_SMS_B300 = 148;
+
+// Device status word bits (set by kernels, read by the host at sync points).
+enum : int32_t {
+  ST_BAD_INDEX = 1 << 0,       // an input index out of range
+  ST_ROW_TOO_LONG = 1 << 1,    // a CSR row beyond the sort capacity
+  ST_NOT_SYMMETRIC = 1 << 2,   // CSR pattern not symmetric
+  ST_POOL_OVERFLOW = 1 << 3,   // a device bump pool ran out (host retries bigger)
+  ST_NODE_TOO_BIG = 1 << 4,    // a tree node beyond the ordering kernel's limit
+  ST_QUOTIENT_TOO_BIG = 1 << 5 // a patch with more cross edges than the sort capacity
+};
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output for generator state s
+// is the finaliser of s + gamma.
+__host__ __device__ __forceinline__ uint64_t splitmix64_state(uint64_t s) {
+  uint64_t z = s + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Workspace;   // per-handle device scratch (fp_api.cu)
+
+}  // namespace fp
+
+struct fp_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  fp_options opt{};
+  int32_t n = 0;         // vertices
+  int32_t b = 1;         // DOFs per vertex
+  int64_t nnz = 0;       // adjacency entries of G (2E)
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+
+  bool permuted = false;
+  bool poisoned = false;
+  int32_t k = 0;         // patches
+  int32_t D = 0;         // tree depth
+  int64_t nnodes = 0;    // 2^(D+1)-1
+
+  // persistent results (vertex level)
+  int32_t* gmap = nullptr;        // [n]
+  int32_t* node_of = nullptr;     // [n]
+  int32_t* perm = nullptr;        // [n]
+  int32_t* iperm = nullptr;       // [n]
+  int32_t* node_begin = nullptr;  // [nnodes]
+  int32_t* node_size = nullptr;   // [nnodes]
+  int64_t node_cap = 0;           // allocated length of node arrays
+
+  int32_t* d_status = nullptr;    // device status word
+  int32_t* h_status = nullptr;    // pinned mirror
+  void* scratch = nullptr;        // generic scratch block
+  size_t scratch_bytes = 0;
+
+  std::string err;
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+};
+
+namespace fp {
+
+// ---- host helpers (fp_api.cu) ------------------------------------------------
+cudaMemPool_t library_pool(int device);
+void* dev_alloc(fp_handle* h, size_t bytes);      // stream-ordered, tracked; nullptr on failure
+void dev_free(fp_handle* h, void* p);
+fp_status fail(fp_handle* h, fp_status s, const std::string& msg);
+fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what);
+fp_status sync_status(fp_handle* h, int32_t* status_out);   // sync stream, read status word
+
+// ---- stage profiling (fp_api.cu) -------------------------------------------------
+bool profiling_on();
+void prof_record(int kind, cudaEvent_t start, cudaEvent_t end);
+cudaEvent_t prof_event();
+// Records an event pair around a scope on `stream` when profiling is on.
+struct ProfScope {
+  int kind;
+  cudaStream_t stream;
+  cudaEvent_t a = nullptr;
+  ProfScope(int k, cudaStream_t s) : kind(k), stream(s) {
+    if (profiling_on()) {
+      a = prof_event();
+      cudaEventRecord(a, stream);
+    }
+  }
+  void end() {
+    if (a) {
+      cudaEvent_t b = prof_event();
+      cudaEventRecord(b, stream);
+      prof_record(kind, a, b);
+      a = nullptr;
+    }
+  }
+  ~ProfScope() { end(); }
+};
+
+// ---- primitives (fp_scan.cu) ---------------------------------------------------
+// Exclusive scan of in[0..n) into out[0..n]; out[n] = total. in != out.
+// `tmp` needs scan_tmp_ints(n) ints.
+int64_t scan_tmp_ints(int64_t n);
+void scan_exclusive(fp_handle* h, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp);
+void fill_i32(fp_handle* h, int32_t* p, int32_t v, int64_t n);
+void iota_i32(fp_handle* h, int32_t* p, int64_t n);
+
+// ---- stages -----------------------------------------------------------------------
+// a1: CSR of G from faces or from a (block) pattern. Allocates h->rowptr/col.
+fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t nf);
+fp_status build_graph_from_csr(fp_handle* h, const int32_t* d_rowptr, const int32_t* d_col, int32_t nrows);
+
+// a2: patching; writes h->gmap and h->k.
+fp_status run_patching(fp_handle* h);
+// a3 + a4: quotient graph and nested dissection; writes h->node_of, h->D.
+fp_status run_nested_dissection(fp_handle* h);
+// a5 + a6: tree layout, local minimum degree, perm/iperm.
+fp_status run_local_order(fp_handle* h);
+// a7: symbolic (vertex level) into parent/colcount [n]; nnz/flops sums.
+fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops);
+// a8: DOF expansion of perm/iperm/parent/colcount (b > 1).
+void launch_dof_expand_perm(fp_handle* h, const int32_t* perm, int32_t* perm_d, int32_t* iperm_d);
+void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32_t* colcount, int32_t* parent_d,
+                                int32_t* colcount_d);
+
+}  // namespace fp
+
+#define FP_LAUNCH(h, kernel, grid, block, smem, ...)                                  \
+  do {                                                                                \
+    kernel<<<(grid), (block), (smem), (h)->stream>>>(__VA_ARGS__);                    \
+    (h)->launches++;                                                                  \
+  } while (0)
+
+#define FP_CHECK_LAUNCH(h, what)                                                      \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess) return fp::check_cuda((h), e_, (what));                    \
+  } while (0)
+
+#define FP_TRY(expr)                                                                  \
+  do {                                                                                \
+    fp_status s_ = (expr);                                                            \
+    if (s_ != FP_OK) return s_;                                                       \
+  } while (0)

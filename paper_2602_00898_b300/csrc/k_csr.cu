@@ -1,0 +1,328 @@
+// a1 CSR assembly (Section 2; Section 4.1 step 2): G = graph of A without its
+// diagonal, as a symmetric CSR with sorted, duplicate-free rows.
+//
+// No global sort: each corner pair is counted and scattered into its row's
+// raw segment (atomics), then every row is sorted and deduplicated on chip
+// (warp-per-row bitonic sort in shared memory; CTA-per-row for long rows), and
+// the unique entries are compacted. Three streaming passes over the faces and
+// two over the raw rows: HBM-bound.
+#include <climits>
+
+#include "fp_internal.cuh"
+
+namespace fp {
+namespace {
+
+constexpr int WARP_ROW_CAP = 256;    // rows up to this many raw entries: one warp
+constexpr int BLOCK_ROW_CAP = 8192;  // longer rows: one CTA; beyond: unsupported
+constexpr int ROW_WARPS = 8;         // warps per CTA in the warp-per-row kernel
+
+// ---- faces ------------------------------------------------------------------------
+
+__global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* __restrict__ cnt,
+                             int32_t* status) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
+    if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) {
+      atomicOr(status, ST_BAD_INDEX);
+      continue;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      int32_t a = c[e], b = c[(e + 1) % 3];
+      if (a == b) continue;
+      atomicAdd(&cnt[a], 1);
+      atomicAdd(&cnt[b], 1);
+    }
+  }
+}
+
+__global__ void k_face_fill(const int32_t* __restrict__ faces, int64_t nf, int32_t n, const int32_t* __restrict__ off,
+                            int32_t* __restrict__ fill, int32_t* __restrict__ raw) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
+    if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) continue;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      int32_t a = c[e], b = c[(e + 1) % 3];
+      if (a == b) continue;
+      raw[off[a] + atomicAdd(&fill[a], 1)] = b;
+      raw[off[b] + atomicAdd(&fill[b], 1)] = a;
+    }
+  }
+}
+
+// ---- CSR pattern (scalar or b x b blocks) -------------------------------------------
+
+__global__ void k_pat_count(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t nrows, int32_t b,
+                            int32_t* __restrict__ cnt, int32_t* status) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+    int32_t u = i / b, c = 0;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int32_t j = col[e];
+      if (j < 0 || j >= nrows) { atomicOr(status, ST_BAD_INDEX); continue; }
+      c += (j / b != u);
+    }
+    if (c) atomicAdd(&cnt[u], c);
+  }
+}
+
+__global__ void k_pat_fill(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t nrows, int32_t b,
+                           const int32_t* __restrict__ off, int32_t* __restrict__ fill, int32_t* __restrict__ raw) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
+    int32_t u = i / b, c = 0;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int32_t j = col[e];
+      c += (j >= 0 && j < nrows && j / b != u);
+    }
+    if (!c) continue;
+    int32_t slot = off[u] + atomicAdd(&fill[u], c);
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      int32_t j = col[e];
+      if (j >= 0 && j < nrows && j / b != u) raw[slot++] = j / b;
+    }
+  }
+}
+
+// ---- row sort + dedupe ----------------------------------------------------------------
+
+// Ascending bitonic sort of buf[0..N) (N a power of two) by the threads
+// [t0, t0 + nthr) of a warp (sync = __syncwarp) or a CTA (sync = __syncthreads).
+template <bool kBlock>
+__device__ __forceinline__ void bitonic_sort(int32_t* buf, int N, int tid, int nthr) {
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < N; i += nthr) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          int32_t a = buf[i], c = buf[ixj];
+          bool up = (i & k) == 0;
+          if ((a > c) == up) { buf[i] = c; buf[ixj] = a; }
+        }
+      }
+      if (kBlock) __syncthreads(); else __syncwarp();
+    }
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 32;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// One warp per row: sort the raw segment, write the unique prefix back in
+// place and its length to ucnt. Rows longer than WARP_ROW_CAP are queued.
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_dedupe_warp(const int32_t* __restrict__ off, int32_t n,
+                                                                      int32_t* __restrict__ raw, int32_t* __restrict__ ucnt,
+                                                                      int32_t* __restrict__ long_rows, int32_t* n_long) {
+  __shared__ int32_t sbuf[ROW_WARPS][WARP_ROW_CAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* buf = sbuf[wid];
+  for (int32_t v = blockIdx.x * ROW_WARPS + wid; v < n; v += gridDim.x * ROW_WARPS) {
+    int32_t b = off[v], L = off[v + 1] - b;
+    if (L > WARP_ROW_CAP) {
+      if (lane == 0) long_rows[atomicAdd(n_long, 1)] = v;
+      continue;
+    }
+    int N = next_pow2(L);
+    for (int i = lane; i < N; i += 32) buf[i] = i < L ? raw[b + i] : INT_MAX;
+    __syncwarp();
+    bitonic_sort<false>(buf, N, lane, 32);
+    int32_t cnt = 0;
+    for (int i0 = 0; i0 < L; i0 += 32) {
+      int i = i0 + lane;
+      bool keep = i < L && (i == 0 || buf[i] != buf[i - 1]);
+      unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) raw[b + cnt + __popc(m & ((1u << lane) - 1))] = buf[i];
+      cnt += __popc(m);
+    }
+    if (lane == 0) ucnt[v] = cnt;
+    __syncwarp();
+  }
+}
+
+__global__ void k_rows_dedupe_block(const int32_t* __restrict__ off, const int32_t* __restrict__ long_rows,
+                                    const int32_t* n_long, int32_t* __restrict__ raw, int32_t* __restrict__ ucnt,
+                                    int32_t* status) {
+  extern __shared__ int32_t buf[];
+  __shared__ int32_t warp_cnt[32];
+  for (int32_t r = blockIdx.x; r < *n_long; r += gridDim.x) {
+    int32_t v = long_rows[r];
+    int32_t b = off[v], L = off[v + 1] - b;
+    if (L > BLOCK_ROW_CAP) {
+      if (threadIdx.x == 0) { atomicOr(status, ST_ROW_TOO_LONG); ucnt[v] = 0; }
+      continue;
+    }
+    int N = next_pow2(L);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) buf[i] = i < L ? raw[b + i] : INT_MAX;
+    __syncthreads();
+    bitonic_sort<true>(buf, N, threadIdx.x, blockDim.x);
+    // serial-order compaction in chunks of blockDim.x
+    int32_t base = 0;
+    for (int i0 = 0; i0 < L; i0 += blockDim.x) {
+      int i = i0 + threadIdx.x;
+      bool keep = i < L && (i == 0 || buf[i] != buf[i - 1]);
+      unsigned m = __ballot_sync(0xffffffffu, keep);
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      if (lane == 0) warp_cnt[wid] = __popc(m);
+      __syncthreads();
+      int32_t before = 0, tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < wid) before += warp_cnt[w];
+        tot += warp_cnt[w];
+      }
+      if (keep) raw[b + base + before + __popc(m & ((1u << lane) - 1))] = buf[i];
+      base += tot;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) ucnt[v] = base;
+    __syncthreads();
+  }
+}
+
+// Copy each row's unique prefix to its final place; warp per row.
+__global__ void k_rows_compact(const int32_t* __restrict__ off, const int32_t* __restrict__ raw, int32_t n,
+                               const int32_t* __restrict__ rowptr, int32_t* __restrict__ col) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
+    int32_t s = off[v], d = rowptr[v], L = rowptr[v + 1] - d;
+    for (int i = lane; i < L; i += 32) col[d + i] = raw[s + i];
+  }
+}
+
+// Structural symmetry: every (u, v) must have (v, u). Warp per row, binary
+// search in the sorted row of v.
+__global__ void k_check_symmetric(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
+                                  int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += (gridDim.x * blockDim.x) >> 5) {
+    for (int32_t e = rowptr[u] + lane; e < rowptr[u + 1]; e += 32) {
+      int32_t v = col[e];
+      int32_t lo = rowptr[v], hi = rowptr[v + 1];
+      while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (col[mid] < u) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= rowptr[v + 1] || col[lo] != u) atomicOr(status, ST_NOT_SYMMETRIC);
+    }
+  }
+}
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// Shared tail: raw rows [off] -> sorted unique CSR in h->rowptr / h->col.
+fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, int32_t* tmp) {
+  const int32_t n = h->n;
+  int32_t* ucnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* long_rows = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* n_long = (int32_t*)dev_alloc(h, sizeof(int32_t));
+  h->rowptr = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  if (!ucnt || !long_rows || !n_long || !h->rowptr) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
+  {
+  ProfScope ps(FP_PROF_GRAPH, h->stream);
+  fill_i32(h, n_long, 0, 1);
+  fill_i32(h, ucnt, 0, n + 1);
+  if (n > 0) {
+    FP_LAUNCH(h, k_rows_dedupe_warp, grid_for(n, ROW_WARPS), ROW_WARPS * 32, 0, off, n, raw, ucnt, long_rows, n_long);
+    FP_LAUNCH(h, k_rows_dedupe_block, NUM_SMS_B300, 512, BLOCK_ROW_CAP * sizeof(int32_t), off, long_rows, n_long, raw,
+              ucnt, h->d_status);
+  }
+  scan_exclusive(h, ucnt, h->rowptr, n, tmp);
+  }
+  FP_CHECK_LAUNCH(h, "graph rows");
+  int32_t nnz = 0;
+  cudaError_t e = cudaMemcpyAsync(&nnz, h->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "read nnz");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, "vertex index out of range");
+  if (st & ST_ROW_TOO_LONG) return fail(h, FP_ERR_UNSUPPORTED, "a vertex has more than 8192 raw adjacency entries");
+  h->nnz = nnz;
+  h->col = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  if (!h->col) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph columns");
+  if (n > 0) {
+    ProfScope ps(FP_PROF_GRAPH, h->stream);
+    FP_LAUNCH(h, k_rows_compact, grid_for((int64_t)n * 32, 256), 256, 0, off, raw, n, h->rowptr, h->col);
+  }
+  FP_CHECK_LAUNCH(h, "graph compact");
+  dev_free(h, ucnt);
+  dev_free(h, long_rows);
+  dev_free(h, n_long);
+  (void)nraw;
+  return FP_OK;
+}
+
+}  // namespace
+
+fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t nf) {
+  const int32_t n = h->n;
+  int32_t* cnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* off = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));
+  if (!cnt || !off || !tmp) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
+  {
+    ProfScope ps(FP_PROF_GRAPH, h->stream);
+    fill_i32(h, cnt, 0, n + 1);
+    if (nf > 0) FP_LAUNCH(h, k_face_count, grid_for(nf, 256), 256, 0, d_faces, nf, n, cnt, h->d_status);
+    scan_exclusive(h, cnt, off, n, tmp);
+  }
+  FP_CHECK_LAUNCH(h, "face count");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, "face corner out of range");
+  int32_t nraw = 0;
+  cudaError_t e = cudaMemcpy(&nraw, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return check_cuda(h, e, "read raw size");
+  if (6 * nf > INT32_MAX) return fail(h, FP_ERR_UNSUPPORTED, "more than 2^31-1 adjacency entries");
+  int32_t* raw = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nraw > 0 ? nraw : 1));
+  if (!raw) return fail(h, FP_ERR_OUT_OF_MEMORY, "raw adjacency");
+  {
+    ProfScope ps(FP_PROF_GRAPH, h->stream);
+    fill_i32(h, cnt, 0, n + 1);
+    if (nf > 0) FP_LAUNCH(h, k_face_fill, grid_for(nf, 256), 256, 0, d_faces, nf, n, off, cnt, raw);
+  }
+  FP_TRY(finish_rows(h, off, raw, nraw, tmp));
+  dev_free(h, cnt);
+  dev_free(h, off);
+  dev_free(h, tmp);
+  dev_free(h, raw);
+  return FP_OK;
+}
+
+fp_status build_graph_from_csr(fp_handle* h, const int32_t* d_rowptr, const int32_t* d_col, int32_t nrows) {
+  const int32_t n = h->n, b = h->b;
+  int32_t* cnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* off = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));
+  if (!cnt || !off || !tmp) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
+  fill_i32(h, cnt, 0, n + 1);
+  if (nrows > 0) FP_LAUNCH(h, k_pat_count, grid_for(nrows, 256), 256, 0, d_rowptr, d_col, nrows, b, cnt, h->d_status);
+  scan_exclusive(h, cnt, off, n, tmp);
+  FP_CHECK_LAUNCH(h, "pattern count");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, "column index out of range");
+  int32_t nraw = 0;
+  cudaError_t e = cudaMemcpy(&nraw, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return check_cuda(h, e, "read raw size");
+  int32_t* raw = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nraw > 0 ? nraw : 1));
+  if (!raw) return fail(h, FP_ERR_OUT_OF_MEMORY, "raw adjacency");
+  fill_i32(h, cnt, 0, n + 1);
+  if (nrows > 0) FP_LAUNCH(h, k_pat_fill, grid_for(nrows, 256), 256, 0, d_rowptr, d_col, nrows, b, off, cnt, raw);
+  FP_TRY(finish_rows(h, off, raw, nraw, tmp));
+  if (n > 0) FP_LAUNCH(h, k_check_symmetric, grid_for((int64_t)n * 32, 256), 256, 0, h->rowptr, h->col, n, h->d_status);
+  FP_CHECK_LAUNCH(h, "symmetry check");
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_NOT_SYMMETRIC) return fail(h, FP_ERR_NOT_SYMMETRIC, "pattern is not structurally symmetric");
+  dev_free(h, cnt);
+  dev_free(h, off);
+  dev_free(h, tmp);
+  dev_free(h, raw);
+  return FP_OK;
+}
+
+}  // namespace fp

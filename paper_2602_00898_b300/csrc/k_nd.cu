@@ -1,0 +1,543 @@
+// a3 quotient graph and a4 patch-guided nested dissection (Section 4.2;
+// Algorithm 2 GetSeparator; Section 5 "Quotient graph computation" and
+// "Separator set computation").
+//
+// The quotient graph (patches as nodes, edge weight = number of G-edges between
+// two patches) is built once; each tree level then
+//   1. bisects every node's patch set on the quotient graph (one CTA per node:
+//      components by smallest patch id, pseudo-peripheral start r1 from two
+//      BFS sweeps, order by (BFS level from r1, id), left = first ceil(m/2));
+//   2. lifts the bisection to the vertices: the superset is every remaining
+//      vertex with a neighbour on the other side (vertex-parallel);
+//   3. refines it to the lexicographically-first maximal independent set of the
+//      crossing graph under the key (cdeg, tie_hash, id) -- Jacobi "local
+//      minimum" rounds in one cooperative launch; the unreleased rest is the
+//      separator (a minimal vertex cover of the crossing edges);
+//   4. removes the separator from the quotient graph by decrementing node and
+//      edge weights (each crossing G-edge once), and moves the other vertices
+//      and patches to the children 2t+1 / 2t+2.
+// All nodes of one depth are processed by the same launches; the host never
+// waits inside the level loop.
+#include <cooperative_groups.h>
+
+#include "fp_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fp {
+namespace {
+
+constexpr int QCAP = 4096;          // cross-edge entries of one patch sorted on chip
+constexpr int ND_THREADS = 256;
+constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
+
+inline int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ---- generic counting sort helpers ----------------------------------------------------
+__global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t* __restrict__ cnt) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t c = key[i];
+    if (c >= 0) atomicAdd(&cnt[c - koff], 1);
+  }
+}
+
+__global__ void k_scatter_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, const int32_t* __restrict__ start,
+                             int32_t* __restrict__ fill, int32_t* __restrict__ list) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t c = key[i];
+    if (c >= 0) list[start[c - koff] + atomicAdd(&fill[c - koff], 1)] = i;
+  }
+}
+
+// ---- a3 quotient graph --------------------------------------------------------------
+// One CTA per patch: gather the patch ids across its cross edges, sort them on
+// chip and run-length encode. kWrite = false counts the distinct neighbours;
+// kWrite = true writes the sorted row (q_col) with its edge weights (q_w).
+template <bool kWrite>
+__global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __restrict__ pstart,
+                                                              const int32_t* __restrict__ pverts,
+                                                              const int32_t* __restrict__ rowptr,
+                                                              const int32_t* __restrict__ col,
+                                                              const int32_t* __restrict__ gmap, int32_t k,
+                                                              const int32_t* __restrict__ q_rowptr, int32_t* qdeg,
+                                                              int32_t* q_col, int32_t* q_w, int32_t* status) {
+  __shared__ int32_t buf[QCAP];
+  __shared__ int32_t starts[QCAP + 1];
+  __shared__ int32_t red[40];
+  __shared__ int32_t cnt;
+  for (int32_t p = blockIdx.x; p < k; p += gridDim.x) {
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int32_t i = pstart[p] + threadIdx.x; i < pstart[p + 1]; i += blockDim.x) {
+      int32_t v = pverts[i];
+      for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        int32_t q = gmap[col[e]];
+        if (q != p) {
+          int32_t s = atomicAdd(&cnt, 1);
+          if (s < QCAP) buf[s] = q;
+        }
+      }
+    }
+    __syncthreads();
+    const int32_t L = cnt;
+    if (L > QCAP) {
+      if (threadIdx.x == 0) { atomicOr(status, ST_QUOTIENT_TOO_BIG); if (!kWrite) qdeg[p] = 0; }
+      __syncthreads();
+      continue;
+    }
+    const int N = pow2_at_least(L, 32);
+    for (int i = L + threadIdx.x; i < N; i += blockDim.x) buf[i] = INT_MAX;
+    __syncthreads();
+    bitonic_sort<true>(buf, N, threadIdx.x, blockDim.x);
+    int32_t base = 0;
+    for (int32_t i0 = 0; i0 < L; i0 += blockDim.x) {
+      int32_t i = i0 + threadIdx.x;
+      int32_t f = (i < L && (i == 0 || buf[i] != buf[i - 1])) ? 1 : 0;
+      int32_t tot;
+      int32_t ex = block_excl_scan_i32(f, &tot, red);
+      if (f) starts[base + ex] = i;
+      base += tot;
+    }
+    if (threadIdx.x == 0) starts[base] = L;
+    __syncthreads();
+    if (!kWrite) {
+      if (threadIdx.x == 0) qdeg[p] = base;
+    } else {
+      const int32_t o = q_rowptr[p];
+      for (int32_t j = threadIdx.x; j < base; j += blockDim.x) {
+        q_col[o + j] = buf[starts[j]];
+        q_w[o + j] = starts[j + 1] - starts[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- a4 step 1: bisection of every node's patch set ----------------------------------
+
+struct BisectArgs {
+  int32_t t0, T;
+  const int32_t* npstart;
+  int32_t* nplist;
+  int32_t* sortbuf;            // [2k + 64]
+  const int32_t* q_rowptr;
+  const int32_t* q_col;
+  const int32_t* q_w;
+  const int32_t* patch_node;
+  int32_t* loc;                // [k] patch -> local index
+  int32_t* ldeg;               // [k] by list position
+  int32_t* ladj;               // [Q] local adjacency inside each patch's quotient row
+  int32_t* lvl;                // [k]
+  int32_t* qa;                 // [k] frontier
+  int32_t* qb;                 // [k] frontier
+  int32_t* mark;               // [k] 0 untouched, 2 current component, 1 done
+  int32_t* hist;               // [k]
+  int32_t* side;               // [k] by patch id
+  int32_t* split;              // [T]
+};
+
+// Level-synchronous BFS over the node's local quotient graph from local `src`.
+// lvl must be -1 on the component. Returns the number of levels.
+__device__ int block_bfs(const BisectArgs& a, const int32_t* L, int32_t base, int32_t src, int32_t* snext) {
+  int32_t* fa = a.qa + base;
+  int32_t* fb = a.qb + base;
+  if (threadIdx.x == 0) {
+    a.lvl[base + src] = 0;
+    fa[0] = src;
+  }
+  __syncthreads();
+  int32_t nf = 1, level = 0;
+  while (nf > 0) {
+    if (threadIdx.x == 0) *snext = 0;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < nf; i += blockDim.x) {
+      int32_t u = __ldcg(&fa[i]);
+      int32_t p = L[u];
+      int32_t e0 = a.q_rowptr[p], e1 = e0 + __ldcg(&a.ldeg[base + u]);
+      for (int32_t e = e0; e < e1; ++e) {
+        int32_t w = __ldcg(&a.ladj[e]);
+        if (atomicCAS(&a.lvl[base + w], -1, level + 1) == -1) fb[atomicAdd(snext, 1)] = w;
+      }
+    }
+    __syncthreads();
+    nf = *snext;
+    int32_t* t = fa; fa = fb; fb = t;
+    ++level;
+    __syncthreads();
+  }
+  return level;
+}
+
+__global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
+  __shared__ int64_t red64[40];
+  __shared__ int32_t red[40];
+  __shared__ int32_t snext;
+  __shared__ int32_t s_lstar, s_rem;
+  for (int32_t ni = blockIdx.x; ni < a.T; ni += gridDim.x) {
+    const int32_t t = a.t0 + ni;
+    const int32_t base = a.npstart[ni];
+    const int32_t m = a.npstart[ni + 1] - base;
+    int32_t* L = a.nplist + base;
+    if (m < 2) {
+      if (threadIdx.x == 0) a.split[ni] = 0;
+      continue;
+    }
+    if (threadIdx.x == 0) a.split[ni] = 1;
+    // sort the node's patches by id (local index order = id order)
+    {
+      int32_t* sb = a.sortbuf + 2 * (int64_t)base;
+      const int N = pow2_at_least(m, 2);
+      for (int32_t i = threadIdx.x; i < N; i += blockDim.x) sb[i] = i < m ? L[i] : INT_MAX;
+      __syncthreads();
+      bitonic_sort<true>(sb, N, threadIdx.x, blockDim.x);
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) L[i] = sb[i];
+      __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.loc[L[i]] = i;
+    __syncthreads();
+    // local quotient subgraph: neighbours in this node with remaining edge weight
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const int32_t p = L[i];
+      int32_t c = 0;
+      const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
+      for (int32_t e = e0; e < e1; ++e) {
+        const int32_t q = a.q_col[e];
+        if (a.q_w[e] > 0 && a.patch_node[q] == t) a.ladj[e0 + c++] = a.loc[q];
+      }
+      a.ldeg[base + i] = c;
+      a.lvl[base + i] = -1;
+      a.mark[base + i] = 0;
+    }
+    __syncthreads();
+    const int32_t half = (m + 1) / 2;
+    int32_t pos = 0;
+    for (;;) {
+      // next component: smallest untouched local index
+      int32_t c0 = INT_MAX;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (__ldcg(&a.mark[base + i]) == 0) { c0 = i; break; }
+      c0 = block_min(c0, red);
+      if (c0 == INT_MAX) break;
+      // sweep 0: discover the component
+      block_bfs(a, L, base, c0, &snext);
+      int64_t best = INT64_MAX;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (__ldcg(&a.mark[base + i]) == 0 && __ldcg(&a.lvl[base + i]) >= 0) {
+          a.mark[base + i] = 2;
+          a.lvl[base + i] = -1;
+          int64_t key = ((int64_t)__ldcg(&a.ldeg[base + i]) << 32) | i;
+          best = key < best ? key : best;
+        }
+      const int32_t r0 = (int32_t)(block_min(best, red64) & 0xffffffff);
+      // sweep 1: from r0 (minimum degree, then id); r1 = min (degree, id) on the last level
+      const int32_t nl0 = block_bfs(a, L, base, r0, &snext);
+      best = INT64_MAX;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (__ldcg(&a.mark[base + i]) == 2) {
+          if (__ldcg(&a.lvl[base + i]) == nl0 - 1) {
+            int64_t key = ((int64_t)__ldcg(&a.ldeg[base + i]) << 32) | i;
+            best = key < best ? key : best;
+          }
+        }
+      const int32_t r1 = (int32_t)(block_min(best, red64) & 0xffffffff);
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (__ldcg(&a.mark[base + i]) == 2) a.lvl[base + i] = -1;
+      __syncthreads();
+      // sweep 2: the order of the component is (level from r1, id)
+      block_bfs(a, L, base, r1, &snext);
+      int32_t cs = 0;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) cs += __ldcg(&a.mark[base + i]) == 2;
+      cs = block_sum(cs, red);
+      if (pos + cs <= half || pos >= half) {
+        const int32_t sd = pos >= half ? 1 : 0;
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (__ldcg(&a.mark[base + i]) == 2) { a.side[L[i]] = sd; a.mark[base + i] = 1; }
+      } else {
+        const int32_t need = half - pos;
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.hist[base + i] = 0;
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (__ldcg(&a.mark[base + i]) == 2) atomicAdd(&a.hist[base + __ldcg(&a.lvl[base + i])], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          int32_t cum = 0, l = 0;
+          while (cum + __ldcg(&a.hist[base + l]) < need) { cum += __ldcg(&a.hist[base + l]); ++l; }
+          s_lstar = l;
+          s_rem = need - cum;
+        }
+        __syncthreads();
+        const int32_t lstar = s_lstar, rem = s_rem;
+        int32_t before = 0;
+        for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
+          const int32_t i = i0 + threadIdx.x;
+          int32_t lv = -2, mk = 0;
+          if (i < m) { mk = __ldcg(&a.mark[base + i]); lv = __ldcg(&a.lvl[base + i]); }
+          const int32_t f = (mk == 2 && lv == lstar) ? 1 : 0;
+          int32_t tot;
+          const int32_t ex = block_excl_scan_i32(f, &tot, red) + before;
+          if (mk == 2) {
+            const int32_t sd = (lv < lstar || (lv == lstar && ex < rem)) ? 0 : 1;
+            a.side[L[i]] = sd;
+            a.mark[base + i] = 1;
+          }
+          before += tot;
+        }
+      }
+      pos += cs;
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// ---- a4 steps 2-4 on the vertices -----------------------------------------------------------------
+
+struct LevelArgs {
+  int32_t n, t0, T;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const int32_t* gmap;
+  int32_t* node_of;
+  int8_t* final_;
+  const int32_t* side;
+  const int32_t* split;
+  int32_t* cdeg;
+  int8_t* vstate;
+  int32_t* cand;
+  int32_t* ctr;                // [0] candidates, [1..3] MIS round flags
+  int32_t* w;
+  const int32_t* q_rowptr;
+  const int32_t* q_col;
+  int32_t* q_w;
+  int32_t* patch_node;
+  int32_t k;
+};
+
+// SuperSeparator (Algorithm 2 step 3): remaining vertices of a split node with
+// a neighbour on the other side. Vertices of nodes that are leaves at this
+// depth become final.
+__global__ void k_nd_superset(LevelArgs a) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+    if (a.final_[v]) continue;
+    const int32_t t = a.node_of[v];
+    if (!a.split[t - a.t0]) { a.final_[v] = 1; continue; }
+    const int32_t sv = a.side[a.gmap[v]];
+    int32_t c = 0;
+    for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+      const int32_t u = a.col[e];
+      c += (a.node_of[u] == t && a.side[a.gmap[u]] != sv);
+    }
+    a.cdeg[v] = c;
+    a.vstate[v] = c ? VS_UND : VS_NONE;
+    if (c) a.cand[atomicAdd(&a.ctr[0], 1)] = v;
+  }
+}
+
+__device__ __forceinline__ bool key_less(int32_t cu, int32_t u, int32_t cv, int32_t v) {
+  if (cu != cv) return cu < cv;
+  const uint32_t hu = tie_hash(u), hv = tie_hash(v);
+  if (hu != hv) return hu < hv;
+  return u < v;
+}
+
+// RefineSeparator (Algorithm 2 step 4): lexicographically-first maximal
+// independent set of the crossing graph in increasing (cdeg, tie_hash, id).
+// A candidate joins (IN = released to its side) when no crossing neighbour is IN
+// and every undecided crossing neighbour has a larger key; it leaves (OUT =
+// separator) once a crossing neighbour is IN. Monotone, so concurrent updates
+// within a round only delay decisions; at most #candidates rounds.
+__global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int32_t nc = __ldcg(&a.ctr[0]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0) { a.ctr[1] = 0; a.ctr[2] = 0; a.ctr[3] = 0; }
+  grid.sync();
+  for (int32_t round = 0; round <= nc; ++round) {
+    if (t0 == 0) a.ctr[1 + (round + 1) % 3] = 0;
+    int32_t undecided = 0;
+    for (int64_t i = t0; i < nc; i += stride) {
+      const int32_t v = __ldcg(&a.cand[i]);
+      if (*(volatile int8_t*)&a.vstate[v] != VS_UND) continue;
+      const int32_t t = a.node_of[v];
+      const int32_t sv = a.side[a.gmap[v]];
+      const int32_t cv = a.cdeg[v];
+      bool any_in = false, is_min = true;
+      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+        const int32_t u = a.col[e];
+        if (a.node_of[u] != t || a.side[a.gmap[u]] == sv) continue;
+        const int8_t s = *(volatile int8_t*)&a.vstate[u];
+        if (s == VS_IN) { any_in = true; break; }
+        if (s == VS_UND && key_less(a.cdeg[u], u, cv, v)) is_min = false;
+      }
+      if (any_in) a.vstate[v] = VS_OUT;
+      else if (is_min) a.vstate[v] = VS_IN;
+      else ++undecided;
+    }
+    if (undecided) atomicAdd(&a.ctr[1 + round % 3], undecided);
+    grid.sync();
+    if (__ldcg(&a.ctr[1 + round % 3]) == 0) break;
+  }
+}
+
+// Separator bookkeeping (Section 5): the OUT vertices stay in node t as its
+// separator; patch weights and quotient edge weights lose them.
+__device__ __forceinline__ void qw_dec(const LevelArgs& a, int32_t p, int32_t q) {
+  int32_t lo = a.q_rowptr[p], hi = a.q_rowptr[p + 1];
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (a.q_col[mid] < q) lo = mid + 1; else hi = mid;
+  }
+  atomicSub(&a.q_w[lo], 1);
+}
+
+__global__ void k_nd_apply(LevelArgs a) {
+  const int32_t nc = a.ctr[0];
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+    const int32_t v = a.cand[i];
+    if (a.vstate[v] != VS_OUT) continue;
+    a.final_[v] = 1;
+    const int32_t pv = a.gmap[v], t = a.node_of[v];
+    atomicSub(&a.w[pv], 1);
+    for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+      const int32_t u = a.col[e];
+      const int32_t pu = a.gmap[u];
+      if (a.node_of[u] != t || pu == pv) continue;
+      if (a.vstate[u] == VS_OUT && u < v) continue;   // counted from u
+      qw_dec(a, pv, pu);
+      qw_dec(a, pu, pv);
+    }
+  }
+}
+
+// LeftRight (Algorithm 2 step 5): the remaining vertices of a split node move to
+// child 2t+1 (left) or 2t+2 (right) with their patch.
+__global__ void k_nd_move(LevelArgs a) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+    if (a.final_[v]) continue;
+    const int32_t t = a.node_of[v];
+    a.node_of[v] = 2 * t + 1 + a.side[a.gmap[v]];
+  }
+}
+
+__global__ void k_nd_patches(LevelArgs a) {
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < a.k; p += gridDim.x * blockDim.x) {
+    const int32_t t = a.patch_node[p];
+    if (t < 0) continue;
+    a.patch_node[p] = (a.split[t - a.t0] && a.w[p] > 0) ? 2 * t + 1 + a.side[p] : -1;
+  }
+}
+
+__global__ void k_zero_i8(int8_t* p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
+}
+
+int ceil_log2(int64_t k) {
+  int d = 0;
+  while (((int64_t)1 << d) < k) ++d;
+  return d;
+}
+
+}  // namespace
+
+fp_status run_nested_dissection(fp_handle* h) {
+  const int32_t n = h->n, k = h->k;
+  const int64_t Q = h->nnz > 0 ? h->nnz : 1;
+  int32_t D = h->opt.nd_level > 0 ? h->opt.nd_level : ceil_log2(k);
+  if (D > 24) return fail(h, FP_ERR_UNSUPPORTED, "nd_level above 24");
+  h->D = D;
+  if (n == 0) return FP_OK;
+  fill_i32(h, h->node_of, 0, n);
+  const int32_t Dsplit = D < ceil_log2(k) ? D : ceil_log2(k);   // deeper nodes hold <= 1 patch
+  if (Dsplit == 0) { FP_CHECK_LAUNCH(h, "nd init"); return FP_OK; }
+
+  const int64_t kk = (int64_t)k + 64;
+  auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
+  int32_t *psize = I(kk), *pstart = I(kk), *pfill = I(kk), *pverts = I(n), *qdeg = I(kk), *q_rowptr = I(kk);
+  int32_t *q_col = I(Q), *q_w = I(Q), *ladj = I(Q), *tmp = I(scan_tmp_ints(kk) + 8);
+  int32_t *patch_node = I(kk), *w = I(kk), *side = I(kk), *loc = I(kk), *ldeg = I(kk), *lvl = I(kk);
+  int32_t *qa = I(kk), *qb = I(kk), *mark = I(kk), *hist = I(kk), *sortbuf = I(2 * kk + 64);
+  int32_t *npcount = I(kk), *npstart = I(kk + 1), *npfill = I(kk), *nplist = I(kk), *split = I(kk);
+  int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8);
+  int8_t* final_ = (int8_t*)dev_alloc(h, n);
+  int8_t* vstate = (int8_t*)dev_alloc(h, n);
+  if (!psize || !pstart || !pfill || !pverts || !qdeg || !q_rowptr || !q_col || !q_w || !ladj || !tmp || !patch_node ||
+      !w || !side || !loc || !ldeg || !lvl || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
+      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate)
+    return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
+
+  const int G = grid_for(n, 256), GK = grid_for(k, 256);
+  ProfScope ps_q(FP_PROF_QUOTIENT, h->stream);
+  // patch vertex lists
+  fill_i32(h, psize, 0, k);
+  FP_LAUNCH(h, k_count_by, G, 256, 0, h->gmap, n, 0, psize);
+  scan_exclusive(h, psize, pstart, k, tmp);
+  fill_i32(h, pfill, 0, k);
+  FP_LAUNCH(h, k_scatter_by, G, 256, 0, h->gmap, n, 0, pstart, pfill, pverts);
+  // quotient graph (a3)
+  const int GQ = k < NUM_SMS_B300 * 8 ? k : NUM_SMS_B300 * 8;
+  FP_LAUNCH(h, k_quotient_rows<false>, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, q_rowptr, qdeg,
+            q_col, q_w, h->d_status);
+  scan_exclusive(h, qdeg, q_rowptr, k, tmp);
+  FP_LAUNCH(h, k_quotient_rows<true>, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, q_rowptr, qdeg,
+            q_col, q_w, h->d_status);
+  // state
+  fill_i32(h, patch_node, 0, k);
+  cudaMemcpyAsync(w, psize, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, h->stream);
+  FP_LAUNCH(h, k_zero_i8, G, 256, 0, final_, (int64_t)n);
+  FP_LAUNCH(h, k_zero_i8, G, 256, 0, vstate, (int64_t)n);
+  FP_CHECK_LAUNCH(h, "quotient graph");
+  ps_q.end();
+
+  int per = 0, sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nd_mis, ND_THREADS, 0);
+  const int gmis_max = sms * (per > 0 ? per : 1);
+
+  for (int32_t d = 0; d < Dsplit; ++d) {
+    const int32_t t0 = (1 << d) - 1, T = 1 << d;
+    ProfScope ps_b(FP_PROF_ND_BISECT, h->stream);
+    fill_i32(h, npcount, 0, T);
+    FP_LAUNCH(h, k_count_by, GK, 256, 0, patch_node, k, t0, npcount);
+    scan_exclusive(h, npcount, npstart, T, tmp);
+    fill_i32(h, npfill, 0, T);
+    FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
+    BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, ladj,
+                  lvl, qa, qb, mark, hist, side, split};
+    const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
+    FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, 0, ba);
+    ps_b.end();
+    ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
+    LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, ctr,
+                 w, q_rowptr, q_col, q_w, patch_node, k};
+    fill_i32(h, ctr, 0, 4);
+    FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
+    {
+      int g = G < gmis_max ? G : gmis_max;
+      void* args[] = {(void*)&la};
+      cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_nd_mis, g, ND_THREADS, args, 0, h->stream);
+      h->launches++;
+      if (e != cudaSuccess) return check_cuda(h, e, "mis launch");
+    }
+    FP_LAUNCH(h, k_nd_apply, G, 256, 0, la);
+    FP_LAUNCH(h, k_nd_move, G, 256, 0, la);
+    FP_LAUNCH(h, k_nd_patches, GK, 256, 0, la);
+    FP_CHECK_LAUNCH(h, "nd level");
+  }
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
+  for (void* p : {(void*)psize, (void*)pstart, (void*)pfill, (void*)pverts, (void*)qdeg, (void*)q_rowptr, (void*)q_col,
+                  (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
+                  (void*)ldeg, (void*)lvl, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
+                  (void*)npcount, (void*)npstart, (void*)npfill, (void*)nplist, (void*)split, (void*)cdeg, (void*)cand,
+                  (void*)ctr, (void*)final_, (void*)vstate})
+    dev_free(h, p);
+  return FP_OK;
+}
+
+}  // namespace fp
