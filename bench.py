@@ -1,0 +1,341 @@
+"""Benchmark: fill-reducing permutation of the icosphere-7 mesh on one B300.
+
+One step = the whole path on one mesh: fp_create_from_faces (CSR assembly) +
+fp_permute (patching, quotient-graph nested dissection, local minimum degree,
+permutation) + fp_symbolic (etree, column counts) + fp_destroy, with the face
+list already resident in HBM. Each step is timed with CUDA events on the
+launching stream; L2 is flushed (256 MB write) between steps, outside the
+events. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload icosphere7|torus1024|grid64]
+
+--impl reference times the CPU oracle (the plain single-threaded statement of
+the method that the tests check the GPU against) on the same workload.
+Under torchrun (N > 1) every rank orders its own replica of the mesh (the path
+does not shard); value counts the vertices of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (generator, patch cap, dof per vertex)
+    "icosphere7": ("icosphere7", 512, 1),
+    "torus1024": ("torus1024", 512, 3),
+    "grid64": ("grid64", 256, 1),
+}
+
+# Algorithmic bytes per mesh vertex and per step for each profiled stage
+# (int32 indices, valence-6 mesh: CSR row 28 B, faces 24 B per vertex).
+#   graph      : read faces 24 + write CSR 28
+#   patch_bfs  : per search: read CSR 28 + neighbour keys 24 + key write 8 = 60
+#   quotient   : one CSR + group-map pass 52
+#   nd         : boundary graph only, about 25% of edges per level, 60 in total
+#   md         : read induced rows + write order 32
+#   perm       : perm + iperm 8
+#   symbolic   : pattern + iperm gather + parent/colcount write 60
+STAGES = ["graph", "patch_bfs", "patch_other", "quotient", "nd_bisect", "nd_separator", "layout",
+          "md_small", "md_mid", "md_large", "perm", "symbolic"]
+BYTES_PER_VERTEX = {"graph": 52, "patch_bfs": 60, "quotient": 52, "nd_separator": 60, "md_small": 32,
+                    "md_mid": 32, "md_large": 32, "perm": 8, "symbolic": 60, "layout": 12}
+PER_LAUNCH_UNITS = {"patch_bfs"}   # bytes per vertex are per launch, not per step
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, lrank
+
+
+def make_mesh(name):
+    import meshgen
+    gen, cap, dof = WORKLOADS[name]
+    return getattr(meshgen, gen)(0), cap, dof
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_step(mesh, cap, dof):
+    import oracle as O
+    g = O.graph_from_faces(mesh.faces, mesh.n)
+    o = O.order(g, cap, seed=0)
+    s = O.symbolic(g, o.perm)
+    if dof > 1:
+        O.dof_expand(dof, o.perm, s.parent, s.colcount)
+    return s
+
+
+def cpu_baseline(mesh, cap, dof, budget_s=20.0, max_runs=8):
+    """The oracle as it stands, single-threaded, on whole copies of the mesh."""
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while len(times) < max_runs and (not times or time.perf_counter() < t_end):
+        t = time.perf_counter()
+        oracle_step(mesh, cap, dof)
+        times.append(time.perf_counter() - t)
+    per = statistics.median(times)
+    return {"value": mesh.n / per / 1e6, "unit": "Mverts/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} whole-mesh runs of the single-threaded oracle (graph + order + symbolic), "
+                      f"median {per * 1e3:.0f} ms, 1 of {os.cpu_count()} host cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    mesh, cap, dof = make_mesh(args.workload)
+    for _ in range(args.warmup):
+        oracle_step(mesh, cap, dof)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s = oracle_step(mesh, cap, dof)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = mesh.n / (ms / 1e3) / 1e6
+    line = {"impl": "reference", "metric": "permutation Mverts/s at 1 GPU", "value": value, "unit": "Mverts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": mesh.n, "faces": mesh.n_faces, "patch_cap": cap,
+                       "dof_per_vertex": dof, "nnzL": s.nnzL},
+            "cpu_baseline": {"value": value, "unit": "Mverts/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} whole-mesh runs of the single-threaded oracle"},
+            "e2e": {"value": value, "unit": "Mverts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2602_00898_b300 as fp
+
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mesh, cap, dof = make_mesh(args.workload)
+    n = mesh.n
+    faces = torch.from_numpy(mesh.faces).to(dev)
+    opts = fp.fp_default_options(patch_cap=cap, dof_per_vertex=dof)
+    N = n * dof
+    perm = torch.empty(N, dtype=torch.int32, device=dev)
+    iperm = torch.empty_like(perm)
+    parent = torch.empty_like(perm)
+    colcount = torch.empty_like(perm)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h = fp.fp_create_from_faces(faces, n, opts)
+        fp.fp_permute(h, perm, iperm)
+        nnz, fl = fp.fp_symbolic(h, parent, colcount)
+        launches = fp.fp_launch_count(h)
+        fp.fp_destroy(h)
+        return nnz, fl, launches
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region
+    fp.lib().fp_profile_reset()
+    fp.lib().fp_profiling(1)
+    clocks = Clocks(lrank)
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        nnz, fl, L = step()
+        ev[i][1].record(stream)
+        launches += L
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    fp.lib().fp_profiling(0)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms_local = sum(ms_steps) / len(ms_steps)
+    import ctypes
+    prof_ms = (ctypes.c_double * 16)()
+    prof_n = (ctypes.c_int64 * 16)()
+    fp.lib().fp_profile_read.restype = ctypes.c_int
+    fp.lib().fp_profile_read(prof_ms, prof_n, 16)
+    stage_ms = {STAGES[i]: prof_ms[i] / args.steps for i in range(len(STAGES))}
+    stage_n = {STAGES[i]: prof_n[i] / args.steps for i in range(len(STAGES))}
+
+    ms = ms_local
+    if ws > 1:
+        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n / (ms / 1e3) / 1e6
+
+    # permutation alone (fp_permute), for the "permutation ms" part of the metric
+    h = fp.fp_create_from_faces(faces, n, opts)
+    torch.cuda.synchronize()
+    pms = []
+    for _ in range(5):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fp.fp_permute(h, perm, iperm)
+        b.record(stream)
+        b.synchronize()
+        pms.append(a.elapsed_time(b))
+    k = fp.fp_get_patches(h)
+    depth = fp.fp_get_tree(h)
+    _, _, nnzA2 = fp.fp_get_sizes(h)
+    fp.fp_destroy(h)
+
+    # end to end through the host-buffer entry point
+    hfaces = torch.from_numpy(mesh.faces).pin_memory()
+    houts = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in range(4)]
+    e2e_ms = []
+    for i in range(3 + max(5, args.steps // 4)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fp.fp_order_faces_host(hfaces, n, opts, None, *houts)
+        b.record(stream)
+        b.synchronize()
+        if i >= 3:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e = statistics.mean(e2e_ms)
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the dominant stage (largest GPU time in the timed region)
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    peak, peak_kind = peaks()
+    roof = None
+    if dom in BYTES_PER_VERTEX and stage_n[dom] > 0:
+        per_launch_ms = stage_ms[dom] / stage_n[dom]
+        units = n if dom in PER_LAUNCH_UNITS else n / stage_n[dom]
+        bytes_launch = BYTES_PER_VERTEX[dom] * units
+        achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_launch, "launch_ms": per_launch_ms}
+    nnzA = nnzA2 // 2 + n
+    line = {
+        "metric": "permutation Mverts/s at 1 GPU", "value": value, "unit": "Mverts/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "faces": mesh.n_faces, "patch_cap": cap, "dof_per_vertex": dof,
+                   "step": "create+permute+symbolic+destroy", "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "permute_ms": statistics.median(pms),
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "nnzL": nnz, "nnzA": nnzA, "fill_ratio": nnz / nnzA, "flops": fl, "patches": k, "tree_depth": depth,
+        "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": n / (e2e / 1e3) / 1e6, "unit": "Mverts/s", "ms": e2e,
+                "h2d_bytes_per_step": int(mesh.faces.nbytes),
+                "d2h_bytes_per_step": int(4 * 4 * N + 16)},
+        "gpu_launches": int(launches),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mesh, cap, dof)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="icosphere7")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

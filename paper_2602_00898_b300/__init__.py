@@ -60,6 +60,9 @@ def lib() -> ctypes.CDLL:
             "fp_last_error": (ctypes.c_char_p, [vp]),
             "fp_status_string": (ctypes.c_char_p, [i32]),
             "fp_launch_count": (i64, [vp]),
+            "fp_profiling": (None, [ctypes.c_int]),
+            "fp_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), P64, ctypes.c_int]),
+            "fp_profile_reset": (None, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
