@@ -116,6 +116,31 @@ fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what) {
   return fail(h, FP_ERR_CUDA, m);
 }
 
+int32_t* pinned_scratch() {
+  thread_local int32_t* buf = nullptr;
+  if (!buf && cudaMallocHost(&buf, 256 * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    buf = nullptr;
+  }
+  return buf;
+}
+
+AuxStream* aux_stream(int device) {
+  thread_local AuxStream cache[128];
+  if (device < 0 || device >= 128) return nullptr;
+  AuxStream& a = cache[device];
+  if (!a.s) {
+    if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      a.s = nullptr;
+      return nullptr;
+    }
+  }
+  return &a;
+}
+
 fp_status sync_status(fp_handle* h, int32_t* status_out) {
   cudaError_t e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -81,6 +81,15 @@ void dev_free(fp_handle* h, void* p);
 fp_status fail(fp_handle* h, fp_status s, const std::string& msg);
 fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what);
 fp_status sync_status(fp_handle* h, int32_t* status_out);   // sync stream, read status word
+// Per-thread pinned host scratch of 256 ints (allocated once per thread).
+int32_t* pinned_scratch();
+// Per-thread, per-device auxiliary stream with a fork and a join event, created
+// once and reused (stage kernels that overlap run on it).
+struct AuxStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+AuxStream* aux_stream(int device);
 
 // ---- stage profiling (fp_api.cu) -------------------------------------------------
 bool profiling_on();

@@ -6,27 +6,40 @@
 // deepest level first, node index ascending), one CTA.
 //
 // LocalOrder: exact minimum degree on the node's induced subgraph (the paper
-// uses AMD; ties go to the smallest original vertex id). One CTA per node holds
-// the elimination graph as a bit matrix (row i = neighbours of local vertex i):
-// each step takes the arg-min of (degree, local index) -- local indices follow
-// the original ids -- and ORs the pivot row into every neighbour's row, which
-// makes the neighbourhood a clique, then recounts those degrees with popc.
-//   * small nodes (m <= 512, the leaf patches): one warp per node, rows in
-//     shared memory, no CTA barriers;
-//   * mid nodes (m <= 1344): 256 threads, rows in shared memory (<= 221 KB);
-//   * large nodes (m <= 32768): 256 threads, rows in global memory.
-// The kinds run on two streams so that the long serial separator orderings
-// overlap the leaves.
+// uses AMD; ties go to the smallest original vertex id, i.e. the smallest local
+// index, local indices being assigned in id order). Each step takes the vertex
+// of minimum (degree, local index), makes its neighbourhood a clique and
+// updates the neighbours' degrees. The arg-min is O(1): alive vertices sit in
+// degree buckets (one bitmap per small degree, one shared overflow bucket); the
+// lowest non-empty bucket is a ballot over the bucket counts and its lowest set
+// bit is the pivot. Only when every remaining degree is in the overflow bucket
+// does a warp scan all degrees. Three kernels by node size:
+//   * leaf (m <= 512, the patch leaves and small separators): the elimination
+//     graph is a bit matrix in shared memory stored word-major (word w of row u
+//     at R[w*S + u], S = m|1 odd so that a row's words fall in distinct banks);
+//     each warp orders its own node and updates one neighbour per lane;
+//   * sparse (separators up to ~4300 vertices): separators' elimination graphs
+//     stay very sparse, so each vertex keeps an adjacency list of at most
+//     SP_CAP entries in shared memory; the CTA builds the lists, one warp
+//     eliminates, one neighbour per lane. A list that would outgrow SP_CAP
+//     flags the node, which is then redone by the global kernel;
+//   * global (anything larger, or a flagged sparse node): bit rows in global
+//     memory, a CTA per node.
+// The separator kernels run on a second stream so that their long serial
+// orderings overlap the leaves; the leaf kernel leaves them free SMs.
 #include "fp_device.cuh"
 
 namespace fp {
 namespace {
 
-constexpr int MD_SMALL = 512;
-constexpr int MD_MID = 1344;
+constexpr int MD_LEAF = 512;
 constexpr int MD_MAX = 32768;
 constexpr int MD_THREADS = 256;
+constexpr int SP_CAP = 24;
+constexpr int NBK_LEAF = 32;
+constexpr int NBK_SP = 16;
 constexpr uint16_t DEG_DEAD = 0xffff;
+constexpr size_t SMEM_MAX = 225 * 1024;
 
 inline int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -110,61 +123,388 @@ struct MdArgs {
   int32_t* perm;              // [n] output
   const int32_t* nodes;       // node ids handled by this launch
   int32_t nnodes_launch;
-  uint32_t* grows;            // large kind: row storage base
-  const int64_t* grow_off;    // large kind: per launched node, word offset into grows
-  int32_t* gsort;             // large kind: sort scratch base
-  const int64_t* gsort_off;   // large kind: per launched node, int offset into gsort
+  uint32_t* grows;            // global kernel: row storage base
+  const int64_t* grow_off;    // global kernel: per launched node, word offset into grows
+  int32_t* gsort;             // global kernel: sort scratch base
+  const int64_t* gsort_off;   // global kernel: per launched node, int offset into gsort
+  int64_t slice_bytes;        // leaf kernel: shared bytes per warp
+  int32_t* overflow;          // sparse kernel: per launched node flag; global kernel: only flagged nodes
 };
 
-// Minimum degree for one node. kNT threads; kind 0 small (one warp, smem rows),
-// 1 mid (smem rows), 2 large (global rows).
-template <int kNT, int kKind>
-__global__ void __launch_bounds__(kNT) k_md(MdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t red32[40];
-  __shared__ int32_t redi[40];
-  __shared__ int32_t s_nnb;
-  constexpr bool kWarp = (kNT == 32);
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int kWarps = kNT / 32;
+template <int NBK>
+__device__ __forceinline__ int bucket_of(uint32_t d) {
+  return d < (uint32_t)(NBK - 1) ? (int)d : NBK - 1;
+}
 
+// Degree buckets of the alive vertices: bit u of bits[d*W + u/32] is set iff u
+// is alive with bucket d (degree d, or >= NBK-1 for d = NBK-1); cnt[d] counts
+// bucket d; bit j of sum[d*SW + s] is set if bits[d*W + 32s + j] may be
+// non-zero (set on insertion, cleared lazily by the arg-min when it finds the
+// word empty). Removals and insertions run in separate warp phases.
+struct Buckets {
+  uint32_t* bits;
+  uint32_t* sum;
+  int32_t* cnt;
+  int W, SW;
+};
+
+__device__ __forceinline__ void bk_remove(const Buckets& B, int d, int u) {
+  atomicAnd(&B.bits[d * B.W + (u >> 5)], ~(1u << (u & 31)));
+  atomicSub(&B.cnt[d], 1);
+}
+
+__device__ __forceinline__ void bk_insert(const Buckets& B, int d, int u) {
+  const int w = u >> 5;
+  atomicOr(&B.bits[d * B.W + w], 1u << (u & 31));
+  atomicOr(&B.sum[d * B.SW + (w >> 5)], 1u << (w & 31));
+  atomicAdd(&B.cnt[d], 1);
+}
+
+// Arg-min of (degree, local index) over the alive vertices, by one warp.
+template <int NBK>
+__device__ __forceinline__ int warp_argmin(const Buckets& B, const uint16_t* deg, int m) {
+  const int lane = threadIdx.x & 31;
+  const unsigned ne = __ballot_sync(0xffffffffu, lane < NBK && B.cnt[lane] > 0);
+  const int dstar = __ffs(ne) - 1;
+  if (dstar >= 0 && dstar < NBK - 1) {
+    // the bucket is not empty, so some summarised word is non-zero; words
+    // found empty get their summary bit cleared (only this warp writes here)
+    for (int s0 = 0; s0 < B.SW;) {
+      const uint32_t sv = s0 + lane < B.SW ? B.sum[dstar * B.SW + s0 + lane] : 0u;
+      const unsigned nz = __ballot_sync(0xffffffffu, sv != 0u);
+      if (!nz) { s0 += 32; continue; }
+      const int l = __ffs(nz) - 1;
+      const uint32_t svl = __shfl_sync(0xffffffffu, sv, l);
+      const int w = (s0 + l) * 32 + __ffs(svl) - 1;
+      const uint32_t x = B.bits[dstar * B.W + w];
+      if (x) return w * 32 + __ffs(x) - 1;
+      if (lane == 0) B.sum[dstar * B.SW + (w >> 5)] = svl & ~(1u << (w & 31));
+      __syncwarp();
+    }
+  }
+  uint32_t best = 0xffffffffu;
+  for (int i = lane; i < m; i += 32) {
+    const uint16_t dg = deg[i];
+    if (dg != DEG_DEAD) {
+      const uint32_t key = ((uint32_t)dg << 16) | (uint32_t)i;
+      best = key < best ? key : best;
+    }
+  }
+  return (int)(__reduce_min_sync(0xffffffffu, best) & 0xffffu);
+}
+
+template <int NBK>
+__device__ __forceinline__ void buckets_build(const Buckets& B, const uint16_t* deg, int m, int me, int nt,
+                                              bool cta) {
+  for (int i = me; i < NBK * B.W; i += nt) B.bits[i] = 0u;
+  for (int i = me; i < NBK * B.SW; i += nt) B.sum[i] = 0u;
+  for (int i = me; i < NBK; i += nt) B.cnt[i] = 0;
+  if (cta) __syncthreads(); else __syncwarp();
+  for (int i = me; i < m; i += nt) bk_insert(B, bucket_of<NBK>(deg[i]), i);
+  if (cta) __syncthreads(); else __syncwarp();
+}
+
+__host__ __device__ __forceinline__ size_t bucket_words(int nbk, int m) {
+  const int W = (m + 31) >> 5, SW = (W + 31) >> 5;
+  return (size_t)nbk * W + (size_t)nbk * SW + nbk;
+}
+
+// ---- leaf kernel ---------------------------------------------------------------------
+
+__global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned char* mine = smem + (size_t)wid * a.slice_bytes;
+  for (int32_t li = blockIdx.x * nw + wid; li < a.nnodes_launch; li += gridDim.x * nw) {
+    const int32_t t = a.nodes[li];
+    const int32_t m = a.node_size[t];
+    const int32_t pbeg = a.node_begin[t];
+    int32_t* verts = a.nvlist + a.nvstart[t];
+    const int W = (m + 31) >> 5;
+    const int S = m | 1;
+    uint32_t* R = (uint32_t*)mine;
+    uint32_t* nzv = R + (size_t)W * S;                 // pivot row: non-zero words
+    uint16_t* nzw = (uint16_t*)(nzv + 32);             //   and their indices
+    uint16_t* deg = nzw + 32;
+    uint16_t* nb = deg + ((m + 1) & ~1);
+    Buckets B;
+    B.W = W;
+    B.SW = (W + 31) >> 5;
+    B.bits = (uint32_t*)(nb + ((m + 1) & ~1));
+    B.sum = B.bits + (size_t)NBK_LEAF * W;
+    B.cnt = (int32_t*)(B.sum + (size_t)NBK_LEAF * B.SW);
+    // sort the node's vertices by original id (buffer overlaps R)
+    int32_t* sb = (int32_t*)mine;
+    const int NS = pow2_at_least(m, 32);
+    for (int i = lane; i < NS; i += 32) sb[i] = i < m ? verts[i] : INT_MAX;
+    __syncwarp();
+    bitonic_sort<false>(sb, NS, lane, 32);
+    for (int i = lane; i < m; i += 32) {
+      const int32_t v = sb[i];
+      verts[i] = v;
+      a.loc[v] = i;
+    }
+    __syncwarp();
+    for (int i = lane; i < W * S; i += 32) R[i] = 0u;
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
+      const int32_t v = verts[i];
+      int c = 0;
+      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+        const int32_t u = a.col[e];
+        if (a.node_of[u] != t) continue;
+        const int j = a.loc[u];
+        R[(j >> 5) * S + i] |= 1u << (j & 31);
+        ++c;
+      }
+      deg[i] = (uint16_t)c;
+    }
+    __syncwarp();
+    buckets_build<NBK_LEAF>(B, deg, m, lane, 32, false);
+    for (int step = 0; step < m; ++step) {
+      const int p = warp_argmin<NBK_LEAF>(B, deg, m);
+      // pivot row (W <= 16: one word per lane): neighbour list + non-zero words
+      const uint32_t bits = lane < W ? R[lane * S + p] : 0u;
+      const unsigned nzm = __ballot_sync(0xffffffffu, bits != 0u);
+      const int nz = __popc(nzm);
+      if (bits) {
+        const int k = __popc(nzm & lanemask_lt());
+        nzv[k] = bits;
+        nzw[k] = (uint16_t)lane;
+      }
+      const int c = __popc(bits);
+      int ex = warp_incl_scan_i32(c) - c;
+      const int nnb = __shfl_sync(0xffffffffu, ex + c, 31);
+      uint32_t x = bits;
+      while (x) {
+        const int bt = __ffs(x) - 1;
+        x &= x - 1;
+        nb[ex++] = (uint16_t)(lane * 32 + bt);
+      }
+      if (lane == 0) {
+        a.perm[pbeg + step] = verts[p];
+        bk_remove(B, bucket_of<NBK_LEAF>(deg[p]), p);
+        deg[p] = DEG_DEAD;
+      }
+      __syncwarp();
+      // clique, one neighbour per lane: row[u] |= row[p] \ {u}, drop p;
+      // degree(u) = degree(u) - 1 + |row[p] \ (row[u] + u)|
+      const int pw = p >> 5;
+      const uint32_t pbit = 1u << (p & 31);
+      int u = -1, ob = 0, nbk = 0;
+      uint32_t ndeg = 0;
+      const int u0 = lane < nnb ? (int)nb[lane] : -1;
+      uint32_t added = 0;
+      {
+        // the pivot's non-zero words come from the lanes that loaded them
+        const int uw = u0 >> 5;
+        const uint32_t ubit = 1u << (u0 & 31);
+        unsigned mm = nzm;
+        while (mm) {
+          const int w = __ffs(mm) - 1;
+          mm &= mm - 1;
+          const uint32_t pv = __shfl_sync(0xffffffffu, bits, w);
+          if (u0 >= 0) {
+            const uint32_t r = R[w * S + u0];
+            uint32_t nv = pv & ~r;
+            if (w == uw) nv &= ~ubit;
+            if (nv) { R[w * S + u0] = r | nv; added += __popc(nv); }
+          }
+        }
+      }
+      if (lane < nnb) {
+        u = u0;
+        R[pw * S + u] &= ~pbit;
+        const uint32_t od = deg[u];
+        ndeg = od - 1u + added;
+        ob = bucket_of<NBK_LEAF>(od);
+        nbk = bucket_of<NBK_LEAF>(ndeg);
+        deg[u] = (uint16_t)ndeg;
+        if (ob != nbk) bk_remove(B, ob, u);
+      }
+      // more than 32 neighbours: the rest, same rule (rare; dense leaves)
+      for (int q = 32 + lane; q < nnb; q += 32) {
+        const int v = nb[q];
+        const int vw = v >> 5;
+        const uint32_t vbit = 1u << (v & 31);
+        uint32_t added = 0;
+        for (int k = 0; k < nz; ++k) {
+          const int w = nzw[k];
+          const uint32_t r = R[w * S + v];
+          uint32_t nv = nzv[k] & ~r;
+          if (w == vw) nv &= ~vbit;
+          if (nv) { R[w * S + v] = r | nv; added += __popc(nv); }
+        }
+        R[pw * S + v] &= ~pbit;
+        const uint32_t od = deg[v];
+        const uint32_t nd = od - 1u + added;
+        deg[v] = (uint16_t)nd;
+        const int o2 = bucket_of<NBK_LEAF>(od), n2 = bucket_of<NBK_LEAF>(nd);
+        if (o2 != n2) { bk_remove(B, o2, v); nb[q] = (uint16_t)(v | 0x8000u); }   // mark: insert later
+      }
+      __syncwarp();
+      if (u >= 0 && ob != nbk) bk_insert(B, nbk, u);
+      for (int q = 32 + lane; q < nnb; q += 32) {
+        const int v = nb[q];
+        if (v & 0x8000) {
+          const int vv = v & 0x7fff;
+          bk_insert(B, bucket_of<NBK_LEAF>(deg[vv]), vv);
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+}
+
+// ---- sparse kernel (separators) --------------------------------------------------------
+
+__global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int32_t s_ovf;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int32_t li = blockIdx.x; li < a.nnodes_launch; li += gridDim.x) {
     const int32_t t = a.nodes[li];
     const int32_t m = a.node_size[t];
     const int32_t pbeg = a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
     const int W = (m + 31) >> 5;
-    // ---- shared memory carve-up
-    uint32_t* rows;
-    uint16_t* deg;
-    uint16_t* nb;
-    int32_t* sortbuf;
+    uint16_t* adj = (uint16_t*)smem;                      // m x SP_CAP local ids (48 B rows)
+    uint16_t* deg = adj + (size_t)m * SP_CAP;
+    Buckets B;
+    B.W = W;
+    B.SW = (W + 31) >> 5;
+    B.bits = (uint32_t*)(deg + ((m + 1) & ~1));
+    B.sum = B.bits + (size_t)NBK_SP * W;
+    B.cnt = (int32_t*)(B.sum + (size_t)NBK_SP * B.SW);
+    // sort the node's vertices by original id (buffer overlaps the lists)
+    int32_t* sb = (int32_t*)smem;
     const int NS = pow2_at_least(m, 32);
-    if (kKind == 2) {
-      deg = (uint16_t*)smem;
-      nb = deg + MD_MAX;
-      rows = a.grows + a.grow_off[li];
-      sortbuf = a.gsort + a.gsort_off[li];
-    } else {
-      rows = (uint32_t*)smem;
-      deg = (uint16_t*)(rows + (size_t)m * W);
-      nb = deg + ((m + 1) & ~1);
-      sortbuf = (int32_t*)smem;          // overlaps rows; used before they are built
+    for (int i = tid; i < NS; i += blockDim.x) sb[i] = i < m ? verts[i] : INT_MAX;
+    if (tid == 0) s_ovf = 0;
+    __syncthreads();
+    bitonic_sort<true>(sb, NS, tid, blockDim.x);
+    for (int i = tid; i < m; i += blockDim.x) {
+      const int32_t v = sb[i];
+      verts[i] = v;
+      a.loc[v] = i;
     }
-    // ---- sort the node's vertices by original id
-    for (int i = tid; i < NS; i += kNT) sortbuf[i] = i < m ? verts[i] : INT_MAX;
-    if (kWarp) __syncwarp(); else __syncthreads();
-    bitonic_sort<!kWarp>(sortbuf, NS, tid, kNT);
-    for (int i = tid; i < m; i += kNT) {
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) {
+      const int32_t v = verts[i];
+      int c = 0;
+      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+        const int32_t u = a.col[e];
+        if (a.node_of[u] != t) continue;
+        if (c < SP_CAP) adj[(size_t)i * SP_CAP + c] = (uint16_t)a.loc[u];
+        ++c;
+      }
+      if (c > SP_CAP) s_ovf = 1;
+      deg[i] = (uint16_t)(c < SP_CAP ? c : SP_CAP);
+    }
+    __syncthreads();
+    if (s_ovf) {
+      if (tid == 0) a.overflow[li] = 1;
+      __syncthreads();
+      continue;
+    }
+    buckets_build<NBK_SP>(B, deg, m, tid, blockDim.x, true);
+    if (tid < 32) {
+      bool ovf = false;
+      for (int step = 0; step < m && !ovf; ++step) {
+        const int p = warp_argmin<NBK_SP>(B, deg, m);
+        const int dp = deg[p];
+        // lane j holds the j-th neighbour of p
+        const int mine_nb = lane < dp ? (int)adj[(size_t)p * SP_CAP + lane] : -1;
+        __syncwarp();
+        if (lane == 0) {
+          a.perm[pbeg + step] = verts[p];
+          bk_remove(B, bucket_of<NBK_SP>(dp), p);
+          deg[p] = DEG_DEAD;
+        }
+        bool my_ovf = false;
+        int u = -1, ob = 0, nbk = 0, pos = 0, du = 0;
+        union L24 { uint4 q[3]; uint16_t e[SP_CAP]; };
+        L24 lu;
+        uint16_t* nu = nullptr;
+        if (lane < dp) {
+          u = mine_nb;
+          nu = adj + (size_t)u * SP_CAP;
+          const uint4* su = (const uint4*)nu;
+          lu.q[0] = su[0]; lu.q[1] = su[1]; lu.q[2] = su[2];
+          du = deg[u];
+          // new list: the old entries except p ...
+#pragma unroll
+          for (int k = 0; k < SP_CAP; ++k) {
+            if (k >= du) break;
+            if (lu.e[k] != p) nu[pos++] = lu.e[k];
+          }
+        }
+        // ... then p's other neighbours not yet present (broadcast one by one)
+        for (int j = 0; j < dp; ++j) {
+          const int y = __shfl_sync(0xffffffffu, mine_nb, j);
+          if (lane < dp && y != u) {
+            bool found = false;
+#pragma unroll
+            for (int k = 0; k < SP_CAP; ++k) {
+              if (k >= du) break;
+              found |= lu.e[k] == y;
+            }
+            if (!found) {
+              if (pos < SP_CAP) nu[pos++] = (uint16_t)y;
+              else my_ovf = true;
+            }
+          }
+        }
+        if (lane < dp) {
+          ob = bucket_of<NBK_SP>((uint32_t)du);
+          nbk = bucket_of<NBK_SP>((uint32_t)pos);
+          deg[u] = (uint16_t)pos;
+          if (ob != nbk) bk_remove(B, ob, u);
+        }
+        ovf = __any_sync(0xffffffffu, my_ovf);
+        __syncwarp();
+        if (u >= 0 && ob != nbk) bk_insert(B, nbk, u);
+        __syncwarp();
+      }
+      if (ovf && lane == 0) a.overflow[li] = 1;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- global kernel -------------------------------------------------------------------
+
+__global__ void __launch_bounds__(MD_THREADS) k_md_global(MdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t red32[40];
+  __shared__ int32_t s_nnb;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int NT = blockDim.x, nw = NT >> 5;
+  for (int32_t li = blockIdx.x; li < a.nnodes_launch; li += gridDim.x) {
+    if (a.overflow && !a.overflow[li]) continue;
+    const int32_t t = a.nodes[li];
+    const int32_t m = a.node_size[t];
+    const int32_t pbeg = a.node_begin[t];
+    int32_t* verts = a.nvlist + a.nvstart[t];
+    const int W = (m + 31) >> 5;
+    uint16_t* deg = (uint16_t*)smem;
+    uint16_t* nb = deg + MD_MAX;
+    uint32_t* rows = a.grows + a.grow_off[li];
+    int32_t* sortbuf = a.gsort + a.gsort_off[li];
+    const int NS = pow2_at_least(m, 32);
+    for (int i = tid; i < NS; i += NT) sortbuf[i] = i < m ? verts[i] : INT_MAX;
+    __syncthreads();
+    bitonic_sort<true>(sortbuf, NS, tid, NT);
+    for (int i = tid; i < m; i += NT) {
       const int32_t v = sortbuf[i];
       verts[i] = v;
       a.loc[v] = i;
     }
-    if (kWarp) __syncwarp(); else __syncthreads();
-    // ---- elimination graph = induced subgraph
-    for (int64_t i = tid; i < (int64_t)m * W; i += kNT) rows[i] = 0u;
-    if (kWarp) __syncwarp(); else __syncthreads();
-    for (int i = tid; i < m; i += kNT) {
+    __syncthreads();
+    for (int64_t i = tid; i < (int64_t)m * W; i += NT) rows[i] = 0u;
+    __syncthreads();
+    for (int i = tid; i < m; i += NT) {
       const int32_t v = verts[i];
       uint32_t* r = rows + (size_t)i * W;
       int c = 0;
@@ -177,24 +517,20 @@ __global__ void __launch_bounds__(kNT) k_md(MdArgs a) {
       }
       deg[i] = (uint16_t)c;
     }
-    if (kWarp) __syncwarp(); else __syncthreads();
-    // ---- elimination
+    __syncthreads();
     for (int step = 0; step < m; ++step) {
       uint32_t best = 0xffffffffu;
-      for (int i = tid; i < m; i += kNT) {
+      for (int i = tid; i < m; i += NT) {
         const uint16_t dg = deg[i];
         if (dg != DEG_DEAD) {
           const uint32_t key = ((uint32_t)dg << 16) | (uint32_t)i;
           best = key < best ? key : best;
         }
       }
-      uint32_t kmin;
-      if (kWarp) kmin = warp_min(best);
-      else kmin = block_min(best, red32);
+      const uint32_t kmin = block_min(best, red32);
       const int p = (int)(kmin & 0xffffu);
       const uint32_t* rp = rows + (size_t)p * W;
-      // neighbour list of p, in increasing local index
-      if (kWarp || wid == 0) {
+      if (wid == 0) {
         int base = 0;
         for (int w0 = 0; w0 < W; w0 += 32) {
           const int w = w0 + lane;
@@ -216,13 +552,12 @@ __global__ void __launch_bounds__(kNT) k_md(MdArgs a) {
           deg[p] = DEG_DEAD;
         }
       }
-      if (kWarp) __syncwarp(); else __syncthreads();
+      __syncthreads();
       const int nnb = s_nnb;
-      // clique: row[u] |= row[p], minus u and p; one warp per neighbour
-      for (int q = wid; q < nnb; q += kWarps) {
+      for (int q = wid; q < nnb; q += nw) {
         const int u = nb[q];
         uint32_t* ru = rows + (size_t)u * W;
-        int c = 0;
+        uint32_t c = 0;
         for (int w = lane; w < W; w += 32) {
           uint32_t x = ru[w] | rp[w];
           if (w == (u >> 5)) x &= ~(1u << (u & 31));
@@ -230,12 +565,12 @@ __global__ void __launch_bounds__(kNT) k_md(MdArgs a) {
           ru[w] = x;
           c += __popc(x);
         }
-        c = warp_sum(c);
+        c = __reduce_add_sync(0xffffffffu, c);
         if (lane == 0) deg[u] = (uint16_t)c;
       }
-      if (kWarp) __syncwarp(); else __syncthreads();
+      __syncthreads();
     }
-    if (kWarp) __syncwarp(); else __syncthreads();
+    __syncthreads();
   }
 }
 
@@ -264,12 +599,17 @@ __global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t
   }
 }
 
-size_t md_smem(int kind, int mmax) {
-  const int W = (mmax + 31) >> 5;
-  if (kind == 2) return (size_t)2 * MD_MAX * sizeof(uint16_t);
-  size_t rows = (size_t)mmax * W * 4;
-  size_t sortb = (size_t)pow2_host(mmax) * 4;
-  size_t need = rows + 2 * (size_t)((mmax + 1) & ~1) * 2;
+size_t leaf_slice(int m) {
+  const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1);
+  const size_t need = W * S * 4 + 32 * 4 + 32 * 2 + 2 * m2 * 2 + bucket_words(NBK_LEAF, m) * 4;
+  const size_t sortb = (size_t)pow2_host(m) * 4;
+  return ((need > sortb ? need : sortb) + 15) & ~(size_t)15;
+}
+
+size_t sparse_smem(int m) {
+  const size_t m2 = (size_t)((m + 1) & ~1);
+  const size_t need = (size_t)m * SP_CAP * 2 + m2 * 2 + bucket_words(NBK_SP, m) * 4;
+  const size_t sortb = (size_t)pow2_host(m) * 4;
   return need > sortb ? need : sortb;
 }
 
@@ -298,96 +638,120 @@ fp_status run_local_order(fp_handle* h) {
   if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
   int32_t st = 0;
   FP_TRY(sync_status(h, &st));
+  // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
+  // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3];
-  std::vector<int64_t> goff, soff;
   int mmax[3] = {0, 0, 0};
-  int64_t gwords = 0, gsort = 0;
   for (int64_t t = 0; t < nn; ++t) {
     const int m = hs[t];
     if (m == 0) continue;
     if (m > MD_MAX) return fail(h, FP_ERR_UNSUPPORTED, "a tree node has more than 32768 vertices");
-    const int kind = m <= MD_SMALL ? 0 : (m <= MD_MID ? 1 : 2);
+    const int kind = m <= MD_LEAF ? 0 : (sparse_smem(m) <= SMEM_MAX ? 1 : 2);
     ls[kind].push_back((int32_t)t);
     if (m > mmax[kind]) mmax[kind] = m;
-    if (kind == 2) {
+  }
+  // global rows and sort scratch for the sparse (fallback) and global nodes
+  std::vector<int64_t> goff, soff;
+  int64_t gwords = 0, gsort = 0;
+  for (int kd = 1; kd <= 2; ++kd)
+    for (int32_t t : ls[kd]) {
+      const int m = hs[t];
       goff.push_back(gwords);
       gwords += (int64_t)m * ((m + 31) / 32);
       soff.push_back(gsort);
       gsort += pow2_host(m);
     }
-  }
-  // node lists + large-kind offsets in one upload
   const int64_t nlist = (int64_t)ls[0].size() + ls[1].size() + ls[2].size();
-  std::vector<int64_t> up(nlist + 2 * goff.size() + 1);
+  const int64_t nsg = (int64_t)goff.size();
+  std::vector<int64_t> up((nlist + 1) / 2 + 2 * nsg + 1);
   int32_t* up32 = (int32_t*)up.data();
   int64_t o = 0;
   for (int kd = 0; kd < 3; ++kd)
     for (int32_t t : ls[kd]) up32[o++] = t;
-  const int64_t off64 = (o + 1) / 2;
-  for (size_t i = 0; i < goff.size(); ++i) { up[off64 + i] = goff[i]; up[off64 + goff.size() + i] = soff[i]; }
+  const int64_t off64 = (nlist + 1) / 2;
+  for (int64_t i = 0; i < nsg; ++i) { up[off64 + i] = goff[i]; up[off64 + nsg + i] = soff[i]; }
   int64_t* dup = (int64_t*)dev_alloc(h, sizeof(int64_t) * (up.size() + 1));
   uint32_t* grows = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * (gwords > 0 ? gwords : 1));
   int32_t* gs = I(gsort);
-  if (!dup || !grows || !gs) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
+  int32_t* ovf = I((int64_t)ls[1].size() + 1);
+  if (!dup || !grows || !gs || !ovf) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
   e = cudaMemcpyAsync(dup, up.data(), sizeof(int64_t) * up.size(), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return check_cuda(h, e, "upload node lists");
+  fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 1);
   const int32_t* dnodes = (const int32_t*)dup;
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
-              nullptr, 0, grows, dup + off64, gs, dup + off64 + goff.size()};
-  // second stream for the large and mid nodes
-  cudaStream_t s2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  if (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)
-    return fail(h, FP_ERR_CUDA, "stream/event create");
-  cudaEventRecord(ev_fork, h->stream);
-  cudaStreamWaitEvent(s2, ev_fork, 0);
-  int64_t lo = 0;
+              nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr};
+  // separators on the auxiliary stream; leaves on the handle's stream in CTAs
+  // that fill whole SMs, leaving `reserved` SMs for the separator CTAs
+  AuxStream* ax = aux_stream(h->device);
+  if (!ax) return fail(h, FP_ERR_CUDA, "auxiliary stream");
+  cudaStream_t s2 = ax->s;
+  cudaEventRecord(ax->fork, h->stream);
+  cudaStreamWaitEvent(s2, ax->fork, 0);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int nbig = (int)(ls[1].size() + ls[2].size());
+  const int reserved = nbig < 16 ? nbig : 16;
   const int64_t lo1 = (int64_t)ls[0].size(), lo2 = lo1 + (int64_t)ls[1].size();
-  if (!ls[2].empty()) {
-    MdArgs a = base;
-    a.nodes = dnodes + lo2;
-    a.nnodes_launch = (int32_t)ls[2].size();
-    size_t sm = md_smem(2, mmax[2]);
-    cudaFuncSetAttribute(k_md<MD_THREADS, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    ProfScope ps(FP_PROF_MD_LARGE, s2);
-    k_md<MD_THREADS, 2><<<(unsigned)ls[2].size(), MD_THREADS, sm, s2>>>(a);
-    h->launches++;
-  }
   if (!ls[1].empty()) {
     MdArgs a = base;
     a.nodes = dnodes + lo1;
     a.nnodes_launch = (int32_t)ls[1].size();
-    size_t sm = md_smem(1, mmax[1]);
-    cudaFuncSetAttribute(k_md<MD_THREADS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    ProfScope ps(FP_PROF_MD_MID, s2);
-    k_md<MD_THREADS, 1><<<(unsigned)ls[1].size(), MD_THREADS, sm, s2>>>(a);
+    a.overflow = ovf;
+    const size_t sm = sparse_smem(mmax[1]);
+    cudaFuncSetAttribute(k_md_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    {
+      ProfScope ps(FP_PROF_MD_MID, s2);
+      k_md_sparse<<<(unsigned)ls[1].size(), MD_THREADS, sm, s2>>>(a);
+      h->launches++;
+    }
+    // redo flagged nodes with global rows (grow_off/gsort_off index from 0 here)
+    const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
+    cudaFuncSetAttribute(k_md_global, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
+    ProfScope ps(FP_PROF_MD_LARGE, s2);
+    k_md_global<<<(unsigned)ls[1].size(), MD_THREADS, smg, s2>>>(a);
+    h->launches++;
+  }
+  if (!ls[2].empty()) {
+    MdArgs a = base;
+    a.nodes = dnodes + lo2;
+    a.nnodes_launch = (int32_t)ls[2].size();
+    a.grow_off = dup + off64 + (int64_t)ls[1].size();
+    a.gsort_off = dup + off64 + nsg + (int64_t)ls[1].size();
+    const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
+    cudaFuncSetAttribute(k_md_global, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
+    ProfScope ps(FP_PROF_MD_LARGE, s2);
+    k_md_global<<<(unsigned)ls[2].size(), MD_THREADS, smg, s2>>>(a);
     h->launches++;
   }
   if (!ls[0].empty()) {
     MdArgs a = base;
-    a.nodes = dnodes + lo;
+    a.nodes = dnodes;
     a.nnodes_launch = (int32_t)ls[0].size();
-    size_t sm = md_smem(0, mmax[0]);
-    cudaFuncSetAttribute(k_md<32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t slice = leaf_slice(mmax[0]);
+    int nw = (int)(220 * 1024 / slice);
+    nw = nw < 1 ? 1 : (nw > MD_THREADS / 32 ? MD_THREADS / 32 : nw);
+    size_t sm = slice * nw;
+    if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
+    a.slice_bytes = (int64_t)slice;
+    int64_t grid = ((int64_t)ls[0].size() + nw - 1) / nw;
+    const int64_t cap = sms - reserved > 1 ? sms - reserved : 1;
+    if (grid > cap) grid = cap;
+    cudaFuncSetAttribute(k_md_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
-    k_md<32, 0><<<(unsigned)ls[0].size(), 32, sm, h->stream>>>(a);
+    k_md_leaf<<<(unsigned)grid, 32 * nw, sm, h->stream>>>(a);
     h->launches++;
   }
-  cudaEventRecord(ev_join, s2);
-  cudaStreamWaitEvent(h->stream, ev_join, 0);
+  cudaEventRecord(ax->join, s2);
+  cudaStreamWaitEvent(h->stream, ax->join, 0);
   FP_CHECK_LAUNCH(h, "minimum degree");
   if (n > 0) {
     ProfScope ps(FP_PROF_PERM, h->stream);
     FP_LAUNCH(h, k_iperm, G, 256, 0, h->perm, n, h->iperm);
   }
   FP_CHECK_LAUNCH(h, "iperm");
-  cudaEventDestroy(ev_fork);
-  cudaEventDestroy(ev_join);
-  cudaStreamDestroy(s2);
   for (void* p : {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup,
-                  (void*)grows, (void*)gs})
+                  (void*)grows, (void*)gs, (void*)ovf})
     dev_free(h, p);
   return FP_OK;
 }

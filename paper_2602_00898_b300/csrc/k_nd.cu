@@ -130,6 +130,7 @@ struct BisectArgs {
   const int32_t* patch_node;
   int32_t* loc;                // [k] patch -> local index
   int32_t* ldeg;               // [k] by list position
+  int32_t* lbeg;               // [k] by list position: row start in ladj
   int32_t* ladj;               // [Q] local adjacency inside each patch's quotient row
   int32_t* lvl;                // [k]
   int32_t* qa;                 // [k] frontier
@@ -138,15 +139,24 @@ struct BisectArgs {
   int32_t* hist;               // [k]
   int32_t* side;               // [k] by patch id
   int32_t* split;              // [T]
+  int32_t mcap, ecap;          // shared-memory staging limits of this launch
+};
+
+// Per-node working set: in shared memory when the node has <= mcap patches and
+// <= ecap local adjacency entries, else in the global arrays at the node's
+// list offset.
+struct BisectView {
+  int32_t* L;
+  int32_t *lvl, *qa, *qb, *mark, *hist, *rbeg, *rlen, *adj;
 };
 
 // Level-synchronous BFS over the node's local quotient graph from local `src`.
 // lvl must be -1 on the component. Returns the number of levels.
-__device__ int block_bfs(const BisectArgs& a, const int32_t* L, int32_t base, int32_t src, int32_t* snext) {
-  int32_t* fa = a.qa + base;
-  int32_t* fb = a.qb + base;
+__device__ int block_bfs(const BisectView& v, int32_t src, int32_t* snext) {
+  int32_t* fa = v.qa;
+  int32_t* fb = v.qb;
   if (threadIdx.x == 0) {
-    a.lvl[base + src] = 0;
+    v.lvl[src] = 0;
     fa[0] = src;
   }
   __syncthreads();
@@ -155,12 +165,11 @@ __device__ int block_bfs(const BisectArgs& a, const int32_t* L, int32_t base, in
     if (threadIdx.x == 0) *snext = 0;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < nf; i += blockDim.x) {
-      int32_t u = __ldcg(&fa[i]);
-      int32_t p = L[u];
-      int32_t e0 = a.q_rowptr[p], e1 = e0 + __ldcg(&a.ldeg[base + u]);
+      const int32_t u = fa[i];
+      const int32_t e0 = v.rbeg[u], e1 = e0 + v.rlen[u];
       for (int32_t e = e0; e < e1; ++e) {
-        int32_t w = __ldcg(&a.ladj[e]);
-        if (atomicCAS(&a.lvl[base + w], -1, level + 1) == -1) fb[atomicAdd(snext, 1)] = w;
+        const int32_t w = v.adj[e];
+        if (atomicCAS(&v.lvl[w], -1, level + 1) == -1) fb[atomicAdd(snext, 1)] = w;
       }
     }
     __syncthreads();
@@ -173,6 +182,7 @@ __device__ int block_bfs(const BisectArgs& a, const int32_t* L, int32_t base, in
 }
 
 __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
+  extern __shared__ __align__(16) int32_t bsm[];
   __shared__ int64_t red64[40];
   __shared__ int32_t red[40];
   __shared__ int32_t snext;
@@ -181,7 +191,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
     const int32_t t = a.t0 + ni;
     const int32_t base = a.npstart[ni];
     const int32_t m = a.npstart[ni + 1] - base;
-    int32_t* L = a.nplist + base;
+    int32_t* Lg = a.nplist + base;
     if (m < 2) {
       if (threadIdx.x == 0) a.split[ni] = 0;
       continue;
@@ -189,19 +199,20 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
     if (threadIdx.x == 0) a.split[ni] = 1;
     // sort the node's patches by id (local index order = id order)
     {
-      int32_t* sb = a.sortbuf + 2 * (int64_t)base;
+      int32_t* sb = (m <= a.mcap) ? bsm : a.sortbuf + 2 * (int64_t)base;
       const int N = pow2_at_least(m, 2);
-      for (int32_t i = threadIdx.x; i < N; i += blockDim.x) sb[i] = i < m ? L[i] : INT_MAX;
+      for (int32_t i = threadIdx.x; i < N; i += blockDim.x) sb[i] = i < m ? Lg[i] : INT_MAX;
       __syncthreads();
       bitonic_sort<true>(sb, N, threadIdx.x, blockDim.x);
-      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) L[i] = sb[i];
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) Lg[i] = sb[i];
       __syncthreads();
     }
-    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.loc[L[i]] = i;
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.loc[Lg[i]] = i;
     __syncthreads();
     // local quotient subgraph: neighbours in this node with remaining edge weight
+    int32_t E = 0;
     for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const int32_t p = L[i];
+      const int32_t p = Lg[i];
       int32_t c = 0;
       const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
       for (int32_t e = e0; e < e1; ++e) {
@@ -209,8 +220,57 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
         if (a.q_w[e] > 0 && a.patch_node[q] == t) a.ladj[e0 + c++] = a.loc[q];
       }
       a.ldeg[base + i] = c;
-      a.lvl[base + i] = -1;
-      a.mark[base + i] = 0;
+      a.lbeg[base + i] = e0;
+      E += c;
+    }
+    E = block_sum(E, red);
+    const bool sm = m <= a.mcap && E <= a.ecap;
+    BisectView v;
+    if (sm) {
+      int32_t* q = bsm;
+      v.L = q; q += a.mcap;
+      v.lvl = q; q += a.mcap;
+      v.qa = q; q += a.mcap;
+      v.qb = q; q += a.mcap;
+      v.mark = q; q += a.mcap;
+      v.hist = q; q += a.mcap;
+      v.rbeg = q; q += a.mcap + 1;
+      v.rlen = a.ldeg + base;        // read once below into the compact rows
+      v.adj = q;
+      // compact CSR in shared memory
+      int32_t carry = 0;
+      for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
+        const int32_t i = i0 + threadIdx.x;
+        const int32_t c = i < m ? a.ldeg[base + i] : 0;
+        int32_t tot;
+        const int32_t ex = block_excl_scan_i32(c, &tot, red);
+        if (i < m) v.rbeg[i] = carry + ex;
+        carry += tot;
+      }
+      __syncthreads();
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const int32_t e0 = a.lbeg[base + i], c = a.ldeg[base + i], o = v.rbeg[i];
+        for (int32_t j = 0; j < c; ++j) v.adj[o + j] = a.ladj[e0 + j];
+        v.L[i] = Lg[i];
+        v.hist[i] = a.ldeg[base + i];   // row lengths, kept in shared memory
+      }
+      v.rlen = v.hist;
+      // hist doubles as the row-length array; the split histogram uses qb's
+      // sibling region below once the BFS sweeps are done (see `hist2`).
+    } else {
+      v.L = Lg;
+      v.lvl = a.lvl + base;
+      v.qa = a.qa + base;
+      v.qb = a.qb + base;
+      v.mark = a.mark + base;
+      v.hist = a.hist + base;
+      v.rbeg = a.lbeg + base;
+      v.rlen = a.ldeg + base;
+      v.adj = a.ladj;
+    }
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      v.lvl[i] = -1;
+      v.mark[i] = 0;
     }
     __syncthreads();
     const int32_t half = (m + 1) / 2;
@@ -219,53 +279,53 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       // next component: smallest untouched local index
       int32_t c0 = INT_MAX;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (__ldcg(&a.mark[base + i]) == 0) { c0 = i; break; }
+        if (v.mark[i] == 0) { c0 = i; break; }
       c0 = block_min(c0, red);
       if (c0 == INT_MAX) break;
       // sweep 0: discover the component
-      block_bfs(a, L, base, c0, &snext);
+      block_bfs(v, c0, &snext);
       int64_t best = INT64_MAX;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (__ldcg(&a.mark[base + i]) == 0 && __ldcg(&a.lvl[base + i]) >= 0) {
-          a.mark[base + i] = 2;
-          a.lvl[base + i] = -1;
-          int64_t key = ((int64_t)__ldcg(&a.ldeg[base + i]) << 32) | i;
+        if (v.mark[i] == 0 && v.lvl[i] >= 0) {
+          v.mark[i] = 2;
+          v.lvl[i] = -1;
+          const int64_t key = ((int64_t)v.rlen[i] << 32) | i;
           best = key < best ? key : best;
         }
       const int32_t r0 = (int32_t)(block_min(best, red64) & 0xffffffff);
       // sweep 1: from r0 (minimum degree, then id); r1 = min (degree, id) on the last level
-      const int32_t nl0 = block_bfs(a, L, base, r0, &snext);
+      const int32_t nl0 = block_bfs(v, r0, &snext);
       best = INT64_MAX;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (__ldcg(&a.mark[base + i]) == 2) {
-          if (__ldcg(&a.lvl[base + i]) == nl0 - 1) {
-            int64_t key = ((int64_t)__ldcg(&a.ldeg[base + i]) << 32) | i;
-            best = key < best ? key : best;
-          }
+        if (v.mark[i] == 2 && v.lvl[i] == nl0 - 1) {
+          const int64_t key = ((int64_t)v.rlen[i] << 32) | i;
+          best = key < best ? key : best;
         }
       const int32_t r1 = (int32_t)(block_min(best, red64) & 0xffffffff);
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (__ldcg(&a.mark[base + i]) == 2) a.lvl[base + i] = -1;
+        if (v.mark[i] == 2) v.lvl[i] = -1;
       __syncthreads();
       // sweep 2: the order of the component is (level from r1, id)
-      block_bfs(a, L, base, r1, &snext);
+      block_bfs(v, r1, &snext);
       int32_t cs = 0;
-      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) cs += __ldcg(&a.mark[base + i]) == 2;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) cs += v.mark[i] == 2;
       cs = block_sum(cs, red);
       if (pos + cs <= half || pos >= half) {
         const int32_t sd = pos >= half ? 1 : 0;
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-          if (__ldcg(&a.mark[base + i]) == 2) { a.side[L[i]] = sd; a.mark[base + i] = 1; }
+          if (v.mark[i] == 2) { a.side[v.L[i]] = sd; v.mark[i] = 1; }
       } else {
+        // levels histogram in the frontier buffer qa (free after the sweeps)
         const int32_t need = half - pos;
-        for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.hist[base + i] = 0;
+        int32_t* hist2 = v.qa;
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x) hist2[i] = 0;
         __syncthreads();
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-          if (__ldcg(&a.mark[base + i]) == 2) atomicAdd(&a.hist[base + __ldcg(&a.lvl[base + i])], 1);
+          if (v.mark[i] == 2) atomicAdd(&hist2[v.lvl[i]], 1);
         __syncthreads();
         if (threadIdx.x == 0) {
           int32_t cum = 0, l = 0;
-          while (cum + __ldcg(&a.hist[base + l]) < need) { cum += __ldcg(&a.hist[base + l]); ++l; }
+          while (cum + hist2[l] < need) { cum += hist2[l]; ++l; }
           s_lstar = l;
           s_rem = need - cum;
         }
@@ -275,14 +335,14 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
         for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
           const int32_t i = i0 + threadIdx.x;
           int32_t lv = -2, mk = 0;
-          if (i < m) { mk = __ldcg(&a.mark[base + i]); lv = __ldcg(&a.lvl[base + i]); }
+          if (i < m) { mk = v.mark[i]; lv = v.lvl[i]; }
           const int32_t f = (mk == 2 && lv == lstar) ? 1 : 0;
           int32_t tot;
           const int32_t ex = block_excl_scan_i32(f, &tot, red) + before;
           if (mk == 2) {
             const int32_t sd = (lv < lstar || (lv == lstar && ex < rem)) ? 0 : 1;
-            a.side[L[i]] = sd;
-            a.mark[base + i] = 1;
+            a.side[v.L[i]] = sd;
+            v.mark[i] = 1;
           }
           before += tot;
         }
@@ -333,7 +393,14 @@ __global__ void k_nd_superset(LevelArgs a) {
     }
     a.cdeg[v] = c;
     a.vstate[v] = c ? VS_UND : VS_NONE;
-    if (c) a.cand[atomicAdd(&a.ctr[0], 1)] = v;
+    if (c) {
+      const unsigned act = __activemask();
+      const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(&a.ctr[0], __popc(act));
+      base = __shfl_sync(act, base, leader);
+      a.cand[base + __popc(act & lanemask_lt())] = v;
+    }
   }
 }
 
@@ -459,14 +526,14 @@ fp_status run_nested_dissection(fp_handle* h) {
   auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
   int32_t *psize = I(kk), *pstart = I(kk), *pfill = I(kk), *pverts = I(n), *qdeg = I(kk), *q_rowptr = I(kk);
   int32_t *q_col = I(Q), *q_w = I(Q), *ladj = I(Q), *tmp = I(scan_tmp_ints(kk) + 8);
-  int32_t *patch_node = I(kk), *w = I(kk), *side = I(kk), *loc = I(kk), *ldeg = I(kk), *lvl = I(kk);
+  int32_t *patch_node = I(kk), *w = I(kk), *side = I(kk), *loc = I(kk), *ldeg = I(kk), *lvl = I(kk), *lbeg = I(kk);
   int32_t *qa = I(kk), *qb = I(kk), *mark = I(kk), *hist = I(kk), *sortbuf = I(2 * kk + 64);
   int32_t *npcount = I(kk), *npstart = I(kk + 1), *npfill = I(kk), *nplist = I(kk), *split = I(kk);
   int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8);
   int8_t* final_ = (int8_t*)dev_alloc(h, n);
   int8_t* vstate = (int8_t*)dev_alloc(h, n);
   if (!psize || !pstart || !pfill || !pverts || !qdeg || !q_rowptr || !q_col || !q_w || !ladj || !tmp || !patch_node ||
-      !w || !side || !loc || !ldeg || !lvl || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
+      !w || !side || !loc || !ldeg || !lvl || !lbeg || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
       !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
 
@@ -506,10 +573,17 @@ fp_status run_nested_dissection(fp_handle* h) {
     scan_exclusive(h, npcount, npstart, T, tmp);
     fill_i32(h, npfill, 0, T);
     FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
-    BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, ladj,
-                  lvl, qa, qb, mark, hist, side, split};
+    // nodes at depth d hold at most ceil(k / 2^d) patches: stage that many in
+    // shared memory (capped at 2048 patches / 16384 adjacency entries)
+    int32_t mcap = (int32_t)(((int64_t)k + T - 1) / T);
+    mcap = mcap < 32 ? 32 : (mcap > 2048 ? 2048 : mcap);
+    const int32_t ecap = 8 * mcap;
+    const size_t bsmem = sizeof(int32_t) * (7 * (size_t)mcap + 1 + (size_t)ecap);
+    BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
+                  lvl, qa, qb, mark, hist, side, split, mcap, ecap};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
-    FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, 0, ba);
+    cudaFuncSetAttribute(k_nd_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
+    FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
     ps_b.end();
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, ctr,
@@ -517,7 +591,9 @@ fp_status run_nested_dissection(fp_handle* h) {
     fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
+      // one CTA per SM: few candidates per level, cheaper grid barriers
       int g = G < gmis_max ? G : gmis_max;
+      if (g > NUM_SMS_B300) g = NUM_SMS_B300;
       void* args[] = {(void*)&la};
       cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_nd_mis, g, ND_THREADS, args, 0, h->stream);
       h->launches++;
@@ -533,7 +609,7 @@ fp_status run_nested_dissection(fp_handle* h) {
   if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
   for (void* p : {(void*)psize, (void*)pstart, (void*)pfill, (void*)pverts, (void*)qdeg, (void*)q_rowptr, (void*)q_col,
                   (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
-                  (void*)ldeg, (void*)lvl, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
+                  (void*)ldeg, (void*)lvl, (void*)lbeg, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
                   (void*)npcount, (void*)npstart, (void*)npfill, (void*)nplist, (void*)split, (void*)cdeg, (void*)cand,
                   (void*)ctr, (void*)final_, (void*)vstate})
     dev_free(h, p);

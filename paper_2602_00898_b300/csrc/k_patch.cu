@@ -12,12 +12,14 @@
 //   cap    : every patch above cap gets a second seed at its vertex farthest
 //            from its seed (ties: lowest id), ranked after all existing ranks in
 //            parent-rank order, and is relabelled from its two seeds.
-// The BFS is one persistent cooperative launch per search: the level loop
-// runs on the device with a grid barrier between levels, and frontier queues
-// are compacted with an atomic counter.
+// Searches over the whole mesh (Voronoi labelling) are one persistent
+// cooperative launch each: the level loop runs on the device with a grid
+// barrier between levels, frontier queues compacted with an atomic counter.
+// Searches confined to one patch (Lloyd depth, cap splits) run one CTA per
+// patch with the patch's adjacency in shared memory and CTA barriers only.
 #include <cooperative_groups.h>
 
-#include "fp_internal.cuh"
+#include "fp_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -59,7 +61,15 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
         const unsigned long long kv = __ldcg(&key[v]);
         if ((kv >> 32) <= level) continue;                 // settled at an earlier level
         const unsigned long long old = atomicMin(&key[v], dnext | lab);
-        if (old == KEY_INF) nxt[atomicAdd(&ctr[(level + 1) % 3], 1)] = v;
+        if (old == KEY_INF) {
+          // first claim: append to the next frontier, one counter update per warp
+          const unsigned act = __activemask();
+          const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+          int base = 0;
+          if (lane == leader) base = atomicAdd(&ctr[(level + 1) % 3], __popc(act));
+          base = __shfl_sync(act, base, leader);
+          nxt[base + __popc(act & lanemask_lt())] = v;
+        }
       }
     }
     int32_t* t = cur; cur = nxt; nxt = t;
@@ -149,32 +159,6 @@ __global__ void k_component_seed_flags(const int32_t* __restrict__ comp, int32_t
     flag[v] = comp[v] == v ? 1 : 0;
 }
 
-// Lloyd: boundary vertices (a neighbour with another label) are the sources
-// of a BFS restricted to the patch.
-__global__ void k_boundary_sources(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
-                                   const int32_t* __restrict__ label, unsigned long long* __restrict__ key2,
-                                   int32_t* __restrict__ frontier, int32_t* ctr) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    int32_t lv = label[v];
-    bool bnd = false;
-    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
-      if (label[col[e]] != lv) { bnd = true; break; }
-    key2[v] = bnd ? 0ull : KEY_INF;
-    if (bnd) frontier[atomicAdd(&ctr[0], 1)] = v;
-  }
-}
-
-// best[label] = max over reached v of (dist << 32 | ~v): the farthest vertex,
-// ties to the smallest id.
-__global__ void k_pick_farthest(const unsigned long long* __restrict__ key2, const int32_t* __restrict__ label, int32_t n,
-                                unsigned long long* __restrict__ best) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    unsigned long long k2 = key2[v];
-    if (k2 == KEY_INF) continue;
-    atomicMax(&best[label[v]], (k2 & 0xffffffff00000000ull) | (unsigned long long)(0xffffffffu - (uint32_t)v));
-  }
-}
-
 __global__ void k_lloyd_apply(const unsigned long long* __restrict__ best, int32_t k, int32_t* __restrict__ seed_of) {
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
     if (best[p]) seed_of[p] = (int32_t)(0xffffffffu - (uint32_t)best[p]);
@@ -190,49 +174,198 @@ __global__ void k_all_seed_sources(const int32_t* __restrict__ seed_of, int32_t 
   if (blockIdx.x == 0 && threadIdx.x == 0) { ctr[0] = k; ctr[1] = 0; ctr[2] = 0; }
 }
 
-__global__ void k_patch_sizes(const int32_t* __restrict__ label, int32_t n, int32_t* __restrict__ psize) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) atomicAdd(&psize[label[v]], 1);
-}
-
 __global__ void k_oversize_flags(const int32_t* __restrict__ psize, int32_t k, int32_t cap, int32_t* __restrict__ over) {
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) over[p] = psize[p] > cap;
 }
 
-// Sources of the "farthest from the seed" search: the seeds of oversize patches.
-__global__ void k_oversize_seed_sources(const int32_t* __restrict__ seed_of, const int32_t* __restrict__ over,
-                                        const int32_t* __restrict__ orank, int32_t k,
-                                        unsigned long long* __restrict__ key2, int32_t* __restrict__ frontier, int32_t* ctr) {
-  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
-    if (over[p]) {
-      key2[seed_of[p]] = 0ull;
-      frontier[orank[p]] = seed_of[p];
+// Cap split: the farthest vertex of every oversize patch p becomes the seed of
+// the new rank kbase + orank[p].
+__global__ void k_split_seeds(const unsigned long long* __restrict__ best, const int32_t* __restrict__ over,
+                              const int32_t* __restrict__ orank, int32_t kbase, int32_t* __restrict__ seed_of) {
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < kbase; p += gridDim.x * blockDim.x)
+    if (over[p]) seed_of[kbase + orank[p]] = (int32_t)(0xffffffffu - (uint32_t)best[p]);
+}
+
+// ---- searches inside one patch: one CTA per patch, no grid barrier ---------------
+//
+// mode 0 (Lloyd): hop depth from the patch boundary; best[p] = max (depth, -v).
+// mode 1 (cap)  : hop distance from the seed; best[p] = max (dist, -v).
+// mode 2 (cap)  : two-seed Voronoi inside the patch (seed with rank p, far vertex
+//                 with rank kbase + orank[p]); writes key[v] = dist << 32 | rank.
+// Modes 1 and 2 only visit patches with over[p] set. A patch's vertices, its
+// internal adjacency (local ids) and the BFS state live in shared memory when
+// the patch has at most LOCAL_SMEM_V vertices and LOCAL_SMEM_E internal
+// adjacency entries, otherwise in global scratch at the patch's offsets.
+constexpr int LOCAL_THREADS = 256;
+constexpr int LOCAL_SMEM_V = 1024;
+constexpr int LOCAL_SMEM_E = 8192;
+
+struct LocalArgs {
+  int32_t k;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const int32_t* label;         // current patch of every vertex
+  const int32_t* pstart;        // [k+1] vertex lists by patch
+  const int32_t* pverts;
+  const int32_t* pedge;         // [k+1] adjacency offsets by patch (sum of degrees)
+  int32_t* g_adj;               // global fallback: internal adjacency
+  int32_t* g_vtx;               // global fallback: [4n + k] (lrow, dist, fa, fb per patch)
+  int32_t* loc;                 // [n] local index of a vertex in its patch
+  const int32_t* over;          // modes 1, 2: patches to process
+  const int32_t* orank;
+  int32_t kbase;
+  const int32_t* seed_of;
+  unsigned long long* best;     // modes 0, 1
+  unsigned long long* key;      // mode 2
+};
+
+template <int kMode>
+__global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
+  __shared__ int32_t s_verts[LOCAL_SMEM_V];
+  __shared__ int32_t s_lrow[LOCAL_SMEM_V + 1];
+  __shared__ uint32_t s_dist[LOCAL_SMEM_V];
+  __shared__ int32_t s_fa[LOCAL_SMEM_V];
+  __shared__ int32_t s_fb[LOCAL_SMEM_V];
+  __shared__ uint16_t s_adj[LOCAL_SMEM_E];
+  __shared__ int32_t red[40];
+  __shared__ unsigned long long red64[40];
+  __shared__ int32_t s_nf;
+  const int tid = threadIdx.x;
+  for (int32_t p = blockIdx.x; p < a.k; p += gridDim.x) {
+    if (kMode != 0 && !a.over[p]) continue;
+    const int32_t v0 = a.pstart[p], m = a.pstart[p + 1] - v0;
+    const int32_t e0 = a.pedge[p], eall = a.pedge[p + 1] - e0;
+    const bool small = m <= LOCAL_SMEM_V && eall <= LOCAL_SMEM_E;
+    const int32_t* verts = small ? s_verts : a.pverts + v0;
+    int32_t* gv = a.g_vtx + 4 * (int64_t)v0 + p;          // 4m + 1 ints of this patch
+    int32_t* lrow = small ? s_lrow : gv;
+    uint32_t* dist = small ? s_dist : (uint32_t*)(gv + m + 1);
+    int32_t* fa = small ? s_fa : gv + 2 * m + 1;
+    int32_t* fb = small ? s_fb : gv + 3 * m + 1;
+    if (small)
+      for (int32_t i = tid; i < m; i += LOCAL_THREADS) s_verts[i] = a.pverts[v0 + i];
+    __syncthreads();
+    for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
+      a.loc[verts[i]] = i;
+      dist[i] = 0xffffffffu;
     }
-  if (blockIdx.x == 0 && threadIdx.x == 0) { ctr[0] = orank[k]; ctr[1] = 0; ctr[2] = 0; }
-}
-
-// Reset the labels of every vertex of an oversize patch.
-__global__ void k_reset_oversize(const int32_t* __restrict__ label, const int32_t* __restrict__ over, int32_t n,
-                                 unsigned long long* __restrict__ key) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    if (over[label[v]]) key[v] = KEY_INF;
-}
-
-// Two sources per oversize patch p: its seed (rank p) and its farthest vertex
-// (new rank k + orank[p]).
-__global__ void k_split_sources(const unsigned long long* __restrict__ best, const int32_t* __restrict__ over,
-                                const int32_t* __restrict__ orank, int32_t k, int32_t* __restrict__ seed_of,
-                                unsigned long long* __restrict__ key, int32_t* __restrict__ frontier, int32_t* ctr) {
-  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
-    if (!over[p]) continue;
-    int32_t r = k + orank[p];
-    int32_t far = (int32_t)(0xffffffffu - (uint32_t)best[p]);
-    seed_of[r] = far;
-    key[seed_of[p]] = (unsigned long long)(uint32_t)p;
-    key[far] = (unsigned long long)(uint32_t)r;
-    frontier[2 * orank[p]] = seed_of[p];
-    frontier[2 * orank[p] + 1] = far;
+    __syncthreads();
+    // internal adjacency as a local CSR
+    int32_t carry = 0;
+    for (int32_t i0 = 0; i0 < m; i0 += LOCAL_THREADS) {
+      const int32_t i = i0 + tid;
+      int32_t c = 0;
+      if (i < m) {
+        const int32_t v = verts[i];
+        for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) c += a.label[a.col[e]] == p;
+      }
+      int32_t tot;
+      const int32_t ex = block_excl_scan_i32(c, &tot, red);
+      if (i < m) lrow[i] = carry + ex;
+      carry += tot;
+    }
+    if (tid == 0) lrow[m] = carry;
+    __syncthreads();
+    for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
+      const int32_t v = verts[i];
+      int32_t o = lrow[i];
+      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
+        const int32_t u = a.col[e];
+        if (a.label[u] != p) continue;
+        const int32_t j = a.loc[u];
+        if (small) s_adj[o++] = (uint16_t)j; else a.g_adj[e0 + o++] = j;
+      }
+    }
+    // sources
+    if (tid == 0) s_nf = 0;
+    __syncthreads();
+    if (kMode == 0) {
+      for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
+        const int32_t v = verts[i];
+        bool bnd = false;
+        for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e)
+          if (a.label[a.col[e]] != p) { bnd = true; break; }
+        if (bnd) { dist[i] = 0u; fa[atomicAdd(&s_nf, 1)] = i; }
+      }
+    } else if (tid == 0) {
+      const int32_t i = a.loc[a.seed_of[p]];
+      dist[i] = 0u;
+      fa[0] = i;
+      s_nf = 1;
+      if (kMode == 2) {
+        const int32_t j = a.loc[a.seed_of[a.kbase + a.orank[p]]];
+        dist[j] = 1u;             // packed (dist << 1 | second seed)
+        fa[1] = j;
+        s_nf = 2;
+      }
+    }
+    __syncthreads();
+    // level-synchronous BFS; mode 2 packs (dist << 1 | which seed) and keeps the min
+    int32_t nf = s_nf;
+    for (uint32_t level = 0; nf > 0; ++level) {
+      __syncthreads();
+      if (tid == 0) s_nf = 0;
+      __syncthreads();
+      for (int32_t i = tid; i < nf; i += LOCAL_THREADS) {
+        const int32_t u = fa[i];
+        const int32_t r0 = lrow[u], r1 = lrow[u + 1];
+        if (kMode == 2) {
+          const uint32_t cand = ((level + 1) << 1) | (dist[u] & 1u);
+          for (int32_t r = r0; r < r1; ++r) {
+            const int32_t w = small ? (int32_t)s_adj[r] : a.g_adj[e0 + r];
+            if ((dist[w] >> 1) <= level) continue;
+            if (atomicMin(&dist[w], cand) == 0xffffffffu) fb[atomicAdd(&s_nf, 1)] = w;
+          }
+        } else {
+          for (int32_t r = r0; r < r1; ++r) {
+            const int32_t w = small ? (int32_t)s_adj[r] : a.g_adj[e0 + r];
+            if (atomicCAS(&dist[w], 0xffffffffu, level + 1) == 0xffffffffu) fb[atomicAdd(&s_nf, 1)] = w;
+          }
+        }
+      }
+      __syncthreads();
+      nf = s_nf;
+      int32_t* t = fa; fa = fb; fb = t;
+    }
+    __syncthreads();
+    if (kMode == 2) {
+      const unsigned long long r_first = (unsigned long long)(uint32_t)p;
+      const unsigned long long r_second = (unsigned long long)(uint32_t)(a.kbase + a.orank[p]);
+      for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
+        const uint32_t d = dist[i];
+        a.key[verts[i]] = ((unsigned long long)(d >> 1) << 32) | ((d & 1u) ? r_second : r_first);
+      }
+    } else {
+      unsigned long long b = 0ull;
+      for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
+        const uint32_t d = dist[i];
+        if (d == 0xffffffffu) continue;
+        const unsigned long long c = ((unsigned long long)d << 32) | (0xffffffffu - (uint32_t)verts[i]);
+        b = c > b ? c : b;
+      }
+      b = block_max(b, red64);
+      if (tid == 0) a.best[p] = b;
+    }
+    __syncthreads();
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) { ctr[0] = 2 * orank[k]; ctr[1] = 0; ctr[2] = 0; }
+}
+
+// Vertex lists by patch: counts of vertices and of adjacency entries.
+__global__ void k_patch_counts(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ label, int32_t n,
+                               int32_t* __restrict__ pcnt, int32_t* __restrict__ pdeg) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t p = label[v];
+    atomicAdd(&pcnt[p], 1);
+    atomicAdd(&pdeg[p], rowptr[v + 1] - rowptr[v]);
+  }
+}
+
+__global__ void k_patch_scatter(const int32_t* __restrict__ label, int32_t n, const int32_t* __restrict__ pstart,
+                                int32_t* __restrict__ fill, int32_t* __restrict__ pverts) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t p = label[v];
+    pverts[pstart[p] + atomicAdd(&fill[p], 1)] = v;
+  }
 }
 
 struct BfsLauncher {
@@ -250,7 +383,10 @@ struct BfsLauncher {
     return FP_OK;
   }
   fp_status bfs(fp_handle* h, unsigned long long* key, const int32_t* group, int32_t* fa, int32_t* fb, int32_t* ctr) {
+    // one CTA per SM: frontiers are small, and the grid barrier between
+    // levels gets cheaper with fewer CTAs
     int g = grid_for(h->n, BFS_THREADS);
+    if (g > NUM_SMS_B300) g = NUM_SMS_B300;
     if (g > maxgrid_bfs) g = maxgrid_bfs;
     const int32_t* rp = h->rowptr;
     const int32_t* cl = h->col;
@@ -284,10 +420,9 @@ fp_status run_patching(fp_handle* h) {
   int32_t* seed_of = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
   int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));
   int32_t* ctr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 8);
-  int32_t* hbuf = nullptr;
-  if (!key || !key2 || !best || !group || !fa || !fb || !flag || !rank || !seed_of || !tmp || !ctr)
+  int32_t* hbuf = pinned_scratch();
+  if (!key || !key2 || !best || !group || !fa || !fb || !flag || !rank || !seed_of || !tmp || !ctr || !hbuf)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "patching workspace");
-  if (cudaMallocHost(&hbuf, 4 * sizeof(int32_t)) != cudaSuccess) return fail(h, FP_ERR_OUT_OF_MEMORY, "pinned");
 
   const int G = grid_for(n, 256);
   // R1 seeds
@@ -331,20 +466,44 @@ fp_status run_patching(fp_handle* h) {
     FP_TRY(sync_status(h, &st));
     k += hbuf[0];
   }
+  // vertex lists by patch (for the searches inside patches)
+  int32_t* pcnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* pdeg = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* pstart = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* pedge = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* pverts = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* loc = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int32_t* g_adj = (int32_t*)dev_alloc(h, sizeof(int32_t) * (h->nnz + 8));
+  int32_t* g_vtx = (int32_t*)dev_alloc(h, sizeof(int32_t) * (5 * (size_t)n + 8));
+  int32_t* orank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  if (!pcnt || !pdeg || !pstart || !pedge || !pverts || !loc || !g_adj || !g_vtx || !orank)
+    return fail(h, FP_ERR_OUT_OF_MEMORY, "patch lists");
+  auto patch_lists = [&](int32_t kk) {
+    ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
+    FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, group);
+    fill_i32(h, pcnt, 0, kk);
+    fill_i32(h, pdeg, 0, kk);
+    FP_LAUNCH(h, k_patch_counts, G, 256, 0, h->rowptr, group, n, pcnt, pdeg);
+    scan_exclusive(h, pcnt, pstart, kk, tmp);
+    scan_exclusive(h, pdeg, pedge, kk, tmp);
+    fill_i32(h, pdeg, 0, kk);
+    FP_LAUNCH(h, k_patch_scatter, G, 256, 0, group, n, pstart, pdeg, pverts);
+  };
+  LocalArgs la{0, h->rowptr, h->col, group, pstart, pverts, pedge, g_adj, g_vtx, loc, nullptr, orank, 0,
+               seed_of, best, key};
+  const int GL = NUM_SMS_B300 * 8;
   // R4 Lloyd rounds
   const int GK = grid_for(k, 256);
   for (int32_t it = 0; it < h->opt.lloyd_rounds; ++it) {
+    patch_lists(k);
+    la.k = k;
+    la.over = nullptr;
     {
-      ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, group);
-      fill_i32(h, ctr, 0, 3);
-      FP_LAUNCH(h, k_boundary_sources, G, 256, 0, h->rowptr, h->col, n, group, key2, fa, ctr);
+      ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
+      FP_LAUNCH(h, k_patch_local<0>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
     }
-    FP_TRY(L.bfs(h, key2, group, fa, fb, ctr));
     {
       ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_fill_u64, GK, 256, 0, best, 0ull, (int64_t)k);
-      FP_LAUNCH(h, k_pick_farthest, G, 256, 0, key2, group, n, best);
       FP_LAUNCH(h, k_lloyd_apply, GK, 256, 0, best, k, seed_of);
       FP_LAUNCH(h, k_fill_u64, G, 256, 0, key, KEY_INF, (int64_t)n);
       FP_LAUNCH(h, k_all_seed_sources, GK, 256, 0, seed_of, k, key, fa, ctr);
@@ -353,18 +512,13 @@ fp_status run_patching(fp_handle* h) {
     FP_TRY(L.bfs(h, key, nullptr, fa, fb, ctr));
   }
   // R5 cap: split until every patch fits
-  int32_t* psize = flag;   // reuse: [k] sizes, then rank for oversize flags
   int32_t* over = rank;
-  int32_t* orank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  if (!orank) return fail(h, FP_ERR_OUT_OF_MEMORY, "split workspace");
   for (int32_t round = 0; round < n; ++round) {
     const int GKr = grid_for(k, 256);
+    patch_lists(k);
     {
       ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, group);
-      fill_i32(h, psize, 0, k);
-      FP_LAUNCH(h, k_patch_sizes, G, 256, 0, group, n, psize);
-      FP_LAUNCH(h, k_oversize_flags, GKr, 256, 0, psize, k, cap, over);
+      FP_LAUNCH(h, k_oversize_flags, GKr, 256, 0, pcnt, k, cap, over);
       scan_exclusive(h, over, orank, k, tmp);
     }
     cudaMemcpyAsync(hbuf, orank + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
@@ -372,21 +526,16 @@ fp_status run_patching(fp_handle* h) {
     FP_TRY(sync_status(h, &st));
     const int32_t nover = hbuf[0];
     if (nover == 0) break;
+    la.k = k;
+    la.over = over;
+    la.kbase = k;
     {
-      ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_fill_u64, G, 256, 0, key2, KEY_INF, (int64_t)n);
-      FP_LAUNCH(h, k_oversize_seed_sources, GKr, 256, 0, seed_of, over, orank, k, key2, fa, ctr);
-    }
-    FP_TRY(L.bfs(h, key2, group, fa, fb, ctr));
-    {
-      ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_fill_u64, GKr, 256, 0, best, 0ull, (int64_t)k);
-      FP_LAUNCH(h, k_pick_farthest, G, 256, 0, key2, group, n, best);
-      FP_LAUNCH(h, k_reset_oversize, G, 256, 0, group, over, n, key);
-      FP_LAUNCH(h, k_split_sources, GKr, 256, 0, best, over, orank, k, seed_of, key, fa, ctr);
+      ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
+      FP_LAUNCH(h, k_patch_local<1>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
+      FP_LAUNCH(h, k_split_seeds, GKr, 256, 0, best, over, orank, k, seed_of);
+      FP_LAUNCH(h, k_patch_local<2>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
     }
     FP_CHECK_LAUNCH(h, "split");
-    FP_TRY(L.bfs(h, key, group, fa, fb, ctr));
     k += nover;
   }
   {
@@ -395,9 +544,10 @@ fp_status run_patching(fp_handle* h) {
   }
   FP_CHECK_LAUNCH(h, "labels");
   h->k = k;
-  cudaFreeHost(hbuf);
-  dev_free(h, key); dev_free(h, key2); dev_free(h, best); dev_free(h, group); dev_free(h, fa); dev_free(h, fb);
-  dev_free(h, flag); dev_free(h, rank); dev_free(h, seed_of); dev_free(h, tmp); dev_free(h, ctr); dev_free(h, orank);
+  for (void* p : {(void*)key, (void*)key2, (void*)best, (void*)group, (void*)fa, (void*)fb, (void*)flag,
+                  (void*)rank, (void*)seed_of, (void*)tmp, (void*)ctr, (void*)orank, (void*)pcnt, (void*)pdeg,
+                  (void*)pstart, (void*)pedge, (void*)pverts, (void*)loc, (void*)g_adj, (void*)g_vtx})
+    dev_free(h, p);
   return FP_OK;
 }
 

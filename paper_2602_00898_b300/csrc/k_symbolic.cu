@@ -29,9 +29,16 @@ namespace {
 
 constexpr int SYM_THREADS = 128;
 constexpr int SYM_MAX_ANC = 32;
-constexpr int CARRY_CHUNKS = 8;                 // register carry for rows of <= 256 words
 constexpr size_t SYM_SMEM_BITMAP = 8 * 1024;    // bitmap + prefix (<= 1024 words each)
-constexpr size_t SYM_SMEM_ROWS = 56 * 1024;     // column rows + local->position map
+constexpr size_t SYM_SMEM_ROWS_SMALL = 40 * 1024;   // rows + local->position map, deep levels
+constexpr size_t SYM_SMEM_ROWS_BIG = 208 * 1024;    // same, shallow levels (few, large nodes)
+
+// Column i's bit row only holds words >= i/32 (its bits are all above i), so
+// the rows are stored as a staircase: row i starts at tri_off(i, W).
+__device__ __forceinline__ int64_t tri_off(int32_t i, int32_t W) {
+  const int64_t q = i >> 5, r = i & 31;
+  return (int64_t)i * W - (32 * q * (q - 1) / 2 + r * q);
+}
 
 struct SymArgs {
   const int32_t* rowptr;
@@ -54,7 +61,128 @@ struct SymArgs {
   int64_t pool_words;
   unsigned long long* pool_ctr;
   int32_t* status;
+  int64_t smem_rows;               // shared bytes available for rows + map in this launch
 };
+
+// Column sweep of one node by one warp (see step 3 below). NCH > 0: rows of at
+// most 32*NCH words, the current column's row is kept in registers (carry)
+// while the etree parent is the next column; NCH = 0: rows of any width,
+// merged through memory.
+template <int NCH>
+__device__ __forceinline__ void sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t* upos, int32_t m,
+                                              int32_t W, int32_t b, unsigned long long& nnz,
+                                              unsigned long long& fl) {
+  const int lane = threadIdx.x & 31;
+  constexpr int NC = NCH > 0 ? NCH : 1;
+  uint32_t carry[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) carry[c] = 0u;
+  bool cv = false;
+  for (int32_t i = 0; i < m; ++i) {
+    const int i0 = i >> 5;
+    const uint32_t* ri = rows + tri_off(i, W) - i0;     // word w of row i at ri[w], w >= i0
+    uint32_t f = 0xffffffffu, cnt = 0;
+    if constexpr (NCH > 0) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int w = lane + 32 * c;
+        uint32_t s = (w < W && w >= i0) ? ri[w] : 0u;
+        if (cv) s |= carry[c];
+        carry[c] = s;
+        if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
+      }
+    } else {
+      for (int w = lane; w < W; w += 32) {
+        const uint32_t s = w >= i0 ? ri[w] : 0u;
+        if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
+      }
+    }
+    f = __reduce_min_sync(0xffffffffu, f);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    const int32_t pf = cnt ? upos[f] : -1;
+    if (lane == 0) {
+      a.parent[b + i] = pf;
+      a.colcount[b + i] = (int32_t)cnt + 1;
+      nnz += (unsigned long long)(cnt + 1);
+      fl += (unsigned long long)(cnt + 1) * (unsigned long long)(cnt + 1);
+    }
+    if (cnt == 0) { cv = false; continue; }
+    if (f >= (uint32_t)m) {
+      // export struct(i) (f first) to the node holding position pf
+      unsigned long long off = 0, hdr = 0;
+      if (lane == 0) {
+        off = atomicAdd(&a.elem_ctr[1], (unsigned long long)cnt);
+        hdr = atomicAdd(&a.elem_ctr[0], 1ull);
+      }
+      off = __shfl_sync(0xffffffffu, off, 0);
+      hdr = __shfl_sync(0xffffffffu, hdr, 0);
+      const bool ok = (int64_t)(off + cnt) <= a.cap_data && (int64_t)hdr < a.cap_hdr;
+      if (!ok) {
+        if (lane == 0) atomicOr(a.status, ST_POOL_OVERFLOW);
+      } else {
+        int32_t base = 0;
+        for (int w0 = 0; w0 < W; w0 += 32) {
+          const int w = w0 + lane;
+          uint32_t s = 0u;
+          if (w < W) {
+            if constexpr (NCH > 0) {
+#pragma unroll
+              for (int c = 0; c < NCH; ++c) if (c == (w0 >> 5)) s = carry[c];
+            } else if (w >= i0) {
+              s = ri[w];
+            }
+          }
+          const int c = __popc(s);
+          int32_t ex = warp_incl_scan_i32(c) - c;
+          const int32_t tot = __shfl_sync(0xffffffffu, ex + c, 31);
+          while (s) {
+            const int bt = __ffs(s) - 1;
+            s &= s - 1;
+            a.elem_data[off + base + ex++] = upos[w * 32 + bt];
+          }
+          base += tot;
+        }
+        if (lane == 0) {
+          const int32_t target = a.node_of[a.perm[pf]];
+          a.elem_hdr[3 * hdr + 1] = (int32_t)off;
+          a.elem_hdr[3 * hdr + 2] = (int32_t)cnt;
+          __threadfence();
+          a.elem_hdr[3 * hdr] = atomicExch(&a.elem_head[target], (int32_t)hdr);
+        }
+      }
+      cv = false;
+      continue;
+    }
+    // merge struct(i) \ {f} into column f
+    const int f0 = (int)(f >> 5);
+    if constexpr (NCH > 0) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int w = lane + 32 * c;
+        if (w == f0) carry[c] &= ~(1u << (f & 31));
+      }
+      if (f == (uint32_t)i + 1) {
+        cv = true;
+      } else {
+        cv = false;
+        uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int w = lane + 32 * c;
+          if (w < W && w >= f0 && carry[c]) rf[w] |= carry[c];
+        }
+      }
+    } else {
+      uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
+      for (int w = lane; w < W; w += 32) {
+        if (w < f0) continue;           // struct(i) \ {f} lies above f
+        uint32_t s = ri[w];
+        if (w == f0) s &= ~(1u << (f & 31));
+        if (s) rf[w] |= s;
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -143,17 +271,18 @@ __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
     }
     const int32_t U = m + acnt;
     const int32_t W = (U + 31) >> 5;
+    const int64_t row_words = tri_off(m, W);
     if (tid == 0) {
-      const size_t need = ((size_t)m * W + U) * 4;
-      if (need <= SYM_SMEM_ROWS) {
+      const int64_t need = (row_words + U) * 4;
+      if (need <= a.smem_rows) {
         s_rows = (uint32_t*)(smem + SYM_SMEM_BITMAP);
       } else {
-        const unsigned long long words = (unsigned long long)m * W + U;
+        const unsigned long long words = (unsigned long long)(row_words + U);
         unsigned long long o = atomicAdd(a.pool_ctr, words);
         if ((int64_t)(o + words) > a.pool_words) { s_fail = 1; atomicOr(a.status, ST_POOL_OVERFLOW); }
         s_rows = a.pool + o;
       }
-      s_upos = (int32_t*)(s_rows + (size_t)m * W);
+      s_upos = (int32_t*)(s_rows + row_words);
     }
     __syncthreads();
     if (s_fail) continue;
@@ -165,7 +294,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
       const int32_t w = c >> 5;
       return m + wpre[w] + __popc(bitmap[w] & ((1u << (c & 31)) - 1u));
     };
-    for (int64_t i = tid; i < (int64_t)m * W; i += SYM_THREADS) rows[i] = 0u;
+    for (int64_t i = tid; i < row_words; i += SYM_THREADS) rows[i] = 0u;
     for (int32_t i = tid; i < m; i += SYM_THREADS) upos[i] = b + i;
     for (int32_t w = tid; w < bw; w += SYM_THREADS) {
       uint32_t x = bitmap[w];
@@ -184,7 +313,7 @@ __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
     // 2. seed the column rows: adjacency above the column, then the elements
     for (int32_t i = tid; i < m; i += SYM_THREADS) {
       const int32_t x = a.perm[b + i];
-      uint32_t* r = rows + (size_t)i * W;
+      uint32_t* r = rows + tri_off(i, W) - (i >> 5);
       for (int32_t e = a.rowptr[x]; e < a.rowptr[x + 1]; ++e) {
         const int32_t pos = a.iperm[a.col[e]];
         if (pos > b + i) {
@@ -196,121 +325,22 @@ __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
     for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
       const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
       const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
-      uint32_t* r = rows + (size_t)r0 * W;
+      uint32_t* r = rows + tri_off(r0, W) - (r0 >> 5);
       for (int32_t j = 1 + tid; j < len; j += SYM_THREADS) {
         const int32_t l = local_of(a.elem_data[off + j]);
         atomicOr(&r[l >> 5], 1u << (l & 31));
       }
     }
     __syncthreads();
-    // 3. column sweep by warp 0
+    // 3. column sweep by warp 0, unrolled for the row width
     if (tid < 32) {
-      uint32_t carry[CARRY_CHUNKS];
-      const bool use_carry = W <= 32 * CARRY_CHUNKS;
-      bool cv = false;
       unsigned long long nnz = 0, fl = 0;
-      for (int32_t i = 0; i < m; ++i) {
-        uint32_t* ri = rows + (size_t)i * W;
-        int32_t f = INT_MAX, cnt = 0;
-        if (use_carry) {
-#pragma unroll
-          for (int c = 0; c < CARRY_CHUNKS; ++c) {
-            const int w = lane + 32 * c;
-            uint32_t s = w < W ? ri[w] : 0u;
-            if (cv) s |= carry[c];
-            carry[c] = s;
-            if (s) { const int bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
-          }
-        } else {
-          for (int w = lane; w < W; w += 32) {
-            const uint32_t s = ri[w];
-            if (s) { const int bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
-          }
-        }
-        f = warp_min(f);
-        cnt = warp_sum(cnt);
-        const int32_t pf = cnt ? upos[f] : -1;
-        if (lane == 0) {
-          a.parent[b + i] = pf;
-          a.colcount[b + i] = cnt + 1;
-          nnz += (unsigned long long)(cnt + 1);
-          fl += (unsigned long long)(cnt + 1) * (unsigned long long)(cnt + 1);
-        }
-        if (cnt == 0) { cv = false; continue; }
-        if (f >= m) {
-          // export struct(i) (f first) to the node holding position pf
-          unsigned long long off = 0, hdr = 0;
-          if (lane == 0) {
-            off = atomicAdd(&a.elem_ctr[1], (unsigned long long)cnt);
-            hdr = atomicAdd(&a.elem_ctr[0], 1ull);
-          }
-          off = __shfl_sync(0xffffffffu, off, 0);
-          hdr = __shfl_sync(0xffffffffu, hdr, 0);
-          const bool ok = (int64_t)(off + cnt) <= a.cap_data && (int64_t)hdr < a.cap_hdr;
-          if (!ok) {
-            if (lane == 0) atomicOr(a.status, ST_POOL_OVERFLOW);
-          } else {
-            int32_t base = 0;
-            for (int w0 = 0; w0 < W; w0 += 32) {
-              const int w = w0 + lane;
-              uint32_t s = 0u;
-              if (w < W) {
-                if (use_carry) {
-                  // the chunk holding word w is w0 / 32
-#pragma unroll
-                  for (int c = 0; c < CARRY_CHUNKS; ++c) if (c == (w0 >> 5)) s = carry[c];
-                } else {
-                  s = ri[w];
-                }
-              }
-              const int c = __popc(s);
-              int32_t ex = warp_incl_scan_i32(c) - c;
-              const int32_t tot = __shfl_sync(0xffffffffu, ex + c, 31);
-              while (s) {
-                const int bt = __ffs(s) - 1;
-                s &= s - 1;
-                a.elem_data[off + base + ex++] = upos[w * 32 + bt];
-              }
-              base += tot;
-            }
-            if (lane == 0) {
-              const int32_t target = a.node_of[a.perm[pf]];
-              a.elem_hdr[3 * hdr + 1] = (int32_t)off;
-              a.elem_hdr[3 * hdr + 2] = cnt;
-              __threadfence();
-              a.elem_hdr[3 * hdr] = atomicExch(&a.elem_head[target], (int32_t)hdr);
-            }
-          }
-          cv = false;
-          continue;
-        }
-        // merge struct(i) \ {f} into column f
-        if (use_carry) {
-#pragma unroll
-          for (int c = 0; c < CARRY_CHUNKS; ++c) {
-            const int w = lane + 32 * c;
-            if (w == (f >> 5)) carry[c] &= ~(1u << (f & 31));
-          }
-          if (f == i + 1) {
-            cv = true;
-          } else {
-            cv = false;
-            uint32_t* rf = rows + (size_t)f * W;
-#pragma unroll
-            for (int c = 0; c < CARRY_CHUNKS; ++c) {
-              const int w = lane + 32 * c;
-              if (w < W && carry[c]) rf[w] |= carry[c];
-            }
-          }
-        } else {
-          uint32_t* rf = rows + (size_t)f * W;
-          for (int w = lane; w < W; w += 32) {
-            uint32_t s = ri[w];
-            if (w == (f >> 5)) s &= ~(1u << (f & 31));
-            if (s) rf[w] |= s;
-          }
-        }
-      }
+      const int nch = (W + 31) >> 5;
+      if (nch <= 1) sweep_columns<1>(a, rows, upos, m, W, b, nnz, fl);
+      else if (nch <= 2) sweep_columns<2>(a, rows, upos, m, W, b, nnz, fl);
+      else if (nch <= 4) sweep_columns<4>(a, rows, upos, m, W, b, nnz, fl);
+      else if (nch <= 8) sweep_columns<8>(a, rows, upos, m, W, b, nnz, fl);
+      else sweep_columns<0>(a, rows, upos, m, W, b, nnz, fl);
       if (lane == 0) {
         atomicAdd(&a.sums[0], nnz);
         atomicAdd(&a.sums[1], fl);
@@ -344,16 +374,19 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     fill_i32(h, head, -1, nn);
     FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
     cudaFuncSetAttribute(k_symbolic_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SYM_SMEM_BITMAP + SYM_SMEM_ROWS));
+                         (int)(SYM_SMEM_BITMAP + SYM_SMEM_ROWS_BIG));
     for (int32_t d = h->D; d >= 0; --d) {
       const int32_t t0 = (1 << d) - 1, T = 1 << d;
+      // shallow levels hold few, large nodes: one CTA per SM with most of its
+      // shared memory; deep levels hold many small nodes: several CTAs per SM
+      const size_t rows_smem = T <= 2 * NUM_SMS_B300 ? SYM_SMEM_ROWS_BIG : SYM_SMEM_ROWS_SMALL;
       SymArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_of, h->node_begin, h->node_size, t0, T,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
-                 ctr + 4, h->d_status};
+                 ctr + 4, h->d_status, (int64_t)rows_smem};
       ProfScope ps(FP_PROF_SYMBOLIC, h->stream);
       FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr + 4, 0ull, (int64_t)1);
       const int grid = T < NUM_SMS_B300 * 16 ? T : NUM_SMS_B300 * 16;
-      FP_LAUNCH(h, k_symbolic_level, grid, SYM_THREADS, SYM_SMEM_BITMAP + SYM_SMEM_ROWS, sa);
+      FP_LAUNCH(h, k_symbolic_level, grid, SYM_THREADS, SYM_SMEM_BITMAP + rows_smem, sa);
     }
     FP_CHECK_LAUNCH(h, "symbolic");
     unsigned long long hs[2] = {0, 0};
