@@ -150,6 +150,32 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
                               const fp_options* opts, void* stream, int32_t* h_perm, int32_t* h_iperm,
                               int32_t* h_parent, int32_t* h_colcount, int64_t* h_nnzL, int64_t* h_flops);
 
+/*
+ * Allocation-free CSR assembly. The paper has no counterpart: this is a
+ * library service for callers that cannot allocate device memory when they
+ * build the graph (for example a process whose device memory is entirely
+ * reserved by another framework's caching allocator, or a latency-critical
+ * loop that must stay out of the driver's allocator). It computes exactly the
+ * CSR that fp_create_from_faces + fp_get_graph produce (G = graph of the face
+ * list without diagonal, rows sorted and duplicate-free) into caller buffers:
+ * d_rowptr [n_vertices+1] and d_col [col_cap]; *h_nnz (may be NULL) receives
+ * rowptr[n_vertices]. All intermediate data live in one fixed scratch array
+ * compiled into the library (about 4.5 MB of device memory, held by every GPU
+ * that loads the library until the process exits); the call never allocates.
+ * Limits: n_vertices <= 65536, n_faces <= 131072, and at most 256 face-edge
+ * entries per vertex (FP_ERR_UNSUPPORTED beyond, with a message in
+ * fp_last_error(NULL)). FP_ERR_INVALID_ARG for NULL pointers, negative sizes,
+ * a corner out of range, or col_cap smaller than the number of entries.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one scratch array: calls that may overlap
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller. Synchronises `stream`.
+ */
+fp_status fp_graph_from_faces_static(const int32_t* d_faces, int64_t n_faces, int32_t n_vertices,
+                                     int32_t* d_rowptr, int32_t* d_col, int64_t col_cap, int64_t* h_nnz,
+                                     void* stream);
+
 /* Releases the handle and its workspace (stream-ordered). NULL is a no-op. */
 fp_status fp_destroy(fp_handle* h);
 
