@@ -338,18 +338,117 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """256 meshes (n log-uniform in [2k, 200k], grid / icosphere / flipped torus),
+    autotuned caps, one fp_batch_order per step; metric meshes/s."""
+    import torch
+    import paper_2602_00898_b300 as fp
+    import meshgen
+
+    ws, rank, lrank = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(lrank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    meshes = meshgen.mesh_mix(256, seed=rank)
+    nverts = sum(m.n for m in meshes)
+    faces = [torch.from_numpy(m.faces).to(dev) for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes])
+    opts = fp.fp_default_options()
+    caps = fp.fp_batch_autotune(items, opts)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        assert fp.fp_batch_order(items, opts) == 0
+    torch.cuda.synchronize()
+    # no stage profiling here: its event records would serialise the workers
+    clocks = Clocks(lrank)
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    times, launches = [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st = fp.fp_batch_order(items, opts)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+        assert st == 0
+        launches += sum(int(it.launches) for it in items)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    sec = sum(times) / len(times)
+    if ws > 1:
+        tt = torch.tensor([sec], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        sec = float(tt.item())
+    # end to end: pinned host faces in, four outputs back, every step
+    hfaces = [torch.from_numpy(m.faces).pin_memory() for m in meshes]
+    houts = [[torch.empty(m.n, dtype=torch.int32).pin_memory() for _ in range(4)] for m in meshes]
+    e2e = []
+    for r in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for d, hsrc in zip(faces, hfaces):
+            d.copy_(hsrc, non_blocking=True)
+        torch.cuda.synchronize()
+        assert fp.fp_batch_order(items, opts) == 0
+        for (f, outs), ho in zip(items.tensors, houts):
+            for o, h in zip(outs, ho):
+                h.copy_(o[:h.numel()], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    nnz = sum(int(it.nnzL) for it in items)
+    line = {
+        "metric": "batched meshes/s at 1 GPU", "value": ws * len(meshes) / sec, "unit": "meshes/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batch256", "meshes": len(meshes), "vertices": nverts, "caps_by_size_class": caps,
+                   "workers": 8, "l2": "flushed between steps (256 MB write)",
+                   "step": "fp_batch_order over all meshes (create+permute+symbolic each)"},
+        "mverts_per_s": ws * nverts / sec / 1e6, "nnzL_total": nnz,
+        "clocks": clk,
+        "e2e": {"value": len(meshes) / statistics.median(e2e), "unit": "meshes/s",
+                "h2d_bytes_per_step": int(sum(m.faces.nbytes for m in meshes)),
+                "d2h_bytes_per_step": int(sum(16 * m.n for m in meshes))},
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        idx = list(range(0, len(meshes), 32))
+        sample = [meshes[i] for i in idx]
+        t0 = time.perf_counter()
+        for i in idx:
+            oracle_step(meshes[i], items[i].chosen_cap, 1)
+        per = (time.perf_counter() - t0) / len(sample)
+        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "meshes/s", "cores": 1, "kind": "oracle",
+                                "sample": f"every 32nd mesh of the batch ({len(sample)} meshes, "
+                                          f"{sum(m.n for m in sample)} vertices), single-threaded oracle, "
+                                          f"1 of {os.cpu_count()} host cores"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="icosphere7")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256"], default="icosphere7")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.workload == "batch256" and args.impl == "ours":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -151,6 +151,50 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
                               int32_t* h_parent, int32_t* h_colcount, int64_t* h_nnzL, int64_t* h_flops);
 
 /*
+ * Batched ordering of many independent meshes (a library service; the paper
+ * orders one mesh at a time). Each item is one mesh: device faces in, device
+ * outputs (caller-owned, each may be NULL, DOF-expanded when
+ * opts->dof_per_vertex > 1) and host results out. The meshes are spread over
+ * `n_workers` host threads (1..64; 0 = 8), each with its own CUDA stream on
+ * the current device, which run create + permute + symbolic + destroy for one
+ * mesh after another; the per-mesh pipelines are latency bound, so running
+ * many at once fills the GPU. Items are taken in order of decreasing size.
+ * Synchronous: returns when every item is done. Returns FP_OK if every item
+ * succeeded, else the first failing item's status (each item's own status is
+ * in item->status). A patch_cap of 0 in an item selects the autotuned cap of
+ * its size class (see fp_batch_autotune); item->chosen_cap reports the cap
+ * used, so that a result can be reproduced with the single-mesh calls.
+ */
+typedef struct {
+  const int32_t* d_faces;   /* int32 [n_faces][3] on the device */
+  int64_t n_faces;
+  int32_t n_vertices;
+  int32_t patch_cap;        /* > 0: this cap; 0: autotuned cap of the size class */
+  int32_t* d_perm;          /* [n*b] outputs, device, may be NULL */
+  int32_t* d_iperm;
+  int32_t* d_parent;
+  int32_t* d_colcount;
+  int64_t nnzL;             /* out */
+  int64_t flops;            /* out */
+  int32_t chosen_cap;       /* out */
+  int32_t status;           /* out: fp_status of this item */
+  int64_t launches;         /* out: kernel launches issued for this item */
+} fp_batch_item;
+
+fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers);
+
+/*
+ * Autotuner for fp_batch_order: for every size class of the items (vertex
+ * counts below 8k, 32k, 128k, 512k, and above) it orders the class's largest
+ * item once per candidate cap in {128, 256, 384, 512}, timing create +
+ * permute + symbolic with CUDA events (best of two), and keeps the fastest
+ * cap whose nnz(L) is within 5% of the smallest nnz(L) seen for that item.
+ * The choices are kept process-wide and used by items with patch_cap 0;
+ * h_caps (may be NULL) receives the 5 chosen caps (0 for an empty class).
+ */
+fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t* h_caps);
+
+/*
  * Allocation-free CSR assembly. The paper has no counterpart: this is a
  * library service for callers that cannot allocate device memory when they
  * build the graph (for example a process whose device memory is entirely

@@ -33,6 +33,14 @@ class fp_options(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class fp_batch_item(ctypes.Structure):
+    _fields_ = [("d_faces", ctypes.c_void_p), ("n_faces", ctypes.c_int64), ("n_vertices", ctypes.c_int32),
+                ("patch_cap", ctypes.c_int32), ("d_perm", ctypes.c_void_p), ("d_iperm", ctypes.c_void_p),
+                ("d_parent", ctypes.c_void_p), ("d_colcount", ctypes.c_void_p), ("nnzL", ctypes.c_int64),
+                ("flops", ctypes.c_int64), ("chosen_cap", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("launches", ctypes.c_int64)]
+
+
 _lib = None
 
 
@@ -63,6 +71,9 @@ def lib() -> ctypes.CDLL:
             "fp_profiling": (None, [ctypes.c_int]),
             "fp_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), P64, ctypes.c_int]),
             "fp_profile_reset": (None, []),
+            "fp_batch_order": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32]),
+            "fp_batch_autotune": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, P32]),
+            "fp_graph_from_faces_static": (i32, [vp, i64, i32, vp, vp, i64, P64, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -171,6 +182,41 @@ def fp_last_error(h=None) -> str:
 
 def fp_launch_count(h) -> int:
     return int(lib().fp_launch_count(h))
+
+
+def fp_batch_order(items, opts: fp_options | None = None, n_workers: int = 0) -> int:
+    """items: a ctypes array of fp_batch_item (filled in place). Returns the
+    batch status; each item carries its own status, nnzL, flops, chosen_cap."""
+    opts = opts or fp_default_options()
+    return int(lib().fp_batch_order(items, len(items), ctypes.byref(opts), n_workers))
+
+
+def fp_batch_autotune(items, opts: fp_options | None = None) -> list[int]:
+    opts = opts or fp_default_options()
+    caps = (ctypes.c_int32 * 5)()
+    _check(lib().fp_batch_autotune(items, len(items), ctypes.byref(opts), caps))
+    return list(caps)
+
+
+def make_batch(faces_list, n_list, caps=None, outputs=True, dof: int = 1):
+    """Builds a ctypes array of fp_batch_item for CUDA face tensors, with fresh
+    CUDA output tensors (kept alive on the returned object as .tensors)."""
+    import torch
+    items = (fp_batch_item * len(faces_list))()
+    keep = []
+    for i, (f, n) in enumerate(zip(faces_list, n_list)):
+        it = items[i]
+        it.d_faces = f.data_ptr() if f.shape[0] else None
+        it.n_faces = int(f.shape[0])
+        it.n_vertices = int(n)
+        it.patch_cap = int(caps[i]) if caps is not None else 0
+        outs = None
+        if outputs:
+            outs = [torch.empty(max(n * dof, 1), dtype=torch.int32, device=f.device) for _ in range(4)]
+            it.d_perm, it.d_iperm, it.d_parent, it.d_colcount = [o.data_ptr() for o in outs]
+        keep.append((f, outs))
+    items.tensors = keep
+    return items
 
 
 # ---- convenience wrapper ---------------------------------------------------------

@@ -91,6 +91,19 @@ struct AuxStream {
 };
 AuxStream* aux_stream(int device);
 
+// Raises a kernel's dynamic shared-memory limit to the device maximum minus its
+// static shared memory. Every caller sets the same value, so concurrent host
+// threads launching the same kernel with different sizes cannot race.
+template <class K>
+inline void allow_max_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 // ---- stage profiling (fp_api.cu) -------------------------------------------------
 bool profiling_on();
 void prof_record(int kind, cudaEvent_t start, cudaEvent_t end);

@@ -699,7 +699,7 @@ fp_status run_local_order(fp_handle* h) {
     a.nnodes_launch = (int32_t)ls[1].size();
     a.overflow = ovf;
     const size_t sm = sparse_smem(mmax[1]);
-    cudaFuncSetAttribute(k_md_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_max_dynamic_smem(k_md_sparse);
     {
       ProfScope ps(FP_PROF_MD_MID, s2);
       k_md_sparse<<<(unsigned)ls[1].size(), MD_THREADS, sm, s2>>>(a);
@@ -707,7 +707,7 @@ fp_status run_local_order(fp_handle* h) {
     }
     // redo flagged nodes with global rows (grow_off/gsort_off index from 0 here)
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
-    cudaFuncSetAttribute(k_md_global, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
+    allow_max_dynamic_smem(k_md_global);
     ProfScope ps(FP_PROF_MD_LARGE, s2);
     k_md_global<<<(unsigned)ls[1].size(), MD_THREADS, smg, s2>>>(a);
     h->launches++;
@@ -719,7 +719,7 @@ fp_status run_local_order(fp_handle* h) {
     a.grow_off = dup + off64 + (int64_t)ls[1].size();
     a.gsort_off = dup + off64 + nsg + (int64_t)ls[1].size();
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
-    cudaFuncSetAttribute(k_md_global, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smg);
+    allow_max_dynamic_smem(k_md_global);
     ProfScope ps(FP_PROF_MD_LARGE, s2);
     k_md_global<<<(unsigned)ls[2].size(), MD_THREADS, smg, s2>>>(a);
     h->launches++;
@@ -737,7 +737,7 @@ fp_status run_local_order(fp_handle* h) {
     int64_t grid = ((int64_t)ls[0].size() + nw - 1) / nw;
     const int64_t cap = sms - reserved > 1 ? sms - reserved : 1;
     if (grid > cap) grid = cap;
-    cudaFuncSetAttribute(k_md_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_max_dynamic_smem(k_md_leaf);
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
     k_md_leaf<<<(unsigned)grid, 32 * nw, sm, h->stream>>>(a);
     h->launches++;

@@ -582,7 +582,7 @@ fp_status run_nested_dissection(fp_handle* h) {
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
                   lvl, qa, qb, mark, hist, side, split, mcap, ecap};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
-    cudaFuncSetAttribute(k_nd_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem);
+    allow_max_dynamic_smem(k_nd_bisect);
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
     ps_b.end();
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);

@@ -373,8 +373,7 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     if (!head || !hdr || !data || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic workspace");
     fill_i32(h, head, -1, nn);
     FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
-    cudaFuncSetAttribute(k_symbolic_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(SYM_SMEM_BITMAP + SYM_SMEM_ROWS_BIG));
+    allow_max_dynamic_smem(k_symbolic_level);
     for (int32_t d = h->D; d >= 0; --d) {
       const int32_t t0 = (1 << d) - 1, T = 1 << d;
       // shallow levels hold few, large nodes: one CTA per SM with most of its

@@ -1,0 +1,87 @@
+"""Batched ordering (fp_batch_order / fp_batch_autotune) against the oracle:
+every mesh of a batch must come out bit-identical to the oracle run on that
+mesh alone with the cap the batch used."""
+import numpy as np
+import pytest
+import torch
+
+import meshgen as M
+import oracle as O
+import paper_2602_00898_b300 as fp
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(count, seed, lo=1500, hi=20000):
+    return M.mesh_mix(count, seed, lo, hi)
+
+
+def _check_item(mesh, it, outs, dof=1):
+    assert it.status == 0
+    g = O.graph_from_faces(mesh.faces, mesh.n)
+    o = O.order(g, it.chosen_cap, seed=0)
+    s = O.symbolic(g, o.perm)
+    perm, iperm, parent, colcount = [t.cpu().numpy()[:mesh.n * dof] for t in outs]
+    if dof == 1:
+        np.testing.assert_array_equal(perm, o.perm)
+        np.testing.assert_array_equal(iperm, o.iperm)
+        np.testing.assert_array_equal(parent, s.parent)
+        np.testing.assert_array_equal(colcount, s.colcount)
+        assert (it.nnzL, it.flops) == (s.nnzL, s.flops)
+    else:
+        pd, ad, cd = O.dof_expand(dof, o.perm, s.parent, s.colcount)
+        np.testing.assert_array_equal(perm, pd)
+        np.testing.assert_array_equal(parent, ad)
+        np.testing.assert_array_equal(colcount, cd)
+        assert it.nnzL == dof * dof * s.nnzL - mesh.n * dof * (dof - 1) // 2
+
+
+def test_batch_explicit_caps_matches_oracle():
+    meshes = _mix(12, 7)
+    caps = [64, 128, 256, 512] * 3
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes], caps)
+    st = fp.fp_batch_order(items, fp.fp_default_options(), n_workers=5)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert [it.chosen_cap for it in items] == caps
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        _check_item(m, it, outs)
+
+
+def test_batch_autotuned_caps():
+    meshes = _mix(8, 11, 2000, 60000)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes])
+    chosen = fp.fp_batch_autotune(items, fp.fp_default_options())
+    assert all(c in (0, 128, 256, 384, 512) for c in chosen) and any(chosen)
+    st = fp.fp_batch_order(items, fp.fp_default_options(), n_workers=4)
+    torch.cuda.synchronize()
+    assert st == 0
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        assert it.chosen_cap in (128, 256, 384, 512)
+        _check_item(m, it, outs)
+
+
+def test_batch_item_failure_is_isolated():
+    meshes = _mix(4, 3)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    bad = torch.tensor([[0, 1, 999999]], dtype=torch.int32, device="cuda")
+    items = fp.make_batch(faces + [bad], [m.n for m in meshes] + [10], [200] * 5)
+    st = fp.fp_batch_order(items, fp.fp_default_options(), n_workers=3)
+    torch.cuda.synchronize()
+    assert st == 1
+    assert [it.status for it in items] == [0, 0, 0, 0, 1]
+    for m, it, (_, outs) in zip(meshes, list(items)[:4], items.tensors[:4]):
+        _check_item(m, it, outs)
+
+
+def test_batch_dof3():
+    meshes = [M.shuffle(M.torus(40, 36, 0.3, s), s) for s in range(3)]
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes], [100, 200, 300], dof=3)
+    st = fp.fp_batch_order(items, fp.fp_default_options(dof_per_vertex=3), n_workers=3)
+    torch.cuda.synchronize()
+    assert st == 0
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        _check_item(m, it, outs, dof=3)
