@@ -102,6 +102,9 @@ inline void allow_max_dynamic_smem(K kernel) {
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  // these kernels live on shared memory: ask for the largest carveout so that
+  // as many CTAs as the shared memory allows are resident
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // ---- stage profiling (fp_api.cu) -------------------------------------------------

@@ -11,7 +11,7 @@
 // descendant -- the structure of a column whose etree parent lies above its own
 // node (merged into that parent, as in the column-merge rule
 //   struct(j) = adj(j)_{>j}  u  U_{c : parent(c) = j} struct(c) \ {j}).
-// Nodes are processed level by level from the deepest, one CTA per node:
+// Nodes are processed level by level from the deepest:
 //   1. mark A_t in a bitmap over the concatenated ancestor ranges and compact
 //      it (prefix popcounts), so U_t gets dense local indices in position order;
 //   2. seed one bit row per column with its adjacency and the elements whose
@@ -19,7 +19,18 @@
 //   3. one warp sweeps the columns in order: parent = first set bit, count =
 //      popc; the row is merged into its parent's row, kept in registers when the
 //      parent is the next column (the chains of separator blocks), or exported
-//      as an element to the node holding its parent.
+//      as an element to the node holding its parent;
+//   4. dense tail: once struct(i) holds every later column of the node, the
+//      rest of the node is a chain (parent(j) = j+1) and struct(j) is
+//      {j+1..m-1} plus the ancestor columns met in the rows i..j. Each ancestor
+//      column is counted from the first row that holds it (an atomicMin per
+//      bit, then a histogram and a prefix sum), all in parallel. The top
+//      separators of a mesh reach this point within a few columns.
+// Small nodes (the deep levels: thousands of nodes of at most a few hundred
+// columns) run one node per single-warp CTA in 30 KB of shared memory, seven
+// CTAs per SM; a node that does not fit is deferred to the block kernel, which
+// also takes every node of the shallow levels (one 256-thread CTA per node,
+// rows in shared memory when they fit, else in a global scratch pool).
 // Positions of a node are contiguous in both schedules and ancestors always
 // come later, so bit order equals position order.
 #include "fp_device.cuh"
@@ -27,11 +38,12 @@
 namespace fp {
 namespace {
 
-constexpr int SYM_THREADS = 128;
 constexpr int SYM_MAX_ANC = 32;
-constexpr size_t SYM_SMEM_BITMAP = 8 * 1024;    // bitmap + prefix (<= 1024 words each)
-constexpr size_t SYM_SMEM_ROWS_SMALL = 40 * 1024;   // rows + local->position map, deep levels
-constexpr size_t SYM_SMEM_ROWS_BIG = 208 * 1024;    // same, shallow levels (few, large nodes)
+constexpr int SW_SMEM_WORDS = 7680;        // single-warp CTAs: 30 KB each
+constexpr int SB_THREADS = 256;
+constexpr int SB_SMEM_WORDS = 54 * 1024;   // block CTAs: 216 KB each
+constexpr int DENSE_MIN = 16;              // shortest chain worth the parallel tail
+constexpr int32_t NO_ROW = INT_MAX;
 
 // Column i's bit row only holds words >= i/32 (its bits are all above i), so
 // the rows are stored as a staircase: row i starts at tri_off(i, W).
@@ -57,36 +69,174 @@ struct SymArgs {
   int32_t* elem_data;              // element entries (positions, ascending)
   int64_t cap_hdr, cap_data;
   unsigned long long* elem_ctr;    // [0] headers used, [1] entries used
-  uint32_t* pool;                  // per-launch scratch words
+  uint32_t* pool;                  // global scratch words for rows that do not fit
   int64_t pool_words;
   unsigned long long* pool_ctr;
+  int32_t* big_list;               // nodes of this level deferred to the block kernel
+  int32_t* big_count;
   int32_t* status;
-  int64_t smem_rows;               // shared bytes available for rows + map in this launch
 };
 
-// Column sweep of one node by one warp (see step 3 below). NCH > 0: rows of at
-// most 32*NCH words, the current column's row is kept in registers (carry)
-// while the etree parent is the next column; NCH = 0: rows of any width,
-// merged through memory.
+__device__ __forceinline__ int64_t r4(int64_t x) { return (x + 3) & ~3ll; }
+
+// Local coordinate of an ancestor position in the concatenated ancestor
+// ranges. Ancestor begins grow with the distance in both schedules, so the
+// range is the last one that starts at or before pos.
+__device__ __forceinline__ int32_t anc_coord(const int32_t* ab, const int32_t* ao, int32_t na, int32_t pos) {
+  int32_t i = 0;
+#pragma unroll
+  for (int st = 16; st; st >>= 1)
+    if (i + st < na && ab[i + st] <= pos) i += st;
+  return ao[i] + pos - ab[i];
+}
+
+// Exports struct(i) (cnt entries; bit words given by word_of(w)) as an element
+// to the node holding position pf. Called by one whole warp.
+template <class WordOf>
+__device__ __forceinline__ void export_element(const SymArgs& a, const int32_t* upos, int32_t W, uint32_t cnt,
+                                               int32_t pf, WordOf word_of) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long off = 0, hdr = 0;
+  if (lane == 0) {
+    off = atomicAdd(&a.elem_ctr[1], (unsigned long long)cnt);
+    hdr = atomicAdd(&a.elem_ctr[0], 1ull);
+  }
+  off = __shfl_sync(0xffffffffu, off, 0);
+  hdr = __shfl_sync(0xffffffffu, hdr, 0);
+  if ((int64_t)(off + cnt) > a.cap_data || (int64_t)hdr >= a.cap_hdr) {
+    if (lane == 0) atomicOr(a.status, ST_POOL_OVERFLOW);
+    return;
+  }
+  int32_t base = 0;
+  for (int w0 = 0; w0 < W; w0 += 32) {
+    const int w = w0 + lane;
+    uint32_t s = w < W ? word_of(w) : 0u;
+    const int c = __popc(s);
+    int32_t ex = warp_incl_scan_i32(c) - c;
+    const int32_t tot = __shfl_sync(0xffffffffu, ex + c, 31);
+    while (s) {
+      const int bt = __ffs(s) - 1;
+      s &= s - 1;
+      a.elem_data[off + base + ex++] = upos[w * 32 + bt];
+    }
+    base += tot;
+  }
+  if (lane == 0) {
+    const int32_t target = a.node_of[a.perm[pf]];
+    a.elem_hdr[3 * hdr + 1] = (int32_t)off;
+    a.elem_hdr[3 * hdr + 2] = (int32_t)cnt;
+    __threadfence();
+    a.elem_hdr[3 * hdr] = atomicExch(&a.elem_head[target], (int32_t)hdr);
+  }
+}
+
+// Calls fn(i, pos) for every adjacency entry (new position pos) of the node's
+// columns i = tid, tid + nthr, ... The gathers perm -> rowptr -> col -> iperm
+// are dependent, so GV columns and up to GE neighbours each are loaded
+// together: a handful of round trips per GV columns instead of a chain per
+// neighbour.
+constexpr int GV = 4, GE = 8;
+template <class Fn>
+__device__ __forceinline__ void for_adjacency(const SymArgs& a, int32_t b, int32_t m, int tid, int nthr, Fn fn) {
+  for (int32_t i0 = tid; i0 < m; i0 += GV * nthr) {
+    int32_t e[GV], f[GV];
+#pragma unroll
+    for (int v = 0; v < GV; ++v) {
+      const int32_t i = i0 + v * nthr;
+      const int32_t x = i < m ? a.perm[b + i] : -1;
+      e[v] = x >= 0 ? a.rowptr[x] : 0;
+      f[v] = x >= 0 ? a.rowptr[x + 1] : 0;
+    }
+    for (;;) {
+      bool more = false;
+#pragma unroll
+      for (int v = 0; v < GV; ++v) more |= e[v] < f[v];
+      if (!more) break;
+      int32_t p[GV][GE];
+#pragma unroll
+      for (int v = 0; v < GV; ++v)
+#pragma unroll
+        for (int k = 0; k < GE; ++k) p[v][k] = e[v] + k < f[v] ? a.col[e[v] + k] : -1;
+#pragma unroll
+      for (int v = 0; v < GV; ++v)
+#pragma unroll
+        for (int k = 0; k < GE; ++k) p[v][k] = p[v][k] >= 0 ? a.iperm[p[v][k]] : -1;
+#pragma unroll
+      for (int v = 0; v < GV; ++v) {
+#pragma unroll
+        for (int k = 0; k < GE; ++k)
+          if (p[v][k] >= 0) fn(i0 + v * nthr, p[v][k]);
+        e[v] += GE;
+      }
+    }
+  }
+}
+
+// Popcount of the bits of word w that fall in columns [lo, hi).
+__device__ __forceinline__ uint32_t popc_range(uint32_t s, int w, int32_t lo, int32_t hi) {
+  const int32_t l = max(lo - 32 * w, 0), h = min(hi - 32 * w, 32);
+  if (l >= h) return 0u;
+  const uint32_t mk = (h == 32 ? 0xffffffffu : ((1u << h) - 1u)) & ~((1u << l) - 1u);
+  return __popc(s & mk);
+}
+
+// Column sweep of one node by one warp (step 3). NCH > 0: rows of at most
+// 32*NCH words; the current column's structure is kept in registers (carry)
+// while the etree parent is the next column, and the next row is loaded one
+// column ahead (a merge from column i never lands in row i+1 except through
+// the carry, so the early load sees its final contents). NCH = 0: rows of any
+// width, merged through memory. Returns the column where the dense tail
+// starts (its structure written back to its row), or m.
 template <int NCH>
-__device__ __forceinline__ void sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t* upos, int32_t m,
-                                              int32_t W, int32_t b, unsigned long long& nnz,
-                                              unsigned long long& fl) {
+__device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t* upos, int32_t m, int32_t W,
+                                 int32_t b, bool tail_ok, unsigned long long& nnz, unsigned long long& fl) {
   const int lane = threadIdx.x & 31;
   constexpr int NC = NCH > 0 ? NCH : 1;
-  uint32_t carry[NC];
+  uint32_t carry[NC], nxt[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) carry[c] = 0u;
+  for (int c = 0; c < NC; ++c) carry[c] = nxt[c] = 0u;
+  if constexpr (NCH > 0) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const int w = lane + 32 * c;
+      nxt[c] = w < W ? rows[w] : 0u;
+    }
+  }
+  // column i's parent and count are held by lane i % 32 and stored 32 at a time
+  int32_t my_par = -1, my_cc = 1;
+  auto flush = [&](int32_t i_last) {
+    const int32_t j = (i_last & ~31) + lane;
+    if (j <= i_last) {
+      a.parent[b + j] = my_par;
+      a.colcount[b + j] = my_cc;
+      nnz += (unsigned long long)my_cc;
+      fl += (unsigned long long)my_cc * (unsigned long long)my_cc;
+    }
+  };
   bool cv = false;
+  int64_t off = 0;                                // tri_off(i, W)
   for (int32_t i = 0; i < m; ++i) {
     const int i0 = i >> 5;
-    const uint32_t* ri = rows + tri_off(i, W) - i0;     // word w of row i at ri[w], w >= i0
+    uint32_t* ri = rows + off - i0;               // word w of row i at ri[w], w >= i0
+    off += W - i0;
     uint32_t f = 0xffffffffu, cnt = 0;
     if constexpr (NCH > 0) {
+      uint32_t cur[NCH];
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) cur[c] = nxt[c];
+      if (i + 1 < m) {
+        const int i1 = (i + 1) >> 5;
+        const uint32_t* rn = rows + off - i1;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int w = lane + 32 * c;
+          nxt[c] = (w < W && w >= i1) ? rn[w] : 0u;
+        }
+      }
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
         const int w = lane + 32 * c;
-        uint32_t s = (w < W && w >= i0) ? ri[w] : 0u;
+        uint32_t s = cur[c];
         if (cv) s |= carry[c];
         carry[c] = s;
         if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
@@ -99,59 +249,55 @@ __device__ __forceinline__ void sweep_columns(const SymArgs& a, uint32_t* rows, 
     }
     f = __reduce_min_sync(0xffffffffu, f);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
-    const int32_t pf = cnt ? upos[f] : -1;
-    if (lane == 0) {
-      a.parent[b + i] = pf;
-      a.colcount[b + i] = (int32_t)cnt + 1;
-      nnz += (unsigned long long)(cnt + 1);
-      fl += (unsigned long long)(cnt + 1) * (unsigned long long)(cnt + 1);
+    const bool inside = f < (uint32_t)m;
+    const int32_t pf = cnt == 0 ? -1 : (inside ? b + (int32_t)f : upos[f]);
+    if (lane == (i & 31)) {
+      my_par = pf;
+      my_cc = (int32_t)cnt + 1;
     }
-    if (cnt == 0) { cv = false; continue; }
-    if (f >= (uint32_t)m) {
-      // export struct(i) (f first) to the node holding position pf
-      unsigned long long off = 0, hdr = 0;
-      if (lane == 0) {
-        off = atomicAdd(&a.elem_ctr[1], (unsigned long long)cnt);
-        hdr = atomicAdd(&a.elem_ctr[0], 1ull);
-      }
-      off = __shfl_sync(0xffffffffu, off, 0);
-      hdr = __shfl_sync(0xffffffffu, hdr, 0);
-      const bool ok = (int64_t)(off + cnt) <= a.cap_data && (int64_t)hdr < a.cap_hdr;
-      if (!ok) {
-        if (lane == 0) atomicOr(a.status, ST_POOL_OVERFLOW);
-      } else {
-        int32_t base = 0;
-        for (int w0 = 0; w0 < W; w0 += 32) {
-          const int w = w0 + lane;
+    const bool flushed = (i & 31) == 31 || i + 1 == m;
+    if (flushed) flush(i);
+    if (cnt == 0) {
+      cv = false;
+      continue;
+    }
+    if (!inside) {
+      if constexpr (NCH > 0) {
+        export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t {
           uint32_t s = 0u;
-          if (w < W) {
-            if constexpr (NCH > 0) {
 #pragma unroll
-              for (int c = 0; c < NCH; ++c) if (c == (w0 >> 5)) s = carry[c];
-            } else if (w >= i0) {
-              s = ri[w];
-            }
-          }
-          const int c = __popc(s);
-          int32_t ex = warp_incl_scan_i32(c) - c;
-          const int32_t tot = __shfl_sync(0xffffffffu, ex + c, 31);
-          while (s) {
-            const int bt = __ffs(s) - 1;
-            s &= s - 1;
-            a.elem_data[off + base + ex++] = upos[w * 32 + bt];
-          }
-          base += tot;
-        }
-        if (lane == 0) {
-          const int32_t target = a.node_of[a.perm[pf]];
-          a.elem_hdr[3 * hdr + 1] = (int32_t)off;
-          a.elem_hdr[3 * hdr + 2] = (int32_t)cnt;
-          __threadfence();
-          a.elem_hdr[3 * hdr] = atomicExch(&a.elem_head[target], (int32_t)hdr);
-        }
+          for (int c = 0; c < NCH; ++c) if (c == (w >> 5)) s = carry[c];
+          return s;
+        });
+      } else {
+        export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t { return w >= i0 ? ri[w] : 0u; });
       }
       cv = false;
       continue;
+    }
+    // dense tail? struct(i) must hold every later column of the node (cnt
+    // bounds that count from above, so most columns skip the exact test)
+    if (tail_ok && f == (uint32_t)i + 1 && m - 1 - i >= DENSE_MIN && cnt >= (uint32_t)(m - 1 - i)) {
+      uint32_t cn = 0;
+      if constexpr (NCH > 0) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) cn += popc_range(carry[c], lane + 32 * c, i + 1, m);
+      } else {
+        for (int w = lane; w < W; w += 32) if (w >= i0) cn += popc_range(ri[w], w, i + 1, m);
+      }
+      cn = __reduce_add_sync(0xffffffffu, cn);
+      if (cn == (uint32_t)(m - 1 - i)) {
+        if constexpr (NCH > 0) {
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) {
+            const int w = lane + 32 * c;
+            if (w < W && w >= i0) ri[w] = carry[c];
+          }
+        }
+        if (!flushed) flush(i);
+        __syncwarp();
+        return i;
+      }
     }
     // merge struct(i) \ {f} into column f
     const int f0 = (int)(f >> 5);
@@ -182,86 +328,186 @@ __device__ __forceinline__ void sweep_columns(const SymArgs& a, uint32_t* rows, 
       }
     }
   }
+  return m;
 }
 
-__global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int32_t anc_b[SYM_MAX_ANC], anc_s[SYM_MAX_ANC], anc_o[SYM_MAX_ANC];
-  __shared__ int32_t s_na, s_atot;
-  __shared__ int32_t red[40];
+// Step 4 for columns is+1 .. m-1 (see the file comment). scratch holds
+// U - m + (m - is) ints. All threads of the CTA call.
+__device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t* upos, int32_t m, int32_t U,
+                           int32_t W, int32_t b, int32_t is, int32_t* scratch, int32_t* red,
+                           unsigned long long& nnz, unsigned long long& fl) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  const int32_t nab = U - m, L = m - is;
+  int32_t* first = scratch;          // [nab]: first row in is..m-1 holding each ancestor column
+  int32_t* hist = scratch + nab;     // [L]: ancestor columns first met in row is + l
+  for (int32_t j = is + 1 + tid; j < m - 1; j += nthr) a.parent[b + j] = b + j + 1;
+  for (int32_t u = tid; u < nab; u += nthr) first[u] = NO_ROW;
+  for (int32_t l = tid; l < L; l += nthr) hist[l] = 0;
+  __syncthreads();
+  const int32_t wa = m >> 5, nwa = W - wa;
+  const uint32_t amask0 = 0xffffffffu << (m & 31);
+  if (nab > 0) {
+    // every (row, ancestor word) pair independently, so that many loads are in flight
+    const int64_t tot = (int64_t)L * nwa;
+    for (int64_t x = tid; x < tot; x += nthr) {
+      const int32_t l = is + (int32_t)(x / nwa), w = wa + (int32_t)(x % nwa);
+      uint32_t s = rows[tri_off(l, W) - (l >> 5) + w];
+      if (w == wa) s &= amask0;
+      while (s) {
+        const int bt = __ffs(s) - 1;
+        s &= s - 1;
+        atomicMin(&first[w * 32 + bt - m], l);
+      }
+    }
+  }
+  __syncthreads();
+  for (int32_t u = tid; u < nab; u += nthr) {
+    const int32_t f = first[u];
+    if (f != NO_ROW) atomicAdd(&hist[f - is], 1);
+  }
+  __syncthreads();
+  int32_t run = 0;
+  for (int32_t l0 = 0; l0 < L; l0 += nthr) {
+    const int32_t l = l0 + tid;
+    const int32_t hcount = l < L ? hist[l] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan_i32(hcount, &tot, red);
+    if (l >= 1 && l < L) {
+      const int32_t j = is + l;
+      const int32_t cc = (m - 1 - j) + run + ex + hcount + 1;
+      a.colcount[b + j] = cc;
+      nnz += (unsigned long long)cc;
+      fl += (unsigned long long)cc * (unsigned long long)cc;
+    }
+    run += tot;
+  }
+  // the last column: its structure is every ancestor column met
+  if (tid < 32) {
+    if (run == 0) {
+      if (lane == 0) a.parent[b + m - 1] = -1;
+    } else {
+      int32_t umin = 0;
+      for (int32_t u0 = 0; u0 < nab; u0 += 32) {
+        const int32_t u = u0 + lane;
+        const unsigned bal = __ballot_sync(0xffffffffu, u < nab && first[u] != NO_ROW);
+        if (bal) {
+          umin = u0 + __ffs(bal) - 1;
+          break;
+        }
+      }
+      const int32_t pf = upos[m + umin];
+      if (lane == 0) a.parent[b + m - 1] = pf;
+      const int32_t Wa = (nab + 31) >> 5;
+      export_element(a, upos + m, Wa, (uint32_t)run, pf, [&](int w) -> uint32_t {
+        const int32_t u = w * 32;
+        uint32_t s = 0u;
+        for (int k = 0; k < 32; ++k)
+          if (u + k < nab && first[u + k] != NO_ROW) s |= 1u << k;
+        return s;
+      });
+    }
+  }
+}
+
+// One node per CTA. Used with 32 threads (single-warp CTAs for the small nodes
+// of deep levels; a node that does not fit in shared memory is deferred to
+// a.big_list) and with SB_THREADS threads (whole levels of few nodes, or the
+// deferred list; rows that do not fit go to the global pool).
+__global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_t smem_words, int32_t from_list,
+                                                               int32_t may_defer) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int32_t s_ab[32], s_ao[32];
+  __shared__ int32_t s_na, s_atot, s_fail, s_is;
   __shared__ uint32_t* s_bitmap;
   __shared__ int32_t* s_wpre;
   __shared__ uint32_t* s_rows;
   __shared__ int32_t* s_upos;
-  __shared__ int32_t s_fail;
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int32_t* s_tail;
+  __shared__ int32_t red[40];
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  unsigned long long nnz = 0, fl = 0;
+  const int32_t count = from_list ? *a.big_count : a.T;
 
-  for (int32_t ni = blockIdx.x; ni < a.T; ni += gridDim.x) {
-    const int32_t t = a.t0 + ni;
+  for (int32_t q = blockIdx.x; q < count; q += gridDim.x) {
+    const int32_t t = from_list ? a.big_list[q] : a.t0 + q;
     const int32_t m = a.node_size[t];
     if (m == 0) continue;
     const int32_t b = a.node_begin[t];
-    if (tid == 0) {
-      int32_t na = 0, off = 0, x = t;
-      while (x > 0 && na < SYM_MAX_ANC) {
-        x = (x - 1) / 2;
-        anc_b[na] = a.node_begin[x];
-        anc_s[na] = a.node_size[x];
-        anc_o[na] = off;
-        off += anc_s[na];
-        ++na;
+    const int32_t end = b + m;
+    if (tid < 32) {
+      const int32_t na = 31 - __clz(t + 1);    // the ancestors of t, nearest first
+      int32_t s = 0, bg = 0;
+      if (lane < na) {
+        const int32_t x = ((t + 1) >> (lane + 1)) - 1;
+        bg = a.node_begin[x];
+        s = a.node_size[x];
       }
-      s_na = na;
-      s_atot = off;
-      s_fail = 0;
-      const int32_t bw = (off + 31) >> 5;
-      if ((size_t)bw * 8 <= SYM_SMEM_BITMAP) {
-        s_bitmap = (uint32_t*)smem;
-        s_wpre = (int32_t*)(smem + SYM_SMEM_BITMAP / 2);
-      } else {
-        unsigned long long o = atomicAdd(a.pool_ctr, (unsigned long long)(2 * bw + 2));
-        if ((int64_t)(o + 2 * bw + 2) > a.pool_words) { s_fail = 1; atomicOr(a.status, ST_POOL_OVERFLOW); }
-        s_bitmap = a.pool + o;
-        s_wpre = (int32_t*)(a.pool + o + bw + 1);
+      const int32_t inc = warp_incl_scan_i32(s);
+      s_ab[lane] = bg;
+      s_ao[lane] = inc - s;
+      if (lane == 31) {
+        s_na = na;
+        s_atot = inc;
       }
     }
     __syncthreads();
-    if (s_fail) continue;
     const int32_t na = s_na, atot = s_atot, bw = (atot + 31) >> 5;
-    uint32_t* bitmap = s_bitmap;
-    int32_t* wpre = s_wpre;
-    auto anc_coord = [&](int32_t pos) -> int32_t {
-      for (int i = 0; i < na; ++i)
-        if (pos >= anc_b[i] && pos < anc_b[i] + anc_s[i]) return anc_o[i] + pos - anc_b[i];
+    int32_t cur = 0;   // shared-memory words taken so far (every thread tracks it)
+    auto take = [&](int64_t words, bool& in_smem) -> int64_t {
+      words = (words + 3) & ~3ll;     // keep every region 16-byte aligned
+      if (cur + words <= smem_words) {
+        in_smem = true;
+        const int64_t o = cur;
+        cur += (int32_t)words;
+        return o;
+      }
+      in_smem = false;
       return -1;
     };
-    for (int32_t w = tid; w < bw; w += SYM_THREADS) bitmap[w] = 0u;
-    __syncthreads();
-    // 1. mark the ancestors reachable from this node
-    const int32_t end = b + m;
-    for (int32_t i = tid; i < m; i += SYM_THREADS) {
-      const int32_t x = a.perm[b + i];
-      for (int32_t e = a.rowptr[x]; e < a.rowptr[x + 1]; ++e) {
-        const int32_t pos = a.iperm[a.col[e]];
-        if (pos >= end) {
-          const int32_t c = anc_coord(pos);
-          atomicOr(&bitmap[c >> 5], 1u << (c & 31));
-        }
+    // 1. bitmap of the reachable ancestor columns
+    bool bm_smem = false;
+    const int64_t bm_off = take(2 * (int64_t)bw, bm_smem);
+    if (tid == 0) {
+      s_fail = 0;
+      if (bm_smem) {
+        s_bitmap = sm + bm_off;
+      } else if (may_defer) {
+        s_fail = 2;
+      } else {
+        const unsigned long long o = atomicAdd(a.pool_ctr, (unsigned long long)r4(2 * bw));
+        if ((int64_t)(o + r4(2 * bw)) > a.pool_words) { s_fail = 1; atomicOr(a.status, ST_POOL_OVERFLOW); }
+        s_bitmap = a.pool + o;
       }
+      s_wpre = (int32_t*)(s_bitmap + bw);
     }
+    __syncthreads();
+    if (s_fail) {
+      if (s_fail == 2 && tid == 0) a.big_list[atomicAdd(a.big_count, 1)] = t;
+      continue;
+    }
+    uint32_t* bitmap = s_bitmap;
+    int32_t* wpre = s_wpre;
+    for (int32_t w = tid; w < bw; w += nthr) bitmap[w] = 0u;
+    __syncthreads();
+    for_adjacency(a, b, m, tid, nthr, [&](int32_t, int32_t pos) {
+      if (pos >= end) {
+        const int32_t c = anc_coord(s_ab, s_ao, na, pos);
+        atomicOr(&bitmap[c >> 5], 1u << (c & 31));
+      }
+    });
     for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
       const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
-      for (int32_t j = tid; j < len; j += SYM_THREADS) {
+      for (int32_t j = tid; j < len; j += nthr) {
         const int32_t pos = a.elem_data[off + j];
         if (pos >= end) {
-          const int32_t c = anc_coord(pos);
+          const int32_t c = anc_coord(s_ab, s_ao, na, pos);
           atomicOr(&bitmap[c >> 5], 1u << (c & 31));
         }
       }
     }
     __syncthreads();
     int32_t acnt = 0;
-    for (int32_t w0 = 0; w0 < bw; w0 += SYM_THREADS) {
+    for (int32_t w0 = 0; w0 < bw; w0 += nthr) {
       const int32_t w = w0 + tid;
       const int32_t c = w < bw ? __popc(bitmap[w]) : 0;
       int32_t tot;
@@ -272,81 +518,106 @@ __global__ void __launch_bounds__(SYM_THREADS) k_symbolic_level(SymArgs a) {
     const int32_t U = m + acnt;
     const int32_t W = (U + 31) >> 5;
     const int64_t row_words = tri_off(m, W);
+    // 2. placement: the local->position map, the rows, the tail scratch
+    bool up_smem = false, rw_smem = false, tl_smem = false;
+    const int64_t up_off = take(U, up_smem);
+    const int64_t rw_off = up_smem ? take(row_words, rw_smem) : (rw_smem = false, -1);
+    const bool tail_in_bitmap = 2 * (int64_t)bw >= U && bm_smem;
+    const int64_t tl_off = tail_in_bitmap ? -1 : take(U, tl_smem);
     if (tid == 0) {
-      const int64_t need = (row_words + U) * 4;
-      if (need <= a.smem_rows) {
-        s_rows = (uint32_t*)(smem + SYM_SMEM_BITMAP);
+      if (may_defer && !(up_smem && rw_smem)) {
+        s_fail = 2;
       } else {
-        const unsigned long long words = (unsigned long long)(row_words + U);
-        unsigned long long o = atomicAdd(a.pool_ctr, words);
-        if ((int64_t)(o + words) > a.pool_words) { s_fail = 1; atomicOr(a.status, ST_POOL_OVERFLOW); }
-        s_rows = a.pool + o;
+        int64_t gwords = (up_smem ? 0 : r4(U)) + (rw_smem ? 0 : r4(row_words));
+        uint32_t* g = nullptr;
+        if (gwords > 0) {
+          const unsigned long long o = atomicAdd(a.pool_ctr, (unsigned long long)gwords);
+          if ((int64_t)(o + gwords) > a.pool_words) { s_fail = 1; atomicOr(a.status, ST_POOL_OVERFLOW); }
+          g = a.pool + o;
+        }
+        s_upos = up_smem ? (int32_t*)(sm + up_off) : (int32_t*)g;
+        s_rows = rw_smem ? sm + rw_off : (up_smem ? g : g + r4(U));
+        if (tail_in_bitmap) {
+          s_tail = (int32_t*)bitmap;
+        } else if (tl_smem) {
+          s_tail = (int32_t*)(sm + tl_off);
+        } else if (!may_defer && !s_fail) {
+          const unsigned long long o = atomicAdd(a.pool_ctr, (unsigned long long)r4(U));
+          s_tail = (int64_t)(o + r4(U)) <= a.pool_words ? (int32_t*)(a.pool + o) : nullptr;
+        } else {
+          s_tail = nullptr;
+        }
       }
-      s_upos = (int32_t*)(s_rows + row_words);
     }
     __syncthreads();
-    if (s_fail) continue;
+    if (s_fail) {
+      if (s_fail == 2 && tid == 0) a.big_list[atomicAdd(a.big_count, 1)] = t;
+      continue;
+    }
     uint32_t* rows = s_rows;
     int32_t* upos = s_upos;
     auto local_of = [&](int32_t pos) -> int32_t {
       if (pos < end) return pos - b;
-      const int32_t c = anc_coord(pos);
+      const int32_t c = anc_coord(s_ab, s_ao, na, pos);
       const int32_t w = c >> 5;
       return m + wpre[w] + __popc(bitmap[w] & ((1u << (c & 31)) - 1u));
     };
-    for (int64_t i = tid; i < row_words; i += SYM_THREADS) rows[i] = 0u;
-    for (int32_t i = tid; i < m; i += SYM_THREADS) upos[i] = b + i;
-    for (int32_t w = tid; w < bw; w += SYM_THREADS) {
+    for (int64_t i = tid; i < r4(row_words) / 4; i += nthr) reinterpret_cast<uint4*>(rows)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int32_t i = tid; i < m; i += nthr) upos[i] = b + i;
+    for (int32_t w = tid; w < bw; w += nthr) {
       uint32_t x = bitmap[w];
       int32_t r = m + wpre[w];
       while (x) {
         const int bt = __ffs(x) - 1;
         x &= x - 1;
         const int32_t c = w * 32 + bt;
-        int32_t pos = -1;
-        for (int i = 0; i < na; ++i)
-          if (c >= anc_o[i] && c < anc_o[i] + anc_s[i]) { pos = anc_b[i] + c - anc_o[i]; break; }
-        upos[r++] = pos;
+        int32_t i = 0;
+#pragma unroll
+        for (int st = 16; st; st >>= 1)
+          if (i + st < na && s_ao[i + st] <= c) i += st;
+        upos[r++] = s_ab[i] + c - s_ao[i];
       }
     }
     __syncthreads();
-    // 2. seed the column rows: adjacency above the column, then the elements
-    for (int32_t i = tid; i < m; i += SYM_THREADS) {
-      const int32_t x = a.perm[b + i];
-      uint32_t* r = rows + tri_off(i, W) - (i >> 5);
-      for (int32_t e = a.rowptr[x]; e < a.rowptr[x + 1]; ++e) {
-        const int32_t pos = a.iperm[a.col[e]];
-        if (pos > b + i) {
-          const int32_t l = local_of(pos);
-          atomicOr(&r[l >> 5], 1u << (l & 31));
-        }
+    // seed the column rows: adjacency above the column, then the elements
+    for_adjacency(a, b, m, tid, nthr, [&](int32_t i, int32_t pos) {
+      if (pos > b + i) {
+        const int32_t l = local_of(pos);
+        atomicOr(&rows[tri_off(i, W) - (i >> 5) + (l >> 5)], 1u << (l & 31));
       }
-    }
+    });
     for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
       const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
       const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
       uint32_t* r = rows + tri_off(r0, W) - (r0 >> 5);
-      for (int32_t j = 1 + tid; j < len; j += SYM_THREADS) {
+      for (int32_t j = 1 + tid; j < len; j += nthr) {
         const int32_t l = local_of(a.elem_data[off + j]);
         atomicOr(&r[l >> 5], 1u << (l & 31));
       }
     }
     __syncthreads();
     // 3. column sweep by warp 0, unrolled for the row width
+    const bool tail_ok = s_tail != nullptr;
     if (tid < 32) {
-      unsigned long long nnz = 0, fl = 0;
       const int nch = (W + 31) >> 5;
-      if (nch <= 1) sweep_columns<1>(a, rows, upos, m, W, b, nnz, fl);
-      else if (nch <= 2) sweep_columns<2>(a, rows, upos, m, W, b, nnz, fl);
-      else if (nch <= 4) sweep_columns<4>(a, rows, upos, m, W, b, nnz, fl);
-      else if (nch <= 8) sweep_columns<8>(a, rows, upos, m, W, b, nnz, fl);
-      else sweep_columns<0>(a, rows, upos, m, W, b, nnz, fl);
-      if (lane == 0) {
-        atomicAdd(&a.sums[0], nnz);
-        atomicAdd(&a.sums[1], fl);
-      }
+      int32_t is;
+      if (nch <= 1) is = sweep_columns<1>(a, rows, upos, m, W, b, tail_ok, nnz, fl);
+      else if (nch <= 2) is = sweep_columns<2>(a, rows, upos, m, W, b, tail_ok, nnz, fl);
+      else if (nch <= 4) is = sweep_columns<4>(a, rows, upos, m, W, b, tail_ok, nnz, fl);
+      else if (nch <= 8) is = sweep_columns<8>(a, rows, upos, m, W, b, tail_ok, nnz, fl);
+      else is = sweep_columns<0>(a, rows, upos, m, W, b, tail_ok, nnz, fl);
+      if (lane == 0) s_is = is;
     }
     __syncthreads();
+    // 4. dense tail
+    if (s_is < m) dense_tail(a, rows, upos, m, U, W, b, s_is, s_tail, red, nnz, fl);
+    __syncthreads();
+  }
+  nnz = warp_sum(nnz);
+  fl = warp_sum(fl);
+  if (lane == 0 && (nnz || fl)) {
+    atomicAdd(&a.sums[0], nnz);
+    atomicAdd(&a.sums[1], fl);
   }
 }
 
@@ -366,26 +637,33 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
   int64_t cap_hdr = (int64_t)n + 1024, cap_data = 8 * (int64_t)n + (1 << 20), pool_words = 4 * (int64_t)n + (1 << 22);
   for (int attempt = 0; attempt < 4; ++attempt) {
     int32_t* head = (int32_t*)dev_alloc(h, sizeof(int32_t) * nn);
+    int32_t* big = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nn + 64));
     int32_t* hdr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 3 * cap_hdr);
     int32_t* data = (int32_t*)dev_alloc(h, sizeof(int32_t) * cap_data);
     uint32_t* pool = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * pool_words);
     unsigned long long* ctr = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 8);
-    if (!head || !hdr || !data || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic workspace");
+    if (!head || !big || !hdr || !data || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic workspace");
     fill_i32(h, head, -1, nn);
+    fill_i32(h, big + nn, 0, 64);                 // per-level deferred-node counts
     FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
-    allow_max_dynamic_smem(k_symbolic_level);
+    allow_max_dynamic_smem(k_symbolic_nodes);
     for (int32_t d = h->D; d >= 0; --d) {
       const int32_t t0 = (1 << d) - 1, T = 1 << d;
-      // shallow levels hold few, large nodes: one CTA per SM with most of its
-      // shared memory; deep levels hold many small nodes: several CTAs per SM
-      const size_t rows_smem = T <= 2 * NUM_SMS_B300 ? SYM_SMEM_ROWS_BIG : SYM_SMEM_ROWS_SMALL;
       SymArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_of, h->node_begin, h->node_size, t0, T,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
-                 ctr + 4, h->d_status, (int64_t)rows_smem};
+                 ctr + 4, big + t0, big + nn + d, h->d_status};
       ProfScope ps(FP_PROF_SYMBOLIC, h->stream);
       FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr + 4, 0ull, (int64_t)1);
-      const int grid = T < NUM_SMS_B300 * 16 ? T : NUM_SMS_B300 * 16;
-      FP_LAUNCH(h, k_symbolic_level, grid, SYM_THREADS, SYM_SMEM_BITMAP + rows_smem, sa);
+      if (T <= NUM_SMS_B300) {
+        // few nodes: one large CTA each
+        FP_LAUNCH(h, k_symbolic_nodes, T, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 0, 0);
+      } else {
+        // many small nodes: one warp each; the ones that do not fit go to the
+        // large CTAs afterwards
+        FP_LAUNCH(h, k_symbolic_nodes, T, 32, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+        FP_LAUNCH(h, k_symbolic_nodes, NUM_SMS_B300, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 1,
+                  0);
+      }
     }
     FP_CHECK_LAUNCH(h, "symbolic");
     unsigned long long hs[2] = {0, 0};
@@ -393,7 +671,7 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     if (e != cudaSuccess) return check_cuda(h, e, "read sums");
     int32_t st = 0;
     FP_TRY(sync_status(h, &st));
-    for (void* p : {(void*)head, (void*)hdr, (void*)data, (void*)pool, (void*)ctr}) dev_free(h, p);
+    for (void* p : {(void*)head, (void*)big, (void*)hdr, (void*)data, (void*)pool, (void*)ctr}) dev_free(h, p);
     if (st & ST_POOL_OVERFLOW) {
       // clear the flag and retry with larger pools
       int32_t zero = 0;
