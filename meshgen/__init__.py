@@ -131,3 +131,24 @@ def mesh_mix(count: int, seed: int, n_lo: int = 2000, n_hi: int = 200000) -> lis
             msh = torus(side, side, 0.3, s)
         out.append(shuffle(msh, s))
     return out
+
+
+def gnn_weights(seed: int, f_in: int = 6, hidden: int = 32, quantized: bool = True) -> dict:
+    """Seeded random weights for the two-layer message-passing priority network
+    (input width f_in, hidden width `hidden`, scalar head). quantized: integer
+    codes (weights in [-48, 48], biases in [-4096, 4096], head bias in
+    [-8192, 8192]); otherwise float64 values (weights ~ N(0, 0.25^2), biases
+    ~ N(0, 0.1^2)). Only random numbers: the meaning of the codes belongs to
+    the method."""
+    r = _rng(seed, 7)
+    shapes = {"w1s": (hidden, f_in), "w1n": (hidden, f_in), "b1": (hidden,), "w2s": (hidden, hidden),
+              "w2n": (hidden, hidden), "b2": (hidden,), "w3": (hidden,), "c": ()}
+    out = {}
+    for k, sh in shapes.items():
+        if quantized:
+            lim = 8192 if k == "c" else (4096 if k.startswith("b") else 48)
+            out[k] = r.integers(-lim, lim + 1, size=sh, dtype=np.int64)
+        else:
+            sd = 0.1 if k in ("b1", "b2", "c") else 0.25
+            out[k] = r.normal(0.0, sd, size=sh)
+    return out

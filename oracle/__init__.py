@@ -59,6 +59,14 @@ def lib():
                                    i32p, i32p, ctypes.c_int32, i32p, i64p]
         L.oracle_symbolic.restype = None
         L.oracle_symbolic.argtypes = [i32p, i32p, ctypes.c_int32, i32p, i32p, i32p, i64p, i64p]
+        L.oracle_min_degree_keyed.restype = None
+        L.oracle_min_degree_keyed.argtypes = [i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int32,
+                                              P(ctypes.c_uint32), i32p]
+        L.oracle_local_orders_keyed.restype = None
+        L.oracle_local_orders_keyed.argtypes = [i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int32, i32p,
+                                                P(ctypes.c_uint32), i32p]
+        L.oracle_tie_key.restype = ctypes.c_uint32
+        L.oracle_tie_key.argtypes = [ctypes.c_uint64, ctypes.c_int32]
         L.oracle_dof_expand.restype = None
         L.oracle_dof_expand.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i32p]
         _lib = L
@@ -159,6 +167,40 @@ def min_degree(g: Graph) -> np.ndarray:
     rp, cp, _keep = _gp(g)
     lib().oracle_min_degree(rp, cp, g.n, _p(o))
     return o[:g.n]
+
+
+def min_degree_keyed(g: Graph, verts, key=None) -> np.ndarray:
+    """Exact minimum degree on the subgraph induced by `verts`, ties to the
+    smaller (key, id) (key: one uint32 per entry of verts, or None)."""
+    vs = _i32(verts)
+    m = vs.size
+    o = np.zeros(max(m, 1), np.int32)
+    rp, cp, _keep = _gp(g)
+    kp = None
+    if key is not None:
+        kk = np.ascontiguousarray(key, dtype=np.uint32)
+        kp = _p(kk, ctypes.c_uint32)
+    lib().oracle_min_degree_keyed(rp, cp, g.n, _p(vs) if m else None, m, kp, _p(o))
+    return o[:m]
+
+
+def local_orders_keyed(g: Graph, ptr, verts, key_of_vertex=None) -> np.ndarray:
+    """Keyed minimum-degree order of each vertex set verts[ptr[s]:ptr[s+1]]
+    (key_of_vertex: uint32 per graph vertex, or None for id ties)."""
+    ptr = _i32(ptr); vs = _i32(verts) if len(verts) else np.zeros(1, np.int32)
+    o = np.zeros(max(len(verts), 1), np.int32)
+    rp, cp, _keep = _gp(g)
+    kp = None
+    if key_of_vertex is not None:
+        kk = np.ascontiguousarray(key_of_vertex, dtype=np.uint32)
+        kp = _p(kk, ctypes.c_uint32)
+    lib().oracle_local_orders_keyed(rp, cp, g.n, _p(ptr), ptr.size - 1, _p(vs), kp, _p(o))
+    return o[:len(verts)]
+
+
+def tie_key(r: int, v: int) -> int:
+    """Seeded tie-break key of vertex v for the r-th random MD order."""
+    return int(lib().oracle_tie_key(r, v))
 
 
 @dataclass

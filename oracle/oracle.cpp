@@ -427,7 +427,8 @@ int32_t ceil_log2(int64_t k) {
 // degree in the elimination graph, ties to the smallest original id, and make
 // its neighbours a clique.
 // ---------------------------------------------------------------------------
-std::vector<int32_t> min_degree(const Adj& adj, const std::vector<int32_t>& verts) {
+std::vector<int32_t> min_degree(const Adj& adj, const std::vector<int32_t>& verts,
+                                const std::vector<uint32_t>* key = nullptr) {
   std::map<int32_t, int32_t> loc;
   for (size_t i = 0; i < verts.size(); ++i) loc[verts[i]] = (int32_t)i;
   std::vector<std::set<int32_t>> g(verts.size());
@@ -442,8 +443,11 @@ std::vector<int32_t> min_degree(const Adj& adj, const std::vector<int32_t>& vert
     int32_t p = -1;
     for (size_t i = 0; i < verts.size(); ++i) {
       if (!alive[i]) continue;
-      if (p == -1 || g[i].size() < g[p].size() ||
-          (g[i].size() == g[p].size() && verts[i] < verts[p])) p = (int32_t)i;
+      if (p == -1 || g[i].size() < g[p].size()) { p = (int32_t)i; continue; }
+      if (g[i].size() != g[p].size()) continue;
+      // equal degrees: the smaller (key, id) wins; without keys, the smaller id
+      const uint32_t ki = key ? (*key)[i] : 0u, kp = key ? (*key)[p] : 0u;
+      if (ki < kp || (ki == kp && verts[i] < verts[p])) p = (int32_t)i;
     }
     order.push_back(verts[p]);
     alive[p] = 0;
@@ -456,6 +460,12 @@ std::vector<int32_t> min_degree(const Adj& adj, const std::vector<int32_t>& vert
   }
   return order;
 }
+
+// The learned-priority variant (the paper is silent on learned orderings; this
+// is the reading used for them): the same exact minimum degree, but a tie
+// between equal degrees goes to the smaller (key, original id), key being a
+// per-vertex priority (a network score mapped to a key, or a seeded hash).
+// With all keys equal it is min_degree above.
 
 // Algorithm 3 step 2 with the two schedules of Section 5: post-order (left
 // subtree, right subtree, node) or level order (deepest level first, nodes in
@@ -602,6 +612,39 @@ void oracle_min_degree(const int32_t* rowptr, const int32_t* col, int32_t n, int
   auto o = min_degree(a, all);
   std::copy(o.begin(), o.end(), order);
 }
+
+// Exact minimum-degree order of the subgraph induced by verts[0..m), ties to
+// the smaller (key[i], verts[i]); key may be NULL (ties to the smaller id).
+void oracle_min_degree_keyed(const int32_t* rowptr, const int32_t* col, int32_t n, const int32_t* verts,
+                             int32_t m, const uint32_t* key, int32_t* order) {
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> vs(verts, verts + m);
+  std::vector<uint32_t> ks;
+  if (key) ks.assign(key, key + m);
+  auto o = min_degree(a, vs, key ? &ks : nullptr);
+  std::copy(o.begin(), o.end(), order);
+}
+
+// Keyed minimum-degree orders of several vertex sets at once: set s is
+// verts[ptr[s] .. ptr[s+1]), its order is written to the same range of
+// `order`; key_of_vertex[v] is the key of vertex v (may be NULL).
+void oracle_local_orders_keyed(const int32_t* rowptr, const int32_t* col, int32_t n, const int32_t* ptr,
+                               int32_t nsets, const int32_t* verts, const uint32_t* key_of_vertex,
+                               int32_t* order) {
+  Adj a = adj_from_csr(rowptr, col, n);
+  for (int32_t s = 0; s < nsets; ++s) {
+    std::vector<int32_t> vs(verts + ptr[s], verts + ptr[s + 1]);
+    std::vector<uint32_t> ks;
+    for (int32_t v : vs) ks.push_back(key_of_vertex ? key_of_vertex[v] : 0u);
+    auto o = min_degree(a, vs, &ks);
+    std::copy(o.begin(), o.end(), order + ptr[s]);
+  }
+}
+
+// The seeded tie-break key of a vertex for the r-th random minimum-degree
+// order: the high 32 bits of the seed hash h_r(v) (SplitMix64 at state
+// r*gamma + v, as for the patch seeds).
+uint32_t oracle_tie_key(uint64_t r, int32_t v) { return (uint32_t)(seed_hash(r, v) >> 32); }
 
 // Algorithm 1: patches -> etree -> perm. Outputs (all caller-allocated):
 // label[n] (gmap), node_of[n], perm[n], iperm[n], node_begin/node_size

@@ -112,3 +112,43 @@ def fill_of_order(adj, order) -> int:
 def min_fill_exhaustive(adj) -> int:
     n = len(adj)
     return min(fill_of_order(adj, o) for o in itertools.permutations(range(n)))
+
+
+def md_keyed_brute(adj, verts, key):
+    """Minimum degree on the subgraph induced by verts, written from the rule
+    itself: at every step recompute every alive vertex's degree in the current
+    elimination graph and take the smallest (degree, key, id)."""
+    vs = list(verts)
+    S = set(vs)
+    nb = {v: {u for u in adj[v] if u in S} for v in vs}
+    k = dict(zip(vs, key))
+    alive = set(vs)
+    order = []
+    while alive:
+        p = min(alive, key=lambda v: (len(nb[v] & alive), k[v], v))
+        order.append(p)
+        alive.discard(p)
+        ns = nb[p] & alive
+        for a in ns:
+            nb[a] |= ns - {a}
+    return order
+
+
+def leaf_fill_brute(adj, leaf_order):
+    """Sum of the column counts of the leaf's columns: eliminate the leaf's
+    vertices in order on the graph of the leaf plus its outside neighbours
+    (which are never eliminated); each column counts itself and its
+    neighbours at elimination time."""
+    L = list(leaf_order)
+    outside = {u for v in L for u in adj[v]} - set(L)
+    S = set(L) | outside
+    nb = {v: {u for u in adj[v] if u in S} for v in S}
+    alive = set(S)
+    total = 0
+    for p in L:
+        ns = nb[p] & alive - {p}
+        total += len(ns) + 1
+        alive.discard(p)
+        for a in ns:
+            nb[a] |= ns - {a}
+    return total
