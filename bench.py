@@ -48,7 +48,7 @@ WORKLOADS = {
 #   perm       : perm + iperm 8
 #   symbolic   : pattern + iperm gather + parent/colcount write 60
 STAGES = ["graph", "patch_bfs", "patch_other", "quotient", "nd_bisect", "nd_separator", "layout",
-          "md_small", "md_mid", "md_large", "perm", "symbolic"]
+          "md_small", "md_mid", "md_large", "perm", "symbolic", "learned", "train"]
 BYTES_PER_VERTEX = {"graph": 52, "patch_bfs": 60, "quotient": 52, "nd_separator": 60, "md_small": 32,
                     "md_mid": 32, "md_large": 32, "perm": 8, "symbolic": 60, "layout": 12}
 PER_LAUNCH_UNITS = {"patch_bfs"}   # bytes per vertex are per launch, not per step

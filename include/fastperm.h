@@ -256,12 +256,98 @@ typedef enum {
   FP_PROF_MD_LARGE,        /* a5 minimum degree, larger nodes */
   FP_PROF_PERM,            /* a6/a8 inverse permutation and DOF expansion */
   FP_PROF_SYMBOLIC,        /* a7 etree and column counts */
+  FP_PROF_LEARNED,         /* a10 network scores, keyed orders, fill choice */
+  FP_PROF_TRAIN,           /* a10 training samples and gradient steps */
   FP_PROF_COUNT
 } fp_prof_kind;
 
 void fp_profiling(int on);
 int fp_profile_read(double* ms, int64_t* launches, int cap);
 void fp_profile_reset(void);
+
+/* ---- a10 learned elimination priorities ---------------------------------------
+ *
+ * The paper orders every patch by (approximate) minimum degree and says
+ * nothing about learned orderings. This part adds, per leaf of the tree (a
+ * node with vertices and no non-empty descendant, at most 512 vertices), a
+ * second candidate: exact minimum degree whose ties between equal degrees go
+ * to the vertex with the higher network score (then the smaller id). The
+ * candidate is kept iff its exact fill -- the sum of the leaf columns' counts
+ * in L -- is smaller than plain minimum degree's. A leaf's column counts
+ * depend on its own order only, so nnz(L) never exceeds the plain method's.
+ *
+ * The network: per leaf vertex, 6 integer feature codes (value code/64):
+ * degree in the leaf/8, degree in G/8, has a neighbour outside the leaf,
+ * hop depth from that boundary/(max depth+1), leaf size/patch_cap, 1. Two
+ * layers h' = ReLU(Ws h + Wn mean_{u in leaf neighbours} h_u + b) of width 32
+ * and a head S = w.h + c. Codes: weights value q/128 (|q| <= 255), biases and
+ * c value q/8192 (|q| <= 2^20), activations value q/64 (q in [0, 255], the
+ * layer output rounded to nearest even and clamped). All dot products are
+ * exact integers, computed on BF16 tensor cores with FP32 accumulation.
+ *
+ * Parameter layout, FP_GNN_NPARAMS entries (int32 codes or float weights):
+ * w1s[32][6] w1n[32][6] b1[32] w2s[32][32] w2n[32][32] b2[32] w3[32] c.
+ */
+#define FP_GNN_NPARAMS 2529
+
+/*
+ * Attaches a network (h_codes: host array of FP_GNN_NPARAMS codes, copied) to
+ * the handle; every later fp_permute then runs the learned choice after the
+ * plain ordering. NULL detaches it. Errors: FP_ERR_INVALID_ARG (a code out of
+ * its range), FP_ERR_OUT_OF_MEMORY.
+ */
+fp_status fp_set_priority_net(fp_handle* h, const int32_t* h_codes);
+
+/* After fp_permute with a network attached: leaves considered, leaves whose
+ * learned order was kept, and the summed fills of those leaves under plain
+ * minimum degree and under the chosen orders. Any pointer may be NULL. */
+fp_status fp_learned_stats(const fp_handle* h, int32_t* h_leaves, int32_t* h_kept, int64_t* h_fill_plain,
+                           int64_t* h_fill_chosen);
+
+/*
+ * After fp_permute: the network's scores S (int32 [n], indexed by position
+ * in perm; 0 off the leaves) and feature codes (uint8 [n][8], 6 used) of the
+ * leaf vertices under the current permutation, for codes h_codes (host).
+ * Either output may be NULL. Synchronises the stream.
+ */
+fp_status fp_gnn_scores(fp_handle* h, const int32_t* h_codes, int32_t* d_scores, uint8_t* d_features);
+
+/*
+ * Training sample of the last fp_permute (call it without a network): for
+ * every position p of perm (n entries), d_x [n][8] uint8 feature codes,
+ * d_mask [n] uint8 (1 on leaf positions), d_target [n] float, d_rank [n]
+ * int32 (may be NULL), and the within-leaf neighbour positions as CSR
+ * d_lrowptr [n+1], d_lcol [lcol_cap] (*h_lnnz entries used). The target of a
+ * leaf vertex at rank k of its leaf's best order among plain minimum degree
+ * and n_seeds minimum-degree orders with seeded tie-break keys (the high 32
+ * bits of SplitMix64 at state r*0x9E3779B97F4A7C15 + v, r = 1..n_seeds;
+ * lowest fill wins, ties to the lower r) is (m-1-k)/(m-1) for an m-vertex
+ * leaf (1 when m = 1). Errors: FP_ERR_STATE (no fp_permute, or a network
+ * attached), FP_ERR_INVALID_ARG (n_seeds outside 0..64, lcol_cap too small:
+ * *h_lnnz then holds the size needed).
+ */
+fp_status fp_gnn_sample(fp_handle* h, int32_t n_seeds, uint8_t* d_x, uint8_t* d_mask, float* d_target,
+                        int32_t* d_rank, int32_t* d_lrowptr, int32_t* d_lcol, int64_t lcol_cap, int64_t* h_lnnz);
+
+/* Device scratch bytes fp_gnn_train_step needs for n positions. */
+int64_t fp_gnn_train_work_bytes(int32_t n);
+
+/*
+ * One gradient-descent step of the float network (same structure, no grid:
+ * activations clamped to [0, 255/64]) on a sample: loss = mean squared error
+ * between the score s and the target over mask positions; d_grad receives
+ * the gradient (FP_GNN_NPARAMS floats), d_params is updated in place by
+ * params -= lr * grad (lr = 0: gradient only), *d_loss the loss before the
+ * step. All pointers are device pointers; d_work holds
+ * fp_gnn_train_work_bytes(n) bytes. Deterministic: every reduction has a
+ * fixed order. Runs on `stream`; does not synchronise.
+ */
+fp_status fp_gnn_train_step(float* d_params, float* d_grad, const uint8_t* d_x, const uint8_t* d_mask,
+                            const float* d_target, const int32_t* d_lrowptr, const int32_t* d_lcol, int32_t n,
+                            float lr, float* d_loss, void* d_work, int64_t work_bytes, void* stream);
+
+/* Float weights -> codes (round to nearest, clamped to the code ranges). */
+fp_status fp_gnn_quantise(const float* d_params, int32_t* d_codes, void* stream);
 
 #ifdef __cplusplus
 }

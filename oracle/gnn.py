@@ -9,7 +9,9 @@ message-passing network's scores, and keeps whichever of the two has the
 smaller exact fill. Each reading below is stated where it is implemented:
 
   L1 leaves: tree nodes with vertices and no non-empty descendant (with the
-     default tree depth, the single-patch leaves of Section 4.2).
+     default tree depth, the single-patch leaves of Section 4.2) and at most
+     512 vertices (a larger leaf, possible only with patch caps above 512,
+     keeps its plain order).
   L2 features of a leaf vertex v on the leaf's induced subgraph H (integer
      codes q, value q/64, q clamped to [0, 255]):
        deg_H(v)/8, deg_G(v)/8, [v has a neighbour outside the leaf],
@@ -61,6 +63,7 @@ H_MAX = 255         # largest activation code
 W_MAX = 255         # largest weight code magnitude
 B_MAX = 1 << 20     # largest bias code magnitude
 KEY_BIAS = 1 << 23  # learned key = KEY_BIAS - S
+LEAF_MAX = 512      # largest leaf that gets a learned candidate
 
 
 def rne_div(a, b):
@@ -85,7 +88,7 @@ def leaves(o: Ordering) -> list[int]:
         for c in (2 * t + 1, 2 * t + 2):
             if c < nn:
                 sub[t] += sub[c]
-    return [t for t in range(nn) if o.node_size[t] > 0 and sub[t] == o.node_size[t]]
+    return [t for t in range(nn) if 0 < o.node_size[t] <= LEAF_MAX and sub[t] == o.node_size[t]]
 
 
 @dataclass

@@ -74,6 +74,13 @@ def lib() -> ctypes.CDLL:
             "fp_batch_order": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32]),
             "fp_batch_autotune": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, P32]),
             "fp_graph_from_faces_static": (i32, [vp, i64, i32, vp, vp, i64, P64, vp]),
+            "fp_set_priority_net": (i32, [vp, P32]),
+            "fp_learned_stats": (i32, [vp, P32, P32, P64, P64]),
+            "fp_gnn_scores": (i32, [vp, P32, vp, vp]),
+            "fp_gnn_sample": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, i64, P64]),
+            "fp_gnn_train_work_bytes": (i64, [i32]),
+            "fp_gnn_train_step": (i32, [vp, vp, vp, vp, vp, vp, vp, i32, ctypes.c_float, vp, vp, i64, vp]),
+            "fp_gnn_quantise": (i32, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -238,14 +245,112 @@ class Result:
     launches: int
 
 
-def order_faces(faces, n_vertices: int, stream=None, symbolic: bool = True, **opt) -> Result:
+# ---- a10 learned priorities -------------------------------------------------------
+
+GNN_NPARAMS = 2529
+GNN_FIELDS = (("w1s", (32, 6)), ("w1n", (32, 6)), ("b1", (32,)), ("w2s", (32, 32)), ("w2n", (32, 32)),
+              ("b2", (32,)), ("w3", (32,)), ("c", ()))
+
+
+def pack_params(d: dict, dtype=None):
+    """Network parameters by name -> the flat FP_GNN_NPARAMS layout."""
+    import numpy as np
+    parts = [np.asarray(d[k]).reshape(-1) for k, _ in GNN_FIELDS]
+    flat = np.concatenate(parts)
+    assert flat.size == GNN_NPARAMS
+    return flat.astype(dtype or flat.dtype)
+
+
+def unpack_params(flat) -> dict:
+    import numpy as np
+    flat = np.asarray(flat)
+    out, o = {}, 0
+    for k, sh in GNN_FIELDS:
+        size = int(np.prod(sh)) if sh else 1
+        out[k] = flat[o:o + size].reshape(sh) if sh else flat[o]
+        o += size
+    return out
+
+
+def fp_set_priority_net(h, codes=None):
+    """codes: FP_GNN_NPARAMS int32 codes (numpy), or None to detach."""
+    import numpy as np
+    if codes is None:
+        _check(lib().fp_set_priority_net(h, None), h)
+        return
+    c = np.ascontiguousarray(codes, dtype=np.int32)
+    assert c.size == GNN_NPARAMS
+    _check(lib().fp_set_priority_net(h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), h)
+
+
+def fp_learned_stats(h) -> tuple[int, int, int, int]:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    c, d = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fp_learned_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), h)
+    return a.value, b.value, c.value, d.value
+
+
+def fp_gnn_scores(h, codes, scores=None, features=None):
+    import numpy as np
+    c = np.ascontiguousarray(codes, dtype=np.int32)
+    assert c.size == GNN_NPARAMS
+    _check(lib().fp_gnn_scores(h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _ptr(scores), _ptr(features)), h)
+
+
+@dataclass
+class Sample:
+    """Training sample of one plain ordering (device tensors, per position)."""
+    n: int
+    x: object         # uint8 [n*8] feature codes
+    mask: object      # uint8 [n]
+    target: object    # float32 [n]
+    rank: object      # int32 [n]
+    lrowptr: object   # int32 [n+1]
+    lcol: object      # int32 [nnz]
+
+
+def fp_gnn_sample(h, n_seeds: int = 8) -> Sample:
+    import torch
+    n, _b, nnz = fp_get_sizes(h)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    x = torch.zeros(max(n, 1) * 8, dtype=torch.uint8, device=dev)
+    mask = torch.zeros(max(n, 1), dtype=torch.uint8, device=dev)
+    target = torch.zeros(max(n, 1), dtype=torch.float32, device=dev)
+    rank = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+    lrp = torch.zeros(n + 1, dtype=torch.int32, device=dev)
+    lcol = torch.zeros(max(nnz, 1), dtype=torch.int32, device=dev)
+    used = ctypes.c_int64()
+    _check(lib().fp_gnn_sample(h, n_seeds, _ptr(x), _ptr(mask), _ptr(target), _ptr(rank), _ptr(lrp), _ptr(lcol),
+                               max(nnz, 1), ctypes.byref(used)), h)
+    return Sample(n, x, mask, target, rank, lrp, lcol[:used.value])
+
+
+def gnn_work(n: int):
+    import torch
+    return torch.empty(int(lib().fp_gnn_train_work_bytes(int(n))), dtype=torch.uint8, device="cuda")
+
+
+def fp_gnn_train_step(params, grad, sample: Sample, lr: float, loss, work, stream=None):
+    """params/grad: float32 CUDA [FP_GNN_NPARAMS]; loss: float32 CUDA [1]."""
+    _check(lib().fp_gnn_train_step(_ptr(params), _ptr(grad), _ptr(sample.x), _ptr(sample.mask),
+                                   _ptr(sample.target), _ptr(sample.lrowptr), _ptr(sample.lcol), sample.n,
+                                   float(lr), _ptr(loss), _ptr(work), work.numel(), _stream(stream)))
+
+
+def fp_gnn_quantise(params, codes, stream=None):
+    _check(lib().fp_gnn_quantise(_ptr(params), _ptr(codes), _stream(stream)))
+
+
+def order_faces(faces, n_vertices: int, stream=None, symbolic: bool = True, net=None, **opt) -> Result:
     """Create + permute (+ symbolic) for a CUDA face tensor; returns every output
     as CUDA tensors (perm/iperm/parent/colcount at DOF level, the rest at
-    vertex level)."""
+    vertex level). net: optional priority-network codes (learned leaf orders)."""
     import torch
     o = fp_default_options(**opt)
     h = fp_create_from_faces(faces, n_vertices, o, stream)
     try:
+        if net is not None:
+            fp_set_priority_net(h, net)
         return _run(h, n_vertices, o, stream, symbolic)
     finally:
         fp_destroy(h)

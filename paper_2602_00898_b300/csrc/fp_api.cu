@@ -265,6 +265,7 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
     h->node_cap = h->nnodes;
   }
   FP_TRY(run_local_order(h));
+  FP_TRY(run_learned(h));
   const int64_t N = (int64_t)h->n * h->b;
   if (N > 0) {
     if (h->b == 1) {
@@ -276,6 +277,70 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
   }
   FP_CHECK_LAUNCH(h, "permute outputs");
   h->permuted = true;
+  return FP_OK;
+}
+
+namespace {
+// Code ranges of the priority network (see the header).
+bool codes_valid(const int32_t* c) {
+  const int ranges[8][3] = {{P_W1S, P_W1N, 255}, {P_W1N, P_B1, 255}, {P_B1, P_W2S, 1 << 20}, {P_W2S, P_W2N, 255},
+                            {P_W2N, P_B2, 255}, {P_B2, P_W3, 1 << 20}, {P_W3, P_C, 255}, {P_C, P_COUNT, 1 << 20}};
+  for (auto& r : ranges)
+    for (int i = r[0]; i < r[1]; ++i)
+      if (c[i] < -r[2] || c[i] > r[2]) return false;
+  return true;
+}
+}  // namespace
+
+fp_status fp_set_priority_net(fp_handle* h, const int32_t* h_codes) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h_codes) {
+    dev_free(h, h->qnet);
+    h->qnet = nullptr;
+    return FP_OK;
+  }
+  if (!codes_valid(h_codes)) return fail(h, FP_ERR_INVALID_ARG, "network code out of range");
+  if (!h->qnet) h->qnet = (int32_t*)dev_alloc(h, sizeof(int32_t) * FP_GNN_NPARAMS);
+  if (!h->qnet) return fail(h, FP_ERR_OUT_OF_MEMORY, "network codes");
+  cudaError_t e = cudaMemcpyAsync(h->qnet, h_codes, sizeof(int32_t) * FP_GNN_NPARAMS, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return check_cuda(h, e, "network codes");
+}
+
+fp_status fp_learned_stats(const fp_handle* h, int32_t* h_leaves, int32_t* h_kept, int64_t* h_fill_plain,
+                           int64_t* h_fill_chosen) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h_leaves) *h_leaves = h->learned_leaves;
+  if (h_kept) *h_kept = h->learned_kept;
+  if (h_fill_plain) *h_fill_plain = h->fill_plain;
+  if (h_fill_chosen) *h_fill_chosen = h->fill_chosen;
+  return FP_OK;
+}
+
+fp_status fp_gnn_scores(fp_handle* h, const int32_t* h_codes, int32_t* d_scores, uint8_t* d_features) {
+  if (!h || !h_codes) return fail(h, FP_ERR_INVALID_ARG, "NULL handle or codes");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "fp_gnn_scores before fp_permute");
+  if (!codes_valid(h_codes)) return fail(h, FP_ERR_INVALID_ARG, "network code out of range");
+  const int32_t n = h->n;
+  if (n == 0) return FP_OK;
+  int32_t* q = (int32_t*)dev_alloc(h, sizeof(int32_t) * FP_GNN_NPARAMS);
+  uint32_t* key = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * n);
+  if (!q || !key) return fail(h, FP_ERR_OUT_OF_MEMORY, "score workspace");
+  cudaError_t e = cudaMemcpyAsync(q, h_codes, sizeof(int32_t) * FP_GNN_NPARAMS, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "network codes");
+  if (d_scores) cudaMemsetAsync(d_scores, 0, sizeof(int32_t) * n, h->stream);
+  if (d_features) cudaMemsetAsync(d_features, 0, (size_t)8 * n, h->stream);
+  std::vector<int32_t> hl;
+  int32_t* dl = nullptr;
+  int32_t mmax = 0;
+  FP_TRY(leaf_list(h, hl, &dl, &mmax));
+  FP_TRY(launch_gnn_score(h, dl, (int32_t)hl.size(), q, key, d_scores, d_features));
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  for (void* p : {(void*)q, (void*)key, (void*)dl}) dev_free(h, p);
+  if (st & ST_TIMEOUT) return fail(h, FP_ERR_TIMEOUT, "tensor-core wait ran out");
   return FP_OK;
 }
 

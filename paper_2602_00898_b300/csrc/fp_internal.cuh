@@ -21,7 +21,8 @@ enum : int32_t {
   ST_NOT_SYMMETRIC = 1 << 2,   // CSR pattern not symmetric
   ST_POOL_OVERFLOW = 1 << 3,   // a device bump pool ran out (host retries bigger)
   ST_NODE_TOO_BIG = 1 << 4,    // a tree node beyond the ordering kernel's limit
-  ST_QUOTIENT_TOO_BIG = 1 << 5 // a patch with more cross edges than the sort capacity
+  ST_QUOTIENT_TOO_BIG = 1 << 5, // a patch with more cross edges than the sort capacity
+  ST_TIMEOUT = 1 << 6           // a bounded device wait ran out
 };
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output for generator state s
@@ -34,6 +35,15 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_state(uint64_t s) {
 }
 
 struct Workspace;   // per-handle device scratch (fp_api.cu)
+
+// a10 priority network: packed parameter layout (codes or floats)
+// w1s[32][6] w1n[32][6] b1[32] w2s[32][32] w2n[32][32] b2[32] w3[32] c
+constexpr int GNN_FIN = 6;
+constexpr int GNN_HID = 32;
+constexpr int GNN_LEAF_MAX = 512;
+constexpr int P_W1S = 0, P_W1N = 192, P_B1 = 384, P_W2S = 416, P_W2N = 1440, P_B2 = 2464, P_W3 = 2496,
+              P_C = 2528, P_COUNT = 2529;
+static_assert(P_COUNT == FP_GNN_NPARAMS, "parameter layout");
 
 }  // namespace fp
 
@@ -66,6 +76,12 @@ struct fp_handle {
   int32_t* h_status = nullptr;    // pinned mirror
   void* scratch = nullptr;        // generic scratch block
   size_t scratch_bytes = 0;
+
+  // a10 learned priorities
+  int32_t* qnet = nullptr;        // device codes [FP_GNN_NPARAMS], or null (plain)
+  int32_t* scores = nullptr;      // optional per-position score output of the learned pass
+  int32_t learned_leaves = 0, learned_kept = 0;
+  int64_t fill_plain = 0, fill_chosen = 0;
 
   std::string err;
   int64_t launches = 0;
@@ -154,6 +170,15 @@ fp_status run_nested_dissection(fp_handle* h);
 fp_status run_local_order(fp_handle* h);
 // a7: symbolic (vertex level) into parent/colcount [n]; nnz/flops sums.
 fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops);
+// a10 (k_gnn.cu, k_md.cu, k_symbolic.cu)
+fp_status run_learned(fp_handle* h);
+fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax);
+fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, const int32_t* d_q, uint32_t* d_key,
+                           int32_t* d_score, uint8_t* d_x);
+fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count, int32_t mmax, int32_t* vlist,
+                            int32_t* loc, const uint32_t* key, int32_t* perm_out);
+fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm, const int32_t* d_nodes,
+                        int32_t count, int64_t* d_fill);
 // a8: DOF expansion of perm/iperm/parent/colcount (b > 1).
 void launch_dof_expand_perm(fp_handle* h, const int32_t* perm, int32_t* perm_d, int32_t* iperm_d);
 void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32_t* colcount, int32_t* parent_d,

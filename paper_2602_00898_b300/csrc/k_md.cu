@@ -129,6 +129,7 @@ struct MdArgs {
   const int64_t* gsort_off;   // global kernel: per launched node, int offset into gsort
   int64_t slice_bytes;        // leaf kernel: shared bytes per warp
   int32_t* overflow;          // sparse kernel: per launched node flag; global kernel: only flagged nodes
+  const uint32_t* key;        // leaf kernel: per-vertex tie-break key (NULL: ties by id alone)
 };
 
 template <int NBK>
@@ -233,14 +234,22 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
     B.bits = (uint32_t*)(nb + ((m + 1) & ~1));
     B.sum = B.bits + (size_t)NBK_LEAF * W;
     B.cnt = (int32_t*)(B.sum + (size_t)NBK_LEAF * B.SW);
-    // sort the node's vertices by original id (buffer overlaps R)
-    int32_t* sb = (int32_t*)mine;
+    // sort the node's vertices by (key, original id) (buffer overlaps R): the
+    // local index order is the tie-break order of the arg-min
+    unsigned long long* sb = (unsigned long long*)mine;
     const int NS = pow2_at_least(m, 32);
-    for (int i = lane; i < NS; i += 32) sb[i] = i < m ? verts[i] : INT_MAX;
+    for (int i = lane; i < NS; i += 32) {
+      unsigned long long e = ~0ull;
+      if (i < m) {
+        const int32_t v = verts[i];
+        e = ((unsigned long long)(a.key ? a.key[v] : 0u) << 32) | (uint32_t)v;
+      }
+      sb[i] = e;
+    }
     __syncwarp();
     bitonic_sort<false>(sb, NS, lane, 32);
     for (int i = lane; i < m; i += 32) {
-      const int32_t v = sb[i];
+      const int32_t v = (int32_t)(uint32_t)sb[i];
       verts[i] = v;
       a.loc[v] = i;
     }
@@ -602,7 +611,7 @@ __global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t
 size_t leaf_slice(int m) {
   const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1);
   const size_t need = W * S * 4 + 32 * 4 + 32 * 2 + 2 * m2 * 2 + bucket_words(NBK_LEAF, m) * 4;
-  const size_t sortb = (size_t)pow2_host(m) * 4;
+  const size_t sortb = (size_t)pow2_host(m) * 8;
   return ((need > sortb ? need : sortb) + 15) & ~(size_t)15;
 }
 
@@ -680,7 +689,7 @@ fp_status run_local_order(fp_handle* h) {
   fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 1);
   const int32_t* dnodes = (const int32_t*)dup;
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
-              nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr};
+              nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr};
   // separators on the auxiliary stream; leaves on the handle's stream in CTAs
   // that fill whole SMs, leaving `reserved` SMs for the separator CTAs
   AuxStream* ax = aux_stream(h->device);
@@ -753,6 +762,29 @@ fp_status run_local_order(fp_handle* h) {
   for (void* p : {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup,
                   (void*)grows, (void*)gs, (void*)ovf})
     dev_free(h, p);
+  return FP_OK;
+}
+
+fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count, int32_t mmax, int32_t* vlist,
+                            int32_t* loc, const uint32_t* key, int32_t* perm_out) {
+  if (count == 0) return FP_OK;
+  if (mmax > MD_LEAF) return fail(h, FP_ERR_UNSUPPORTED, "keyed ordering of a node above 512 vertices");
+  MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->node_begin, vlist, loc, perm_out,
+           d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key};
+  const size_t slice = leaf_slice(mmax);
+  int nw = (int)(220 * 1024 / slice);
+  nw = nw < 1 ? 1 : (nw > MD_THREADS / 32 ? MD_THREADS / 32 : nw);
+  size_t sm = slice * nw;
+  if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
+  a.slice_bytes = (int64_t)slice;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  int64_t grid = ((int64_t)count + nw - 1) / nw;
+  if (grid > sms) grid = sms;
+  allow_max_dynamic_smem(k_md_leaf);
+  ProfScope ps(FP_PROF_LEARNED, h->stream);
+  FP_LAUNCH(h, k_md_leaf, (int)grid, 32 * nw, sm, a);
+  FP_CHECK_LAUNCH(h, "keyed minimum degree");
   return FP_OK;
 }
 

@@ -75,6 +75,9 @@ struct SymArgs {
   int32_t* big_list;               // nodes of this level deferred to the block kernel
   int32_t* big_count;
   int32_t* status;
+  const int32_t* in_list;          // explicit node list (else the level t0 .. t0+T-1)
+  int32_t in_count;
+  int64_t* node_fill;              // fill mode: per node, the sum of its columns' counts; no exports
 };
 
 __device__ __forceinline__ int64_t r4(int64_t x) { return (x + 3) & ~3ll; }
@@ -262,7 +265,9 @@ __device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t
       continue;
     }
     if (!inside) {
-      if constexpr (NCH > 0) {
+      if (a.node_fill) {
+        // fill mode: the structure goes nowhere
+      } else if constexpr (NCH > 0) {
         export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t {
           uint32_t s = 0u;
 #pragma unroll
@@ -398,7 +403,7 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
       const int32_t pf = upos[m + umin];
       if (lane == 0) a.parent[b + m - 1] = pf;
       const int32_t Wa = (nab + 31) >> 5;
-      export_element(a, upos + m, Wa, (uint32_t)run, pf, [&](int w) -> uint32_t {
+      if (!a.node_fill) export_element(a, upos + m, Wa, (uint32_t)run, pf, [&](int w) -> uint32_t {
         const int32_t u = w * 32;
         uint32_t s = 0u;
         for (int k = 0; k < 32; ++k)
@@ -423,15 +428,16 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
   __shared__ uint32_t* s_rows;
   __shared__ int32_t* s_upos;
   __shared__ int32_t* s_tail;
-  __shared__ int32_t red[40];
+  __shared__ __align__(8) int32_t red[80];
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   unsigned long long nnz = 0, fl = 0;
-  const int32_t count = from_list ? *a.big_count : a.T;
+  const int32_t count = from_list ? *a.big_count : (a.in_list ? a.in_count : a.T);
 
   for (int32_t q = blockIdx.x; q < count; q += gridDim.x) {
-    const int32_t t = from_list ? a.big_list[q] : a.t0 + q;
+    const int32_t t = from_list ? a.big_list[q] : (a.in_list ? a.in_list[q] : a.t0 + q);
     const int32_t m = a.node_size[t];
     if (m == 0) continue;
+    const unsigned long long nnz0 = nnz;
     const int32_t b = a.node_begin[t];
     const int32_t end = b + m;
     if (tid < 32) {
@@ -612,6 +618,10 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     // 4. dense tail
     if (s_is < m) dense_tail(a, rows, upos, m, U, W, b, s_is, s_tail, red, nnz, fl);
     __syncthreads();
+    if (a.node_fill) {
+      const unsigned long long f = block_sum(nnz - nnz0, (unsigned long long*)red);
+      if (tid == 0) a.node_fill[t] = (int64_t)f;
+    }
   }
   nnz = warp_sum(nnz);
   fl = warp_sum(fl);
@@ -651,7 +661,7 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
       const int32_t t0 = (1 << d) - 1, T = 1 << d;
       SymArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_of, h->node_begin, h->node_size, t0, T,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
-                 ctr + 4, big + t0, big + nn + d, h->d_status};
+                 ctr + 4, big + t0, big + nn + d, h->d_status, nullptr, 0, nullptr};
       ProfScope ps(FP_PROF_SYMBOLIC, h->stream);
       FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr + 4, 0ull, (int64_t)1);
       if (T <= NUM_SMS_B300) {
@@ -684,6 +694,50 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     return FP_OK;
   }
   return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic pools exhausted");
+}
+
+}  // namespace fp
+
+namespace fp {
+
+fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm, const int32_t* d_nodes,
+                        int32_t count, int64_t* d_fill) {
+  if (count == 0) return FP_OK;
+  const int32_t n = h->n;
+  const int64_t nn = h->nnodes;
+  if (h->D + 1 > SYM_MAX_ANC) return fail(h, FP_ERR_UNSUPPORTED, "tree deeper than 31 levels");
+  int64_t pool_words = 4 * (int64_t)n + (1 << 22);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int32_t* head = (int32_t*)dev_alloc(h, sizeof(int32_t) * nn);
+    int32_t* big = (int32_t*)dev_alloc(h, sizeof(int32_t) * ((int64_t)count + 64));
+    int32_t* scr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 2 * (int64_t)(n > 0 ? n : 1));
+    uint32_t* pool = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * pool_words);
+    unsigned long long* ctr = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 8);
+    if (!head || !big || !scr || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "leaf fill workspace");
+    fill_i32(h, head, -1, nn);
+    fill_i32(h, big + count, 0, 64);
+    FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
+    allow_max_dynamic_smem(k_symbolic_nodes);
+    // leaves export nothing and receive nothing: no element lists are needed
+    SymArgs sa{h->rowptr, h->col, perm, iperm, h->node_of, h->node_begin, h->node_size, 0, 0, scr, scr + n, ctr,
+               head, nullptr, nullptr, 0, 0, ctr + 2, pool, pool_words, ctr + 4, big, big + count, h->d_status,
+               d_nodes, count, d_fill};
+    FP_LAUNCH(h, k_symbolic_nodes, count, 32, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+    sa.in_list = nullptr;
+    FP_LAUNCH(h, k_symbolic_nodes, NUM_SMS_B300, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 1, 0);
+    FP_CHECK_LAUNCH(h, "leaf fill");
+    int32_t st = 0;
+    FP_TRY(sync_status(h, &st));
+    for (void* p : {(void*)head, (void*)big, (void*)scr, (void*)pool, (void*)ctr}) dev_free(h, p);
+    if (st & ST_POOL_OVERFLOW) {
+      int32_t zero = 0;
+      cudaMemcpyAsync(h->d_status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+      pool_words *= 4;
+      continue;
+    }
+    return FP_OK;
+  }
+  return fail(h, FP_ERR_OUT_OF_MEMORY, "leaf fill pools exhausted");
 }
 
 }  // namespace fp
