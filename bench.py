@@ -137,11 +137,16 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_step(mesh, cap, dof):
+def oracle_step(mesh, cap, dof, codes=None):
     import oracle as O
     g = O.graph_from_faces(mesh.faces, mesh.n)
     o = O.order(g, cap, seed=0)
-    s = O.symbolic(g, o.perm)
+    perm = o.perm
+    if codes is not None:
+        import paper_2602_00898_b300 as fp
+        from oracle import gnn as G
+        perm = G.order_learned(g, o, G.QParams.from_dict(fp.unpack_params(codes)), cap).perm
+    s = O.symbolic(g, perm)
     if dof > 1:
         O.dof_expand(dof, o.perm, s.parent, s.colcount)
     return s
@@ -340,10 +345,14 @@ def run_ours(args):
 
 def run_batch(args):
     """256 meshes (n log-uniform in [2k, 200k], grid / icosphere / flipped torus),
-    autotuned caps, one fp_batch_order per step; metric meshes/s."""
+    autotuned caps, one fp_batch_order per step; metric meshes/s.
+    batch256_learned: the same mix plus one 2048x2048 flipped torus (4.2M
+    vertices), ordered with the trained leaf-priority network
+    (fp_batch_order_learned); nnz(L) is reported against the plain batch."""
     import torch
     import paper_2602_00898_b300 as fp
     import meshgen
+    learned = args.workload == "batch256_learned"
 
     ws, rank, lrank = dist_env()
     if ws > 1:
@@ -352,14 +361,27 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
     dev = torch.device("cuda", torch.cuda.current_device())
     meshes = meshgen.mesh_mix(256, seed=rank)
+    codes = None
+    if learned:
+        from paper_2602_00898_b300.train_priorities import load_codes
+        codes = load_codes()
+        meshes.append(meshgen.shuffle(meshgen.torus(2048, 2048, 0.3, 4096 + rank), 4096 + rank))
     nverts = sum(m.n for m in meshes)
     faces = [torch.from_numpy(m.faces).to(dev) for m in meshes]
     items = fp.make_batch(faces, [m.n for m in meshes])
     opts = fp.fp_default_options()
     caps = fp.fp_batch_autotune(items, opts)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
+
+    def order_all():
+        return fp.fp_batch_order_learned(items, codes, opts) if learned else fp.fp_batch_order(items, opts)
+
+    plain_nnz = None
+    if learned:
         assert fp.fp_batch_order(items, opts) == 0
+        plain_nnz = sum(int(it.nnzL) for it in items)
+    for _ in range(args.warmup):
+        assert order_all() == 0
     torch.cuda.synchronize()
     # no stage profiling here: its event records would serialise the workers
     clocks = Clocks(lrank)
@@ -371,7 +393,7 @@ def run_batch(args):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        st = fp.fp_batch_order(items, opts)
+        st = order_all()
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t)
         assert st == 0
@@ -394,7 +416,7 @@ def run_batch(args):
         for d, hsrc in zip(faces, hfaces):
             d.copy_(hsrc, non_blocking=True)
         torch.cuda.synchronize()
-        assert fp.fp_batch_order(items, opts) == 0
+        assert order_all() == 0
         for (f, outs), ho in zip(items.tensors, houts):
             for o, h in zip(outs, ho):
                 h.copy_(o[:h.numel()], non_blocking=True)
@@ -409,9 +431,10 @@ def run_batch(args):
         "metric": "batched meshes/s at 1 GPU", "value": ws * len(meshes) / sec, "unit": "meshes/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "batch256", "meshes": len(meshes), "vertices": nverts, "caps_by_size_class": caps,
-                   "workers": 8, "l2": "flushed between steps (256 MB write)",
-                   "step": "fp_batch_order over all meshes (create+permute+symbolic each)"},
+        "config": {"workload": args.workload, "meshes": len(meshes), "vertices": nverts,
+                   "caps_by_size_class": caps, "workers": 8, "l2": "flushed between steps (256 MB write)",
+                   "step": ("fp_batch_order_learned" if learned else "fp_batch_order")
+                           + " over all meshes (create+permute+symbolic each)"},
         "mverts_per_s": ws * nverts / sec / 1e6, "nnzL_total": nnz,
         "clocks": clk,
         "e2e": {"value": len(meshes) / statistics.median(e2e), "unit": "meshes/s",
@@ -419,16 +442,24 @@ def run_batch(args):
                 "d2h_bytes_per_step": int(sum(16 * m.n for m in meshes))},
         "gpu_launches": launches,
     }
+    if learned:
+        line["learned"] = {"nnzL_plain_total": plain_nnz, "nnzL_learned_total": nnz,
+                           "nnzL_ratio": nnz / plain_nnz,
+                           "leaves": sum(int(it.learned_leaves) for it in items),
+                           "leaves_learned_kept": sum(int(it.learned_kept) for it in items),
+                           "network": "paper_2602_00898_b300/priority_net.json (trained on the GPU)"}
     if not args.no_cpu_baseline:
-        idx = list(range(0, len(meshes), 32))
+        idx = list(range(0, 256, 32))
         sample = [meshes[i] for i in idx]
         t0 = time.perf_counter()
         for i in idx:
-            oracle_step(meshes[i], items[i].chosen_cap, 1)
+            oracle_step(meshes[i], items[i].chosen_cap, 1, codes)
         per = (time.perf_counter() - t0) / len(sample)
         line["cpu_baseline"] = {"value": 1.0 / per, "unit": "meshes/s", "cores": 1, "kind": "oracle",
-                                "sample": f"every 32nd mesh of the batch ({len(sample)} meshes, "
-                                          f"{sum(m.n for m in sample)} vertices), single-threaded oracle, "
+                                "sample": f"every 32nd mesh of the 256-mesh mix ({len(sample)} meshes, "
+                                          f"{sum(m.n for m in sample)} vertices"
+                                          + (", learned form; the 4.2M-vertex torus is not sampled" if learned
+                                             else "") + f"), single-threaded oracle, "
                                           f"1 of {os.cpu_count()} host cores"}
     print(json.dumps(line), flush=True)
     if ws > 1:
@@ -441,12 +472,12 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256"], default="icosphere7")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256", "batch256_learned"], default="icosphere7")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.workload == "batch256" and args.impl == "ours":
+    if args.workload in ("batch256", "batch256_learned") and args.impl == "ours":
         run_batch(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -179,9 +179,24 @@ typedef struct {
   int32_t chosen_cap;       /* out */
   int32_t status;           /* out: fp_status of this item */
   int64_t launches;         /* out: kernel launches issued for this item */
+  int32_t learned_leaves;   /* out (fp_batch_order_learned): leaves considered */
+  int32_t learned_kept;     /* out: leaves whose learned order was kept */
+  int64_t fill_plain;       /* out: summed leaf fills under plain minimum degree */
+  int64_t fill_chosen;      /* out: summed leaf fills of the chosen orders */
 } fp_batch_item;
 
 fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers);
+
+/*
+ * fp_batch_order with learned priorities: every mesh gets the network h_codes
+ * (FP_GNN_NPARAMS codes, see fp_set_priority_net) attached before its
+ * fp_permute, so each leaf keeps the lower-fill of its learned and plain
+ * orders; the per-item learned_* and fill_* fields report the choices.
+ * h_codes NULL is fp_batch_order. Errors as fp_batch_order, plus
+ * FP_ERR_INVALID_ARG for a code out of range.
+ */
+fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers,
+                                 const int32_t* h_codes);
 
 /*
  * Autotuner for fp_batch_order: for every size class of the items (vertex

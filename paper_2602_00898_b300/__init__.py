@@ -38,7 +38,8 @@ class fp_batch_item(ctypes.Structure):
                 ("patch_cap", ctypes.c_int32), ("d_perm", ctypes.c_void_p), ("d_iperm", ctypes.c_void_p),
                 ("d_parent", ctypes.c_void_p), ("d_colcount", ctypes.c_void_p), ("nnzL", ctypes.c_int64),
                 ("flops", ctypes.c_int64), ("chosen_cap", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("learned_leaves", ctypes.c_int32), ("learned_kept", ctypes.c_int32),
+                ("fill_plain", ctypes.c_int64), ("fill_chosen", ctypes.c_int64)]
 
 
 _lib = None
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "fp_profile_reset": (None, []),
             "fp_batch_order": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32]),
             "fp_batch_autotune": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, P32]),
+            "fp_batch_order_learned": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32, P32]),
             "fp_graph_from_faces_static": (i32, [vp, i64, i32, vp, vp, i64, P64, vp]),
             "fp_set_priority_net": (i32, [vp, P32]),
             "fp_learned_stats": (i32, [vp, P32, P32, P64, P64]),
@@ -196,6 +198,16 @@ def fp_batch_order(items, opts: fp_options | None = None, n_workers: int = 0) ->
     batch status; each item carries its own status, nnzL, flops, chosen_cap."""
     opts = opts or fp_default_options()
     return int(lib().fp_batch_order(items, len(items), ctypes.byref(opts), n_workers))
+
+
+def fp_batch_order_learned(items, codes, opts: fp_options | None = None, n_workers: int = 0) -> int:
+    """fp_batch_order with the priority network `codes` attached to every mesh."""
+    import numpy as np
+    opts = opts or fp_default_options()
+    c = np.ascontiguousarray(codes, dtype=np.int32)
+    assert c.size == GNN_NPARAMS
+    return int(lib().fp_batch_order_learned(items, len(items), ctypes.byref(opts), n_workers,
+                                            c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
 
 
 def fp_batch_autotune(items, opts: fp_options | None = None) -> list[int]:

@@ -49,11 +49,15 @@ int32_t cap_for(const fp_batch_item& it, const fp_options& base) {
 }
 
 fp_status run_one(const fp_batch_item& it, fp_options o, cudaStream_t s, int32_t* d_perm, int32_t* d_iperm,
-                  int32_t* d_parent, int32_t* d_colcount, int64_t* nnz, int64_t* fl, int64_t* launches) {
+                  int32_t* d_parent, int32_t* d_colcount, int64_t* nnz, int64_t* fl, int64_t* launches,
+                  const int32_t* codes = nullptr, fp_batch_item* stats = nullptr) {
   fp_handle* h = nullptr;
   fp_status st = fp_create_from_faces(it.d_faces, it.n_faces, it.n_vertices, &o, s, &h);
+  if (st == FP_OK && codes) st = fp_set_priority_net(h, codes);
   if (st == FP_OK) st = fp_permute(h, d_perm, d_iperm);
   if (st == FP_OK) st = fp_symbolic(h, d_parent, d_colcount, nnz, fl);
+  if (st == FP_OK && stats)
+    fp_learned_stats(h, &stats->learned_leaves, &stats->learned_kept, &stats->fill_plain, &stats->fill_chosen);
   if (launches) *launches = fp_launch_count(h);
   fp_destroy(h);
   return st;
@@ -65,6 +69,11 @@ fp_status run_one(const fp_batch_item& it, fp_options o, cudaStream_t s, int32_t
 using namespace fp;
 
 extern "C" fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers) {
+  return fp_batch_order_learned(items, count, opts, n_workers, nullptr);
+}
+
+extern "C" fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_options* opts,
+                                            int32_t n_workers, const int32_t* h_codes) {
   if (count < 0 || (count > 0 && !items) || !opts || n_workers < 0 || n_workers > 64)
     return fail(nullptr, FP_ERR_INVALID_ARG, "bad batch arguments");
   if (count == 0) return FP_OK;
@@ -93,8 +102,10 @@ extern "C" fp_status fp_batch_order(fp_batch_item* items, int32_t count, const f
       it.chosen_cap = o.patch_cap;
       it.nnzL = it.flops = 0;
       it.launches = 0;
+      it.learned_leaves = it.learned_kept = 0;
+      it.fill_plain = it.fill_chosen = 0;
       it.status = run_one(it, o, s, it.d_perm, it.d_iperm, it.d_parent, it.d_colcount, &it.nnzL, &it.flops,
-                          &it.launches);
+                          &it.launches, h_codes, &it);
     }
   };
   std::vector<std::thread> pool;

@@ -85,3 +85,31 @@ def test_batch_dof3():
     assert st == 0
     for m, it, (_, outs) in zip(meshes, items, items.tensors):
         _check_item(m, it, outs, dof=3)
+
+
+def test_batch_learned_matches_oracle():
+    """fp_batch_order_learned: every mesh equals the oracle's learned ordering
+    of that mesh alone (same cap, same network), with the same choices."""
+    from oracle import gnn as G
+    meshes = _mix(6, 19, 1500, 12000)
+    caps = [128, 256, 512, 128, 256, 512]
+    d = M.gnn_weights(31)
+    codes = fp.pack_params(d, np.int32)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes], caps)
+    st = fp.fp_batch_order_learned(items, codes, fp.fp_default_options(), n_workers=3)
+    torch.cuda.synchronize()
+    assert st == 0
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        g = O.graph_from_faces(m.faces, m.n)
+        o = O.order(g, it.chosen_cap, seed=0)
+        L = G.order_learned(g, o, G.QParams.from_dict(d), it.chosen_cap)
+        s = O.symbolic(g, L.perm)
+        perm, iperm, parent, colcount = [t.cpu().numpy()[:m.n] for t in outs]
+        np.testing.assert_array_equal(perm, L.perm)
+        np.testing.assert_array_equal(parent, s.parent)
+        np.testing.assert_array_equal(colcount, s.colcount)
+        assert (it.nnzL, it.flops) == (s.nnzL, s.flops)
+        assert it.learned_leaves == len(L.leaves) and it.learned_kept == int(L.kept.sum())
+        assert it.fill_plain == int(L.fill_plain.sum())
+        assert it.fill_chosen == int(np.where(L.kept, L.fill_learned, L.fill_plain).sum())
