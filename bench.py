@@ -79,6 +79,32 @@ def measured_traffic(stage: str, workload: str):
     return float(d["dram_bytes_per_launch"])
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest value of x over the ranks (x itself on one rank)."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, seconds: float) -> float:
+    """Units of all ranks (each rank processes its own, equal-sized shard) per
+    second of the slowest rank."""
+    return ws * units_per_rank / seconds
+
+
+def batch_meshes(rank: int, learned: bool):
+    """The meshes rank `rank` orders in the batch workloads: its own mix (seed =
+    rank), plus the 4.2M-vertex torus for the learned form."""
+    import meshgen
+    meshes = meshgen.mesh_mix(256, seed=rank)
+    if learned:
+        meshes.append(meshgen.shuffle(meshgen.torus(2048, 2048, 0.3, 4096 + rank), 4096 + rank))
+    return meshes
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -259,12 +285,8 @@ def run_ours(args):
     stage_ms = {STAGES[i]: prof_ms[i] / args.steps for i in range(len(STAGES))}
     stage_n = {STAGES[i]: prof_n[i] / args.steps for i in range(len(STAGES))}
 
-    ms = ms_local
-    if ws > 1:
-        t = torch.tensor([ms_local], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n / (ms / 1e3) / 1e6
+    ms = max_over_ranks(ms_local, ws, dev)
+    value = whole_job_rate(n, ws, ms / 1e3) / 1e6
 
     # permutation alone (fp_permute), for the "permutation ms" part of the metric
     h = fp.fp_create_from_faces(faces, n, opts)
@@ -360,12 +382,11 @@ def run_batch(args):
         torch.cuda.set_device(lrank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
     dev = torch.device("cuda", torch.cuda.current_device())
-    meshes = meshgen.mesh_mix(256, seed=rank)
+    meshes = batch_meshes(rank, learned)
     codes = None
     if learned:
         from paper_2602_00898_b300.train_priorities import load_codes
         codes = load_codes()
-        meshes.append(meshgen.shuffle(meshgen.torus(2048, 2048, 0.3, 4096 + rank), 4096 + rank))
     nverts = sum(m.n for m in meshes)
     faces = [torch.from_numpy(m.faces).to(dev) for m in meshes]
     items = fp.make_batch(faces, [m.n for m in meshes])
@@ -401,11 +422,7 @@ def run_batch(args):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    sec = sum(times) / len(times)
-    if ws > 1:
-        tt = torch.tensor([sec], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        sec = float(tt.item())
+    sec = max_over_ranks(sum(times) / len(times), ws, dev)
     # end to end: pinned host faces in, four outputs back, every step
     hfaces = [torch.from_numpy(m.faces).pin_memory() for m in meshes]
     houts = [[torch.empty(m.n, dtype=torch.int32).pin_memory() for _ in range(4)] for m in meshes]
@@ -428,7 +445,7 @@ def run_batch(args):
         return
     nnz = sum(int(it.nnzL) for it in items)
     line = {
-        "metric": "batched meshes/s at 1 GPU", "value": ws * len(meshes) / sec, "unit": "meshes/s",
+        "metric": "batched meshes/s at 1 GPU", "value": whole_job_rate(len(meshes), ws, sec), "unit": "meshes/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "meshes": len(meshes), "vertices": nverts,
