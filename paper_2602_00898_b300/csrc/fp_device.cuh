@@ -141,6 +141,25 @@ __device__ __forceinline__ void bitonic_sort(T* buf, int N, int tid, int nthr) {
     }
 }
 
+// Calls fn(u, aux[u]) for every neighbour u of v in CSR order. The gathers
+// col -> aux are dependent, so B neighbours are loaded per round: two round
+// trips per B neighbours instead of two per neighbour.
+template <int B, class Fn>
+__device__ __forceinline__ void for_row_gather(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                               int32_t v, const int32_t* __restrict__ aux, Fn fn) {
+  const int32_t e1 = rowptr[v + 1];
+  for (int32_t e0 = rowptr[v]; e0 < e1; e0 += B) {
+    int32_t u[B], x[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) u[k] = e0 + k < e1 ? col[e0 + k] : -1;
+#pragma unroll
+    for (int k = 0; k < B; ++k) x[k] = u[k] >= 0 ? aux[u[k]] : 0;
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (u[k] >= 0) fn(u[k], x[k]);
+  }
+}
+
 __device__ __forceinline__ int pow2_at_least(int x, int lo) {
   int p = lo;
   while (p < x) p <<= 1;

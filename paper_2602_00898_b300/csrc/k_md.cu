@@ -259,12 +259,23 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
     for (int i = lane; i < m; i += 32) {
       const int32_t v = verts[i];
       int c = 0;
-      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-        const int32_t u = a.col[e];
-        if (a.node_of[u] != t) continue;
-        const int j = a.loc[u];
-        R[(j >> 5) * S + i] |= 1u << (j & 31);
-        ++c;
+      // eight neighbours per round: their ids, then their node and local index
+      const int32_t e1 = a.rowptr[v + 1];
+      for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += 8) {
+        int32_t u[8], nt[8], j[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
+          j[k] = u[k] >= 0 ? a.loc[u[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (nt[k] == t) {
+            R[(j[k] >> 5) * S + i] |= 1u << (j[k] & 31);
+            ++c;
+          }
       }
       deg[i] = (uint16_t)c;
     }

@@ -29,6 +29,7 @@ namespace {
 
 constexpr int QCAP = 4096;          // cross-edge entries of one patch sorted on chip
 constexpr int ND_THREADS = 256;
+constexpr int ND_BATCH = 8;
 constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
 
 inline int grid_for(int64_t n, int threads) {
@@ -73,14 +74,12 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     for (int32_t i = pstart[p] + threadIdx.x; i < pstart[p + 1]; i += blockDim.x) {
-      int32_t v = pverts[i];
-      for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
-        int32_t q = gmap[col[e]];
+      for_row_gather<8>(rowptr, col, pverts[i], gmap, [&](int32_t, int32_t q) {
         if (q != p) {
           int32_t s = atomicAdd(&cnt, 1);
           if (s < QCAP) buf[s] = q;
         }
-      }
+      });
     }
     __syncthreads();
     const int32_t L = cnt;
@@ -135,7 +134,7 @@ struct BisectArgs {
   int32_t* lvl;                // [k]
   int32_t* qa;                 // [k] frontier
   int32_t* qb;                 // [k] frontier
-  int32_t* mark;               // [k] 0 untouched, 2 current component, 1 done
+  int8_t* mark;                // [k] 0 untouched, 2 current component, 1 done
   int32_t* hist;               // [k]
   int32_t* side;               // [k] by patch id
   int32_t* split;              // [T]
@@ -147,7 +146,8 @@ struct BisectArgs {
 // list offset.
 struct BisectView {
   int32_t* L;
-  int32_t *lvl, *qa, *qb, *mark, *hist, *rbeg, *rlen, *adj;
+  int32_t *lvl, *qa, *qb, *hist, *rbeg, *rlen, *adj;
+  int8_t* mark;
 };
 
 // Level-synchronous BFS over the node's local quotient graph from local `src`.
@@ -227,16 +227,19 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
     const bool sm = m <= a.mcap && E <= a.ecap;
     BisectView v;
     if (sm) {
+      // shared layout: lvl, qa, qb, hist (row lengths), rbeg [mcap+1], adj
+      // [ecap] as int32, then mark [mcap] as int8; the patch ids stay in
+      // global memory (read only to write the sides)
       int32_t* q = bsm;
-      v.L = q; q += a.mcap;
+      v.L = Lg;
       v.lvl = q; q += a.mcap;
       v.qa = q; q += a.mcap;
       v.qb = q; q += a.mcap;
-      v.mark = q; q += a.mcap;
       v.hist = q; q += a.mcap;
       v.rbeg = q; q += a.mcap + 1;
       v.rlen = a.ldeg + base;        // read once below into the compact rows
       v.adj = q;
+      v.mark = (int8_t*)(q + a.ecap);
       // compact CSR in shared memory
       int32_t carry = 0;
       for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
@@ -251,7 +254,6 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
         const int32_t e0 = a.lbeg[base + i], c = a.ldeg[base + i], o = v.rbeg[i];
         for (int32_t j = 0; j < c; ++j) v.adj[o + j] = a.ladj[e0 + j];
-        v.L[i] = Lg[i];
         v.hist[i] = a.ldeg[base + i];   // row lengths, kept in shared memory
       }
       v.rlen = v.hist;
@@ -387,9 +389,21 @@ __global__ void k_nd_superset(LevelArgs a) {
     if (!a.split[t - a.t0]) { a.final_[v] = 1; continue; }
     const int32_t sv = a.side[a.gmap[v]];
     int32_t c = 0;
-    for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-      const int32_t u = a.col[e];
-      c += (a.node_of[u] == t && a.side[a.gmap[u]] != sv);
+    // neighbours in batches of ND_BATCH: col, then node and patch, then side
+    const int32_t e1 = a.rowptr[v + 1];
+    for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += ND_BATCH) {
+      int32_t u[ND_BATCH], nt[ND_BATCH], sd[ND_BATCH];
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) {
+        nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
+        sd[k] = u[k] >= 0 ? a.gmap[u[k]] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) sd[k] = nt[k] == t ? a.side[sd[k]] : sv;
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) c += (nt[k] == t && sd[k] != sv);
     }
     a.cdeg[v] = c;
     a.vstate[v] = c ? VS_UND : VS_NONE;
@@ -434,12 +448,33 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
       const int32_t sv = a.side[a.gmap[v]];
       const int32_t cv = a.cdeg[v];
       bool any_in = false, is_min = true;
-      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-        const int32_t u = a.col[e];
-        if (a.node_of[u] != t || a.side[a.gmap[u]] == sv) continue;
-        const int8_t s = *(volatile int8_t*)&a.vstate[u];
-        if (s == VS_IN) { any_in = true; break; }
-        if (s == VS_UND && key_less(a.cdeg[u], u, cv, v)) is_min = false;
+      const int32_t e1 = a.rowptr[v + 1];
+      for (int32_t e0 = a.rowptr[v]; e0 < e1 && !any_in; e0 += ND_BATCH) {
+        int32_t u[ND_BATCH], nt[ND_BATCH], sd[ND_BATCH];
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
+          sd[k] = u[k] >= 0 ? a.gmap[u[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          sd[k] = nt[k] == t ? a.side[sd[k]] : sv;
+          if (nt[k] != t || sd[k] == sv) u[k] = -1;        // not a crossing neighbour
+        }
+        int8_t st[ND_BATCH];
+        int32_t cd[ND_BATCH];
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          st[k] = u[k] >= 0 ? *(volatile int8_t*)&a.vstate[u[k]] : (int8_t)VS_NONE;
+          cd[k] = u[k] >= 0 ? a.cdeg[u[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          if (st[k] == VS_IN) any_in = true;
+          else if (st[k] == VS_UND && key_less(cd[k], u[k], cv, v)) is_min = false;
+        }
       }
       if (any_in) a.vstate[v] = VS_OUT;
       else if (is_min) a.vstate[v] = VS_IN;
@@ -573,14 +608,16 @@ fp_status run_nested_dissection(fp_handle* h) {
     scan_exclusive(h, npcount, npstart, T, tmp);
     fill_i32(h, npfill, 0, T);
     FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
-    // nodes at depth d hold at most ceil(k / 2^d) patches: stage that many in
-    // shared memory (capped at 2048 patches / 16384 adjacency entries)
+    // nodes at depth d hold at most ceil(k / 2^d) patches (left = ceil(|S|/2)):
+    // stage that many in shared memory with 7 adjacency entries per patch
+    // (quotient graphs of meshes have degree ~6), up to what fits in a CTA
+    constexpr int32_t MCAP_MAX = (225 * 1024 - 64) / (4 * 12 + 1);
     int32_t mcap = (int32_t)(((int64_t)k + T - 1) / T);
-    mcap = mcap < 32 ? 32 : (mcap > 2048 ? 2048 : mcap);
-    const int32_t ecap = 8 * mcap;
-    const size_t bsmem = sizeof(int32_t) * (7 * (size_t)mcap + 1 + (size_t)ecap);
+    mcap = mcap < 32 ? 32 : (mcap > MCAP_MAX ? MCAP_MAX : mcap);
+    const int32_t ecap = 7 * mcap;
+    const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + (size_t)mcap;
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
-                  lvl, qa, qb, mark, hist, side, split, mcap, ecap};
+                  lvl, qa, qb, (int8_t*)mark, hist, side, split, mcap, ecap};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
     allow_max_dynamic_smem(k_nd_bisect);
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);

@@ -27,6 +27,7 @@ namespace fp {
 namespace {
 
 constexpr int BFS_THREADS = 256;
+constexpr int BFS_BATCH = 8;
 
 inline int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -50,26 +51,52 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
     if (ncur == 0) break;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
     const unsigned long long dnext = (unsigned long long)(level + 1) << 32;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncur; i += stride) {
-      const int32_t u = __ldcg(&cur[i]);
-      const unsigned long long lab = __ldcg(&key[u]) & 0xffffffffull;
-      const int32_t gu = group ? group[u] : 0;
-      const int32_t e1 = rowptr[u + 1];
-      for (int32_t e = rowptr[u]; e < e1; ++e) {
-        const int32_t v = col[e];
-        if (group && group[v] != gu) continue;
-        const unsigned long long kv = __ldcg(&key[v]);
-        if ((kv >> 32) <= level) continue;                 // settled at an earlier level
-        const unsigned long long old = atomicMin(&key[v], dnext | lab);
-        if (old == KEY_INF) {
-          // first claim: append to the next frontier, one counter update per warp
-          const unsigned act = __activemask();
-          const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
-          int base = 0;
-          if (lane == leader) base = atomicAdd(&ctr[(level + 1) % 3], __popc(act));
-          base = __shfl_sync(act, base, leader);
-          nxt[base + __popc(act & lanemask_lt())] = v;
+    // warp-uniform sweep of the frontier: every lane of a warp runs the same
+    // number of batches, so the claims of a batch are appended with one
+    // scanned atomicAdd per warp
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < ncur; i0 += stride) {
+      const int64_t i = i0 + lane;
+      int32_t u = 0, e = 0, e1 = 0, gu = 0;
+      unsigned long long lab = 0;
+      if (i < ncur) {
+        u = __ldcg(&cur[i]);
+        lab = __ldcg(&key[u]) & 0xffffffffull;
+        gu = group ? group[u] : 0;
+        e = rowptr[u];
+        e1 = rowptr[u + 1];
+      }
+      // up to BFS_BATCH neighbours per round: their column indices, then their
+      // keys, then the claims are issued together (independent round trips)
+      while (__any_sync(0xffffffffu, e < e1)) {
+        int32_t v[BFS_BATCH];
+        unsigned long long old[BFS_BATCH];
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k) v[k] = e + k < e1 ? col[e + k] : -1;
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k)
+          if (v[k] >= 0 && group && group[v[k]] != gu) v[k] = -1;
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k) {
+          old[k] = v[k] >= 0 ? __ldcg(&key[v[k]]) : 0ull;
+          if ((old[k] >> 32) <= level) v[k] = -1;       // settled at an earlier level
         }
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k) old[k] = v[k] >= 0 ? atomicMin(&key[v[k]], dnext | lab) : 0ull;
+        uint32_t claim = 0;
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k)
+          if (old[k] == KEY_INF) claim |= 1u << k;      // first claim: goes to the next frontier
+        const int32_t c = __popc(claim);
+        const int32_t incl = warp_incl_scan_i32(c);
+        const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        int32_t base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&ctr[(level + 1) % 3], tot);
+        base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k)
+          if (claim >> k & 1u) nxt[base++] = v[k];
+        e += BFS_BATCH;
       }
     }
     int32_t* t = cur; cur = nxt; nxt = t;
@@ -255,10 +282,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
     for (int32_t i0 = 0; i0 < m; i0 += LOCAL_THREADS) {
       const int32_t i = i0 + tid;
       int32_t c = 0;
-      if (i < m) {
-        const int32_t v = verts[i];
-        for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) c += a.label[a.col[e]] == p;
-      }
+      if (i < m) for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t, int32_t lu) { c += lu == p; });
       int32_t tot;
       const int32_t ex = block_excl_scan_i32(c, &tot, red);
       if (i < m) lrow[i] = carry + ex;
@@ -267,24 +291,20 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
     if (tid == 0) lrow[m] = carry;
     __syncthreads();
     for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
-      const int32_t v = verts[i];
       int32_t o = lrow[i];
-      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-        const int32_t u = a.col[e];
-        if (a.label[u] != p) continue;
+      for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t u, int32_t lu) {
+        if (lu != p) return;
         const int32_t j = a.loc[u];
         if (small) s_adj[o++] = (uint16_t)j; else a.g_adj[e0 + o++] = j;
-      }
+      });
     }
     // sources
     if (tid == 0) s_nf = 0;
     __syncthreads();
     if (kMode == 0) {
       for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
-        const int32_t v = verts[i];
         bool bnd = false;
-        for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e)
-          if (a.label[a.col[e]] != p) { bnd = true; break; }
+        for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t, int32_t lu) { bnd |= lu != p; });
         if (bnd) { dist[i] = 0u; fa[atomicAdd(&s_nf, 1)] = i; }
       }
     } else if (tid == 0) {
@@ -383,10 +403,13 @@ struct BfsLauncher {
     return FP_OK;
   }
   fp_status bfs(fp_handle* h, unsigned long long* key, const int32_t* group, int32_t* fa, int32_t* fb, int32_t* ctr) {
-    // one CTA per SM: frontiers are small, and the grid barrier between
-    // levels gets cheaper with fewer CTAs
-    int g = grid_for(h->n, BFS_THREADS);
-    if (g > NUM_SMS_B300) g = NUM_SMS_B300;
+    // frontiers peak near n/8 vertices (seeds every ~cap/2 vertices, about 25
+    // levels): one CTA per SM while that fits in one pass, more CTAs (up to
+    // full occupancy) for large meshes, whose frontiers are too big for 148
+    // CTAs to hide the gather latency; the grid barrier is the price of
+    // every extra CTA
+    int g = grid_for(h->n / 8, BFS_THREADS);
+    if (g < NUM_SMS_B300) g = NUM_SMS_B300;
     if (g > maxgrid_bfs) g = maxgrid_bfs;
     const int32_t* rp = h->rowptr;
     const int32_t* cl = h->col;
