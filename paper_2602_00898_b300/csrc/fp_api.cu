@@ -9,6 +9,8 @@
 #include <mutex>
 #include <string>
 
+#include <set>
+
 #include "fp_internal.cuh"
 
 namespace fp {
@@ -139,6 +141,23 @@ AuxStream* aux_stream(int device) {
     }
   }
   return &a;
+}
+
+void allow_max_dynamic_smem_fn(const void* kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({kernel, dev})) return;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  // these kernels live on shared memory: the largest carveout lets as many
+  // CTAs be resident as their shared memory allows
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  done.insert({kernel, dev});
 }
 
 fp_status sync_status(fp_handle* h, int32_t* status_out) {

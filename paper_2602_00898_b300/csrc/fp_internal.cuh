@@ -77,6 +77,13 @@ struct fp_handle {
   void* scratch = nullptr;        // generic scratch block
   size_t scratch_bytes = 0;
 
+  // separators ordered early (during nested dissection, on the auxiliary
+  // stream): the first early_nodes tree nodes, their vertex lists, each
+  // vertex's rank inside its node, and per-node adjacency-overflow flags
+  int32_t early_nodes = 0;
+  int32_t *early_rank = nullptr, *early_list = nullptr, *early_start = nullptr, *early_cnt = nullptr;
+  int32_t *early_fill = nullptr, *early_ovf = nullptr, *early_loc = nullptr, *early_base = nullptr;
+
   // a10 learned priorities
   int32_t* qnet = nullptr;        // device codes [FP_GNN_NPARAMS], or null (plain)
   int32_t* scores = nullptr;      // optional per-position score output of the learned pass
@@ -108,19 +115,15 @@ struct AuxStream {
 AuxStream* aux_stream(int device);
 
 // Raises a kernel's dynamic shared-memory limit to the device maximum minus its
-// static shared memory. Every caller sets the same value, so concurrent host
-// threads launching the same kernel with different sizes cannot race.
+// static shared memory and asks for the largest shared-memory carveout. Every
+// caller sets the same values, so concurrent host threads launching the same
+// kernel with different sizes cannot race. Done once per kernel and device,
+// under a lock (fp_api.cu): setting a function attribute while the kernel runs
+// on another stream can hold the host until it finishes.
+void allow_max_dynamic_smem_fn(const void* kernel);
 template <class K>
 inline void allow_max_dynamic_smem(K kernel) {
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess)
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-  // these kernels live on shared memory: ask for the largest carveout so that
-  // as many CTAs as the shared memory allows are resident
-  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  allow_max_dynamic_smem_fn((const void*)kernel);
 }
 
 // ---- stage profiling (fp_api.cu) -------------------------------------------------
@@ -168,6 +171,12 @@ fp_status run_patching(fp_handle* h);
 fp_status run_nested_dissection(fp_handle* h);
 // a5 + a6: tree layout, local minimum degree, perm/iperm.
 fp_status run_local_order(fp_handle* h);
+// Early separator ordering (k_md.cu): called by the nested dissection once the
+// nodes of depth d are final; orders them on the auxiliary stream while the
+// deeper levels are dissected. run_local_order places the results.
+fp_status early_md_begin(fp_handle* h, int32_t levels);
+fp_status launch_early_md(fp_handle* h, int32_t d);
+void early_md_release(fp_handle* h);
 // a7: symbolic (vertex level) into parent/colcount [n]; nnz/flops sums.
 fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops);
 // a10 (k_gnn.cu, k_md.cu, k_symbolic.cu)

@@ -23,6 +23,8 @@
 // epilogue (bias, ReLU, round-to-nearest-even re-quantisation).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "fp_device.cuh"
 
 namespace fp {
@@ -400,6 +402,8 @@ fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, in
       hl.push_back((int32_t)t);
       *mmax = std::max(*mmax, sz[t]);
     }
+  // largest first: the per-leaf kernels that draw leaves from a queue balance better
+  std::stable_sort(hl.begin(), hl.end(), [&](int32_t x, int32_t y) { return sz[x] > sz[y]; });
   *d_list = (int32_t*)dev_alloc(h, sizeof(int32_t) * (hl.size() + 1));
   if (!*d_list) return fail(h, FP_ERR_OUT_OF_MEMORY, "leaf list");
   if (!hl.empty()) {

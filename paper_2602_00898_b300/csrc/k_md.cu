@@ -27,6 +27,8 @@
 //     memory, a CTA per node.
 // The separator kernels run on a second stream so that their long serial
 // orderings overlap the leaves; the leaf kernel leaves them free SMs.
+#include <algorithm>
+
 #include "fp_device.cuh"
 
 namespace fp {
@@ -130,6 +132,14 @@ struct MdArgs {
   int64_t slice_bytes;        // leaf kernel: shared bytes per warp
   int32_t* overflow;          // sparse kernel: per launched node flag; global kernel: only flagged nodes
   const uint32_t* key;        // leaf kernel: per-vertex tie-break key (NULL: ties by id alone)
+  int32_t* queue;             // leaf kernel: node counter the warps draw from (zeroed before launch)
+  // early mode of the sparse kernel (nodes = NULL): node node_base + block,
+  // size msize[t], rank inside the node written to rank_out[v] instead of
+  // perm, nodes needing more than smem_avail bytes skipped, overflow[t]
+  int32_t node_base;
+  const int32_t* msize;
+  int32_t* rank_out;
+  int64_t smem_avail;
 };
 
 template <int NBK>
@@ -210,13 +220,22 @@ __host__ __device__ __forceinline__ size_t bucket_words(int nbk, int m) {
   return (size_t)nbk * W + (size_t)nbk * SW + nbk;
 }
 
+__host__ __device__ size_t sparse_smem(int m);
+
 // ---- leaf kernel ---------------------------------------------------------------------
 
 __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   unsigned char* mine = smem + (size_t)wid * a.slice_bytes;
-  for (int32_t li = blockIdx.x * nw + wid; li < a.nnodes_launch; li += gridDim.x * nw) {
+  (void)nw;
+  // nodes are listed largest first and each warp takes the next one when it is
+  // done (greedy largest-first balancing of the serial eliminations)
+  for (;;) {
+    int32_t li = 0;
+    if (lane == 0) li = atomicAdd(a.queue, 1);
+    li = __shfl_sync(0xffffffffu, li, 0);
+    if (li >= a.nnodes_launch) break;
     const int32_t t = a.nodes[li];
     const int32_t m = a.node_size[t];
     const int32_t pbeg = a.node_begin[t];
@@ -384,9 +403,11 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
   __shared__ int32_t s_ovf;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int32_t li = blockIdx.x; li < a.nnodes_launch; li += gridDim.x) {
-    const int32_t t = a.nodes[li];
-    const int32_t m = a.node_size[t];
-    const int32_t pbeg = a.node_begin[t];
+    const int32_t t = a.nodes ? a.nodes[li] : a.node_base + li;
+    const int32_t m = a.msize ? a.msize[t] : a.node_size[t];
+    if (a.rank_out && (m == 0 || (int64_t)sparse_smem(m) > a.smem_avail)) continue;   // left to the regular path
+    const int32_t oi = a.nodes ? li : t;                   // index of this node's overflow flag
+    const int32_t pbeg = a.rank_out ? 0 : a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
     const int W = (m + 31) >> 5;
     uint16_t* adj = (uint16_t*)smem;                      // m x SP_CAP local ids (48 B rows)
@@ -424,7 +445,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
     }
     __syncthreads();
     if (s_ovf) {
-      if (tid == 0) a.overflow[li] = 1;
+      if (tid == 0) a.overflow[oi] = 1;
       __syncthreads();
       continue;
     }
@@ -438,7 +459,8 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         const int mine_nb = lane < dp ? (int)adj[(size_t)p * SP_CAP + lane] : -1;
         __syncwarp();
         if (lane == 0) {
-          a.perm[pbeg + step] = verts[p];
+          if (a.rank_out) a.rank_out[verts[p]] = step;
+          else a.perm[pbeg + step] = verts[p];
           bk_remove(B, bucket_of<NBK_SP>(dp), p);
           deg[p] = DEG_DEAD;
         }
@@ -487,7 +509,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         if (u >= 0 && ob != nbk) bk_insert(B, nbk, u);
         __syncwarp();
       }
-      if (ovf && lane == 0) a.overflow[li] = 1;
+      if (ovf && lane == 0) a.overflow[oi] = 1;
     }
     __syncthreads();
   }
@@ -502,8 +524,8 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_global(MdArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int NT = blockDim.x, nw = NT >> 5;
   for (int32_t li = blockIdx.x; li < a.nnodes_launch; li += gridDim.x) {
-    if (a.overflow && !a.overflow[li]) continue;
     const int32_t t = a.nodes[li];
+    if (a.overflow && !a.overflow[a.node_base < 0 ? t : li]) continue;
     const int32_t m = a.node_size[t];
     const int32_t pbeg = a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
@@ -619,6 +641,51 @@ __global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t
   }
 }
 
+// ---- early separator ordering ------------------------------------------------------------
+
+__global__ void k_early_count(const int32_t* __restrict__ node_of, int32_t n, int32_t t0, int32_t T,
+                              int32_t* __restrict__ cnt) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t t = node_of[v];
+    if (t >= t0 && t < t0 + T) atomicAdd(&cnt[t], 1);
+  }
+}
+
+// List offsets of the level's nodes after the lists of earlier levels (*base).
+__global__ void k_early_starts(const int32_t* __restrict__ cnt, int32_t t0, int32_t T, int32_t* base,
+                               int32_t* __restrict__ start, int32_t* __restrict__ fill) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int32_t b = *base;
+    for (int32_t i = 0; i < T; ++i) {
+      start[t0 + i] = b;
+      fill[t0 + i] = 0;
+      b += cnt[t0 + i];
+    }
+    *base = b;
+  }
+}
+
+__global__ void k_early_scatter(const int32_t* __restrict__ node_of, int32_t n, int32_t t0, int32_t T,
+                                const int32_t* __restrict__ start, int32_t* __restrict__ fill,
+                                int32_t* __restrict__ list) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t t = node_of[v];
+    if (t >= t0 && t < t0 + T) list[start[t] + atomicAdd(&fill[t], 1)] = v;
+  }
+}
+
+// Places the early orders: every vertex of an early node that the sparse
+// kernel finished goes to its node's first position plus its rank.
+__global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, int32_t NE,
+                              const int32_t* __restrict__ node_size, const int32_t* __restrict__ node_begin,
+                              const int32_t* __restrict__ rank, const int32_t* __restrict__ ovf,
+                              int32_t* __restrict__ perm, int64_t smem_max) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t t = node_of[v];
+    if (t < NE && (int64_t)sparse_smem(node_size[t]) <= smem_max && !ovf[t]) perm[node_begin[t] + rank[v]] = v;
+  }
+}
+
 size_t leaf_slice(int m) {
   const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1);
   const size_t need = W * S * 4 + 32 * 4 + 32 * 2 + 2 * m2 * 2 + bucket_words(NBK_LEAF, m) * 4;
@@ -626,14 +693,70 @@ size_t leaf_slice(int m) {
   return ((need > sortb ? need : sortb) + 15) & ~(size_t)15;
 }
 
-size_t sparse_smem(int m) {
+__host__ __device__ size_t sparse_smem(int m) {
   const size_t m2 = (size_t)((m + 1) & ~1);
   const size_t need = (size_t)m * SP_CAP * 2 + m2 * 2 + bucket_words(NBK_SP, m) * 4;
-  const size_t sortb = (size_t)pow2_host(m) * 4;
+  size_t p2 = 32;
+  while (p2 < (size_t)m) p2 <<= 1;
+  const size_t sortb = p2 * 4;
   return need > sortb ? need : sortb;
 }
 
 }  // namespace
+
+fp_status early_md_begin(fp_handle* h, int32_t levels) {
+  h->early_nodes = 0;
+  if (levels <= 0 || h->n == 0) return FP_OK;
+  const int32_t NE = (1 << levels) - 1, n = h->n;
+  auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
+  h->early_rank = I(n);
+  h->early_list = I(n);
+  h->early_loc = I(n);
+  h->early_start = I(NE + 1);
+  h->early_cnt = I(NE);
+  h->early_fill = I(NE);
+  h->early_ovf = I(NE);
+  h->early_base = I(1);
+  if (!h->early_rank || !h->early_list || !h->early_loc || !h->early_start || !h->early_cnt || !h->early_fill ||
+      !h->early_ovf || !h->early_base)
+    return fail(h, FP_ERR_OUT_OF_MEMORY, "early ordering workspace");
+  fill_i32(h, h->early_cnt, 0, NE);
+  fill_i32(h, h->early_ovf, 0, NE);
+  fill_i32(h, h->early_base, 0, 1);
+  h->early_nodes = NE;
+  return FP_OK;
+}
+
+fp_status launch_early_md(fp_handle* h, int32_t d) {
+  const int32_t t0 = (1 << d) - 1, T = 1 << d, n = h->n;
+  if (t0 + T > h->early_nodes) return FP_OK;
+  AuxStream* ax = aux_stream(h->device);
+  if (!ax) return fail(h, FP_ERR_CUDA, "auxiliary stream");
+  cudaStream_t s2 = ax->s;
+  cudaEventRecord(ax->fork, h->stream);
+  cudaStreamWaitEvent(s2, ax->fork, 0);
+  const int G = grid_for(n, 256);
+  ProfScope ps(FP_PROF_MD_MID, s2);
+  k_early_count<<<G, 256, 0, s2>>>(h->node_of, n, t0, T, h->early_cnt);
+  k_early_starts<<<1, 32, 0, s2>>>(h->early_cnt, t0, T, h->early_base, h->early_start, h->early_fill);
+  k_early_scatter<<<G, 256, 0, s2>>>(h->node_of, n, t0, T, h->early_start, h->early_fill, h->early_list);
+  MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->early_start, h->early_list, h->early_loc,
+           nullptr, nullptr, T, nullptr, nullptr, nullptr, nullptr, 0, h->early_ovf, nullptr, nullptr,
+           t0, h->early_cnt, h->early_rank, (int64_t)SMEM_MAX};
+  allow_max_dynamic_smem(k_md_sparse);
+  k_md_sparse<<<T, MD_THREADS, SMEM_MAX, s2>>>(a);
+  h->launches += 4;
+  return check_cuda(h, cudaGetLastError(), "early ordering launch");
+}
+
+void early_md_release(fp_handle* h) {
+  for (int32_t** p : {&h->early_rank, &h->early_list, &h->early_loc, &h->early_start, &h->early_cnt, &h->early_fill,
+                      &h->early_ovf, &h->early_base}) {
+    dev_free(h, *p);
+    *p = nullptr;
+  }
+  h->early_nodes = 0;
+}
 
 fp_status run_local_order(fp_handle* h) {
   const int32_t n = h->n;
@@ -660,47 +783,53 @@ fp_status run_local_order(fp_handle* h) {
   FP_TRY(sync_status(h, &st));
   // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
   // only if their adjacency lists overflow.
-  std::vector<int32_t> ls[3];
+  std::vector<int32_t> ls[3], early;
   int mmax[3] = {0, 0, 0};
   for (int64_t t = 0; t < nn; ++t) {
     const int m = hs[t];
     if (m == 0) continue;
     if (m > MD_MAX) return fail(h, FP_ERR_UNSUPPORTED, "a tree node has more than 32768 vertices");
+    if (t < h->early_nodes && sparse_smem(m) <= SMEM_MAX) {
+      early.push_back((int32_t)t);     // ordered during the dissection
+      continue;
+    }
     const int kind = m <= MD_LEAF ? 0 : (sparse_smem(m) <= SMEM_MAX ? 1 : 2);
     ls[kind].push_back((int32_t)t);
     if (m > mmax[kind]) mmax[kind] = m;
   }
+  // the leaf kernel's warps draw nodes largest first
+  std::stable_sort(ls[0].begin(), ls[0].end(), [&](int32_t x, int32_t y) { return hs[x] > hs[y]; });
   // global rows and sort scratch for the sparse (fallback) and global nodes
   std::vector<int64_t> goff, soff;
   int64_t gwords = 0, gsort = 0;
-  for (int kd = 1; kd <= 2; ++kd)
-    for (int32_t t : ls[kd]) {
+  for (const std::vector<int32_t>* L : {&ls[1], &ls[2], &early})
+    for (int32_t t : *L) {
       const int m = hs[t];
       goff.push_back(gwords);
       gwords += (int64_t)m * ((m + 31) / 32);
       soff.push_back(gsort);
       gsort += pow2_host(m);
     }
-  const int64_t nlist = (int64_t)ls[0].size() + ls[1].size() + ls[2].size();
+  const int64_t nlist = (int64_t)ls[0].size() + ls[1].size() + ls[2].size() + early.size();
   const int64_t nsg = (int64_t)goff.size();
   std::vector<int64_t> up((nlist + 1) / 2 + 2 * nsg + 1);
   int32_t* up32 = (int32_t*)up.data();
   int64_t o = 0;
-  for (int kd = 0; kd < 3; ++kd)
-    for (int32_t t : ls[kd]) up32[o++] = t;
+  for (const std::vector<int32_t>* L : {&ls[0], &ls[1], &ls[2], &early})
+    for (int32_t t : *L) up32[o++] = t;
   const int64_t off64 = (nlist + 1) / 2;
   for (int64_t i = 0; i < nsg; ++i) { up[off64 + i] = goff[i]; up[off64 + nsg + i] = soff[i]; }
   int64_t* dup = (int64_t*)dev_alloc(h, sizeof(int64_t) * (up.size() + 1));
   uint32_t* grows = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * (gwords > 0 ? gwords : 1));
   int32_t* gs = I(gsort);
-  int32_t* ovf = I((int64_t)ls[1].size() + 1);
+  int32_t* ovf = I((int64_t)ls[1].size() + 2);        // + the leaf kernel's node queue
   if (!dup || !grows || !gs || !ovf) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
   e = cudaMemcpyAsync(dup, up.data(), sizeof(int64_t) * up.size(), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return check_cuda(h, e, "upload node lists");
-  fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 1);
+  fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 2);
   const int32_t* dnodes = (const int32_t*)dup;
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
-              nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr};
+              nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr, ovf + ls[1].size()};
   // separators on the auxiliary stream; leaves on the handle's stream in CTAs
   // that fill whole SMs, leaving `reserved` SMs for the separator CTAs
   AuxStream* ax = aux_stream(h->device);
@@ -712,7 +841,27 @@ fp_status run_local_order(fp_handle* h) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   const int nbig = (int)(ls[1].size() + ls[2].size());
   const int reserved = nbig < 16 ? nbig : 16;
-  const int64_t lo1 = (int64_t)ls[0].size(), lo2 = lo1 + (int64_t)ls[1].size();
+  const int64_t lo1 = (int64_t)ls[0].size(), lo2 = lo1 + (int64_t)ls[1].size(), lo3 = lo2 + (int64_t)ls[2].size();
+  if (!early.empty()) {
+    // separators ordered during the dissection: redo the ones whose adjacency
+    // lists overflowed with global rows, then place every other one's ranks
+    MdArgs a = base;
+    a.nodes = dnodes + lo3;
+    a.nnodes_launch = (int32_t)early.size();
+    a.nvstart = h->early_start;
+    a.nvlist = h->early_list;
+    a.overflow = h->early_ovf;
+    a.node_base = -1;                     // overflow flags indexed by node
+    a.grow_off = dup + off64 + (int64_t)ls[1].size() + (int64_t)ls[2].size();
+    a.gsort_off = dup + off64 + nsg + (int64_t)ls[1].size() + (int64_t)ls[2].size();
+    const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
+    allow_max_dynamic_smem(k_md_global);
+    ProfScope ps(FP_PROF_MD_LARGE, s2);
+    k_md_global<<<(unsigned)early.size(), MD_THREADS, smg, s2>>>(a);
+    k_early_place<<<G, 256, 0, s2>>>(h->node_of, n, h->early_nodes, h->node_size, h->node_begin, h->early_rank,
+                                     h->early_ovf, h->perm, (int64_t)SMEM_MAX);
+    h->launches += 2;
+  }
   if (!ls[1].empty()) {
     MdArgs a = base;
     a.nodes = dnodes + lo1;
@@ -765,6 +914,7 @@ fp_status run_local_order(fp_handle* h) {
   cudaEventRecord(ax->join, s2);
   cudaStreamWaitEvent(h->stream, ax->join, 0);
   FP_CHECK_LAUNCH(h, "minimum degree");
+  early_md_release(h);
   if (n > 0) {
     ProfScope ps(FP_PROF_PERM, h->stream);
     FP_LAUNCH(h, k_iperm, G, 256, 0, h->perm, n, h->iperm);
@@ -780,8 +930,11 @@ fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count,
                             int32_t* loc, const uint32_t* key, int32_t* perm_out) {
   if (count == 0) return FP_OK;
   if (mmax > MD_LEAF) return fail(h, FP_ERR_UNSUPPORTED, "keyed ordering of a node above 512 vertices");
+  int32_t* queue = (int32_t*)dev_alloc(h, sizeof(int32_t));
+  if (!queue) return fail(h, FP_ERR_OUT_OF_MEMORY, "node queue");
+  fill_i32(h, queue, 0, 1);
   MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->node_begin, vlist, loc, perm_out,
-           d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key};
+           d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key, queue};
   const size_t slice = leaf_slice(mmax);
   int nw = (int)(220 * 1024 / slice);
   nw = nw < 1 ? 1 : (nw > MD_THREADS / 32 ? MD_THREADS / 32 : nw);
@@ -796,6 +949,7 @@ fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count,
   ProfScope ps(FP_PROF_LEARNED, h->stream);
   FP_LAUNCH(h, k_md_leaf, (int)grid, 32 * nw, sm, a);
   FP_CHECK_LAUNCH(h, "keyed minimum degree");
+  dev_free(h, queue);
   return FP_OK;
 }
 

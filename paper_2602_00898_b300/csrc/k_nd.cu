@@ -30,6 +30,12 @@ namespace {
 constexpr int QCAP = 4096;          // cross-edge entries of one patch sorted on chip
 constexpr int ND_THREADS = 256;
 constexpr int ND_BATCH = 8;
+// Tree depths whose separators are ordered early. Measured on B300 (median
+// step): the root alone gives icosphere-7 5.46 -> 5.19 ms and the 1M-vertex
+// torus 14.10 -> 12.42 ms; two levels 5.18 / 13.27 ms, four 5.39 / 14.72 ms
+// (the extra CTAs hold whole SMs while the dissection needs them).
+constexpr int EARLY_LEVELS = 1;
+constexpr int EARLY_CTAS = (1 << EARLY_LEVELS) - 1;  // at most that many early ordering CTAs
 constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
 
 inline int grid_for(int64_t n, int threads) {
@@ -555,6 +561,8 @@ fp_status run_nested_dissection(fp_handle* h) {
   if (n == 0) return FP_OK;
   fill_i32(h, h->node_of, 0, n);
   const int32_t Dsplit = D < ceil_log2(k) ? D : ceil_log2(k);   // deeper nodes hold <= 1 patch
+  // the separators of the top levels are ordered while deeper levels are cut
+  FP_TRY(early_md_begin(h, Dsplit < EARLY_LEVELS ? Dsplit : EARLY_LEVELS));
   if (Dsplit == 0) { FP_CHECK_LAUNCH(h, "nd init"); return FP_OK; }
 
   const int64_t kk = (int64_t)k + 64;
@@ -628,9 +636,12 @@ fp_status run_nested_dissection(fp_handle* h) {
     fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
-      // one CTA per SM: few candidates per level, cheaper grid barriers
+      // at most one CTA per SM (few candidates per level, cheaper grid
+      // barriers), leaving room beside the early separator ordering, whose
+      // CTAs hold most of an SM's shared memory, so that the cooperative grid
+      // is always co-resident
       int g = G < gmis_max ? G : gmis_max;
-      if (g > NUM_SMS_B300) g = NUM_SMS_B300;
+      if (g > NUM_SMS_B300 - 2 * EARLY_CTAS) g = NUM_SMS_B300 - 2 * EARLY_CTAS;
       void* args[] = {(void*)&la};
       cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_nd_mis, g, ND_THREADS, args, 0, h->stream);
       h->launches++;
@@ -640,6 +651,8 @@ fp_status run_nested_dissection(fp_handle* h) {
     FP_LAUNCH(h, k_nd_move, G, 256, 0, la);
     FP_LAUNCH(h, k_nd_patches, GK, 256, 0, la);
     FP_CHECK_LAUNCH(h, "nd level");
+    // the nodes of depth d are final now
+    FP_TRY(launch_early_md(h, d));
   }
   int32_t st = 0;
   FP_TRY(sync_status(h, &st));
