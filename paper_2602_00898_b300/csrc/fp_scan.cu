@@ -1,5 +1,6 @@
 // Device-wide exclusive scan and fills: three launches (tile sums, scan of the
-// tile sums by one CTA, tile-local scan plus offset). 1024 items per tile.
+// tile sums by one CTA, tile-local scan plus offset; 1024 items per tile), or
+// one CTA for arrays of up to 16k items.
 #include "fp_internal.cuh"
 
 namespace fp {
@@ -85,6 +86,32 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int64_t n, const int
   }
 }
 
+// Whole scan in one CTA for short arrays (node and patch counts): chunks of
+// 1024 x 4 items with a carry, out[n] = total.
+__global__ void __launch_bounds__(1024) k_scan_small(const int32_t* __restrict__ in, int64_t n,
+                                                     int32_t* __restrict__ out) {
+  int32_t carry = 0;
+  for (int64_t c = 0; c < n; c += 1024 * SCAN_ITEMS) {
+    const int64_t base = c + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      v[i] = base + i < n ? in[base + i] : 0;
+      s += v[i];
+    }
+    int32_t tot;
+    int32_t ex = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      if (base + i < n) out[base + i] = ex;
+      ex += v[i];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
 __global__ void k_fill(int32_t* p, int32_t v, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -109,6 +136,11 @@ void scan_exclusive(fp_handle* h, const int32_t* in, int32_t* out, int64_t n, in
   int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nt == 0) {
     FP_LAUNCH(h, k_fill, 1, 32, 0, out, 0, 1);
+    return;
+  }
+  if (n <= 4 * 1024 * SCAN_ITEMS) {
+    // short arrays: one launch instead of three
+    FP_LAUNCH(h, k_scan_small, 1, 1024, 0, in, n, out);
     return;
   }
   FP_LAUNCH(h, k_tile_sums, (unsigned)nt, SCAN_THREADS, 0, in, n, tmp);

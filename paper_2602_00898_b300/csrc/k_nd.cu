@@ -60,6 +60,45 @@ __global__ void k_scatter_by(const int32_t* __restrict__ key, int32_t n, int32_t
   }
 }
 
+// The three steps above in one CTA (one launch) when the keys span at most
+// GROUP_SMALL_MAX values: counts in shared memory, their exclusive scan, then
+// the scatter. start gets nk+1 entries; list order within a key is arbitrary.
+constexpr int GROUP_SMALL_MAX = 8192;
+__global__ void __launch_bounds__(1024) k_group_small(const int32_t* __restrict__ key, int32_t n, int32_t koff,
+                                                      int32_t nk, int32_t* __restrict__ start,
+                                                      int32_t* __restrict__ list, int32_t* __restrict__ zero4) {
+  extern __shared__ int32_t gsm[];
+  __shared__ int32_t red[40];
+  int32_t* cnt = gsm;          // [nk]
+  int32_t* pos = gsm + nk;     // [nk]
+  if (zero4 && threadIdx.x < 4) zero4[threadIdx.x] = 0;   // the caller's next counters
+  for (int32_t i = threadIdx.x; i < nk; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int32_t c = key[i];
+    if (c >= 0) atomicAdd(&cnt[c - koff], 1);
+  }
+  __syncthreads();
+  int32_t carry = 0;
+  for (int32_t b = 0; b < nk; b += blockDim.x) {
+    const int32_t i = b + threadIdx.x;
+    const int32_t x = i < nk ? cnt[i] : 0;
+    int32_t tot;
+    const int32_t ex = block_excl_scan_i32(x, &tot, red) + carry;
+    if (i < nk) {
+      start[i] = ex;
+      pos[i] = ex;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) start[nk] = carry;
+  __syncthreads();
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int32_t c = key[i];
+    if (c >= 0) list[atomicAdd(&pos[c - koff], 1)] = i;
+  }
+}
+
 // ---- a3 quotient graph --------------------------------------------------------------
 // One CTA per patch: gather the patch ids across its cross edges, sort them on
 // chip and run-length encode. kWrite = false counts the distinct neighbours;
@@ -608,14 +647,22 @@ fp_status run_nested_dissection(fp_handle* h) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nd_mis, ND_THREADS, 0);
   const int gmis_max = sms * (per > 0 ? per : 1);
 
+  allow_max_dynamic_smem(k_group_small);
   for (int32_t d = 0; d < Dsplit; ++d) {
     const int32_t t0 = (1 << d) - 1, T = 1 << d;
     ProfScope ps_b(FP_PROF_ND_BISECT, h->stream);
-    fill_i32(h, npcount, 0, T);
-    FP_LAUNCH(h, k_count_by, GK, 256, 0, patch_node, k, t0, npcount);
-    scan_exclusive(h, npcount, npstart, T, tmp);
-    fill_i32(h, npfill, 0, T);
-    FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
+    const bool grouped_small = T <= GROUP_SMALL_MAX;
+    if (grouped_small) {
+      // also zeroes the level's candidate and refinement counters
+      FP_LAUNCH(h, k_group_small, 1, 1024, sizeof(int32_t) * 2 * (size_t)T, patch_node, k, t0, T, npstart, nplist,
+                ctr);
+    } else {
+      fill_i32(h, npcount, 0, T);
+      FP_LAUNCH(h, k_count_by, GK, 256, 0, patch_node, k, t0, npcount);
+      scan_exclusive(h, npcount, npstart, T, tmp);
+      fill_i32(h, npfill, 0, T);
+      FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
+    }
     // nodes at depth d hold at most ceil(k / 2^d) patches (left = ceil(|S|/2)):
     // stage that many in shared memory with 7 adjacency entries per patch
     // (quotient graphs of meshes have degree ~6), up to what fits in a CTA
@@ -633,7 +680,7 @@ fp_status run_nested_dissection(fp_handle* h) {
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, ctr,
                  w, q_rowptr, q_col, q_w, patch_node, k};
-    fill_i32(h, ctr, 0, 4);
+    if (!grouped_small) fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
       // at most one CTA per SM (few candidates per level, cheaper grid

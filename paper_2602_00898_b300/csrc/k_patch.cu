@@ -28,6 +28,7 @@ namespace {
 
 constexpr int BFS_THREADS = 256;
 constexpr int BFS_BATCH = 8;
+constexpr int BFS_TAIL = 1024;   // frontiers up to this size run in one CTA
 
 inline int grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -45,17 +46,15 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
   cg::grid_group grid = cg::this_grid();
   int32_t* cur = fa;
   int32_t* nxt = fb;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (uint32_t level = 0;; ++level) {
-    const int32_t ncur = __ldcg(&ctr[level % 3]);
-    if (ncur == 0) break;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
+  const int lane = threadIdx.x & 31;
+  // one level: every frontier vertex claims its unsettled neighbours. The
+  // sweep is warp-uniform (every lane of a warp runs the same number of
+  // batches), so a batch's claims are appended with one scanned atomicAdd per
+  // warp; up to BFS_BATCH neighbours are loaded per round (their ids, then
+  // their keys, then the claims: independent round trips).
+  auto sweep = [&](uint32_t level, int32_t ncur, int64_t first, int64_t stride) {
     const unsigned long long dnext = (unsigned long long)(level + 1) << 32;
-    // warp-uniform sweep of the frontier: every lane of a warp runs the same
-    // number of batches, so the claims of a batch are appended with one
-    // scanned atomicAdd per warp
-    const int lane = threadIdx.x & 31;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; i0 < ncur; i0 += stride) {
+    for (int64_t i0 = first - lane; i0 < ncur; i0 += stride) {
       const int64_t i = i0 + lane;
       int32_t u = 0, e = 0, e1 = 0, gu = 0;
       unsigned long long lab = 0;
@@ -66,8 +65,6 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
         e = rowptr[u];
         e1 = rowptr[u + 1];
       }
-      // up to BFS_BATCH neighbours per round: their column indices, then their
-      // keys, then the claims are issued together (independent round trips)
       while (__any_sync(0xffffffffu, e < e1)) {
         int32_t v[BFS_BATCH];
         unsigned long long old[BFS_BATCH];
@@ -99,8 +96,31 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
         e += BFS_BATCH;
       }
     }
+  };
+  uint32_t level = 0;
+  int32_t nprev = 0;
+  for (;; ++level) {
+    const int32_t ncur = __ldcg(&ctr[level % 3]);
+    if (ncur == 0) return;
+    // the frontier grows from the seeds, peaks and dies out: the shrinking
+    // tail goes to one CTA (the same decision in every CTA)
+    if (ncur <= BFS_TAIL && ncur < nprev) break;
+    nprev = ncur;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
+    sweep(level, ncur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
     int32_t* t = cur; cur = nxt; nxt = t;
     grid.sync();
+  }
+  // small frontiers (the last levels): CTA 0 alone, with CTA barriers instead
+  // of grid barriers
+  if (blockIdx.x != 0) return;
+  for (;; ++level) {
+    const int32_t ncur = __ldcg(&ctr[level % 3]);
+    if (ncur == 0) return;
+    if (threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
+    sweep(level, ncur, threadIdx.x, blockDim.x);
+    int32_t* t = cur; cur = nxt; nxt = t;
+    __syncthreads();
   }
 }
 

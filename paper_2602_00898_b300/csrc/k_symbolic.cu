@@ -651,19 +651,19 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     int32_t* hdr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 3 * cap_hdr);
     int32_t* data = (int32_t*)dev_alloc(h, sizeof(int32_t) * cap_data);
     uint32_t* pool = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * pool_words);
-    unsigned long long* ctr = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 8);
+    // [0..1] sums, [2..3] element counters, [4 + d] the scratch-pool counter of level d
+    unsigned long long* ctr = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (8 + 32));
     if (!head || !big || !hdr || !data || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic workspace");
     fill_i32(h, head, -1, nn);
     fill_i32(h, big + nn, 0, 64);                 // per-level deferred-node counts
-    FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
+    FP_LAUNCH(h, k_fill_u64, 1, 64, 0, ctr, 0ull, (int64_t)(8 + 32));
     allow_max_dynamic_smem(k_symbolic_nodes);
     for (int32_t d = h->D; d >= 0; --d) {
       const int32_t t0 = (1 << d) - 1, T = 1 << d;
       SymArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_of, h->node_begin, h->node_size, t0, T,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
-                 ctr + 4, big + t0, big + nn + d, h->d_status, nullptr, 0, nullptr};
+                 ctr + 4 + d, big + t0, big + nn + d, h->d_status, nullptr, 0, nullptr};
       ProfScope ps(FP_PROF_SYMBOLIC, h->stream);
-      FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr + 4, 0ull, (int64_t)1);
       if (T <= NUM_SMS_B300) {
         // few nodes: one large CTA each
         FP_LAUNCH(h, k_symbolic_nodes, T, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 0, 0);
