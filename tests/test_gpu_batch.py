@@ -113,3 +113,25 @@ def test_batch_learned_matches_oracle():
         assert it.learned_leaves == len(L.leaves) and it.learned_kept == int(L.kept.sum())
         assert it.fill_plain == int(L.fill_plain.sum())
         assert it.fill_chosen == int(np.where(L.kept, L.fill_learned, L.fill_plain).sum())
+
+
+def test_full_batch_256_sampled():
+    """The benchmark's full batch: 256 meshes of 2k-200k vertices with
+    autotuned caps. Every 16th mesh is checked bit for bit against the oracle
+    run alone with the cap the batch chose; every mesh gets the invariants
+    (perm a bijection, iperm its inverse, nnz(L) >= n, a root etree column)."""
+    meshes = M.mesh_mix(256, seed=0)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes])
+    fp.fp_batch_autotune(items, fp.fp_default_options())
+    st = fp.fp_batch_order(items, fp.fp_default_options())
+    torch.cuda.synchronize()
+    assert st == 0
+    for i, (m, it, (_, outs)) in enumerate(zip(meshes, items, items.tensors)):
+        assert it.status == 0 and it.nnzL >= m.n
+        perm, iperm, parent = [t.cpu().numpy()[:m.n] for t in outs[:3]]
+        assert np.array_equal(np.sort(perm), np.arange(m.n))
+        assert np.array_equal(iperm[perm], np.arange(m.n))
+        assert (parent == -1).any() and ((parent == -1) | (parent > np.arange(m.n))).all()
+        if i % 16 == 0:
+            _check_item(m, it, outs)

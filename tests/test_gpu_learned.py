@@ -118,3 +118,45 @@ def test_bad_codes_rejected():
             fp.fp_set_priority_net(h, codes)
     finally:
         fp.fp_destroy(h)
+
+
+def test_learned_full_size_properties():
+    """1M-vertex flipped torus with the GPU-trained network: properties that
+    hold for any network. Every leaf keeps its vertex set and position range,
+    separators do not move, the permutation is a bijection, and nnz(L) is at
+    most the plain method's, lower by exactly the kept leaves' fill gains."""
+    fp = _fp()
+    from paper_2602_00898_b300.train_priorities import load_codes
+    mesh = meshgen.torus1024()
+    faces = torch.from_numpy(mesh.faces).cuda()
+    plain = fp.order_faces(faces, mesh.n, patch_cap=512)
+    h = fp.fp_create_from_faces(faces, mesh.n, fp.fp_default_options(patch_cap=512))
+    try:
+        fp.fp_set_priority_net(h, load_codes())
+        perm = torch.empty(mesh.n, dtype=torch.int32, device="cuda")
+        fp.fp_permute(h, perm)
+        nnz, _ = fp.fp_symbolic(h)
+        leaves, kept, f_plain, f_chosen = fp.fp_learned_stats(h)
+    finally:
+        fp.fp_destroy(h)
+    p_l = perm.cpu().numpy()
+    p_p = plain.perm.cpu().numpy()
+    assert np.array_equal(np.sort(p_l), np.arange(mesh.n))
+    nb = plain.node_begin.cpu().numpy()
+    ns = plain.node_size.cpu().numpy()
+    sub = ns.astype(np.int64).copy()
+    for t in range(ns.size - 1, -1, -1):
+        for c in (2 * t + 1, 2 * t + 2):
+            if c < ns.size:
+                sub[t] += sub[c]
+    is_leaf_pos = np.zeros(mesh.n, bool)
+    nleaves = 0
+    for t in range(ns.size):
+        if 0 < ns[t] <= 512 and sub[t] == ns[t]:
+            nleaves += 1
+            a, b = nb[t], nb[t] + ns[t]
+            is_leaf_pos[a:b] = True
+            assert np.array_equal(np.sort(p_l[a:b]), np.sort(p_p[a:b]))
+    assert leaves == nleaves and kept > 0
+    assert np.array_equal(p_l[~is_leaf_pos], p_p[~is_leaf_pos])
+    assert nnz <= plain.nnzL and plain.nnzL - nnz == f_plain - f_chosen
