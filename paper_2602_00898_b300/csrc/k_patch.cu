@@ -19,6 +19,8 @@
 // patch with the patch's adjacency in shared memory and CTA barriers only.
 #include <cooperative_groups.h>
 
+#include <utility>
+
 #include "fp_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -264,6 +266,9 @@ struct LocalArgs {
   const int32_t* seed_of;
   unsigned long long* best;     // modes 0, 1
   unsigned long long* key;      // mode 2
+  int32_t* next_over;           // mode 2: the halves still above cap (flag by new patch id)
+  int32_t* next_cnt;            // mode 2: how many
+  int32_t cap;
 };
 
 template <int kMode>
@@ -369,11 +374,21 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
     }
     __syncthreads();
     if (kMode == 2) {
+      const int32_t p2 = a.kbase + a.orank[p];
       const unsigned long long r_first = (unsigned long long)(uint32_t)p;
-      const unsigned long long r_second = (unsigned long long)(uint32_t)(a.kbase + a.orank[p]);
+      const unsigned long long r_second = (unsigned long long)(uint32_t)p2;
+      int32_t c2 = 0;
       for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
         const uint32_t d = dist[i];
         a.key[verts[i]] = ((unsigned long long)(d >> 1) << 32) | ((d & 1u) ? r_second : r_first);
+        c2 += (int32_t)(d & 1u);
+      }
+      // sizes of the two halves decide the next round (the patch is connected,
+      // so every vertex is reached from one of the two seeds)
+      c2 = block_sum(c2, red);
+      if (tid == 0) {
+        if (m - c2 > a.cap) { a.next_over[p] = 1; atomicAdd(a.next_cnt, 1); }
+        if (c2 > a.cap) { a.next_over[p2] = 1; atomicAdd(a.next_cnt, 1); }
       }
     } else {
       unsigned long long b = 0ull;
@@ -533,7 +548,7 @@ fp_status run_patching(fp_handle* h) {
     FP_LAUNCH(h, k_patch_scatter, G, 256, 0, group, n, pstart, pdeg, pverts);
   };
   LocalArgs la{0, h->rowptr, h->col, group, pstart, pverts, pedge, g_adj, g_vtx, loc, nullptr, orank, 0,
-               seed_of, best, key};
+               seed_of, best, key, nullptr, nullptr, cap};
   const int GL = NUM_SMS_B300 * 8;
   // R4 Lloyd rounds
   const int GK = grid_for(k, 256);
@@ -554,32 +569,49 @@ fp_status run_patching(fp_handle* h) {
     FP_CHECK_LAUNCH(h, "lloyd");
     FP_TRY(L.bfs(h, key, nullptr, fa, fb, ctr));
   }
-  // R5 cap: split until every patch fits
+  // R5 cap: split until every patch fits. The first round counts the patch
+  // sizes; every split counts its two halves, so a later round rebuilds the
+  // vertex lists only when some half is still above cap.
   int32_t* over = rank;
-  for (int32_t round = 0; round < n; ++round) {
+  int32_t* over_next = flag;
+  int32_t* ocnt = ctr + 5;
+  patch_lists(k);
+  {
+    ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
+    FP_LAUNCH(h, k_oversize_flags, grid_for(k, 256), 256, 0, pcnt, k, cap, over);
+    scan_exclusive(h, over, orank, k, tmp);
+  }
+  cudaMemcpyAsync(hbuf, orank + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  FP_CHECK_LAUNCH(h, "sizes");
+  FP_TRY(sync_status(h, &st));
+  int32_t nover = hbuf[0];
+  for (int32_t round = 0; round < n && nover > 0; ++round) {
     const int GKr = grid_for(k, 256);
-    patch_lists(k);
-    {
-      ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-      FP_LAUNCH(h, k_oversize_flags, GKr, 256, 0, pcnt, k, cap, over);
-      scan_exclusive(h, over, orank, k, tmp);
-    }
-    cudaMemcpyAsync(hbuf, orank + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-    FP_CHECK_LAUNCH(h, "sizes");
-    FP_TRY(sync_status(h, &st));
-    const int32_t nover = hbuf[0];
-    if (nover == 0) break;
     la.k = k;
     la.over = over;
     la.kbase = k;
+    la.next_over = over_next;
+    la.next_cnt = ocnt;
+    fill_i32(h, over_next, 0, (int64_t)k + nover);
+    fill_i32(h, ocnt, 0, 1);
     {
       ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
       FP_LAUNCH(h, k_patch_local<1>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
       FP_LAUNCH(h, k_split_seeds, GKr, 256, 0, best, over, orank, k, seed_of);
       FP_LAUNCH(h, k_patch_local<2>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
     }
+    cudaMemcpyAsync(hbuf, ocnt, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
     FP_CHECK_LAUNCH(h, "split");
+    FP_TRY(sync_status(h, &st));
     k += nover;
+    nover = hbuf[0];
+    if (nover == 0) break;
+    std::swap(over, over_next);
+    {
+      ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
+      scan_exclusive(h, over, orank, k, tmp);
+    }
+    patch_lists(k);
   }
   {
     ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
