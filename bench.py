@@ -70,9 +70,10 @@ def measured_traffic(stage: str, workload: str):
     p = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(stage)
-    if not d or d.get("workload") != workload:
+    found = [e for e in json.load(open(p)).get("entries", []) if e.get("stage") == stage and e.get("workload") == workload]
+    if not found:
         return None
+    d = found[0]
     src = os.path.join(ROOT, d["source"])
     if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != d["source_sha1"]:
         return None
