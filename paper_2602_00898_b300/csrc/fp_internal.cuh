@@ -158,6 +158,10 @@ struct ProfScope {
 int64_t scan_tmp_ints(int64_t n);
 void scan_exclusive(fp_handle* h, const int32_t* in, int32_t* out, int64_t n, int32_t* tmp);
 void fill_i32(fp_handle* h, int32_t* p, int32_t v, int64_t n);
+// Exclusive scans a -> oa and b -> ob (each of n items, out[n] = total), then
+// b is zeroed. One launch for short arrays.
+void scan_exclusive_pair_zero(fp_handle* h, const int32_t* a, int32_t* oa, int32_t* b, int32_t* ob, int64_t n,
+                              int32_t* tmp);
 void iota_i32(fp_handle* h, int32_t* p, int64_t n);
 
 // ---- stages -----------------------------------------------------------------------

@@ -112,6 +112,38 @@ __global__ void __launch_bounds__(1024) k_scan_small(const int32_t* __restrict__
   if (threadIdx.x == 0) out[n] = carry;
 }
 
+// Two short scans in one launch (block 0: a -> oa, block 1: b -> ob), then b
+// is zeroed (so that it can serve as the scatter cursors).
+__global__ void __launch_bounds__(1024) k_scan_pair_small(const int32_t* __restrict__ a, int32_t* __restrict__ oa,
+                                                          int32_t* b, int32_t* __restrict__ ob, int64_t n) {
+  const int32_t* in = blockIdx.x == 0 ? a : b;
+  int32_t* out = blockIdx.x == 0 ? oa : ob;
+  int32_t carry = 0;
+  for (int64_t c = 0; c < n; c += 1024 * SCAN_ITEMS) {
+    const int64_t base = c + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      v[i] = base + i < n ? in[base + i] : 0;
+      s += v[i];
+    }
+    int32_t tot;
+    int32_t ex = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      if (base + i < n) out[base + i] = ex;
+      ex += v[i];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+  if (blockIdx.x == 1) {
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) b[i] = 0;
+  }
+}
+
 __global__ void k_fill(int32_t* p, int32_t v, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -146,6 +178,17 @@ void scan_exclusive(fp_handle* h, const int32_t* in, int32_t* out, int64_t n, in
   FP_LAUNCH(h, k_tile_sums, (unsigned)nt, SCAN_THREADS, 0, in, n, tmp);
   FP_LAUNCH(h, k_scan_sums, 1, 1024, 0, tmp, nt, out + n);
   FP_LAUNCH(h, k_tile_scan, (unsigned)nt, SCAN_THREADS, 0, in, n, tmp, out);
+}
+
+void scan_exclusive_pair_zero(fp_handle* h, const int32_t* a, int32_t* oa, int32_t* b, int32_t* ob, int64_t n,
+                              int32_t* tmp) {
+  if (n > 0 && n <= 4 * 1024 * SCAN_ITEMS) {
+    FP_LAUNCH(h, k_scan_pair_small, 2, 1024, 0, a, oa, b, ob, n);
+    return;
+  }
+  scan_exclusive(h, a, oa, n, tmp);
+  scan_exclusive(h, b, ob, n, tmp);
+  fill_i32(h, b, 0, n);
 }
 
 void fill_i32(fp_handle* h, int32_t* p, int32_t v, int64_t n) {

@@ -563,21 +563,22 @@ __global__ void k_nd_apply(LevelArgs a) {
 
 // LeftRight (Algorithm 2 step 5): the remaining vertices of a split node move to
 // child 2t+1 (left) or 2t+2 (right) with their patch.
-__global__ void k_nd_move(LevelArgs a) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-    if (a.final_[v]) continue;
-    const int32_t t = a.node_of[v];
-    a.node_of[v] = 2 * t + 1 + a.side[a.gmap[v]];
+// The patches follow: a split node's patch moves with its side, others drop out
+// (one launch, threads cover both ranges).
+__global__ void k_nd_move_patches(LevelArgs a) {
+  const int32_t span = a.n > a.k ? a.n : a.k;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < span; i += gridDim.x * blockDim.x) {
+    if (i < a.n && !a.final_[i]) {
+      const int32_t t = a.node_of[i];
+      a.node_of[i] = 2 * t + 1 + a.side[a.gmap[i]];
+    }
+    if (i < a.k) {
+      const int32_t t = a.patch_node[i];
+      if (t >= 0) a.patch_node[i] = (a.split[t - a.t0] && a.w[i] > 0) ? 2 * t + 1 + a.side[i] : -1;
+    }
   }
 }
 
-__global__ void k_nd_patches(LevelArgs a) {
-  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < a.k; p += gridDim.x * blockDim.x) {
-    const int32_t t = a.patch_node[p];
-    if (t < 0) continue;
-    a.patch_node[p] = (a.split[t - a.t0] && a.w[p] > 0) ? 2 * t + 1 + a.side[p] : -1;
-  }
-}
 
 __global__ void k_zero_i8(int8_t* p, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
@@ -695,8 +696,7 @@ fp_status run_nested_dissection(fp_handle* h) {
       if (e != cudaSuccess) return check_cuda(h, e, "mis launch");
     }
     FP_LAUNCH(h, k_nd_apply, G, 256, 0, la);
-    FP_LAUNCH(h, k_nd_move, G, 256, 0, la);
-    FP_LAUNCH(h, k_nd_patches, GK, 256, 0, la);
+    FP_LAUNCH(h, k_nd_move_patches, G > GK ? G : GK, 256, 0, la);
     FP_CHECK_LAUNCH(h, "nd level");
     // the nodes of depth d are final now
     FP_TRY(launch_early_md(h, d));

@@ -161,6 +161,26 @@ __global__ void k_labels_of(const unsigned long long* __restrict__ key, int32_t 
     label[v] = key[v] == KEY_INF ? -1 : (int32_t)(uint32_t)key[v];
 }
 
+// Labels of every vertex (all reached) and, per patch, its vertex count and
+// the sum of its vertices' degrees (counts zeroed by the caller).
+__global__ void k_labels_counts(const unsigned long long* __restrict__ key, const int32_t* __restrict__ rowptr,
+                                int32_t n, int32_t* __restrict__ label, int32_t* __restrict__ pcnt,
+                                int32_t* __restrict__ pdeg) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t p = (int32_t)(uint32_t)key[v];
+    label[v] = p;
+    atomicAdd(&pcnt[p], 1);
+    atomicAdd(&pdeg[p], rowptr[v + 1] - rowptr[v]);
+  }
+}
+
+__global__ void k_zero2(int32_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = 0;
+    b[i] = 0;
+  }
+}
+
 __global__ void k_count_unreached(const unsigned long long* __restrict__ key, int32_t n, int32_t* cnt) {
   int32_t c = 0;
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += key[v] == KEY_INF;
@@ -405,16 +425,6 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
   }
 }
 
-// Vertex lists by patch: counts of vertices and of adjacency entries.
-__global__ void k_patch_counts(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ label, int32_t n,
-                               int32_t* __restrict__ pcnt, int32_t* __restrict__ pdeg) {
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const int32_t p = label[v];
-    atomicAdd(&pcnt[p], 1);
-    atomicAdd(&pdeg[p], rowptr[v + 1] - rowptr[v]);
-  }
-}
-
 __global__ void k_patch_scatter(const int32_t* __restrict__ label, int32_t n, const int32_t* __restrict__ pstart,
                                 int32_t* __restrict__ fill, int32_t* __restrict__ pverts) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
@@ -536,15 +546,13 @@ fp_status run_patching(fp_handle* h) {
   int32_t* orank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
   if (!pcnt || !pdeg || !pstart || !pedge || !pverts || !loc || !g_adj || !g_vtx || !orank)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "patch lists");
+  // vertex lists by patch: labels and counts, their scans (pdeg is cleared to
+  // serve as the scatter cursors), the scatter
   auto patch_lists = [&](int32_t kk) {
     ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-    FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, group);
-    fill_i32(h, pcnt, 0, kk);
-    fill_i32(h, pdeg, 0, kk);
-    FP_LAUNCH(h, k_patch_counts, G, 256, 0, h->rowptr, group, n, pcnt, pdeg);
-    scan_exclusive(h, pcnt, pstart, kk, tmp);
-    scan_exclusive(h, pdeg, pedge, kk, tmp);
-    fill_i32(h, pdeg, 0, kk);
+    FP_LAUNCH(h, k_zero2, grid_for(kk, 256), 256, 0, pcnt, pdeg, (int64_t)kk);
+    FP_LAUNCH(h, k_labels_counts, G, 256, 0, key, h->rowptr, n, group, pcnt, pdeg);
+    scan_exclusive_pair_zero(h, pcnt, pstart, pdeg, pedge, kk, tmp);
     FP_LAUNCH(h, k_patch_scatter, G, 256, 0, group, n, pstart, pdeg, pverts);
   };
   LocalArgs la{0, h->rowptr, h->col, group, pstart, pverts, pedge, g_adj, g_vtx, loc, nullptr, orank, 0,
