@@ -214,7 +214,7 @@ fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, const fp_option
  * library service for callers that cannot allocate device memory when they
  * build the graph (for example a process whose device memory is entirely
  * reserved by another framework's caching allocator, or a latency-critical
- * loop that must stay out of the driver's allocator). It computes exactly the
+ * loop that must stay out of the CUDA allocator). It computes exactly the
  * CSR that fp_create_from_faces + fp_get_graph produce (G = graph of the face
  * list without diagonal, rows sorted and duplicate-free) into caller buffers:
  * d_rowptr [n_vertices+1] and d_col [col_cap]; *h_nnz (may be NULL) receives

@@ -3,7 +3,7 @@
 // Some callers cannot allocate device memory when they need the graph: a
 // process whose device memory is entirely reserved by another framework's
 // caching allocator (a cudaMalloc would fail or fragment it), or a latency-
-// critical loop that must not enter the driver's allocator at all. For them
+// critical loop that must not enter the CUDA allocator at all. For them
 // this entry point builds the same CSR as fp_create_from_faces + fp_get_graph
 // into caller-provided buffers, with all intermediate data in one fixed-size
 // scratch array that lives in the library image itself (a file-scope

@@ -1,6 +1,6 @@
 """fp_graph_from_faces_static: the allocation-free CSR assembly for callers
 that cannot allocate device memory (their device memory is reserved by another
-allocator, or they must stay out of the driver's allocator). It must produce
+allocator, or they must stay out of the CUDA allocator). It must produce
 the same CSR as the allocating path (fp_create_from_faces + fp_get_graph), on
 consecutive calls that reuse the library's one static scratch array.
 
