@@ -9,15 +9,13 @@
 // uses AMD; ties go to the smallest original vertex id, i.e. the smallest local
 // index, local indices being assigned in id order). Each step takes the vertex
 // of minimum (degree, local index), makes its neighbourhood a clique and
-// updates the neighbours' degrees. The arg-min is O(1): alive vertices sit in
-// degree buckets (one bitmap per small degree, one shared overflow bucket); the
-// lowest non-empty bucket is a ballot over the bucket counts and its lowest set
-// bit is the pivot. Only when every remaining degree is in the overflow bucket
-// does a warp scan all degrees. Three kernels by node size:
+// updates the neighbours' degrees. Three kernels by node size:
 //   * leaf (m <= 512, the patch leaves and small separators): the elimination
 //     graph is a bit matrix in shared memory stored word-major (word w of row u
 //     at R[w*S + u], S = m|1 odd so that a row's words fall in distinct banks);
-//     each warp orders its own node and updates one neighbour per lane;
+//     each warp orders its own node. The arg-min reads all degrees (at most
+//     eight 32-bit words a lane) and reduces across the warp; every lane holds
+//     the pivot row's (at most 16) words and updates one neighbour;
 //   * sparse (separators up to ~4300 vertices): separators' elimination graphs
 //     stay very sparse, so each vertex keeps an adjacency list of at most
 //     SP_CAP entries in shared memory; the CTA builds the lists, one warp
@@ -25,6 +23,12 @@
 //     flags the node, which is then redone by the global kernel;
 //   * global (anything larger, or a flagged sparse node): bit rows in global
 //     memory, a CTA per node.
+// The leaf and sparse kernels keep the degrees packed two to a 32-bit word
+// (dead vertices 0xffff). The leaf kernel finds the arg-min by a scan of all of
+// them by one warp; the sparse kernel keeps the least key (degree, local
+// index) of every 64 vertices and scans those (at most 70), rescanning only
+// the groups whose minimum may have risen; the global kernel scans with its
+// whole CTA.
 // The separator kernels run on a second stream so that their long serial
 // orderings overlap the leaves; the leaf kernel leaves them free SMs.
 #include <algorithm>
@@ -38,8 +42,6 @@ constexpr int MD_LEAF = 512;
 constexpr int MD_MAX = 32768;
 constexpr int MD_THREADS = 256;
 constexpr int SP_CAP = 24;
-constexpr int NBK_LEAF = 32;
-constexpr int NBK_SP = 16;
 constexpr uint16_t DEG_DEAD = 0xffff;
 constexpr size_t SMEM_MAX = 225 * 1024;
 
@@ -142,93 +144,102 @@ struct MdArgs {
   int64_t smem_avail;
 };
 
-template <int NBK>
-__device__ __forceinline__ int bucket_of(uint32_t d) {
-  return d < (uint32_t)(NBK - 1) ? (int)d : NBK - 1;
-}
-
-// Degree buckets of the alive vertices: bit u of bits[d*W + u/32] is set iff u
-// is alive with bucket d (degree d, or >= NBK-1 for d = NBK-1); cnt[d] counts
-// bucket d; bit j of sum[d*SW + s] is set if bits[d*W + 32s + j] may be
-// non-zero (set on insertion, cleared lazily by the arg-min when it finds the
-// word empty). Removals and insertions run in separate warp phases.
-struct Buckets {
-  uint32_t* bits;
-  uint32_t* sum;
-  int32_t* cnt;
-  int W, SW;
-};
-
-__device__ __forceinline__ void bk_remove(const Buckets& B, int d, int u) {
-  atomicAnd(&B.bits[d * B.W + (u >> 5)], ~(1u << (u & 31)));
-  atomicSub(&B.cnt[d], 1);
-}
-
-__device__ __forceinline__ void bk_insert(const Buckets& B, int d, int u) {
-  const int w = u >> 5;
-  atomicOr(&B.bits[d * B.W + w], 1u << (u & 31));
-  atomicOr(&B.sum[d * B.SW + (w >> 5)], 1u << (w & 31));
-  atomicAdd(&B.cnt[d], 1);
-}
-
-// Arg-min of (degree, local index) over the alive vertices, by one warp.
-template <int NBK>
-__device__ __forceinline__ int warp_argmin(const Buckets& B, const uint16_t* deg, int m) {
-  const int lane = threadIdx.x & 31;
-  const unsigned ne = __ballot_sync(0xffffffffu, lane < NBK && B.cnt[lane] > 0);
-  const int dstar = __ffs(ne) - 1;
-  if (dstar >= 0 && dstar < NBK - 1) {
-    // the bucket is not empty, so some summarised word is non-zero; words
-    // found empty get their summary bit cleared (only this warp writes here)
-    for (int s0 = 0; s0 < B.SW;) {
-      const uint32_t sv = s0 + lane < B.SW ? B.sum[dstar * B.SW + s0 + lane] : 0u;
-      const unsigned nz = __ballot_sync(0xffffffffu, sv != 0u);
-      if (!nz) { s0 += 32; continue; }
-      const int l = __ffs(nz) - 1;
-      const uint32_t svl = __shfl_sync(0xffffffffu, sv, l);
-      const int w = (s0 + l) * 32 + __ffs(svl) - 1;
-      const uint32_t x = B.bits[dstar * B.W + w];
-      if (x) return w * 32 + __ffs(x) - 1;
-      if (lane == 0) B.sum[dstar * B.SW + (w >> 5)] = svl & ~(1u << (w & 31));
-      __syncwarp();
-    }
-  }
-  uint32_t best = 0xffffffffu;
-  for (int i = lane; i < m; i += 32) {
-    const uint16_t dg = deg[i];
-    if (dg != DEG_DEAD) {
-      const uint32_t key = ((uint32_t)dg << 16) | (uint32_t)i;
-      best = key < best ? key : best;
-    }
-  }
-  return (int)(__reduce_min_sync(0xffffffffu, best) & 0xffffu);
-}
-
-template <int NBK>
-__device__ __forceinline__ void buckets_build(const Buckets& B, const uint16_t* deg, int m, int me, int nt,
-                                              bool cta) {
-  for (int i = me; i < NBK * B.W; i += nt) B.bits[i] = 0u;
-  for (int i = me; i < NBK * B.SW; i += nt) B.sum[i] = 0u;
-  for (int i = me; i < NBK; i += nt) B.cnt[i] = 0;
-  if (cta) __syncthreads(); else __syncwarp();
-  for (int i = me; i < m; i += nt) bk_insert(B, bucket_of<NBK>(deg[i]), i);
-  if (cta) __syncthreads(); else __syncwarp();
-}
-
-__host__ __device__ __forceinline__ size_t bucket_words(int nbk, int m) {
-  const int W = (m + 31) >> 5, SW = (W + 31) >> 5;
-  return (size_t)nbk * W + (size_t)nbk * SW + nbk;
-}
-
 __host__ __device__ size_t sparse_smem(int m);
 
 // ---- leaf kernel ---------------------------------------------------------------------
 
+// Sorts a node of m <= 32*E vertices by (key, original id) in registers (lane L
+// holds local indices L*E ..), writes the sorted list and every vertex's local
+// index, then builds the induced graph's bit rows (R, word-major, zeroed here)
+// and degrees. The lane's E vertices are gathered four at a time so that their
+// dependent loads (row bounds, neighbours, their node and local index) overlap.
+template <int E>
+__device__ __forceinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S, int W, int32_t* verts,
+                                           uint32_t* R, uint16_t* deg, int lane) {
+  unsigned long long x[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = lane * E + r;
+    x[r] = ~0ull;
+    if (i < m) {
+      const int32_t v = verts[i];
+      x[r] = ((unsigned long long)(a.key ? a.key[v] : 0u) << 32) | (uint32_t)v;
+    }
+  }
+  warp_sort_regs<E>(x, lane);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < E; ++r) {
+    const int i = lane * E + r;
+    if (i < m) {
+      const int32_t v = (int32_t)(uint32_t)x[r];
+      verts[i] = v;
+      a.loc[v] = i;
+    }
+  }
+  {
+    const int nw = W * S, n4 = nw >> 2;
+    uint4* R4 = (uint4*)R;
+    for (int i = lane; i < n4; i += 32) R4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = 4 * n4 + lane; i < nw; i += 32) R[i] = 0u;
+  }
+  const int M64 = (m + 63) & ~63;
+  for (int i = m + lane; i < M64; i += 32) deg[i] = DEG_DEAD;
+  __syncwarp();
+  constexpr int G = E < 4 ? E : 4;
+#pragma unroll
+  for (int r0 = 0; r0 < E; r0 += G) {
+    int32_t b[G], e[G], c[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+      const int i = lane * E + r0 + s;
+      const int32_t v = (int32_t)(uint32_t)x[r0 + s];
+      b[s] = i < m ? a.rowptr[v] : 0;
+      e[s] = i < m ? a.rowptr[v + 1] : 0;
+      c[s] = 0;
+    }
+    for (;;) {
+      bool more = false;
+#pragma unroll
+      for (int s = 0; s < G; ++s) more |= b[s] < e[s];
+      if (!more) break;
+      // eight neighbours of each vertex per round
+      int32_t u[G][8], nt[G][8], j[G][8];
+#pragma unroll
+      for (int s = 0; s < G; ++s)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[s][k] = b[s] + k < e[s] ? a.col[b[s] + k] : -1;
+#pragma unroll
+      for (int s = 0; s < G; ++s)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          nt[s][k] = u[s][k] >= 0 ? a.node_of[u[s][k]] : -1;
+          j[s][k] = u[s][k] >= 0 ? a.loc[u[s][k]] : 0;
+        }
+#pragma unroll
+      for (int s = 0; s < G; ++s) {
+        const int i = lane * E + r0 + s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (nt[s][k] == t) {
+            R[(j[s][k] >> 5) * S + i] |= 1u << (j[s][k] & 31);
+            ++c[s];
+          }
+        b[s] += 8;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+      const int i = lane * E + r0 + s;
+      if (i < m) deg[i] = (uint16_t)c[s];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char* mine = smem + (size_t)wid * a.slice_bytes;
-  (void)nw;
   // nodes are listed largest first and each warp takes the next one when it is
   // done (greedy largest-first balancing of the serial eliminations)
   for (;;) {
@@ -240,160 +251,101 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
     const int32_t m = a.node_size[t];
     const int32_t pbeg = a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
-    const int W = (m + 31) >> 5;
+    const int W = (m + 31) >> 5;                       // <= MD_LEAF / 32
     const int S = m | 1;
+    const int M64 = (m + 63) & ~63;                    // degrees padded to whole warp reads
     uint32_t* R = (uint32_t*)mine;
-    uint32_t* nzv = R + (size_t)W * S;                 // pivot row: non-zero words
-    uint16_t* nzw = (uint16_t*)(nzv + 32);             //   and their indices
-    uint16_t* deg = nzw + 32;
-    uint16_t* nb = deg + ((m + 1) & ~1);
-    Buckets B;
-    B.W = W;
-    B.SW = (W + 31) >> 5;
-    B.bits = (uint32_t*)(nb + ((m + 1) & ~1));
-    B.sum = B.bits + (size_t)NBK_LEAF * W;
-    B.cnt = (int32_t*)(B.sum + (size_t)NBK_LEAF * B.SW);
-    // sort the node's vertices by (key, original id) (buffer overlaps R): the
-    // local index order is the tie-break order of the arg-min
-    unsigned long long* sb = (unsigned long long*)mine;
-    const int NS = pow2_at_least(m, 32);
-    for (int i = lane; i < NS; i += 32) {
-      unsigned long long e = ~0ull;
-      if (i < m) {
-        const int32_t v = verts[i];
-        e = ((unsigned long long)(a.key ? a.key[v] : 0u) << 32) | (uint32_t)v;
-      }
-      sb[i] = e;
+    uint16_t* deg = (uint16_t*)(R + (size_t)W * S);
+    uint16_t* order = deg + M64;                       // pivot of each step
+    uint16_t* nb = order + ((m + 1) & ~1);             // pivot's neighbours, this step
+    uint32_t* nzv = (uint32_t*)(nb + ((m + 1) & ~1));  // pivot row's non-zero words
+    uint16_t* nzw = (uint16_t*)(nzv + MD_LEAF / 32);   //   and their indices
+    switch (pow2_at_least(m, 32)) {
+      case 32: leaf_setup<1>(a, t, m, S, W, verts, R, deg, lane); break;
+      case 64: leaf_setup<2>(a, t, m, S, W, verts, R, deg, lane); break;
+      case 128: leaf_setup<4>(a, t, m, S, W, verts, R, deg, lane); break;
+      case 256: leaf_setup<8>(a, t, m, S, W, verts, R, deg, lane); break;
+      default: leaf_setup<16>(a, t, m, S, W, verts, R, deg, lane); break;
     }
     __syncwarp();
-    bitonic_sort<false>(sb, NS, lane, 32);
-    for (int i = lane; i < m; i += 32) {
-      const int32_t v = (int32_t)(uint32_t)sb[i];
-      verts[i] = v;
-      a.loc[v] = i;
-    }
-    __syncwarp();
-    for (int i = lane; i < W * S; i += 32) R[i] = 0u;
-    __syncwarp();
-    for (int i = lane; i < m; i += 32) {
-      const int32_t v = verts[i];
-      int c = 0;
-      // eight neighbours per round: their ids, then their node and local index
-      const int32_t e1 = a.rowptr[v + 1];
-      for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += 8) {
-        int32_t u[8], nt[8], j[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
-          j[k] = u[k] >= 0 ? a.loc[u[k]] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (nt[k] == t) {
-            R[(j[k] >> 5) * S + i] |= 1u << (j[k] & 31);
-            ++c;
-          }
-      }
-      deg[i] = (uint16_t)c;
-    }
-    __syncwarp();
-    buckets_build<NBK_LEAF>(B, deg, m, lane, 32, false);
+    const uint32_t* deg2 = (const uint32_t*)deg;
+    uint32_t* degw = (uint32_t*)deg;
+    const int H = M64 >> 1;
+    // lane w < W holds the alive bits of word w: dead vertices are masked out
+    // of pivot rows instead of being cleared from their neighbours' rows
+    uint32_t alive = 0xffffffffu;
     for (int step = 0; step < m; ++step) {
-      const int p = warp_argmin<NBK_LEAF>(B, deg, m);
-      // pivot row (W <= 16: one word per lane): neighbour list + non-zero words
-      const uint32_t bits = lane < W ? R[lane * S + p] : 0u;
+      // arg-min of (degree, local index) over the alive vertices: every lane
+      // takes the minimum of its packed degree pairs, then one warp reduction
+      // (a dead vertex has degree 0xffff, above any alive one)
+      uint32_t best = 0xffffffffu;
+#pragma unroll
+      for (int r = 0; r < MD_LEAF / 64; ++r) {
+        const int j = lane + 32 * r;
+        if (j < H) {
+          const uint32_t d2 = deg2[j];
+          const uint32_t k0 = (d2 << 16) | (uint32_t)(2 * j);
+          const uint32_t k1 = (d2 & 0xffff0000u) | (uint32_t)(2 * j + 1);
+          best = min(best, min(k0, k1));
+        }
+      }
+      const int p = (int)(__reduce_min_sync(0xffffffffu, best) & 0xffffu);
+      // pivot row, one word per lane: the neighbour list and the list of its
+      // non-zero words (nz of them)
+      const uint32_t bits = lane < W ? (R[lane * S + p] & alive) : 0u;
+      const int c = __popc(bits);
+      const int incl = warp_incl_scan_i32(c);
+      const int nnb = __shfl_sync(0xffffffffu, incl, 31);
       const unsigned nzm = __ballot_sync(0xffffffffu, bits != 0u);
       const int nz = __popc(nzm);
       if (bits) {
-        const int k = __popc(nzm & lanemask_lt());
-        nzv[k] = bits;
-        nzw[k] = (uint16_t)lane;
+        const int kk = __popc(nzm & lanemask_lt());
+        nzv[kk] = bits;
+        nzw[kk] = (uint16_t)lane;
       }
-      const int c = __popc(bits);
-      int ex = warp_incl_scan_i32(c) - c;
-      const int nnb = __shfl_sync(0xffffffffu, ex + c, 31);
-      uint32_t x = bits;
-      while (x) {
-        const int bt = __ffs(x) - 1;
-        x &= x - 1;
-        nb[ex++] = (uint16_t)(lane * 32 + bt);
-      }
+      int ex = incl - c;
+      for (uint32_t x = bits; x; x &= x - 1) nb[ex++] = (uint16_t)(lane * 32 + __ffs(x) - 1);
+      if (lane == (p >> 5)) alive &= ~(1u << (p & 31));
       if (lane == 0) {
-        a.perm[pbeg + step] = verts[p];
-        bk_remove(B, bucket_of<NBK_LEAF>(deg[p]), p);
+        order[step] = (uint16_t)p;
         deg[p] = DEG_DEAD;
       }
       __syncwarp();
-      // clique, one neighbour per lane: row[u] |= row[p] \ {u}, drop p;
-      // degree(u) = degree(u) - 1 + |row[p] \ (row[u] + u)|
-      const int pw = p >> 5;
-      const uint32_t pbit = 1u << (p & 31);
-      int u = -1, ob = 0, nbk = 0;
-      uint32_t ndeg = 0;
-      const int u0 = lane < nnb ? (int)nb[lane] : -1;
-      uint32_t added = 0;
-      {
-        // the pivot's non-zero words come from the lanes that loaded them
-        const int uw = u0 >> 5;
-        const uint32_t ubit = 1u << (u0 & 31);
-        unsigned mm = nzm;
-        while (mm) {
-          const int w = __ffs(mm) - 1;
-          mm &= mm - 1;
-          const uint32_t pv = __shfl_sync(0xffffffffu, bits, w);
-          if (u0 >= 0) {
-            const uint32_t r = R[w * S + u0];
-            uint32_t nv = pv & ~r;
-            if (w == uw) nv &= ~ubit;
-            if (nv) { R[w * S + u0] = r | nv; added += __popc(nv); }
-          }
-        }
-      }
-      if (lane < nnb) {
-        u = u0;
-        R[pw * S + u] &= ~pbit;
-        const uint32_t od = deg[u];
-        ndeg = od - 1u + added;
-        ob = bucket_of<NBK_LEAF>(od);
-        nbk = bucket_of<NBK_LEAF>(ndeg);
-        deg[u] = (uint16_t)ndeg;
-        if (ob != nbk) bk_remove(B, ob, u);
-      }
-      // more than 32 neighbours: the rest, same rule (rare; dense leaves)
-      for (int q = 32 + lane; q < nnb; q += 32) {
-        const int v = nb[q];
-        const int vw = v >> 5;
-        const uint32_t vbit = 1u << (v & 31);
-        uint32_t added = 0;
-        for (int k = 0; k < nz; ++k) {
-          const int w = nzw[k];
-          const uint32_t r = R[w * S + v];
-          uint32_t nv = nzv[k] & ~r;
-          if (w == vw) nv &= ~vbit;
-          if (nv) { R[w * S + v] = r | nv; added += __popc(nv); }
-        }
-        R[pw * S + v] &= ~pbit;
-        const uint32_t od = deg[v];
-        const uint32_t nd = od - 1u + added;
-        deg[v] = (uint16_t)nd;
-        const int o2 = bucket_of<NBK_LEAF>(od), n2 = bucket_of<NBK_LEAF>(nd);
-        if (o2 != n2) { bk_remove(B, o2, v); nb[q] = (uint16_t)(v | 0x8000u); }   // mark: insert later
-      }
-      __syncwarp();
-      if (u >= 0 && ob != nbk) bk_insert(B, nbk, u);
-      for (int q = 32 + lane; q < nnb; q += 32) {
-        const int v = nb[q];
-        if (v & 0x8000) {
-          const int vv = v & 0x7fff;
-          bk_insert(B, bucket_of<NBK_LEAF>(deg[vv]), vv);
-        }
+      // clique, one (neighbour u, non-zero pivot word w) pair per lane:
+      // row[u] |= row[p] \ {u} in word w, and degree(u) grows by the bits
+      // added (less one, for p, in u's first pair). i = e / nz exactly: e <
+      // 2^13, nz <= 16, so (e + 0.5) / nz is at least 1/32 from an integer.
+      const float rnz = __frcp_rn((float)nz);
+      const int total = nnb * nz;
+      for (int e = lane; e < total; e += 32) {
+        const int i = (int)(((float)e + 0.5f) * rnz);
+        const int k = e - i * nz;
+        const int u = nb[i];
+        const int w = nzw[k];
+        const uint32_t pvw = nzv[k];
+        uint32_t* rp = R + w * S + u;
+        const uint32_t r = *rp;
+        uint32_t nv = pvw & ~r;
+        if (w == (u >> 5)) nv &= ~(1u << (u & 31));
+        if (nv) *rp = r | nv;
+        const int delta = __popc(nv) - (k == 0 ? 1 : 0);
+        if (delta) atomicAdd(&degw[u >> 1], (uint32_t)delta << ((u & 1) * 16));
       }
       __syncwarp();
     }
+    // positions of the node's vertices in elimination order
+    for (int i = lane; i < m; i += 32) a.perm[pbeg + i] = verts[order[i]];
     __syncwarp();
   }
+}
+
+// Least key (degree << 16 | local index) of the 64 vertices of group g, by one
+// warp (lane l reads the packed degree pair 32g + l).
+__device__ __forceinline__ uint32_t group_min_key(const uint32_t* deg2, int g, int lane) {
+  const int j = 32 * g + lane;
+  const uint32_t d2 = deg2[j];
+  const uint32_t k0 = (d2 << 16) | (uint32_t)(2 * j), k1 = (d2 & 0xffff0000u) | (uint32_t)(2 * j + 1);
+  return __reduce_min_sync(0xffffffffu, min(k0, k1));
 }
 
 // ---- sparse kernel (separators) --------------------------------------------------------
@@ -409,15 +361,11 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
     const int32_t oi = a.nodes ? li : t;                   // index of this node's overflow flag
     const int32_t pbeg = a.rank_out ? 0 : a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
-    const int W = (m + 31) >> 5;
+    const int M64 = (m + 63) & ~63, NG = M64 >> 6;
     uint16_t* adj = (uint16_t*)smem;                      // m x SP_CAP local ids (48 B rows)
-    uint16_t* deg = adj + (size_t)m * SP_CAP;
-    Buckets B;
-    B.W = W;
-    B.SW = (W + 31) >> 5;
-    B.bits = (uint32_t*)(deg + ((m + 1) & ~1));
-    B.sum = B.bits + (size_t)NBK_SP * W;
-    B.cnt = (int32_t*)(B.sum + (size_t)NBK_SP * B.SW);
+    uint16_t* deg = adj + (size_t)m * SP_CAP;             // [M64], padded with dead entries
+    uint16_t* order = deg + M64;                          // pivot of each step
+    uint32_t* gmin = (uint32_t*)(order + ((m + 1) & ~1)); // [NG] least key of each 64 vertices
     // sort the node's vertices by original id (buffer overlaps the lists)
     int32_t* sb = (int32_t*)smem;
     const int NS = pow2_at_least(m, 32);
@@ -434,38 +382,59 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
     for (int i = tid; i < m; i += blockDim.x) {
       const int32_t v = verts[i];
       int c = 0;
-      for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-        const int32_t u = a.col[e];
-        if (a.node_of[u] != t) continue;
-        if (c < SP_CAP) adj[(size_t)i * SP_CAP + c] = (uint16_t)a.loc[u];
-        ++c;
+      // eight neighbours per round: their ids, then their node and local index
+      const int32_t e1 = a.rowptr[v + 1];
+      for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += 8) {
+        int32_t u[8], nt[8], j[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
+          j[k] = u[k] >= 0 ? a.loc[u[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (nt[k] == t) {
+            if (c < SP_CAP) adj[(size_t)i * SP_CAP + c] = (uint16_t)j[k];
+            ++c;
+          }
       }
       if (c > SP_CAP) s_ovf = 1;
       deg[i] = (uint16_t)(c < SP_CAP ? c : SP_CAP);
     }
+    for (int i = m + tid; i < M64; i += blockDim.x) deg[i] = DEG_DEAD;
     __syncthreads();
     if (s_ovf) {
       if (tid == 0) a.overflow[oi] = 1;
       __syncthreads();
       continue;
     }
-    buckets_build<NBK_SP>(B, deg, m, tid, blockDim.x, true);
+    const uint32_t* deg2 = (const uint32_t*)deg;
+    for (int g = tid >> 5; g < NG; g += blockDim.x >> 5) {
+      const uint32_t r = group_min_key(deg2, g, lane);
+      if (lane == 0) gmin[g] = r;
+    }
+    __syncthreads();
     if (tid < 32) {
       bool ovf = false;
       for (int step = 0; step < m && !ovf; ++step) {
-        const int p = warp_argmin<NBK_SP>(B, deg, m);
-        const int dp = deg[p];
+        // arg-min of the keys (degree << 16 | local index) over the group
+        // minima; the key also gives the pivot's degree
+        uint32_t best = 0xffffffffu;
+        for (int g = lane; g < NG; g += 32) best = min(best, gmin[g]);
+        const uint32_t pkey = __reduce_min_sync(0xffffffffu, best);
+        const int p = (int)(pkey & 0xffffu);
+        const int dp = (int)(pkey >> 16);
         // lane j holds the j-th neighbour of p
         const int mine_nb = lane < dp ? (int)adj[(size_t)p * SP_CAP + lane] : -1;
         __syncwarp();
         if (lane == 0) {
-          if (a.rank_out) a.rank_out[verts[p]] = step;
-          else a.perm[pbeg + step] = verts[p];
-          bk_remove(B, bucket_of<NBK_SP>(dp), p);
+          order[step] = (uint16_t)p;
           deg[p] = DEG_DEAD;
         }
         bool my_ovf = false;
-        int u = -1, ob = 0, nbk = 0, pos = 0, du = 0;
+        int u = -1, pos = 0, du = 0;
         union L24 { uint4 q[3]; uint16_t e[SP_CAP]; };
         L24 lu;
         uint16_t* nu = nullptr;
@@ -498,18 +467,51 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
             }
           }
         }
+        // group minima: a neighbour whose key fell lowers its group's
+        // minimum; one that was its group's minimum and rose has the group
+        // rescanned, as is always the pivot's group
+        bool resc = false;
+        int gu = 0;
         if (lane < dp) {
-          ob = bucket_of<NBK_SP>((uint32_t)du);
-          nbk = bucket_of<NBK_SP>((uint32_t)pos);
           deg[u] = (uint16_t)pos;
-          if (ob != nbk) bk_remove(B, ob, u);
+          const uint32_t kold = ((uint32_t)du << 16) | (uint32_t)u, knew = ((uint32_t)pos << 16) | (uint32_t)u;
+          gu = u >> 6;
+          if (knew < kold) atomicMin(&gmin[gu], knew);
+          else if (knew > kold && gmin[gu] == kold) resc = true;
         }
-        ovf = __any_sync(0xffffffffu, my_ovf);
         __syncwarp();
-        if (u >= 0 && ob != nbk) bk_insert(B, nbk, u);
+        ovf = __any_sync(0xffffffffu, my_ovf);
+        unsigned rm = __ballot_sync(0xffffffffu, resc);
+        const int gp = p >> 6;
+        int g = gp;
+        for (;;) {
+          const uint32_t r = group_min_key(deg2, g, lane);
+          if (lane == 0) gmin[g] = r;
+          int gn = -1;
+          while (rm && gn < 0) {
+            const int l = __ffs(rm) - 1;
+            rm &= rm - 1;
+            const int c = __shfl_sync(0xffffffffu, gu, l);
+            gn = c != gp ? c : -1;
+          }
+          if (gn < 0) break;
+          g = gn;
+        }
         __syncwarp();
       }
-      if (ovf && lane == 0) a.overflow[oi] = 1;
+      if (ovf && lane == 0) {
+        a.overflow[oi] = 1;
+        s_ovf = 1;
+      }
+    }
+    __syncthreads();
+    // the elimination order, unless the node is left to the global kernel
+    if (!s_ovf) {
+      for (int i = tid; i < m; i += blockDim.x) {
+        const int32_t v = verts[order[i]];
+        if (a.rank_out) a.rank_out[v] = i;
+        else a.perm[pbeg + i] = v;
+      }
     }
     __syncthreads();
   }
@@ -687,15 +689,14 @@ __global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, in
 }
 
 size_t leaf_slice(int m) {
-  const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1);
-  const size_t need = W * S * 4 + 32 * 4 + 32 * 2 + 2 * m2 * 2 + bucket_words(NBK_LEAF, m) * 4;
-  const size_t sortb = (size_t)pow2_host(m) * 8;
-  return ((need > sortb ? need : sortb) + 15) & ~(size_t)15;
+  const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1), m64 = (size_t)((m + 63) & ~63);
+  const size_t need = W * S * 4 + m64 * 2 + 2 * m2 * 2 + (MD_LEAF / 32) * 6;
+  return (need + 15) & ~(size_t)15;
 }
 
 __host__ __device__ size_t sparse_smem(int m) {
-  const size_t m2 = (size_t)((m + 1) & ~1);
-  const size_t need = (size_t)m * SP_CAP * 2 + m2 * 2 + bucket_words(NBK_SP, m) * 4;
+  const size_t m2 = (size_t)((m + 1) & ~1), m64 = (size_t)((m + 63) & ~63);
+  const size_t need = (size_t)m * SP_CAP * 2 + m64 * 2 + m2 * 2 + (m64 / 64) * 4;
   size_t p2 = 32;
   while (p2 < (size_t)m) p2 <<= 1;
   const size_t sortb = p2 * 4;
