@@ -127,10 +127,10 @@ int32_t* pinned_scratch() {
   return buf;
 }
 
-AuxStream* aux_stream(int device) {
-  thread_local AuxStream cache[128];
-  if (device < 0 || device >= 128) return nullptr;
-  AuxStream& a = cache[device];
+AuxStream* aux_stream(int device, int which) {
+  thread_local AuxStream cache[128][2];
+  if (device < 0 || device >= 128 || which < 0 || which > 1) return nullptr;
+  AuxStream& a = cache[device][which];
   if (!a.s) {
     if (cudaStreamCreateWithFlags(&a.s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||

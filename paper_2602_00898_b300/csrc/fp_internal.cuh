@@ -106,13 +106,14 @@ fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what);
 fp_status sync_status(fp_handle* h, int32_t* status_out);   // sync stream, read status word
 // Per-thread pinned host scratch of 256 ints (allocated once per thread).
 int32_t* pinned_scratch();
-// Per-thread, per-device auxiliary stream with a fork and a join event, created
-// once and reused (stage kernels that overlap run on it).
+// Per-thread, per-device auxiliary streams (which = 0 or 1) with a fork and a
+// join event each, created once and reused (stage kernels that overlap run on
+// them).
 struct AuxStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
-AuxStream* aux_stream(int device);
+AuxStream* aux_stream(int device, int which = 0);
 
 // Raises a kernel's dynamic shared-memory limit to the device maximum minus its
 // static shared memory and asks for the largest shared-memory carveout. Every

@@ -42,6 +42,7 @@ constexpr int MD_LEAF = 512;
 constexpr int MD_MAX = 32768;
 constexpr int MD_THREADS = 256;
 constexpr int SP_CAP = 24;
+constexpr int SP_GROUPS = 96;   // group minima the sparse kernel's arg-min reads (m <= 6144)
 constexpr uint16_t DEG_DEAD = 0xffff;
 constexpr size_t SMEM_MAX = 225 * 1024;
 
@@ -148,35 +149,101 @@ __host__ __device__ size_t sparse_smem(int m);
 
 // ---- leaf kernel ---------------------------------------------------------------------
 
-// Sorts a node of m <= 32*E vertices by (key, original id) in registers (lane L
-// holds local indices L*E ..), writes the sorted list and every vertex's local
-// index, then builds the induced graph's bit rows (R, word-major, zeroed here)
-// and degrees. The lane's E vertices are gathered four at a time so that their
-// dependent loads (row bounds, neighbours, their node and local index) overlap.
-template <int E>
-__device__ __forceinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S, int W, int32_t* verts,
-                                           uint32_t* R, uint16_t* deg, int lane) {
-  unsigned long long x[E];
+// Set bits of every 4-bit value v: their count (NIB_COUNT, 4 bits at 4v) and
+// their positions in increasing order (2 bits each, 8 bits at 8(v & 7) of
+// NIB_POS_LO for v < 8, of NIB_POS_HI otherwise).
+__host__ __device__ constexpr uint64_t nib_positions(int v0) {
+  uint64_t r = 0;
+  for (int v = v0; v < v0 + 8; ++v) {
+    uint64_t e = 0;
+    int j = 0;
+    for (int b = 0; b < 4; ++b)
+      if ((v >> b) & 1) e |= (uint64_t)b << (2 * j++);
+    r |= e << (8 * (v - v0));
+  }
+  return r;
+}
+__host__ __device__ constexpr uint64_t nib_counts() {
+  uint64_t r = 0;
+  for (int v = 0; v < 16; ++v) r |= (uint64_t)(((v >> 0) & 1) + ((v >> 1) & 1) + ((v >> 2) & 1) + ((v >> 3) & 1)) << (4 * v);
+  return r;
+}
+constexpr uint64_t NIB_POS_LO = nib_positions(0), NIB_POS_HI = nib_positions(8), NIB_COUNT = nib_counts();
+static_assert(NIB_COUNT == 0x4332322132212110ull, "nibble counts");
+
+// e / d for 0 <= e < 2^13 and 1 <= d <= 16 as (e * ceil(2^31 / d)) >> 31: the
+// rounding of the multiplier adds less than e / 2^31 < 2^-18, below the
+// 1/16 that separates e / d from the next integer, so the quotient is exact.
+#define FP_INV31(d) (uint32_t)((0x80000000ull + (d) - 1) / (d))
+__constant__ uint32_t c_inv31[17] = {0u,          FP_INV31(1),  FP_INV31(2),  FP_INV31(3),  FP_INV31(4),
+                                     FP_INV31(5),  FP_INV31(6),  FP_INV31(7),  FP_INV31(8),  FP_INV31(9),
+                                     FP_INV31(10), FP_INV31(11), FP_INV31(12), FP_INV31(13), FP_INV31(14),
+                                     FP_INV31(15), FP_INV31(16)};
+#undef FP_INV31
+__device__ __forceinline__ int div_small(int e, uint32_t inv) {
+  return (int)(((unsigned long long)(uint32_t)e * inv) >> 31);
+}
+
+// Bitonic sort (Batcher, AFIPS 1968) of N <= 512 keys in shared memory by one
+// warp, ascending. Each stage's compare-exchanges (at most 8 a lane) load all
+// their pairs before storing any, so that their shared-memory round trips
+// overlap; the code is one short loop whatever N is.
+__device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int N, int lane) {
+  const int half = N >> 1;
+  for (int k = 2; k <= N; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int jj = __ffs(j) - 1;
+      unsigned long long x[MD_LEAF / 64], y[MD_LEAF / 64];
+      int ix[MD_LEAF / 64];
 #pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int i = lane * E + r;
-    x[r] = ~0ull;
+      for (int q = 0; q < MD_LEAF / 64; ++q) {
+        const int c = lane + 32 * q;
+        ix[q] = ((c >> jj) << (jj + 1)) | (c & (j - 1));
+        if (c < half) {
+          x[q] = buf[ix[q]];
+          y[q] = buf[ix[q] + j];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MD_LEAF / 64; ++q) {
+        const int c = lane + 32 * q;
+        if (c < half && ((y[q] < x[q]) == ((ix[q] & k) == 0))) {
+          buf[ix[q]] = y[q];
+          buf[ix[q] + j] = x[q];
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// Sorts a node's m <= 512 vertices by (key, original id), writes the sorted
+// list (to verts and to lv in shared memory) and every vertex's local index,
+// then builds the induced graph's bit rows (R, word-major, zeroed here) and
+// degrees. Each lane gathers two vertices at a time, eight neighbours each,
+// so that their dependent loads (row bounds, neighbours, their node and local
+// index) overlap.
+__device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S, int W, int32_t* verts,
+                                        unsigned char* mine, uint32_t* R, uint16_t* deg, int32_t* lv,
+                                        int lane) {
+  unsigned long long* sb = (unsigned long long*)mine;   // overlaps R
+  const int N = pow2_at_least(m, 32);
+  for (int i = lane; i < N; i += 32) {
+    unsigned long long e = ~0ull;
     if (i < m) {
       const int32_t v = verts[i];
-      x[r] = ((unsigned long long)(a.key ? a.key[v] : 0u) << 32) | (uint32_t)v;
+      e = ((unsigned long long)(a.key ? a.key[v] : 0u) << 32) | (uint32_t)v;
     }
+    sb[i] = e;
   }
-  warp_sort_regs<E>(x, lane);
   __syncwarp();
-#pragma unroll
-  for (int r = 0; r < E; ++r) {
-    const int i = lane * E + r;
-    if (i < m) {
-      const int32_t v = (int32_t)(uint32_t)x[r];
-      verts[i] = v;
-      a.loc[v] = i;
-    }
+  warp_sort_smem(sb, N, lane);
+  for (int i = lane; i < m; i += 32) {
+    const int32_t v = (int32_t)(uint32_t)sb[i];
+    lv[i] = v;
+    verts[i] = v;
+    a.loc[v] = i;
   }
+  __syncwarp();
   {
     const int nw = W * S, n4 = nw >> 2;
     uint4* R4 = (uint4*)R;
@@ -186,39 +253,31 @@ __device__ __forceinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, in
   const int M64 = (m + 63) & ~63;
   for (int i = m + lane; i < M64; i += 32) deg[i] = DEG_DEAD;
   __syncwarp();
-  constexpr int G = E < 4 ? E : 4;
+  for (int i0 = lane; i0 < m; i0 += 64) {
+    int32_t b[2], e[2], c[2] = {0, 0};
 #pragma unroll
-  for (int r0 = 0; r0 < E; r0 += G) {
-    int32_t b[G], e[G], c[G];
-#pragma unroll
-    for (int s = 0; s < G; ++s) {
-      const int i = lane * E + r0 + s;
-      const int32_t v = (int32_t)(uint32_t)x[r0 + s];
+    for (int s = 0; s < 2; ++s) {
+      const int i = i0 + 32 * s;
+      const int32_t v = i < m ? lv[i] : 0;
       b[s] = i < m ? a.rowptr[v] : 0;
       e[s] = i < m ? a.rowptr[v + 1] : 0;
-      c[s] = 0;
     }
-    for (;;) {
-      bool more = false;
+    while (b[0] < e[0] || b[1] < e[1]) {
+      int32_t u[2][8], nt[2][8], j[2][8];
 #pragma unroll
-      for (int s = 0; s < G; ++s) more |= b[s] < e[s];
-      if (!more) break;
-      // eight neighbours of each vertex per round
-      int32_t u[G][8], nt[G][8], j[G][8];
-#pragma unroll
-      for (int s = 0; s < G; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int k = 0; k < 8; ++k) u[s][k] = b[s] + k < e[s] ? a.col[b[s] + k] : -1;
 #pragma unroll
-      for (int s = 0; s < G; ++s)
+      for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           nt[s][k] = u[s][k] >= 0 ? a.node_of[u[s][k]] : -1;
           j[s][k] = u[s][k] >= 0 ? a.loc[u[s][k]] : 0;
         }
 #pragma unroll
-      for (int s = 0; s < G; ++s) {
-        const int i = lane * E + r0 + s;
+      for (int s = 0; s < 2; ++s) {
+        const int i = i0 + 32 * s;
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           if (nt[s][k] == t) {
@@ -229,10 +288,8 @@ __device__ __forceinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, in
       }
     }
 #pragma unroll
-    for (int s = 0; s < G; ++s) {
-      const int i = lane * E + r0 + s;
-      if (i < m) deg[i] = (uint16_t)c[s];
-    }
+    for (int s = 0; s < 2; ++s)
+      if (i0 + 32 * s < m) deg[i0 + 32 * s] = (uint16_t)c[s];
   }
 }
 
@@ -260,20 +317,17 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
     uint16_t* nb = order + ((m + 1) & ~1);             // pivot's neighbours, this step
     uint32_t* nzv = (uint32_t*)(nb + ((m + 1) & ~1));  // pivot row's non-zero words
     uint16_t* nzw = (uint16_t*)(nzv + MD_LEAF / 32);   //   and their indices
-    switch (pow2_at_least(m, 32)) {
-      case 32: leaf_setup<1>(a, t, m, S, W, verts, R, deg, lane); break;
-      case 64: leaf_setup<2>(a, t, m, S, W, verts, R, deg, lane); break;
-      case 128: leaf_setup<4>(a, t, m, S, W, verts, R, deg, lane); break;
-      case 256: leaf_setup<8>(a, t, m, S, W, verts, R, deg, lane); break;
-      default: leaf_setup<16>(a, t, m, S, W, verts, R, deg, lane); break;
-    }
+    // the sorted vertex list, during the setup only (overlaps order and nb)
+    leaf_setup(a, t, m, S, W, verts, mine, R, deg, (int32_t*)order, lane);
     __syncwarp();
     const uint32_t* deg2 = (const uint32_t*)deg;
     uint32_t* degw = (uint32_t*)deg;
     const int H = M64 >> 1;
-    // lane w < W holds the alive bits of word w: dead vertices are masked out
-    // of pivot rows instead of being cleared from their neighbours' rows
+    // lanes 2w and 2w+1 (w < W) hold the alive bits of word w: dead vertices
+    // are masked out of pivot rows instead of being cleared from their
+    // neighbours' rows
     uint32_t alive = 0xffffffffu;
+    const unsigned lt = lanemask_lt();
     for (int step = 0; step < m; ++step) {
       // arg-min of (degree, local index) over the alive vertices: every lane
       // takes the minimum of its packed degree pairs, then one warp reduction
@@ -290,46 +344,79 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
         }
       }
       const int p = (int)(__reduce_min_sync(0xffffffffu, best) & 0xffffu);
-      // pivot row, one word per lane: the neighbour list and the list of its
-      // non-zero words (nz of them)
-      const uint32_t bits = lane < W ? (R[lane * S + p] & alive) : 0u;
-      const int c = __popc(bits);
-      const int incl = warp_incl_scan_i32(c);
-      const int nnb = __shfl_sync(0xffffffffu, incl, 31);
-      const unsigned nzm = __ballot_sync(0xffffffffu, bits != 0u);
-      const int nz = __popc(nzm);
-      if (bits) {
-        const int kk = __popc(nzm & lanemask_lt());
-        nzv[kk] = bits;
-        nzw[kk] = (uint16_t)lane;
+      // pivot row, half a word per lane (lane 2w + h holds bits 16h.. of word
+      // w): the neighbour list and the list of the non-zero words (nz of
+      // them). The neighbour list offsets are an exclusive prefix sum of the
+      // halves' bit counts (at most 16, five bits), taken bit plane by bit
+      // plane with independent ballots.
+      const int hw = lane >> 1, hh = lane & 1;
+      const uint32_t word = hw < W ? (R[hw * S + p] & alive) : 0u;
+      const uint32_t half = (word >> (16 * hh)) & 0xffffu;
+      const int c = __popc(half);
+      int ex = 0, nnb = 0;
+#pragma unroll
+      for (int bp = 0; bp < 5; ++bp) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (c >> bp) & 1);
+        ex += __popc(bb & lt) << bp;
+        nnb += __popc(bb) << bp;
       }
-      int ex = incl - c;
-      for (uint32_t x = bits; x; x &= x - 1) nb[ex++] = (uint16_t)(lane * 32 + __ffs(x) - 1);
-      if (lane == (p >> 5)) alive &= ~(1u << (p & 31));
+      const unsigned nzm = __ballot_sync(0xffffffffu, hh == 0 && word != 0u);
+      const int nz = __popc(nzm);
+      if (hh == 0 && word != 0u) {
+        const int kk = __popc(nzm & lt);
+        nzv[kk] = word;
+        nzw[kk] = (uint16_t)hw;
+      }
+      {
+        // the half's set bits, a nibble at a time, from the tables of the set
+        // bit positions and counts of every 4-bit value (no serial bit scan)
+        int off = ex;
+        const int base = 32 * hw + 16 * hh;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const uint32_t v = (half >> (4 * n)) & 15u;
+          const uint32_t pos = (uint32_t)(((v & 8u) ? NIB_POS_HI : NIB_POS_LO) >> (8 * (v & 7u))) & 0xffu;
+          const int cn = (int)((NIB_COUNT >> (4 * v)) & 15u);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < cn) nb[off + j] = (uint16_t)(base + 4 * n + ((pos >> (2 * j)) & 3u));
+          off += cn;
+        }
+      }
+      if (hw == (p >> 5)) alive &= ~(1u << (p & 31));
       if (lane == 0) {
         order[step] = (uint16_t)p;
         deg[p] = DEG_DEAD;
       }
+      const uint32_t inv = c_inv31[nz];
       __syncwarp();
-      // clique, one (neighbour u, non-zero pivot word w) pair per lane:
-      // row[u] |= row[p] \ {u} in word w, and degree(u) grows by the bits
-      // added (less one, for p, in u's first pair). i = e / nz exactly: e <
-      // 2^13, nz <= 16, so (e + 0.5) / nz is at least 1/32 from an integer.
-      const float rnz = __frcp_rn((float)nz);
+      // clique, one (neighbour u, non-zero pivot word w) pair per lane, two
+      // pairs a lane per round: row[u] |= row[p] \ {u} in word w, and
+      // degree(u) grows by the bits added (less one, for p, in u's first
+      // pair). Distinct pairs are distinct row words, so both loads go first.
       const int total = nnb * nz;
-      for (int e = lane; e < total; e += 32) {
-        const int i = (int)(((float)e + 0.5f) * rnz);
-        const int k = e - i * nz;
-        const int u = nb[i];
-        const int w = nzw[k];
-        const uint32_t pvw = nzv[k];
-        uint32_t* rp = R + w * S + u;
-        const uint32_t r = *rp;
-        uint32_t nv = pvw & ~r;
-        if (w == (u >> 5)) nv &= ~(1u << (u & 31));
-        if (nv) *rp = r | nv;
-        const int delta = __popc(nv) - (k == 0 ? 1 : 0);
-        if (delta) atomicAdd(&degw[u >> 1], (uint32_t)delta << ((u & 1) * 16));
+      for (int e0 = lane; e0 < total; e0 += 64) {
+        const int e1 = e0 + 32;
+        const bool two = e1 < total;
+        const int i0 = div_small(e0, inv), k0 = e0 - i0 * nz;
+        const int i1 = two ? div_small(e1, inv) : i0, k1 = two ? e1 - i1 * nz : k0;
+        const int u0 = nb[i0], u1 = nb[i1];
+        const int w0 = nzw[k0], w1 = nzw[k1];
+        const uint32_t pv0 = nzv[k0], pv1 = nzv[k1];
+        uint32_t* rp0 = R + w0 * S + u0;
+        uint32_t* rp1 = R + w1 * S + u1;
+        const uint32_t r0 = *rp0, r1 = two ? *rp1 : 0u;
+        uint32_t n0 = pv0 & ~r0, n1 = pv1 & ~r1;
+        if (w0 == (u0 >> 5)) n0 &= ~(1u << (u0 & 31));
+        if (w1 == (u1 >> 5)) n1 &= ~(1u << (u1 & 31));
+        if (n0) *rp0 = r0 | n0;
+        const int d0 = __popc(n0) - (k0 == 0 ? 1 : 0);
+        if (d0) atomicAdd(&degw[u0 >> 1], (uint32_t)d0 << ((u0 & 1) * 16));
+        if (two) {
+          if (n1) *rp1 = r1 | n1;
+          const int d1 = __popc(n1) - (k1 == 0 ? 1 : 0);
+          if (d1) atomicAdd(&degw[u1 >> 1], (uint32_t)d1 << ((u1 & 1) * 16));
+        }
       }
       __syncwarp();
     }
@@ -422,7 +509,11 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         // arg-min of the keys (degree << 16 | local index) over the group
         // minima; the key also gives the pivot's degree
         uint32_t best = 0xffffffffu;
-        for (int g = lane; g < NG; g += 32) best = min(best, gmin[g]);
+#pragma unroll
+        for (int r = 0; r < SP_GROUPS / 32; ++r) {
+          const int g = lane + 32 * r;
+          if (g < NG) best = min(best, gmin[g]);
+        }
         const uint32_t pkey = __reduce_min_sync(0xffffffffu, best);
         const int p = (int)(pkey & 0xffffu);
         const int dp = (int)(pkey >> 16);
@@ -691,7 +782,8 @@ __global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, in
 size_t leaf_slice(int m) {
   const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1), m64 = (size_t)((m + 63) & ~63);
   const size_t need = W * S * 4 + m64 * 2 + 2 * m2 * 2 + (MD_LEAF / 32) * 6;
-  return (need + 15) & ~(size_t)15;
+  const size_t sortb = (size_t)pow2_host(m) * 8;
+  return ((need > sortb ? need : sortb) + 15) & ~(size_t)15;
 }
 
 __host__ __device__ size_t sparse_smem(int m) {
@@ -798,8 +890,15 @@ fp_status run_local_order(fp_handle* h) {
     ls[kind].push_back((int32_t)t);
     if (m > mmax[kind]) mmax[kind] = m;
   }
-  // the leaf kernel's warps draw nodes largest first
-  std::stable_sort(ls[0].begin(), ls[0].end(), [&](int32_t x, int32_t y) { return hs[x] > hs[y]; });
+  // the leaf kernel's warps draw nodes largest first (ties by node index): a
+  // counting sort over the sizes 1..MD_LEAF
+  {
+    std::vector<int32_t> cnt(MD_LEAF + 2, 0), sorted(ls[0].size());
+    for (int32_t t : ls[0]) ++cnt[MD_LEAF - hs[t] + 1];
+    for (int i = 1; i <= MD_LEAF + 1; ++i) cnt[i] += cnt[i - 1];
+    for (int32_t t : ls[0]) sorted[cnt[MD_LEAF - hs[t]]++] = t;
+    ls[0].swap(sorted);
+  }
   // global rows and sort scratch for the sparse (fallback) and global nodes
   std::vector<int64_t> goff, soff;
   int64_t gwords = 0, gsort = 0;
@@ -831,17 +930,22 @@ fp_status run_local_order(fp_handle* h) {
   const int32_t* dnodes = (const int32_t*)dup;
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
               nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr, ovf + ls[1].size()};
-  // separators on the auxiliary stream; leaves on the handle's stream in CTAs
-  // that fill whole SMs, leaving `reserved` SMs for the separator CTAs
-  AuxStream* ax = aux_stream(h->device);
-  if (!ax) return fail(h, FP_ERR_CUDA, "auxiliary stream");
-  cudaStream_t s2 = ax->s;
+  // the separators ordered during the dissection are completed on the first
+  // auxiliary stream, the other separators run on the second one (so that
+  // they need not wait for the early ones), the leaves on the handle's stream
+  // in CTAs that fill whole SMs, leaving `reserved` SMs for separator CTAs
+  AuxStream* ax = aux_stream(h->device, 0);
+  AuxStream* ax3 = aux_stream(h->device, 1);
+  if (!ax || !ax3) return fail(h, FP_ERR_CUDA, "auxiliary stream");
+  cudaStream_t s2 = ax->s, s3 = ax3->s;
   cudaEventRecord(ax->fork, h->stream);
   cudaStreamWaitEvent(s2, ax->fork, 0);
+  cudaEventRecord(ax3->fork, h->stream);
+  cudaStreamWaitEvent(s3, ax3->fork, 0);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  const int nbig = (int)(ls[1].size() + ls[2].size());
-  const int reserved = nbig < 16 ? nbig : 16;
+  const int nbig = (int)(ls[1].size() + ls[2].size() + early.size());
+  const int reserved = nbig < 24 ? nbig : 24;
   const int64_t lo1 = (int64_t)ls[0].size(), lo2 = lo1 + (int64_t)ls[1].size(), lo3 = lo2 + (int64_t)ls[2].size();
   if (!early.empty()) {
     // separators ordered during the dissection: redo the ones whose adjacency
@@ -871,15 +975,15 @@ fp_status run_local_order(fp_handle* h) {
     const size_t sm = sparse_smem(mmax[1]);
     allow_max_dynamic_smem(k_md_sparse);
     {
-      ProfScope ps(FP_PROF_MD_MID, s2);
-      k_md_sparse<<<(unsigned)ls[1].size(), MD_THREADS, sm, s2>>>(a);
+      ProfScope ps(FP_PROF_MD_MID, s3);
+      k_md_sparse<<<(unsigned)ls[1].size(), MD_THREADS, sm, s3>>>(a);
       h->launches++;
     }
     // redo flagged nodes with global rows (grow_off/gsort_off index from 0 here)
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
-    ProfScope ps(FP_PROF_MD_LARGE, s2);
-    k_md_global<<<(unsigned)ls[1].size(), MD_THREADS, smg, s2>>>(a);
+    ProfScope ps(FP_PROF_MD_LARGE, s3);
+    k_md_global<<<(unsigned)ls[1].size(), MD_THREADS, smg, s3>>>(a);
     h->launches++;
   }
   if (!ls[2].empty()) {
@@ -890,8 +994,8 @@ fp_status run_local_order(fp_handle* h) {
     a.gsort_off = dup + off64 + nsg + (int64_t)ls[1].size();
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
-    ProfScope ps(FP_PROF_MD_LARGE, s2);
-    k_md_global<<<(unsigned)ls[2].size(), MD_THREADS, smg, s2>>>(a);
+    ProfScope ps(FP_PROF_MD_LARGE, s3);
+    k_md_global<<<(unsigned)ls[2].size(), MD_THREADS, smg, s3>>>(a);
     h->launches++;
   }
   if (!ls[0].empty()) {
@@ -914,6 +1018,8 @@ fp_status run_local_order(fp_handle* h) {
   }
   cudaEventRecord(ax->join, s2);
   cudaStreamWaitEvent(h->stream, ax->join, 0);
+  cudaEventRecord(ax3->join, s3);
+  cudaStreamWaitEvent(h->stream, ax3->join, 0);
   FP_CHECK_LAUNCH(h, "minimum degree");
   early_md_release(h);
   if (n > 0) {
