@@ -352,16 +352,38 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
   const int32_t wa = m >> 5, nwa = W - wa;
   const uint32_t amask0 = 0xffffffffu << (m & 31);
   if (nab > 0) {
-    // every (row, ancestor word) pair independently, so that many loads are in flight
+    // every (row, ancestor word) pair independently, TAIL_ILP pairs a thread
+    // per round with all their loads issued first, so that many loads are in
+    // flight; thread tid starts at pair tid and steps nthr pairs (dl rows and
+    // dw words) at a time
+    constexpr int TAIL_ILP = 8;
     const int64_t tot = (int64_t)L * nwa;
-    for (int64_t x = tid; x < tot; x += nthr) {
-      const int32_t l = is + (int32_t)(x / nwa), w = wa + (int32_t)(x % nwa);
-      uint32_t s = rows[tri_off(l, W) - (l >> 5) + w];
-      if (w == wa) s &= amask0;
-      while (s) {
-        const int bt = __ffs(s) - 1;
-        s &= s - 1;
-        atomicMin(&first[w * 32 + bt - m], l);
+    const int32_t dl = nthr / nwa, dw = nthr % nwa;
+    int32_t l = is + tid / nwa, w = wa + tid % nwa;
+    for (int64_t x0 = tid; x0 < tot; x0 += (int64_t)TAIL_ILP * nthr) {
+      uint32_t s[TAIL_ILP];
+      int32_t ls[TAIL_ILP], ws[TAIL_ILP];
+#pragma unroll
+      for (int k = 0; k < TAIL_ILP; ++k) {
+        ls[k] = l;
+        ws[k] = w;
+        s[k] = x0 + (int64_t)k * nthr < tot ? rows[tri_off(l, W) - (l >> 5) + w] : 0u;
+        l += dl;
+        w += dw;
+        if (w >= W) {
+          w -= nwa;
+          ++l;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < TAIL_ILP; ++k) {
+        uint32_t v = s[k];
+        if (ws[k] == wa) v &= amask0;
+        while (v) {
+          const int bt = __ffs(v) - 1;
+          v &= v - 1;
+          atomicMin(&first[ws[k] * 32 + bt - m], ls[k]);
+        }
       }
     }
   }
