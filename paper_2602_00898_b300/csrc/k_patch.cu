@@ -39,66 +39,74 @@ inline int grid_for(int64_t n, int threads) {
 }
 
 // Level-synchronous multi-source BFS on packed keys (dist << 32 | label).
-// ctr[0] holds the size of the initial frontier `fa`. An edge {u,v} is
-// followed iff group is null or group[u] == group[v]. On exit key[] holds the
+// ctr[0] holds the size of the initial frontier `fa`. Frontier entries are
+// (vertex, first edge, end edge, 0), so that a level's first round trip
+// brings the edge range along with the vertex. On exit key[] holds the
 // distance and the minimum label for every reached vertex.
-__global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                                     unsigned long long* key, const int32_t* __restrict__ group,
-                                                     int32_t* fa, int32_t* fb, int32_t* ctr) {
+__global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                                     unsigned long long* key, int4* fa, int4* fb, int32_t* ctr) {
   cg::grid_group grid = cg::this_grid();
-  int32_t* cur = fa;
-  int32_t* nxt = fb;
+  int4* cur = fa;
+  int4* nxt = fb;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
   // one level: every frontier vertex claims its unsettled neighbours. The
   // sweep is warp-uniform (every lane of a warp runs the same number of
-  // batches), so a batch's claims are appended with one scanned atomicAdd per
-  // warp; up to BFS_BATCH neighbours are loaded per round (their ids, then
-  // their keys, then the claims: independent round trips).
+  // batches), so a batch's claims are appended with one atomicAdd per warp
+  // (offsets by bit-plane ballots); up to BFS_BATCH neighbours are loaded
+  // per round. Round trips per level: the entry; its label and neighbours;
+  // the claims (atomicMin returns the old key: a vertex settled at an
+  // earlier level keeps it, and only the first claim of a vertex moves it to
+  // the next frontier); the queue slots, with the claimed vertices' edge
+  // ranges loaded meanwhile.
   auto sweep = [&](uint32_t level, int32_t ncur, int64_t first, int64_t stride) {
     const unsigned long long dnext = (unsigned long long)(level + 1) << 32;
     for (int64_t i0 = first - lane; i0 < ncur; i0 += stride) {
       const int64_t i = i0 + lane;
-      int32_t u = 0, e = 0, e1 = 0, gu = 0;
-      unsigned long long lab = 0;
+      int32_t u = 0, e = 0, e1 = 0;
       if (i < ncur) {
-        u = __ldcg(&cur[i]);
-        lab = __ldcg(&key[u]) & 0xffffffffull;
-        gu = group ? group[u] : 0;
-        e = rowptr[u];
-        e1 = rowptr[u + 1];
+        const int4 q = __ldcg(&cur[i]);
+        u = q.x;
+        e = q.y;
+        e1 = q.z;
       }
+      const unsigned long long lab = i < ncur ? (__ldcg(&key[u]) & 0xffffffffull) : 0ull;
       while (__any_sync(0xffffffffu, e < e1)) {
         int32_t v[BFS_BATCH];
         unsigned long long old[BFS_BATCH];
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k) v[k] = e + k < e1 ? col[e + k] : -1;
 #pragma unroll
-        for (int k = 0; k < BFS_BATCH; ++k)
-          if (v[k] >= 0 && group && group[v[k]] != gu) v[k] = -1;
-#pragma unroll
-        for (int k = 0; k < BFS_BATCH; ++k) {
-          old[k] = v[k] >= 0 ? __ldcg(&key[v[k]]) : 0ull;
-          if ((old[k] >> 32) <= level) v[k] = -1;       // settled at an earlier level
-        }
-#pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k) old[k] = v[k] >= 0 ? atomicMin(&key[v[k]], dnext | lab) : 0ull;
         uint32_t claim = 0;
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k)
           if (old[k] == KEY_INF) claim |= 1u << k;      // first claim: goes to the next frontier
+        int32_t rb[BFS_BATCH], re[BFS_BATCH];
+#pragma unroll
+        for (int k = 0; k < BFS_BATCH; ++k) {
+          rb[k] = (claim >> k & 1u) ? rowptr[v[k]] : 0;
+          re[k] = (claim >> k & 1u) ? rowptr[v[k] + 1] : 0;
+        }
         const int32_t c = __popc(claim);
-        const int32_t incl = warp_incl_scan_i32(c);
-        const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        int32_t ex = 0, tot = 0;
+#pragma unroll
+        for (int bp = 0; bp < 4; ++bp) {      // c <= BFS_BATCH = 8: four bit planes
+          const unsigned bb = __ballot_sync(0xffffffffu, (c >> bp) & 1);
+          ex += __popc(bb & lt) << bp;
+          tot += __popc(bb) << bp;
+        }
         int32_t base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&ctr[(level + 1) % 3], tot);
-        base = __shfl_sync(0xffffffffu, base, 31) + incl - c;
+        if (lane == 0 && tot) base = atomicAdd(&ctr[(level + 1) % 3], tot);
+        base = __shfl_sync(0xffffffffu, base, 0) + ex;
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k)
-          if (claim >> k & 1u) nxt[base++] = v[k];
+          if (claim >> k & 1u) nxt[base++] = make_int4(v[k], rb[k], re[k], 0);
         e += BFS_BATCH;
       }
     }
   };
+  static_assert(BFS_BATCH <= 15, "claim counts must fit four bit planes");
   uint32_t level = 0;
   int32_t nprev = 0;
   for (;; ++level) {
@@ -110,7 +118,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
     nprev = ncur;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
     sweep(level, ncur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
-    int32_t* t = cur; cur = nxt; nxt = t;
+    int4* t = cur; cur = nxt; nxt = t;
     grid.sync();
   }
   // small frontiers (the last levels): CTA 0 alone, with CTA barriers instead
@@ -121,7 +129,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs(const int32_t* __restrict__
     if (ncur == 0) return;
     if (threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
     sweep(level, ncur, threadIdx.x, blockDim.x);
-    int32_t* t = cur; cur = nxt; nxt = t;
+    int4* t = cur; cur = nxt; nxt = t;
     __syncthreads();
   }
 }
@@ -134,15 +142,15 @@ __global__ void k_seed_flags(int32_t n, uint64_t kt, uint64_t seed, int32_t* __r
 }
 
 // Seeds (flag[v] = 1) with rank = base + rank[v] become BFS sources.
-__global__ void k_seed_sources(int32_t n, const int32_t* __restrict__ flag, const int32_t* __restrict__ rank,
-                               int32_t base, unsigned long long* __restrict__ key, int32_t* __restrict__ seed_of,
-                               int32_t* __restrict__ frontier, int32_t* ctr) {
+__global__ void k_seed_sources(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ flag,
+                               const int32_t* __restrict__ rank, int32_t base, unsigned long long* __restrict__ key,
+                               int32_t* __restrict__ seed_of, int4* __restrict__ frontier, int32_t* ctr) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     if (flag[v]) {
       int32_t r = rank[v];
       key[v] = (unsigned long long)(uint32_t)(base + r);
       seed_of[base + r] = v;
-      frontier[r] = v;
+      frontier[r] = make_int4(v, rowptr[v], rowptr[v + 1], 0);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -234,11 +242,12 @@ __global__ void k_lloyd_apply(const unsigned long long* __restrict__ best, int32
 }
 
 // All k seeds become sources with their own rank.
-__global__ void k_all_seed_sources(const int32_t* __restrict__ seed_of, int32_t k, unsigned long long* __restrict__ key,
-                                   int32_t* __restrict__ frontier, int32_t* ctr) {
+__global__ void k_all_seed_sources(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ seed_of, int32_t k,
+                                   unsigned long long* __restrict__ key, int4* __restrict__ frontier, int32_t* ctr) {
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
-    key[seed_of[p]] = (unsigned long long)(uint32_t)p;
-    frontier[p] = seed_of[p];
+    const int32_t v = seed_of[p];
+    key[v] = (unsigned long long)(uint32_t)p;
+    frontier[p] = make_int4(v, rowptr[v], rowptr[v + 1], 0);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) { ctr[0] = k; ctr[1] = 0; ctr[2] = 0; }
 }
@@ -447,7 +456,7 @@ struct BfsLauncher {
     maxgrid_cc = sms * (per > 0 ? per : 1);
     return FP_OK;
   }
-  fp_status bfs(fp_handle* h, unsigned long long* key, const int32_t* group, int32_t* fa, int32_t* fb, int32_t* ctr) {
+  fp_status bfs(fp_handle* h, unsigned long long* key, int4* fa, int4* fb, int32_t* ctr) {
     // frontiers peak near n/8 vertices (seeds every ~cap/2 vertices, about 25
     // levels): one CTA per SM while that fits in one pass, more CTAs (up to
     // full occupancy) for large meshes, whose frontiers are too big for 148
@@ -458,7 +467,7 @@ struct BfsLauncher {
     if (g > maxgrid_bfs) g = maxgrid_bfs;
     const int32_t* rp = h->rowptr;
     const int32_t* cl = h->col;
-    void* args[] = {(void*)&rp, (void*)&cl, (void*)&key, (void*)&group, (void*)&fa, (void*)&fb, (void*)&ctr};
+    void* args[] = {(void*)&rp, (void*)&cl, (void*)&key, (void*)&fa, (void*)&fb, (void*)&ctr};
     ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_bfs, g, BFS_THREADS, args, 0, h->stream);
     h->launches++;
@@ -481,8 +490,8 @@ fp_status run_patching(fp_handle* h) {
   unsigned long long* key2 = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * n);
   unsigned long long* best = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (n + 1));
   int32_t* group = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* fa = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* fb = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
+  int4* fa = (int4*)dev_alloc(h, sizeof(int4) * ints);      // frontier queues
+  int4* fb = (int4*)dev_alloc(h, sizeof(int4) * ints);
   int32_t* flag = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
   int32_t* rank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
   int32_t* seed_of = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
@@ -501,11 +510,11 @@ fp_status run_patching(fp_handle* h) {
     FP_LAUNCH(h, k_fill_u64, G, 256, 0, key, KEY_INF, (int64_t)n);
     FP_LAUNCH(h, k_seed_flags, G, 256, 0, n, kt, h->opt.seed, flag);
     scan_exclusive(h, flag, rank, n, tmp);
-    FP_LAUNCH(h, k_seed_sources, G, 256, 0, n, flag, rank, 0, key, seed_of, fa, ctr);
+    FP_LAUNCH(h, k_seed_sources, G, 256, 0, n, h->rowptr, flag, rank, 0, key, seed_of, fa, ctr);
   }
   FP_CHECK_LAUNCH(h, "seeds");
   // R2 Voronoi labelling
-  FP_TRY(L.bfs(h, key, nullptr, fa, fb, ctr));
+  FP_TRY(L.bfs(h, key, fa, fb, ctr));
   // R3 unreached components
   {
     ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
@@ -519,7 +528,7 @@ fp_status run_patching(fp_handle* h) {
   FP_TRY(sync_status(h, &st));
   int32_t k = hbuf[0];
   if (hbuf[1] > 0) {
-    int32_t* comp = fb;           // fb is free between searches
+    int32_t* comp = (int32_t*)fb;   // fb is free between searches
     int g = L.maxgrid_cc < G ? L.maxgrid_cc : G;
     void* args[] = {(void*)&h->rowptr, (void*)&h->col, (void*)&key, (void*)&n, (void*)&comp, (void*)&ctr};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_unreached_components, g, BFS_THREADS, args, 0, h->stream);
@@ -527,9 +536,9 @@ fp_status run_patching(fp_handle* h) {
     if (e != cudaSuccess) return check_cuda(h, e, "components launch");
     FP_LAUNCH(h, k_component_seed_flags, G, 256, 0, comp, n, flag);
     scan_exclusive(h, flag, rank, n, tmp);
-    FP_LAUNCH(h, k_seed_sources, G, 256, 0, n, flag, rank, k, key, seed_of, fa, ctr);
+    FP_LAUNCH(h, k_seed_sources, G, 256, 0, n, h->rowptr, flag, rank, k, key, seed_of, fa, ctr);
     FP_CHECK_LAUNCH(h, "component seeds");
-    FP_TRY(L.bfs(h, key, nullptr, fa, fb, ctr));
+    FP_TRY(L.bfs(h, key, fa, fb, ctr));
     cudaMemcpyAsync(hbuf, rank + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
     FP_TRY(sync_status(h, &st));
     k += hbuf[0];
@@ -572,10 +581,10 @@ fp_status run_patching(fp_handle* h) {
       ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
       FP_LAUNCH(h, k_lloyd_apply, GK, 256, 0, best, k, seed_of);
       FP_LAUNCH(h, k_fill_u64, G, 256, 0, key, KEY_INF, (int64_t)n);
-      FP_LAUNCH(h, k_all_seed_sources, GK, 256, 0, seed_of, k, key, fa, ctr);
+      FP_LAUNCH(h, k_all_seed_sources, GK, 256, 0, h->rowptr, seed_of, k, key, fa, ctr);
     }
     FP_CHECK_LAUNCH(h, "lloyd");
-    FP_TRY(L.bfs(h, key, nullptr, fa, fb, ctr));
+    FP_TRY(L.bfs(h, key, fa, fb, ctr));
   }
   // R5 cap: split until every patch fits. The first round counts the patch
   // sizes; every split counts its two halves, so a later round rebuilds the
