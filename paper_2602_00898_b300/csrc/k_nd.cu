@@ -533,15 +533,6 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
 
 // Separator bookkeeping (Section 5): the OUT vertices stay in node t as its
 // separator; patch weights and quotient edge weights lose them.
-__device__ __forceinline__ void qw_dec(const LevelArgs& a, int32_t p, int32_t q) {
-  int32_t lo = a.q_rowptr[p], hi = a.q_rowptr[p + 1];
-  while (lo < hi) {
-    int32_t mid = (lo + hi) >> 1;
-    if (a.q_col[mid] < q) lo = mid + 1; else hi = mid;
-  }
-  atomicSub(&a.q_w[lo], 1);
-}
-
 __global__ void k_nd_apply(LevelArgs a) {
   const int32_t nc = a.ctr[0];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
@@ -550,13 +541,65 @@ __global__ void k_nd_apply(LevelArgs a) {
     a.final_[v] = 1;
     const int32_t pv = a.gmap[v], t = a.node_of[v];
     atomicSub(&a.w[pv], 1);
-    for (int32_t e = a.rowptr[v]; e < a.rowptr[v + 1]; ++e) {
-      const int32_t u = a.col[e];
-      const int32_t pu = a.gmap[u];
-      if (a.node_of[u] != t || pu == pv) continue;
-      if (a.vstate[u] == VS_OUT && u < v) continue;   // counted from u
-      qw_dec(a, pv, pu);
-      qw_dec(a, pu, pv);
+    const int32_t pb = a.q_rowptr[pv], pe = a.q_rowptr[pv + 1];
+    // ND_BATCH edges per round: their ends, then the ends' node, patch and
+    // state, then both quotient entries of every qualifying edge by binary
+    // searches run in lockstep (independent loads per step)
+    const int32_t e1 = a.rowptr[v + 1];
+    for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += ND_BATCH) {
+      int32_t u[ND_BATCH], pu[ND_BATCH], nt[ND_BATCH];
+      int8_t st[ND_BATCH];
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) {
+        pu[k] = u[k] >= 0 ? a.gmap[u[k]] : -1;
+        nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
+        st[k] = u[k] >= 0 ? a.vstate[u[k]] : (int8_t)VS_NONE;
+      }
+      int32_t lo1[ND_BATCH], hi1[ND_BATCH], lo2[ND_BATCH], hi2[ND_BATCH];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k) {
+        // an edge to another patch of the same node; one between two
+        // separator vertices is counted from its smaller-id end only
+        const bool q = u[k] >= 0 && nt[k] == t && pu[k] != pv && !(st[k] == VS_OUT && u[k] < v);
+        if (!q) u[k] = -1;
+        any |= q;
+        lo1[k] = pb;
+        hi1[k] = q ? pe : pb;
+        lo2[k] = q ? a.q_rowptr[pu[k]] : 0;
+        hi2[k] = q ? a.q_rowptr[pu[k] + 1] : 0;
+      }
+      if (!any) continue;
+      for (;;) {
+        bool more = false;
+        int32_t m1[ND_BATCH], m2[ND_BATCH], c1[ND_BATCH], c2[ND_BATCH];
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          m1[k] = (lo1[k] + hi1[k]) >> 1;
+          m2[k] = (lo2[k] + hi2[k]) >> 1;
+          c1[k] = lo1[k] < hi1[k] ? a.q_col[m1[k]] : 0;
+          c2[k] = lo2[k] < hi2[k] ? a.q_col[m2[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          if (lo1[k] < hi1[k]) {
+            if (c1[k] < pu[k]) lo1[k] = m1[k] + 1; else hi1[k] = m1[k];
+          }
+          if (lo2[k] < hi2[k]) {
+            if (c2[k] < pv) lo2[k] = m2[k] + 1; else hi2[k] = m2[k];
+          }
+          more |= lo1[k] < hi1[k] || lo2[k] < hi2[k];
+        }
+        if (!more) break;
+      }
+#pragma unroll
+      for (int k = 0; k < ND_BATCH; ++k)
+        if (u[k] >= 0) {
+          atomicSub(&a.q_w[lo1[k]], 1);
+          atomicSub(&a.q_w[lo2[k]], 1);
+        }
     }
   }
 }
