@@ -260,9 +260,24 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       const int32_t p = Lg[i];
       int32_t c = 0;
       const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
-      for (int32_t e = e0; e < e1; ++e) {
-        const int32_t q = a.q_col[e];
-        if (a.q_w[e] > 0 && a.patch_node[q] == t) a.ladj[e0 + c++] = a.loc[q];
+      // ND_BATCH quotient edges per round: their ends and weights, then the
+      // ends' node and local index
+      for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
+        int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
+          wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          const bool live = q[k] >= 0 && wq[k] > 0;
+          nq[k] = live ? a.patch_node[q[k]] : -1;
+          lq[k] = live ? a.loc[q[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k)
+          if (nq[k] == t) a.ladj[e0 + c++] = lq[k];
       }
       a.ldeg[base + i] = c;
       a.lbeg[base + i] = e0;
