@@ -874,6 +874,7 @@ fp_status run_local_order(fp_handle* h) {
   if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
   int32_t st = 0;
   FP_TRY(sync_status(h, &st));
+  if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
   // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
   // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3], early;

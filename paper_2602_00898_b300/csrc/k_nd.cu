@@ -759,9 +759,9 @@ fp_status run_nested_dissection(fp_handle* h) {
     // the nodes of depth d are final now
     FP_TRY(launch_early_md(h, d));
   }
-  int32_t st = 0;
-  FP_TRY(sync_status(h, &st));
-  if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
+  // no host sync here: a quotient overflow (ST_QUOTIENT_TOO_BIG, the patch
+  // keeps no quotient edges, every node index stays in range) is reported by
+  // the ordering stage's first sync, before any ordering kernel runs
   for (void* p : {(void*)psize, (void*)pstart, (void*)pfill, (void*)pverts, (void*)qdeg, (void*)q_rowptr, (void*)q_col,
                   (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
                   (void*)ldeg, (void*)lvl, (void*)lbeg, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
