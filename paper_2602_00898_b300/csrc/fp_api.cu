@@ -118,6 +118,39 @@ fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what) {
   return fail(h, FP_ERR_CUDA, m);
 }
 
+// Page-locked status words of the handles, carved from slabs that are
+// allocated once and never returned: page-locking (and unlocking) memory per
+// handle costs tens of microseconds and synchronises the device.
+struct StatusWords {
+  std::mutex mu;
+  std::vector<int32_t*> free_words;
+};
+StatusWords& status_words() {
+  static StatusWords sw;
+  return sw;
+}
+int32_t* status_word_take() {
+  StatusWords& sw = status_words();
+  std::lock_guard<std::mutex> lk(sw.mu);
+  if (sw.free_words.empty()) {
+    constexpr int SLAB = 1024;
+    int32_t* slab = nullptr;
+    if (cudaMallocHost(&slab, SLAB * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = SLAB - 1; i >= 0; --i) sw.free_words.push_back(slab + i);
+  }
+  int32_t* w = sw.free_words.back();
+  sw.free_words.pop_back();
+  return w;
+}
+void status_word_give(int32_t* w) {
+  StatusWords& sw = status_words();
+  std::lock_guard<std::mutex> lk(sw.mu);
+  sw.free_words.push_back(w);
+}
+
 int32_t* pinned_scratch() {
   thread_local int32_t* buf = nullptr;
   if (!buf && cudaMallocHost(&buf, 256 * sizeof(int32_t)) != cudaSuccess) {
@@ -189,13 +222,14 @@ fp_status new_handle(const fp_options* opts, void* stream, int32_t n, fp_handle*
   h->opt = *opts;
   h->n = n;
   h->b = opts->dof_per_vertex;
-  if (cudaMallocHost(&h->h_status, sizeof(int32_t)) != cudaSuccess) {
+  h->h_status = status_word_take();
+  if (!h->h_status) {
     delete h;
     return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "pinned status word");
   }
   h->d_status = (int32_t*)dev_alloc(h, sizeof(int32_t));
   if (!h->d_status) {
-    cudaFreeHost(h->h_status);
+    status_word_give(h->h_status);
     delete h;
     return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "status word");
   }
@@ -469,10 +503,10 @@ fp_status fp_destroy(fp_handle* h) {
   if (!h) return FP_OK;
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
-  if (h->h_status) {
-    cudaStreamSynchronize(h->stream);
-    cudaFreeHost(h->h_status);
-  }
+  // stream-ordered frees only: every copy into the status word was waited
+  // for when it was made, and the auxiliary streams' work was joined into
+  // the handle's stream before the call that launched it returned
+  if (h->h_status) status_word_give(h->h_status);
   delete h;
   return FP_OK;
 }
