@@ -101,8 +101,10 @@ fp_status fp_create_from_csr(const int32_t* d_rowptr, const int32_t* d_col, int3
  * [n*b], caller-owned device buffers (either may be NULL to skip it).
  * Synchronises `stream` (the number of patches decides the tree depth).
  * Errors: FP_ERR_UNSUPPORTED (a tree node larger than 32768 vertices, which
- * happens only with a small nd_level or a huge patch_cap), FP_ERR_OUT_OF_MEMORY,
- * FP_ERR_CUDA, FP_ERR_STATE.
+ * happens only with a small nd_level or a huge patch_cap; or a patch with more
+ * than 4096 edges to other patches, counted with multiplicity, which happens
+ * only on graphs far denser than meshes), FP_ERR_OUT_OF_MEMORY, FP_ERR_CUDA,
+ * FP_ERR_STATE.
  */
 fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm);
 

@@ -220,3 +220,73 @@ def test_host_buffer_entry_point():
     np.testing.assert_array_equal(outs[2].numpy(), s.parent)
     np.testing.assert_array_equal(outs[3].numpy(), s.colcount)
     assert (nnz, fl) == (s.nnzL, s.flops)
+
+
+def _sym_rows(n, edges):
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        if u != v:
+            adj[u].add(v)
+            adj[v].add(u)
+    return [sorted(a) for a in adj]
+
+
+def _dense_random(n, p, seed):
+    rng = np.random.default_rng(seed)
+    m = np.triu(rng.random((n, n)) < p, 1)
+    edges = list(zip(*np.nonzero(m)))
+    edges += [(i, i + 1) for i in range(n - 1)]          # connected
+    return _sym_rows(n, edges)
+
+
+# single = one patch, hence one leaf of n vertices and no dissection (checked
+# on the oracle: the seeds are drawn by a hash threshold, so the cap alone
+# does not fix the patch count)
+@pytest.mark.parametrize("kind,n,cap,seed,single", [
+    ("clique", 200, 512, 0, True),
+    ("dense", 33, 1 << 20, 0, True), ("dense", 63, 1 << 20, 0, True), ("dense", 64, 1 << 20, 0, True),
+    ("dense", 65, 1 << 20, 0, True), ("dense", 129, 512, 5, True), ("dense", 512, 1 << 20, 0, True),
+    ("star", 300, 1024, 7, True),
+    ("chords", 512, 1 << 20, 0, True),
+    ("medium", 500, 128, 9, False), ("medium", 400, 96, 10, False),
+    ("medium", 2000, 128, 12, False), ("medium", 3000, 128, 13, False),
+])
+def test_adversarial_graphs_parity(kind, n, cap, seed, single):
+    """Leaves up to the 512-vertex limit with pivot rows of up to 16 non-zero
+    words and hundreds of neighbours, the 64-vertex padding boundaries of the
+    degree scan, a hub of degree n-1, and dense separators whose adjacency
+    lists outgrow the separator kernel (global-row fallback: the 570-vertex
+    separator of the 3000-vertex graph)."""
+    rng = np.random.default_rng(seed)
+    if kind == "clique":
+        rows = [[u for u in range(n) if u != v] for v in range(n)]
+    elif kind == "dense":
+        rows = _dense_random(n, 0.3, seed)
+    elif kind == "medium":
+        rows = _dense_random(n, 20.0 / n, seed)   # mean degree ~20: patch cross edges within capacity
+    elif kind == "star":
+        rows = _sym_rows(n, [(0, v) for v in range(1, n)])
+    else:
+        rows = _sym_rows(n, [(i, i + 1) for i in range(n - 1)] +
+                         [tuple(rng.integers(0, n, 2)) for _ in range(n // 2)])
+    rp, col = _csr_tensors(rows)
+    g = O.graph_from_pattern(np_(rp), np_(col))
+    o = O.order(g, cap, seed=seed)
+    assert (o.k == 1) == single
+    s = O.symbolic(g, o.perm)
+    r = fp.order_csr(rp, col, n, patch_cap=cap, seed=seed)
+    assert_parity(r, o, s)
+
+
+def test_quotient_capacity_error():
+    """A patch with more than 4096 cross-patch edges (a 30%-dense 512-vertex
+    graph cut into two patches) is outside the quotient-graph kernel's
+    capacity: the call fails with FP_ERR_UNSUPPORTED before any ordering
+    kernel runs, and the handle is left unusable."""
+    rows = _dense_random(512, 0.3, 6)
+    rp, col = _csr_tensors(rows)
+    g = O.graph_from_pattern(np_(rp), np_(col))
+    assert O.order(g, 512, seed=6).k == 2
+    with pytest.raises(fp.FpError) as e:
+        fp.order_csr(rp, col, 512, patch_cap=512, seed=6)
+    assert fp.STATUS[e.value.status] == "FP_ERR_UNSUPPORTED" and "cross edges" in str(e.value)
