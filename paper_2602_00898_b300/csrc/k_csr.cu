@@ -214,8 +214,11 @@ inline int grid_for(int64_t n, int threads) {
   return (int)(g < 1 ? 1 : g);
 }
 
-// Shared tail: raw rows [off] -> sorted unique CSR in h->rowptr / h->col.
-fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, int32_t* tmp) {
+// Shared tail: raw rows [off] -> sorted unique CSR in h->rowptr / h->col. The
+// column array is sized for nraw entries (an upper bound of the unique ones);
+// one host sync at the end reads the entry count and the status word
+// (bad_index: the message for ST_BAD_INDEX).
+fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, int32_t* tmp, const char* bad_index) {
   const int32_t n = h->n;
   int32_t* ucnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* long_rows = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
@@ -234,25 +237,25 @@ fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, in
   scan_exclusive(h, ucnt, h->rowptr, n, tmp);
   }
   FP_CHECK_LAUNCH(h, "graph rows");
-  int32_t nnz = 0;
-  cudaError_t e = cudaMemcpyAsync(&nnz, h->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
-  if (e != cudaSuccess) return check_cuda(h, e, "read nnz");
-  int32_t st = 0;
-  FP_TRY(sync_status(h, &st));
-  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, "vertex index out of range");
-  if (st & ST_ROW_TOO_LONG) return fail(h, FP_ERR_UNSUPPORTED, "a vertex has more than 8192 raw adjacency entries");
-  h->nnz = nnz;
-  h->col = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nnz > 0 ? nnz : 1));
+  h->col = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nraw > 0 ? nraw : 1));
   if (!h->col) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph columns");
   if (n > 0) {
     ProfScope ps(FP_PROF_GRAPH, h->stream);
     FP_LAUNCH(h, k_rows_compact, grid_for((int64_t)n * 32, 256), 256, 0, off, raw, n, h->rowptr, h->col);
   }
   FP_CHECK_LAUNCH(h, "graph compact");
+  int32_t* hb = pinned_scratch();
+  if (!hb) return fail(h, FP_ERR_OUT_OF_MEMORY, "pinned scratch");
+  cudaError_t e = cudaMemcpyAsync(hb, h->rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "read nnz");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, bad_index);
+  if (st & ST_ROW_TOO_LONG) return fail(h, FP_ERR_UNSUPPORTED, "a vertex has more than 8192 raw adjacency entries");
+  h->nnz = hb[0];
   dev_free(h, ucnt);
   dev_free(h, long_rows);
   dev_free(h, n_long);
-  (void)nraw;
   return FP_OK;
 }
 
@@ -271,13 +274,11 @@ fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t n
     scan_exclusive(h, cnt, off, n, tmp);
   }
   FP_CHECK_LAUNCH(h, "face count");
-  int32_t st = 0;
-  FP_TRY(sync_status(h, &st));
-  if (st & ST_BAD_INDEX) return fail(h, FP_ERR_INVALID_ARG, "face corner out of range");
-  int32_t nraw = 0;
-  cudaError_t e = cudaMemcpy(&nraw, off + n, sizeof(int32_t), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return check_cuda(h, e, "read raw size");
+  // no host round trip here: every face contributes at most 6 raw entries,
+  // faces with a corner out of range are skipped by both kernels and
+  // reported at the sync that ends the build
   if (6 * nf > INT32_MAX) return fail(h, FP_ERR_UNSUPPORTED, "more than 2^31-1 adjacency entries");
+  const int64_t nraw = 6 * nf;
   int32_t* raw = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nraw > 0 ? nraw : 1));
   if (!raw) return fail(h, FP_ERR_OUT_OF_MEMORY, "raw adjacency");
   {
@@ -285,7 +286,7 @@ fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t n
     fill_i32(h, cnt, 0, n + 1);
     if (nf > 0) FP_LAUNCH(h, k_face_fill, grid_for(nf, 256), 256, 0, d_faces, nf, n, off, cnt, raw);
   }
-  FP_TRY(finish_rows(h, off, raw, nraw, tmp));
+  FP_TRY(finish_rows(h, off, raw, nraw, tmp, "face corner out of range"));
   dev_free(h, cnt);
   dev_free(h, off);
   dev_free(h, tmp);
@@ -313,7 +314,7 @@ fp_status build_graph_from_csr(fp_handle* h, const int32_t* d_rowptr, const int3
   if (!raw) return fail(h, FP_ERR_OUT_OF_MEMORY, "raw adjacency");
   fill_i32(h, cnt, 0, n + 1);
   if (nrows > 0) FP_LAUNCH(h, k_pat_fill, grid_for(nrows, 256), 256, 0, d_rowptr, d_col, nrows, b, off, cnt, raw);
-  FP_TRY(finish_rows(h, off, raw, nraw, tmp));
+  FP_TRY(finish_rows(h, off, raw, nraw, tmp, "column index out of range"));
   if (n > 0) FP_LAUNCH(h, k_check_symmetric, grid_for((int64_t)n * 32, 256), 256, 0, h->rowptr, h->col, n, h->d_status);
   FP_CHECK_LAUNCH(h, "symmetry check");
   FP_TRY(sync_status(h, &st));
