@@ -132,6 +132,21 @@ fp_status fp_get_graph(fp_handle* h, int32_t* d_rowptr, int32_t* d_col);
 fp_status fp_get_patches(fp_handle* h, int32_t* d_gmap, int32_t* h_k);
 
 /*
+ * Supplies the patch partition instead of computing it (Section 4, opening:
+ * with the patches given, the mesh is not needed). d_gmap: int32 [n], caller-
+ * owned device buffer read during this call; d_gmap[v] in [0, k) is the group
+ * of vertex v. Every later fp_permute on h skips the patching step
+ * (Algorithm 1 step 1) and dissects over these groups: they need not be
+ * connected nor bounded in size (tree nodes above 512 vertices use the
+ * separator kernels; above 32768 fp_permute fails with FP_ERR_UNSUPPORTED),
+ * and a label no vertex carries is an empty group that takes no part
+ * (zero weight). patch_cap, seed and lloyd_rounds are then unused.
+ * Errors: FP_ERR_INVALID_ARG (NULL map with n > 0, k < 1, a label outside
+ * [0, k)), FP_ERR_OUT_OF_MEMORY, FP_ERR_STATE. Synchronises the stream.
+ */
+fp_status fp_set_patches(fp_handle* h, const int32_t* d_gmap, int32_t k);
+
+/*
  * After fp_permute: the nested-dissection tree of Section 4.2 stored as a
  * binary tree in a 1-D array (children of node t are 2t+1 and 2t+2).
  * *h_depth = D; the tree has 2^(D+1)-1 nodes. d_node_begin / d_node_size

@@ -57,6 +57,9 @@ def lib():
         L.oracle_order.restype = ctypes.c_int32
         L.oracle_order.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_void_p, i32p, i32p, i32p, i32p,
                                    i32p, i32p, ctypes.c_int32, i32p, i64p]
+        L.oracle_order_given.restype = ctypes.c_int32
+        L.oracle_order_given.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_void_p, i32p, ctypes.c_int32, i32p,
+                                         i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, i32p, i64p]
         L.oracle_symbolic.restype = None
         L.oracle_symbolic.argtypes = [i32p, i32p, ctypes.c_int32, i32p, i32p, i32p, i64p, i64p]
         L.oracle_min_degree_keyed.restype = None
@@ -237,6 +240,34 @@ def order(g: Graph, cap: int, seed: int = 0, lloyd_rounds: int = 2, nd_level: in
     D = int(depth[0])
     nn = (1 << (D + 1)) - 1
     return Ordering(int(k), D, lab[:n], nod[:n], perm[:n], iperm[:n], nb[:nn].copy(), ns[:nn].copy(),
+                    qs[:nn].copy())
+
+
+def order_given(g: Graph, label, k: int, nd_level: int = 0, schedule: int = 0) -> Ordering:
+    """Algorithm 1 steps 2-4 with the patches supplied (Section 4, opening):
+    label[v] in [0, k) is the group of vertex v; groups need not be connected,
+    and an empty group takes no part (zero weight)."""
+    n = g.n
+    given = _i32(label)
+    assert given.shape == (n,)
+    o = _Opts(1, 0, 0, nd_level, schedule)
+    lab = np.zeros(max(n, 1), np.int32); nod = np.zeros(max(n, 1), np.int32)
+    perm = np.zeros(max(n, 1), np.int32); iperm = np.zeros(max(n, 1), np.int32)
+    tree_cap = 4 * max(n, k, 1) + 8
+    if nd_level > 0:
+        tree_cap = max(tree_cap, (1 << (nd_level + 1)))
+    nb = np.zeros(tree_cap, np.int32); ns = np.zeros(tree_cap, np.int32)
+    depth = np.zeros(1, np.int32)
+    qs = np.zeros(tree_cap, np.int64)
+    rp, cp, _keep = _gp(g)
+    r = lib().oracle_order_given(rp, cp, n, ctypes.byref(o), _p(given if n else np.zeros(1, np.int32)), int(k),
+                                 _p(lab), _p(nod), _p(perm), _p(iperm), _p(nb), _p(ns), tree_cap, _p(depth),
+                                 _p(qs, ctypes.c_int64))
+    if r < 0:
+        raise ValueError(f"oracle_order_given failed ({r})")
+    D = int(depth[0])
+    nn = (1 << (D + 1)) - 1
+    return Ordering(int(r), D, lab[:n], nod[:n], perm[:n], iperm[:n], nb[:nn].copy(), ns[:nn].copy(),
                     qs[:nn].copy())
 
 

@@ -646,20 +646,14 @@ void oracle_local_orders_keyed(const int32_t* rowptr, const int32_t* col, int32_
 // r*gamma + v, as for the patch seeds).
 uint32_t oracle_tie_key(uint64_t r, int32_t v) { return (uint32_t)(seed_hash(r, v) >> 32); }
 
-// Algorithm 1: patches -> etree -> perm. Outputs (all caller-allocated):
-// label[n] (gmap), node_of[n], perm[n], iperm[n], node_begin/node_size
-// [tree_cap] (positions in perm per tree node), *depth_out. Returns k, or a
-// negative code: -1 bad options, -3 tree_cap too small.
-// node_qsum (nullable, [tree_cap]): for each bisected node, the sum of the
-// quotient edge weights w(p,q) over ordered pairs of its patches at the time
-// it is bisected; -1 for leaves and unused nodes.
-int32_t oracle_order(const int32_t* rowptr, const int32_t* col, int32_t n, const oracle_opts* o,
-                     int32_t* label, int32_t* node_of, int32_t* perm, int32_t* iperm,
-                     int32_t* node_begin, int32_t* node_size, int32_t tree_cap, int32_t* depth_out,
-                     int64_t* node_qsum) {
-  if (o->patch_cap < 1 || o->nd_level < 0 || o->lloyd_rounds < 0) return -1;
-  Adj a = adj_from_csr(rowptr, col, n);
-  Patching P = get_patches(a, o->patch_cap, o->seed, o->lloyd_rounds);
+}  // extern "C"
+
+// Algorithm 1 steps 2-4 for given patches: etree (Algorithm 2), local orders
+// and their concatenation (Algorithm 3). Outputs as for oracle_order.
+static int32_t order_from_patches(const Adj& a, int32_t n, const Patching& P, const oracle_opts* o,
+                                  int32_t* label, int32_t* node_of, int32_t* perm, int32_t* iperm,
+                                  int32_t* node_begin, int32_t* node_size, int32_t tree_cap, int32_t* depth_out,
+                                  int64_t* node_qsum) {
   int32_t D = o->nd_level > 0 ? o->nd_level : ceil_log2(P.k);
   int64_t nnodes = ((int64_t)1 << (D + 1)) - 1;
   if (nnodes > tree_cap) return -3;
@@ -693,6 +687,46 @@ int32_t oracle_order(const int32_t* rowptr, const int32_t* col, int32_t n, const
       node_qsum[t] = it == nd.qsum_at.end() ? -1 : it->second;
     }
   return P.k;
+}
+
+extern "C" {
+
+// Algorithm 1: patches -> etree -> perm. Outputs (all caller-allocated):
+// label[n] (gmap), node_of[n], perm[n], iperm[n], node_begin/node_size
+// [tree_cap] (positions in perm per tree node), *depth_out. Returns k, or a
+// negative code: -1 bad options, -3 tree_cap too small.
+// node_qsum (nullable, [tree_cap]): for each bisected node, the sum of the
+// quotient edge weights w(p,q) over ordered pairs of its patches at the time
+// it is bisected; -1 for leaves and unused nodes.
+int32_t oracle_order(const int32_t* rowptr, const int32_t* col, int32_t n, const oracle_opts* o,
+                     int32_t* label, int32_t* node_of, int32_t* perm, int32_t* iperm,
+                     int32_t* node_begin, int32_t* node_size, int32_t tree_cap, int32_t* depth_out,
+                     int64_t* node_qsum) {
+  if (o->patch_cap < 1 || o->nd_level < 0 || o->lloyd_rounds < 0) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  Patching P = get_patches(a, o->patch_cap, o->seed, o->lloyd_rounds);
+  return order_from_patches(a, n, P, o, label, node_of, perm, iperm, node_begin, node_size, tree_cap, depth_out,
+                            node_qsum);
+}
+
+// Algorithm 1 with the patches supplied (Section 4, opening: given a patch
+// partition, the mesh is not needed): given[v] in [0, k) is the patch of
+// vertex v. Groups need not be connected; an empty group has zero weight and
+// takes no part in the dissection. patch_cap, seed and lloyd_rounds of `o`
+// are not used. Returns k, or -1 (bad options or a label out of range), -3.
+int32_t oracle_order_given(const int32_t* rowptr, const int32_t* col, int32_t n, const oracle_opts* o,
+                           const int32_t* given, int32_t k, int32_t* label, int32_t* node_of, int32_t* perm,
+                           int32_t* iperm, int32_t* node_begin, int32_t* node_size, int32_t tree_cap,
+                           int32_t* depth_out, int64_t* node_qsum) {
+  if (k < 1 || o->nd_level < 0) return -1;
+  for (int32_t v = 0; v < n; ++v)
+    if (given[v] < 0 || given[v] >= k) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  Patching P;
+  P.k = k;
+  P.label.assign(given, given + n);
+  return order_from_patches(a, n, P, o, label, node_of, perm, iperm, node_begin, node_size, tree_cap, depth_out,
+                            node_qsum);
 }
 
 // Elimination tree and column counts of P (G + I) P^T.

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             "fp_get_sizes": (i32, [vp, P32, P32, P64]),
             "fp_get_graph": (i32, [vp, vp, vp]),
             "fp_get_patches": (i32, [vp, vp, P32]),
+            "fp_set_patches": (i32, [vp, vp, i32]),
             "fp_get_tree": (i32, [vp, P32, vp, vp, vp]),
             "fp_order_faces_host": (i32, [vp, i64, i32, opt, vp, vp, vp, vp, vp, P64, P64]),
             "fp_destroy": (i32, [vp]),
@@ -160,6 +161,12 @@ def fp_get_patches(h, gmap=None) -> int:
     k = ctypes.c_int32()
     _check(lib().fp_get_patches(h, _ptr(gmap), ctypes.byref(k)), h)
     return k.value
+
+
+def fp_set_patches(h, gmap, k: int):
+    """Supplies the patch of every vertex (int32 CUDA tensor, values in [0, k));
+    later fp_permute calls dissect over these groups instead of patching."""
+    _check(lib().fp_set_patches(h, _ptr(gmap), int(k)), h)
 
 
 def fp_get_tree(h, node_begin=None, node_size=None, node_of=None) -> int:
@@ -353,25 +360,31 @@ def fp_gnn_quantise(params, codes, stream=None):
     _check(lib().fp_gnn_quantise(_ptr(params), _ptr(codes), _stream(stream)))
 
 
-def order_faces(faces, n_vertices: int, stream=None, symbolic: bool = True, net=None, **opt) -> Result:
+def order_faces(faces, n_vertices: int, stream=None, symbolic: bool = True, net=None, gmap=None, k=None,
+                **opt) -> Result:
     """Create + permute (+ symbolic) for a CUDA face tensor; returns every output
     as CUDA tensors (perm/iperm/parent/colcount at DOF level, the rest at
-    vertex level). net: optional priority-network codes (learned leaf orders)."""
+    vertex level). net: optional priority-network codes (learned leaf orders);
+    gmap, k: optional supplied patches (fp_set_patches)."""
     import torch
     o = fp_default_options(**opt)
     h = fp_create_from_faces(faces, n_vertices, o, stream)
     try:
         if net is not None:
             fp_set_priority_net(h, net)
+        if gmap is not None:
+            fp_set_patches(h, gmap, k)
         return _run(h, n_vertices, o, stream, symbolic)
     finally:
         fp_destroy(h)
 
 
-def order_csr(rowptr, col, n_rows: int, stream=None, symbolic: bool = True, **opt) -> Result:
+def order_csr(rowptr, col, n_rows: int, stream=None, symbolic: bool = True, gmap=None, k=None, **opt) -> Result:
     o = fp_default_options(**opt)
     h = fp_create_from_csr(rowptr, col, n_rows, o, stream)
     try:
+        if gmap is not None:
+            fp_set_patches(h, gmap, k)
         return _run(h, n_rows // o.dof_per_vertex, o, stream, symbolic)
     finally:
         fp_destroy(h)

@@ -306,7 +306,13 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
   if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
   if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
   h->permuted = false;
-  FP_TRY(run_patching(h));
+  if (h->user_k > 0) {
+    // patches supplied by the caller (fp_set_patches)
+    h->k = h->user_k;
+    if (h->n > 0) cudaMemcpyAsync(h->gmap, h->user_gmap, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream);
+  } else {
+    FP_TRY(run_patching(h));
+  }
   FP_TRY(run_nested_dissection(h));
   h->nnodes = ((int64_t)1 << (h->D + 1)) - 1;
   if (h->nnodes > h->node_cap) {
@@ -448,6 +454,44 @@ fp_status fp_get_patches(fp_handle* h, int32_t* d_gmap, int32_t* h_k) {
   if (d_gmap && h->n) cudaMemcpyAsync(d_gmap, h->gmap, sizeof(int32_t) * h->n, cudaMemcpyDeviceToDevice, h->stream);
   if (h_k) *h_k = h->k;
   FP_CHECK_LAUNCH(h, "get patches");
+  return FP_OK;
+}
+
+namespace fp {
+// Copies a caller's patch map, flagging labels outside [0, k).
+__global__ void k_copy_labels(const int32_t* __restrict__ g, int32_t n, int32_t k, int32_t* __restrict__ out,
+                              int32_t* status) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t p = g[v];
+    if (p < 0 || p >= k) atomicOr(status, ST_BAD_INDEX);
+    out[v] = p;
+  }
+}
+}  // namespace fp
+
+fp_status fp_set_patches(fp_handle* h, const int32_t* d_gmap, int32_t k) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (k < 1 || (h->n > 0 && !d_gmap)) return fail(h, FP_ERR_INVALID_ARG, "patch map: NULL map or k < 1");
+  if (!h->user_gmap) {
+    h->user_gmap = (int32_t*)dev_alloc(h, sizeof(int32_t) * (h->n > 0 ? h->n : 1));
+    if (!h->user_gmap) return fail(h, FP_ERR_OUT_OF_MEMORY, "patch map");
+  }
+  if (h->n > 0) {
+    int64_t g = ((int64_t)h->n + 255) / 256;
+    if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
+    FP_LAUNCH(h, k_copy_labels, (int)g, 256, 0, d_gmap, h->n, k, h->user_gmap, h->d_status);
+  }
+  FP_CHECK_LAUNCH(h, "patch map");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  h->permuted = false;
+  if (st & ST_BAD_INDEX) {
+    h->user_k = 0;
+    cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream);
+    return fail(h, FP_ERR_INVALID_ARG, "patch map: a label outside [0, k)");
+  }
+  h->user_k = k;
   return FP_OK;
 }
 

@@ -84,6 +84,10 @@ struct fp_handle {
   int32_t *early_rank = nullptr, *early_list = nullptr, *early_start = nullptr, *early_cnt = nullptr;
   int32_t *early_fill = nullptr, *early_ovf = nullptr, *early_loc = nullptr, *early_base = nullptr;
 
+  // patches supplied by the caller (fp_set_patches): device copy and count
+  int32_t* user_gmap = nullptr;
+  int32_t user_k = 0;
+
   // a10 learned priorities
   int32_t* qnet = nullptr;        // device codes [FP_GNN_NPARAMS], or null (plain)
   int32_t* scores = nullptr;      // optional per-position score output of the learned pass

@@ -638,6 +638,11 @@ __global__ void k_nd_move_patches(LevelArgs a) {
 }
 
 
+__global__ void k_patch_node_init(const int32_t* __restrict__ psize, int32_t k, int32_t* __restrict__ patch_node) {
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+    patch_node[p] = psize[p] > 0 ? 0 : -1;
+}
+
 __global__ void k_zero_i8(int8_t* p, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
 }
@@ -693,8 +698,9 @@ fp_status run_nested_dissection(fp_handle* h) {
   scan_exclusive(h, qdeg, q_rowptr, k, tmp);
   FP_LAUNCH(h, k_quotient_rows<true>, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, q_rowptr, qdeg,
             q_col, q_w, h->d_status);
-  // state
-  fill_i32(h, patch_node, 0, k);
+  // state: every patch with vertices starts in the root; an empty one (a
+  // label of a supplied patch map that no vertex carries) takes no part
+  FP_LAUNCH(h, k_patch_node_init, GK, 256, 0, psize, k, patch_node);
   cudaMemcpyAsync(w, psize, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, h->stream);
   FP_LAUNCH(h, k_zero_i8, G, 256, 0, final_, (int64_t)n);
   FP_LAUNCH(h, k_zero_i8, G, 256, 0, vstate, (int64_t)n);

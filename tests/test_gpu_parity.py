@@ -290,3 +290,69 @@ def test_quotient_capacity_error():
     with pytest.raises(fp.FpError) as e:
         fp.order_csr(rp, col, 512, patch_cap=512, seed=6)
     assert fp.STATUS[e.value.status] == "FP_ERR_UNSUPPORTED" and "cross edges" in str(e.value)
+
+
+def _oracle_given(g, label, k, **kw):
+    o = O.order_given(g, label, k, **kw)
+    return o, O.symbolic(g, o.perm)
+
+
+@pytest.mark.parametrize("case", ["computed", "scattered", "empty_labels", "one_group_large", "strips4", "strips2"])
+def test_supplied_patches_parity(case):
+    """fp_set_patches (Section 4, opening: the patch partition may be
+    supplied) against the oracle's order_given: the method's own patches,
+    scattered disconnected groups, labels no vertex carries (empty groups),
+    one group of 4,096 vertices (a single separator-kernel node), and strips
+    of an unshuffled 100x100 grid: four (leaves of ~2,400 vertices, separator
+    kernel) and two (leaves of ~4,900, global-row kernel)."""
+    if case in ("computed", "scattered", "empty_labels"):
+        mesh = M.shuffle(M.torus(30, 22, 0.3, 9), 9)
+    elif case == "one_group_large":
+        mesh = M.grid64(1)
+    else:
+        mesh = M.grid(100, 100)        # unshuffled: index ranges are strips of rows
+    g = O.graph_from_faces(mesh.faces, mesh.n)
+    n = g.n
+    if case == "computed":
+        oc = O.order(g, 60, seed=9)
+        label, k = oc.label, oc.k
+    elif case == "scattered":
+        label, k = (np.arange(n) * 7919 % 13).astype(np.int32), 13
+    elif case == "empty_labels":
+        label = (np.arange(n) * 104729 % 40).astype(np.int32)
+        label[label % 3 == 1] = 0                 # labels 1, 4, 7, ... left empty
+        k = 40
+    elif case == "one_group_large":
+        label, k = np.zeros(n, np.int32), 1
+    else:
+        k = 4 if case == "strips4" else 2
+        label = (np.arange(n) * k // n).astype(np.int32)
+    o, s = _oracle_given(g, label, k)
+    faces = torch.from_numpy(np.ascontiguousarray(mesh.faces)).cuda()
+    r = fp.order_faces(faces, mesh.n, gmap=torch.from_numpy(np.ascontiguousarray(label, np.int32)).cuda(), k=k)
+    assert_parity(r, o, s)
+
+
+def test_supplied_patches_errors_and_reuse():
+    mesh = M.grid(64, 64)                  # unshuffled: index ranges are strips of rows
+    faces = torch.from_numpy(np.ascontiguousarray(mesh.faces)).cuda()
+    h = fp.fp_create_from_faces(faces, mesh.n)
+    try:
+        bad = torch.full((mesh.n,), 5, dtype=torch.int32, device="cuda")
+        with pytest.raises(fp.FpError) as e:
+            fp.fp_set_patches(h, bad, 5)
+        assert fp.STATUS[e.value.status] == "FP_ERR_INVALID_ARG"
+        with pytest.raises(fp.FpError):
+            fp.fp_set_patches(h, bad, 0)
+        # the handle stays usable: computed patches, then supplied ones
+        perm = torch.empty(mesh.n, dtype=torch.int32, device="cuda")
+        fp.fp_permute(h, perm)
+        g = O.graph_from_faces(mesh.faces, mesh.n)
+        o = O.order(g, 512, seed=0)
+        assert np.array_equal(np_(perm), o.perm)
+        lab = (np.arange(mesh.n) * 3 // mesh.n).astype(np.int32)
+        fp.fp_set_patches(h, torch.from_numpy(lab).cuda(), 3)
+        fp.fp_permute(h, perm)
+        assert np.array_equal(np_(perm), O.order_given(g, lab, 3).perm)
+    finally:
+        fp.fp_destroy(h)

@@ -442,3 +442,27 @@ def test_empty_and_tiny_inputs():
     check_nd_invariants(g, o)
     s = O.symbolic(g, o.perm)
     assert s.nnzL == 7 and np.all(s.parent == -1)
+
+
+def test_supplied_patches():
+    """Algorithm 1 with the patch partition supplied (Section 4, opening):
+    given the patches the method computes itself it reproduces them exactly;
+    one group is plain minimum degree of G; disconnected groups and empty
+    labels (zero-weight patches, which take no part) still give a valid
+    dissection."""
+    mesh = M.shuffle(M.torus(30, 22, 0.3, 9), 9)
+    g = _faces_graph(mesh)
+    o = O.order(g, 60, seed=9)
+    same = O.order_given(g, o.label, o.k)
+    for f in ("label", "node_of", "perm", "iperm", "node_begin", "node_size"):
+        assert np.array_equal(getattr(o, f), getattr(same, f)), f
+    one = O.order_given(g, np.zeros(g.n, np.int32), 1)
+    assert one.depth == 0 and np.array_equal(one.perm, O.min_degree(g))
+    lab = (np.arange(g.n) * 7919 % 13).astype(np.int32)        # 13 scattered, disconnected groups
+    lab[lab == 5] = 3                                           # label 5 left empty
+    d = O.order_given(g, lab, 13)
+    assert d.k == 13 and np.array_equal(d.label, lab)
+    assert np.array_equal(np.sort(d.perm), np.arange(g.n))
+    check_nd_invariants(g, d)
+    with pytest.raises(ValueError):
+        O.order_given(g, np.full(g.n, 13, np.int32), 13)
