@@ -113,10 +113,10 @@ def dist_env():
     return ws, rank, lrank
 
 
-def make_mesh(name):
+def make_mesh(name, cap_override=None):
     import meshgen
     gen, cap, dof = WORKLOADS[name]
-    return getattr(meshgen, gen)(0), cap, dof
+    return getattr(meshgen, gen)(0), (cap_override or cap), dof
 
 
 class Clocks:
@@ -197,7 +197,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    mesh, cap, dof = make_mesh(args.workload)
+    mesh, cap, dof = make_mesh(args.workload, args.patch_cap)
     for _ in range(args.warmup):
         oracle_step(mesh, cap, dof)
     times = []
@@ -229,7 +229,7 @@ def run_ours(args):
         torch.cuda.set_device(lrank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
     dev = torch.device("cuda", torch.cuda.current_device())
-    mesh, cap, dof = make_mesh(args.workload)
+    mesh, cap, dof = make_mesh(args.workload, args.patch_cap)
     n = mesh.n
     faces = torch.from_numpy(mesh.faces).to(dev)
     opts = fp.fp_default_options(patch_cap=cap, dof_per_vertex=dof)
@@ -510,6 +510,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256", "batch256_learned"], default="icosphere7")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--patch-cap", type=int, default=None,
+                    help="patch cap of a single-mesh workload instead of its default (patch-size studies)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
