@@ -300,8 +300,11 @@ struct LocalArgs {
   int32_t cap;
 };
 
+// Mode 0 visits every patch: five CTAs per SM keep one wave for a mesh of
+// ~700 patches; modes 1 and 2 run on the few oversize patches only and may
+// use more registers (four CTAs per SM) instead of spilling.
 template <int kMode>
-__global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
+__global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_local(LocalArgs a) {
   __shared__ int32_t s_verts[LOCAL_SMEM_V];
   __shared__ int32_t s_lrow[LOCAL_SMEM_V + 1];
   __shared__ uint32_t s_dist[LOCAL_SMEM_V];
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
   __shared__ uint16_t s_adj[LOCAL_SMEM_E];
   __shared__ int32_t red[40];
   __shared__ unsigned long long red64[40];
-  __shared__ int32_t s_nf;
+  __shared__ int32_t s_cnt[3];
   const int tid = threadIdx.x;
   for (int32_t p = blockIdx.x; p < a.k; p += gridDim.x) {
     if (kMode != 0 && !a.over[p]) continue;
@@ -323,82 +326,132 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_patch_local(LocalArgs a) {
     uint32_t* dist = small ? s_dist : (uint32_t*)(gv + m + 1);
     int32_t* fa = small ? s_fa : gv + 2 * m + 1;
     int32_t* fb = small ? s_fb : gv + 3 * m + 1;
-    if (small)
-      for (int32_t i = tid; i < m; i += LOCAL_THREADS) s_verts[i] = a.pverts[v0 + i];
-    __syncthreads();
     for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
-      a.loc[verts[i]] = i;
-      dist[i] = 0xffffffffu;
+      const int32_t v = a.pverts[v0 + i];
+      if (small) s_verts[i] = v;
+      a.loc[v] = i;
     }
     __syncthreads();
-    // internal adjacency as a local CSR
+    // internal adjacency as a local CSR: one gather of every vertex's
+    // neighbours' patches gives its internal degree and (mode 0) whether it
+    // lies on the patch boundary, the BFS sources of that mode
     int32_t carry = 0;
     for (int32_t i0 = 0; i0 < m; i0 += LOCAL_THREADS) {
       const int32_t i = i0 + tid;
       int32_t c = 0;
-      if (i < m) for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t, int32_t lu) { c += lu == p; });
+      bool bnd = false;
+      if (i < m)
+        for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t, int32_t lu) {
+          if (lu == p) ++c;
+          else bnd = true;
+        });
       int32_t tot;
       const int32_t ex = block_excl_scan_i32(c, &tot, red);
-      if (i < m) lrow[i] = carry + ex;
+      if (i < m) {
+        lrow[i] = carry + ex;
+        dist[i] = (kMode == 0 && bnd) ? 0u : 0xffffffffu;
+      }
       carry += tot;
     }
     if (tid == 0) lrow[m] = carry;
     __syncthreads();
+    // rows: eight neighbours a round (ids, then their patch, then the local
+    // index of the internal ones)
     for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
       int32_t o = lrow[i];
-      for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t u, int32_t lu) {
-        if (lu != p) return;
-        const int32_t j = a.loc[u];
-        if (small) s_adj[o++] = (uint16_t)j; else a.g_adj[e0 + o++] = j;
-      });
+      const int32_t v = verts[i];
+      const int32_t ee = a.rowptr[v + 1];
+      for (int32_t eb = a.rowptr[v]; eb < ee; eb += 8) {
+        int32_t u[8], j[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) u[k] = eb + k < ee ? a.col[eb + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) j[k] = u[k] >= 0 ? a.label[u[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) j[k] = j[k] == p ? a.loc[u[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (j[k] >= 0) {
+            if (small) s_adj[o++] = (uint16_t)j[k]; else a.g_adj[e0 + o++] = j[k];
+          }
+      }
     }
-    // sources
-    if (tid == 0) s_nf = 0;
+    // sources; the BFS counts level L's frontier in s_cnt[L % 3]
+    if (tid == 0) {
+      s_cnt[0] = 0;
+      s_cnt[1] = 0;
+      s_cnt[2] = 0;
+    }
     __syncthreads();
     if (kMode == 0) {
-      for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
-        bool bnd = false;
-        for_row_gather<8>(a.rowptr, a.col, verts[i], a.label, [&](int32_t, int32_t lu) { bnd |= lu != p; });
-        if (bnd) { dist[i] = 0u; fa[atomicAdd(&s_nf, 1)] = i; }
-      }
+      for (int32_t i = tid; i < m; i += LOCAL_THREADS)
+        if (dist[i] == 0u) fa[atomicAdd(&s_cnt[0], 1)] = i;
     } else if (tid == 0) {
       const int32_t i = a.loc[a.seed_of[p]];
       dist[i] = 0u;
       fa[0] = i;
-      s_nf = 1;
+      s_cnt[0] = 1;
       if (kMode == 2) {
         const int32_t j = a.loc[a.seed_of[a.kbase + a.orank[p]]];
         dist[j] = 1u;             // packed (dist << 1 | second seed)
         fa[1] = j;
-        s_nf = 2;
+        s_cnt[0] = 2;
       }
     }
     __syncthreads();
-    // level-synchronous BFS; mode 2 packs (dist << 1 | which seed) and keeps the min
-    int32_t nf = s_nf;
-    for (uint32_t level = 0; nf > 0; ++level) {
-      __syncthreads();
-      if (tid == 0) s_nf = 0;
-      __syncthreads();
-      for (int32_t i = tid; i < nf; i += LOCAL_THREADS) {
-        const int32_t u = fa[i];
-        const int32_t r0 = lrow[u], r1 = lrow[u + 1];
-        if (kMode == 2) {
-          const uint32_t cand = ((level + 1) << 1) | (dist[u] & 1u);
-          for (int32_t r = r0; r < r1; ++r) {
-            const int32_t w = small ? (int32_t)s_adj[r] : a.g_adj[e0 + r];
-            if ((dist[w] >> 1) <= level) continue;
-            if (atomicMin(&dist[w], cand) == 0xffffffffu) fb[atomicAdd(&s_nf, 1)] = w;
+    // level-synchronous BFS, one CTA barrier a level: eight edges a round
+    // per frontier vertex, a warp's claims appended with one atomicAdd
+    // (offsets by bit-plane ballots); mode 2 packs (dist << 1 | which seed)
+    // and keeps the minimum
+    const int lane = tid & 31;
+    const unsigned lt = lanemask_lt();
+    for (uint32_t level = 0;; ++level) {
+      const int32_t nf = s_cnt[level % 3];
+      if (nf == 0) break;
+      if (tid == 0) s_cnt[(level + 2) % 3] = 0;
+      for (int32_t i0 = 0; i0 < nf; i0 += LOCAL_THREADS) {
+        const int32_t i = i0 + tid;
+        int32_t r0 = 0, r1 = 0;
+        uint32_t cand = 0;
+        if (i < nf) {
+          const int32_t u = fa[i];
+          r0 = lrow[u];
+          r1 = lrow[u + 1];
+          cand = kMode == 2 ? (((level + 1) << 1) | (dist[u] & 1u)) : level + 1;
+        }
+        while (__any_sync(0xffffffffu, r0 < r1)) {
+          int32_t w[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            w[k] = r0 + k < r1 ? (small ? (int32_t)s_adj[r0 + k] : a.g_adj[e0 + r0 + k]) : -1;
+          uint32_t claim = 0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (w[k] < 0) continue;
+            if (kMode == 2) {
+              if ((dist[w[k]] >> 1) > level && atomicMin(&dist[w[k]], cand) == 0xffffffffu) claim |= 1u << k;
+            } else {
+              if (atomicCAS(&dist[w[k]], 0xffffffffu, cand) == 0xffffffffu) claim |= 1u << k;
+            }
           }
-        } else {
-          for (int32_t r = r0; r < r1; ++r) {
-            const int32_t w = small ? (int32_t)s_adj[r] : a.g_adj[e0 + r];
-            if (atomicCAS(&dist[w], 0xffffffffu, level + 1) == 0xffffffffu) fb[atomicAdd(&s_nf, 1)] = w;
+          const int32_t c = __popc(claim);
+          int32_t ex = 0, tot = 0;
+#pragma unroll
+          for (int bp = 0; bp < 4; ++bp) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (c >> bp) & 1);
+            ex += __popc(bb & lt) << bp;
+            tot += __popc(bb) << bp;
           }
+          int32_t base = 0;
+          if (lane == 0 && tot) base = atomicAdd(&s_cnt[(level + 1) % 3], tot);
+          base = __shfl_sync(0xffffffffu, base, 0) + ex;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (claim >> k & 1u) fb[base++] = w[k];
+          r0 += 8;
         }
       }
       __syncthreads();
-      nf = s_nf;
       int32_t* t = fa; fa = fb; fb = t;
     }
     __syncthreads();
