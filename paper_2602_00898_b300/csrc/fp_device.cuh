@@ -141,44 +141,26 @@ __device__ __forceinline__ void bitonic_sort(T* buf, int N, int tid, int nthr) {
     }
 }
 
-// Bitonic sort (Batcher, AFIPS 1968) of 32*E keys held in registers by one
-// warp, ascending: lane L holds the keys of positions L*E .. L*E+E-1. Partners
-// less than E apart are in the same lane, farther ones E*2^s apart are in lane
-// L ^ 2^s and are exchanged with a shuffle.
-template <int E, class T>
-__device__ __forceinline__ void warp_sort_regs(T (&x)[E], int lane) {
-  constexpr int LOGN = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16) + (E >= 32);
-  static_assert((32 * E) == (1 << LOGN), "E must be a power of two <= 32");
+// Bitonic sort (Batcher, AFIPS 1968) of N keys (a power of two) held in one
+// thread's registers, ascending: every index is a compile-time constant, so
+// the array stays in registers.
+template <int N, class T>
+__device__ __forceinline__ void thread_sort_regs(T (&x)[N]) {
 #pragma unroll
-  for (int kk = 1; kk <= LOGN; ++kk) {
-    const int k = 1 << kk;
+  for (int k = 2; k <= N; k <<= 1)
 #pragma unroll
-    for (int jj = kk - 1; jj >= 0; --jj) {
-      const int j = 1 << jj;
-      if (j >= E) {
-        const int lm = j / E;
-        // k > j >= E: the direction depends on the lane only
-        const bool up = ((lane * E) & k) == 0;
-        const bool keep_min = ((lane & lm) == 0) == up;
+    for (int j = k >> 1; j > 0; j >>= 1)
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-          const T y = __shfl_xor_sync(0xffffffffu, x[r], lm);
-          x[r] = keep_min ? (y < x[r] ? y : x[r]) : (y < x[r] ? x[r] : y);
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-          if ((r & j) == 0) {
-            const int s = r | j;
-            const bool up = ((lane * E + r) & k) == 0;
-            const T lo = x[s] < x[r] ? x[s] : x[r], hi = x[s] < x[r] ? x[r] : x[s];
-            x[r] = up ? lo : hi;
-            x[s] = up ? hi : lo;
-          }
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const T a = x[i], c = x[l];
+          const bool sw = up ? (c < a) : (a < c);
+          x[i] = sw ? c : a;
+          x[l] = sw ? a : c;
         }
       }
-    }
-  }
 }
 
 // Calls fn(u, aux[u]) for every neighbour u of v in CSR order. The gathers

@@ -3,12 +3,13 @@
 //
 // No global sort: each corner pair is counted and scattered into its row's
 // raw segment (atomics), then every row is sorted and deduplicated on chip
-// (warp-per-row bitonic sort in shared memory; CTA-per-row for long rows), and
-// the unique entries are compacted. Three streaming passes over the faces and
-// two over the raw rows: HBM-bound.
+// (one thread per row of at most 32 raw entries, sorted in registers; a warp
+// per longer row in shared memory; a CTA per row above 256), and the unique
+// entries are compacted. Three streaming passes over the faces and two over
+// the raw rows: HBM-bound.
 #include <climits>
 
-#include "fp_internal.cuh"
+#include "fp_device.cuh"
 
 namespace fp {
 namespace {
@@ -86,39 +87,56 @@ __global__ void k_pat_fill(const int32_t* __restrict__ rp, const int32_t* __rest
 
 // ---- row sort + dedupe ----------------------------------------------------------------
 
-// Ascending bitonic sort of buf[0..N) (N a power of two) by the threads
-// [t0, t0 + nthr) of a warp (sync = __syncwarp) or a CTA (sync = __syncthreads).
-template <bool kBlock>
-__device__ __forceinline__ void bitonic_sort(int32_t* buf, int N, int tid, int nthr) {
-  for (int k = 2; k <= N; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < N; i += nthr) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          int32_t a = buf[i], c = buf[ixj];
-          bool up = (i & k) == 0;
-          if ((a > c) == up) { buf[i] = c; buf[ixj] = a; }
-        }
-      }
-      if (kBlock) __syncthreads(); else __syncwarp();
-    }
-}
-
 __device__ __forceinline__ int next_pow2(int x) {
   int p = 32;
   while (p < x) p <<= 1;
   return p;
 }
 
-// One warp per row: sort the raw segment, write the unique prefix back in
-// place and its length to ucnt. Rows longer than WARP_ROW_CAP are queued.
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_dedupe_warp(const int32_t* __restrict__ off, int32_t n,
-                                                                      int32_t* __restrict__ raw, int32_t* __restrict__ ucnt,
+// Sorts a row of at most N raw entries in registers and writes its unique
+// prefix back in place; returns its length.
+template <int N>
+__device__ __forceinline__ int32_t dedupe_row_regs(int32_t* __restrict__ raw, int32_t b, int32_t L) {
+  int32_t x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = i < L ? raw[b + i] : INT_MAX;
+  thread_sort_regs<N>(x);
+  int32_t c = 0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < L && (i == 0 || x[i] != x[i - 1])) raw[b + c++] = x[i];
+  return c;
+}
+
+// One thread per row of at most 32 raw entries (mesh rows hold about twelve):
+// sort in registers, write the unique prefix back in place and its length to
+// ucnt. Longer rows are listed for the warp kernel.
+__global__ void k_rows_dedupe_thread(const int32_t* __restrict__ off, int32_t n, int32_t* __restrict__ raw,
+                                     int32_t* __restrict__ ucnt, int32_t* __restrict__ mid_rows, int32_t* n_mid) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t b = off[v], L = off[v + 1] - b;
+    if (L > 32) {
+      mid_rows[atomicAdd(n_mid, 1)] = v;
+      continue;
+    }
+    ucnt[v] = L <= 16 ? dedupe_row_regs<16>(raw, b, L) : dedupe_row_regs<32>(raw, b, L);
+  }
+}
+
+// One warp per listed row: sort the raw segment, write the unique prefix back
+// in place and its length to ucnt. Rows longer than WARP_ROW_CAP are queued
+// for the CTA kernel.
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_dedupe_warp(const int32_t* __restrict__ off,
+                                                                      const int32_t* __restrict__ mid_rows,
+                                                                      const int32_t* n_mid, int32_t* __restrict__ raw,
+                                                                      int32_t* __restrict__ ucnt,
                                                                       int32_t* __restrict__ long_rows, int32_t* n_long) {
   __shared__ int32_t sbuf[ROW_WARPS][WARP_ROW_CAP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* buf = sbuf[wid];
-  for (int32_t v = blockIdx.x * ROW_WARPS + wid; v < n; v += gridDim.x * ROW_WARPS) {
+  const int32_t nm = *n_mid;
+  for (int32_t r = blockIdx.x * ROW_WARPS + wid; r < nm; r += gridDim.x * ROW_WARPS) {
+    const int32_t v = mid_rows[r];
     int32_t b = off[v], L = off[v + 1] - b;
     if (L > WARP_ROW_CAP) {
       if (lane == 0) long_rows[atomicAdd(n_long, 1)] = v;
@@ -180,13 +198,13 @@ __global__ void k_rows_dedupe_block(const int32_t* __restrict__ off, const int32
   }
 }
 
-// Copy each row's unique prefix to its final place; warp per row.
+// Copy each row's unique prefix to its final place; thread per row (mesh rows
+// hold about six entries).
 __global__ void k_rows_compact(const int32_t* __restrict__ off, const int32_t* __restrict__ raw, int32_t n,
                                const int32_t* __restrict__ rowptr, int32_t* __restrict__ col) {
-  const int lane = threadIdx.x & 31;
-  for (int32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
-    int32_t s = off[v], d = rowptr[v], L = rowptr[v + 1] - d;
-    for (int i = lane; i < L; i += 32) col[d + i] = raw[s + i];
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int32_t s = off[v], d = rowptr[v], L = rowptr[v + 1] - d;
+    for (int32_t i = 0; i < L; ++i) col[d + i] = raw[s + i];
   }
 }
 
@@ -222,15 +240,18 @@ fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, in
   const int32_t n = h->n;
   int32_t* ucnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* long_rows = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
-  int32_t* n_long = (int32_t*)dev_alloc(h, sizeof(int32_t));
+  int32_t* mid_rows = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
+  int32_t* n_long = (int32_t*)dev_alloc(h, sizeof(int32_t) * 2);     // [0] long rows, [1] mid rows
   h->rowptr = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
-  if (!ucnt || !long_rows || !n_long || !h->rowptr) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
+  if (!ucnt || !long_rows || !mid_rows || !n_long || !h->rowptr) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
   {
   ProfScope ps(FP_PROF_GRAPH, h->stream);
-  fill_i32(h, n_long, 0, 1);
+  fill_i32(h, n_long, 0, 2);
   fill_i32(h, ucnt, 0, n + 1);
   if (n > 0) {
-    FP_LAUNCH(h, k_rows_dedupe_warp, grid_for(n, ROW_WARPS), ROW_WARPS * 32, 0, off, n, raw, ucnt, long_rows, n_long);
+    FP_LAUNCH(h, k_rows_dedupe_thread, grid_for(n, 256), 256, 0, off, n, raw, ucnt, mid_rows, n_long + 1);
+    FP_LAUNCH(h, k_rows_dedupe_warp, NUM_SMS_B300 * 8, ROW_WARPS * 32, 0, off, mid_rows, n_long + 1, raw, ucnt,
+              long_rows, n_long);
     FP_LAUNCH(h, k_rows_dedupe_block, NUM_SMS_B300, 512, BLOCK_ROW_CAP * sizeof(int32_t), off, long_rows, n_long, raw,
               ucnt, h->d_status);
   }
@@ -241,7 +262,7 @@ fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, in
   if (!h->col) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph columns");
   if (n > 0) {
     ProfScope ps(FP_PROF_GRAPH, h->stream);
-    FP_LAUNCH(h, k_rows_compact, grid_for((int64_t)n * 32, 256), 256, 0, off, raw, n, h->rowptr, h->col);
+    FP_LAUNCH(h, k_rows_compact, grid_for(n, 256), 256, 0, off, raw, n, h->rowptr, h->col);
   }
   FP_CHECK_LAUNCH(h, "graph compact");
   int32_t* hb = pinned_scratch();
@@ -255,6 +276,7 @@ fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, in
   h->nnz = hb[0];
   dev_free(h, ucnt);
   dev_free(h, long_rows);
+  dev_free(h, mid_rows);
   dev_free(h, n_long);
   return FP_OK;
 }
