@@ -20,8 +20,11 @@ constexpr int ROW_WARPS = 8;         // warps per CTA in the warp-per-row kernel
 
 // ---- faces ------------------------------------------------------------------------
 
+// Counts the raw entries of every row; the count each increment returns is the
+// entry's slot in its row, kept (6 per face: the two ends of each edge) so
+// that the fill pass places entries without atomics.
 __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* __restrict__ cnt,
-                             int32_t* status) {
+                             int2* __restrict__ slots, int32_t* status) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) {
@@ -30,25 +33,26 @@ __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int3
     }
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      int32_t a = c[e], b = c[(e + 1) % 3];
-      if (a == b) continue;
-      atomicAdd(&cnt[a], 1);
-      atomicAdd(&cnt[b], 1);
+      const int32_t a = c[e], b = c[(e + 1) % 3];
+      int2 sl = make_int2(0, 0);
+      if (a != b) sl = make_int2(atomicAdd(&cnt[a], 1), atomicAdd(&cnt[b], 1));
+      slots[3 * f + e] = sl;
     }
   }
 }
 
 __global__ void k_face_fill(const int32_t* __restrict__ faces, int64_t nf, int32_t n, const int32_t* __restrict__ off,
-                            int32_t* __restrict__ fill, int32_t* __restrict__ raw) {
+                            const int2* __restrict__ slots, int32_t* __restrict__ raw) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) continue;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      int32_t a = c[e], b = c[(e + 1) % 3];
+      const int32_t a = c[e], b = c[(e + 1) % 3];
       if (a == b) continue;
-      raw[off[a] + atomicAdd(&fill[a], 1)] = b;
-      raw[off[b] + atomicAdd(&fill[b], 1)] = a;
+      const int2 sl = slots[3 * f + e];
+      raw[off[a] + sl.x] = b;
+      raw[off[b] + sl.y] = a;
     }
   }
 }
@@ -285,29 +289,30 @@ fp_status finish_rows(fp_handle* h, int32_t* off, int32_t* raw, int64_t nraw, in
 
 fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t nf) {
   const int32_t n = h->n;
+  if (6 * nf > INT32_MAX) return fail(h, FP_ERR_UNSUPPORTED, "more than 2^31-1 adjacency entries");
   int32_t* cnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* off = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));
-  if (!cnt || !off || !tmp) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
+  int2* slots = (int2*)dev_alloc(h, sizeof(int2) * 3 * (nf > 0 ? nf : 1));
+  if (!cnt || !off || !tmp || !slots) return fail(h, FP_ERR_OUT_OF_MEMORY, "graph workspace");
   {
     ProfScope ps(FP_PROF_GRAPH, h->stream);
     fill_i32(h, cnt, 0, n + 1);
-    if (nf > 0) FP_LAUNCH(h, k_face_count, grid_for(nf, 256), 256, 0, d_faces, nf, n, cnt, h->d_status);
+    if (nf > 0) FP_LAUNCH(h, k_face_count, grid_for(nf, 256), 256, 0, d_faces, nf, n, cnt, slots, h->d_status);
     scan_exclusive(h, cnt, off, n, tmp);
   }
   FP_CHECK_LAUNCH(h, "face count");
   // no host round trip here: every face contributes at most 6 raw entries,
   // faces with a corner out of range are skipped by both kernels and
   // reported at the sync that ends the build
-  if (6 * nf > INT32_MAX) return fail(h, FP_ERR_UNSUPPORTED, "more than 2^31-1 adjacency entries");
   const int64_t nraw = 6 * nf;
   int32_t* raw = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nraw > 0 ? nraw : 1));
   if (!raw) return fail(h, FP_ERR_OUT_OF_MEMORY, "raw adjacency");
-  {
+  if (nf > 0) {
     ProfScope ps(FP_PROF_GRAPH, h->stream);
-    fill_i32(h, cnt, 0, n + 1);
-    if (nf > 0) FP_LAUNCH(h, k_face_fill, grid_for(nf, 256), 256, 0, d_faces, nf, n, off, cnt, raw);
+    FP_LAUNCH(h, k_face_fill, grid_for(nf, 256), 256, 0, d_faces, nf, n, off, slots, raw);
   }
+  dev_free(h, slots);
   FP_TRY(finish_rows(h, off, raw, nraw, tmp, "face corner out of range"));
   dev_free(h, cnt);
   dev_free(h, off);
