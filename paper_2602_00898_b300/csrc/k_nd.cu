@@ -344,19 +344,42 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
         if (v.mark[i] == 0) { c0 = i; break; }
       c0 = block_min(c0, red);
       if (c0 == INT_MAX) break;
-      // sweep 0: discover the component
-      block_bfs(v, c0, &snext);
+      // the sweep from r0 = min (degree, id) of c0's component: tried first
+      // from the minimum over all untouched patches, which is r0 whenever its
+      // sweep reaches c0 (the usual, connected case), so that the discovery
+      // sweep is needed only when the minimum lies in another component
       int64_t best = INT64_MAX;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-        if (v.mark[i] == 0 && v.lvl[i] >= 0) {
-          v.mark[i] = 2;
-          v.lvl[i] = -1;
+        if (v.mark[i] == 0) {
           const int64_t key = ((int64_t)v.rlen[i] << 32) | i;
           best = key < best ? key : best;
         }
-      const int32_t r0 = (int32_t)(block_min(best, red64) & 0xffffffff);
-      // sweep 1: from r0 (minimum degree, then id); r1 = min (degree, id) on the last level
-      const int32_t nl0 = block_bfs(v, r0, &snext);
+      const int32_t ra = (int32_t)(block_min(best, red64) & 0xffffffff);
+      int32_t nl0 = block_bfs(v, ra, &snext);
+      if (v.lvl[c0] >= 0) {
+        // ra's component is c0's: its levels are those of the sweep from r0 = ra
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (v.mark[i] == 0 && v.lvl[i] >= 0) v.mark[i] = 2;
+        __syncthreads();
+      } else {
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (v.mark[i] == 0 && v.lvl[i] >= 0) v.lvl[i] = -1;
+        __syncthreads();
+        // sweep 0: discover c0's component
+        block_bfs(v, c0, &snext);
+        best = INT64_MAX;
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (v.mark[i] == 0 && v.lvl[i] >= 0) {
+            v.mark[i] = 2;
+            v.lvl[i] = -1;
+            const int64_t key = ((int64_t)v.rlen[i] << 32) | i;
+            best = key < best ? key : best;
+          }
+        const int32_t r0 = (int32_t)(block_min(best, red64) & 0xffffffff);
+        // sweep 1: from r0 (minimum degree, then id)
+        nl0 = block_bfs(v, r0, &snext);
+      }
+      // r1 = min (degree, id) on the last level of the sweep from r0
       best = INT64_MAX;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
         if (v.mark[i] == 2 && v.lvl[i] == nl0 - 1) {
