@@ -183,6 +183,7 @@ struct BisectArgs {
   int32_t* hist;               // [k]
   int32_t* side;               // [k] by patch id
   int32_t* split;              // [T]
+  int8_t* cross;               // [k] by patch id: some local neighbour lies on the other side
   int32_t mcap, ecap;          // shared-memory staging limits of this launch
 };
 
@@ -435,6 +436,15 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       pos += cs;
       __syncthreads();
     }
+    // crossing patches: a neighbour of positive weight in this node on the
+    // other side (only their vertices can be superset vertices)
+    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+      const int32_t si = a.side[v.L[i]];
+      int8_t c = 0;
+      const int32_t rb = v.rbeg[i], re = rb + v.rlen[i];
+      for (int32_t e = rb; e < re; ++e) c |= (int8_t)(a.side[v.L[v.adj[e]]] != si);
+      a.cross[v.L[i]] = c;
+    }
     __syncthreads();
   }
 }
@@ -460,6 +470,7 @@ struct LevelArgs {
   int32_t* q_w;
   int32_t* patch_node;
   int32_t k;
+  const int8_t* cross;         // [k] crossing patches of this level (k_nd_bisect)
 };
 
 // SuperSeparator (Algorithm 2 step 3): remaining vertices of a split node with
@@ -470,7 +481,11 @@ __global__ void k_nd_superset(LevelArgs a) {
     if (a.final_[v]) continue;
     const int32_t t = a.node_of[v];
     if (!a.split[t - a.t0]) { a.final_[v] = 1; continue; }
-    const int32_t sv = a.side[a.gmap[v]];
+    const int32_t pv = a.gmap[v];
+    // no neighbour across in its patch's quotient row: not a candidate (its
+    // cdeg and state are not read this level)
+    if (!a.cross[pv]) continue;
+    const int32_t sv = a.side[pv];
     int32_t c = 0;
     // neighbours in batches of ND_BATCH: col, then node and patch, then side
     const int32_t e1 = a.rowptr[v + 1];
@@ -701,9 +716,10 @@ fp_status run_nested_dissection(fp_handle* h) {
   int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8);
   int8_t* final_ = (int8_t*)dev_alloc(h, n);
   int8_t* vstate = (int8_t*)dev_alloc(h, n);
+  int8_t* cross = (int8_t*)dev_alloc(h, kk);
   if (!psize || !pstart || !pfill || !pverts || !qdeg || !q_rowptr || !q_col || !q_w || !ladj || !tmp || !patch_node ||
       !w || !side || !loc || !ldeg || !lvl || !lbeg || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
-      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate)
+      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate || !cross)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
 
   const int G = grid_for(n, 256), GK = grid_for(k, 256);
@@ -760,14 +776,14 @@ fp_status run_nested_dissection(fp_handle* h) {
     const int32_t ecap = 7 * mcap;
     const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + (size_t)mcap;
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
-                  lvl, qa, qb, (int8_t*)mark, hist, side, split, mcap, ecap};
+                  lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
     allow_max_dynamic_smem(k_nd_bisect);
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
     ps_b.end();
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, ctr,
-                 w, q_rowptr, q_col, q_w, patch_node, k};
+                 w, q_rowptr, q_col, q_w, patch_node, k, cross};
     if (!grouped_small) fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
@@ -795,7 +811,7 @@ fp_status run_nested_dissection(fp_handle* h) {
                   (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
                   (void*)ldeg, (void*)lvl, (void*)lbeg, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
                   (void*)npcount, (void*)npstart, (void*)npfill, (void*)nplist, (void*)split, (void*)cdeg, (void*)cand,
-                  (void*)ctr, (void*)final_, (void*)vstate})
+                  (void*)ctr, (void*)final_, (void*)vstate, (void*)cross})
     dev_free(h, p);
   return FP_OK;
 }
