@@ -463,6 +463,8 @@ struct LevelArgs {
   int32_t* cdeg;
   int8_t* vstate;
   int32_t* cand;
+  int2* cand_x;                // per candidate: start of its crossing list, cdeg
+  int32_t* xcol;               // [nnz] crossing neighbours of v at rowptr[v]..
   int32_t* ctr;                // [0] candidates, [1..3] MIS round flags
   int32_t* w;
   const int32_t* q_rowptr;
@@ -487,9 +489,11 @@ __global__ void k_nd_superset(LevelArgs a) {
     if (!a.cross[pv]) continue;
     const int32_t sv = a.side[pv];
     int32_t c = 0;
-    // neighbours in batches of ND_BATCH: col, then node and patch, then side
-    const int32_t e1 = a.rowptr[v + 1];
-    for (int32_t e0 = a.rowptr[v]; e0 < e1; e0 += ND_BATCH) {
+    // neighbours in batches of ND_BATCH: col, then node and patch, then side;
+    // the crossing ones are listed in v's own row range of xcol, so that the
+    // refinement rounds read only them
+    const int32_t eb = a.rowptr[v], e1 = a.rowptr[v + 1];
+    for (int32_t e0 = eb; e0 < e1; e0 += ND_BATCH) {
       int32_t u[ND_BATCH], nt[ND_BATCH], sd[ND_BATCH];
 #pragma unroll
       for (int k = 0; k < ND_BATCH; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
@@ -501,7 +505,8 @@ __global__ void k_nd_superset(LevelArgs a) {
 #pragma unroll
       for (int k = 0; k < ND_BATCH; ++k) sd[k] = nt[k] == t ? a.side[sd[k]] : sv;
 #pragma unroll
-      for (int k = 0; k < ND_BATCH; ++k) c += (nt[k] == t && sd[k] != sv);
+      for (int k = 0; k < ND_BATCH; ++k)
+        if (nt[k] == t && sd[k] != sv) a.xcol[eb + c++] = u[k];
     }
     a.cdeg[v] = c;
     a.vstate[v] = c ? VS_UND : VS_NONE;
@@ -511,7 +516,9 @@ __global__ void k_nd_superset(LevelArgs a) {
       int base = 0;
       if (lane == leader) base = atomicAdd(&a.ctr[0], __popc(act));
       base = __shfl_sync(act, base, leader);
-      a.cand[base + __popc(act & lanemask_lt())] = v;
+      const int32_t slot = base + __popc(act & lanemask_lt());
+      a.cand[slot] = v;
+      a.cand_x[slot] = make_int2(eb, c);
     }
   }
 }
@@ -541,26 +548,15 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
     int32_t undecided = 0;
     for (int64_t i = t0; i < nc; i += stride) {
       const int32_t v = __ldcg(&a.cand[i]);
+      const int2 x = __ldcg(&a.cand_x[i]);
       if (*(volatile int8_t*)&a.vstate[v] != VS_UND) continue;
-      const int32_t t = a.node_of[v];
-      const int32_t sv = a.side[a.gmap[v]];
-      const int32_t cv = a.cdeg[v];
+      const int32_t cv = x.y;
       bool any_in = false, is_min = true;
-      const int32_t e1 = a.rowptr[v + 1];
-      for (int32_t e0 = a.rowptr[v]; e0 < e1 && !any_in; e0 += ND_BATCH) {
-        int32_t u[ND_BATCH], nt[ND_BATCH], sd[ND_BATCH];
+      // the crossing neighbours listed by k_nd_superset, ND_BATCH at a time
+      for (int32_t j = 0; j < cv && !any_in; j += ND_BATCH) {
+        int32_t u[ND_BATCH];
 #pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) u[k] = e0 + k < e1 ? a.col[e0 + k] : -1;
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          nt[k] = u[k] >= 0 ? a.node_of[u[k]] : -1;
-          sd[k] = u[k] >= 0 ? a.gmap[u[k]] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          sd[k] = nt[k] == t ? a.side[sd[k]] : sv;
-          if (nt[k] != t || sd[k] == sv) u[k] = -1;        // not a crossing neighbour
-        }
+        for (int k = 0; k < ND_BATCH; ++k) u[k] = j + k < cv ? __ldcg(&a.xcol[x.x + j + k]) : -1;
         int8_t st[ND_BATCH];
         int32_t cd[ND_BATCH];
 #pragma unroll
@@ -713,13 +709,14 @@ fp_status run_nested_dissection(fp_handle* h) {
   int32_t *patch_node = I(kk), *w = I(kk), *side = I(kk), *loc = I(kk), *ldeg = I(kk), *lvl = I(kk), *lbeg = I(kk);
   int32_t *qa = I(kk), *qb = I(kk), *mark = I(kk), *hist = I(kk), *sortbuf = I(2 * kk + 64);
   int32_t *npcount = I(kk), *npstart = I(kk + 1), *npfill = I(kk), *nplist = I(kk), *split = I(kk);
-  int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8);
+  int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8), *xcol = I(Q);
+  int2* cand_x = (int2*)dev_alloc(h, sizeof(int2) * (n > 0 ? n : 1));
   int8_t* final_ = (int8_t*)dev_alloc(h, n);
   int8_t* vstate = (int8_t*)dev_alloc(h, n);
   int8_t* cross = (int8_t*)dev_alloc(h, kk);
   if (!psize || !pstart || !pfill || !pverts || !qdeg || !q_rowptr || !q_col || !q_w || !ladj || !tmp || !patch_node ||
       !w || !side || !loc || !ldeg || !lvl || !lbeg || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
-      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate || !cross)
+      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate || !cross || !xcol || !cand_x)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
 
   const int G = grid_for(n, 256), GK = grid_for(k, 256);
@@ -782,8 +779,8 @@ fp_status run_nested_dissection(fp_handle* h) {
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
     ps_b.end();
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
-    LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, ctr,
-                 w, q_rowptr, q_col, q_w, patch_node, k, cross};
+    LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, cand_x, xcol,
+                 ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross};
     if (!grouped_small) fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
@@ -811,7 +808,7 @@ fp_status run_nested_dissection(fp_handle* h) {
                   (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
                   (void*)ldeg, (void*)lvl, (void*)lbeg, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
                   (void*)npcount, (void*)npstart, (void*)npfill, (void*)nplist, (void*)split, (void*)cdeg, (void*)cand,
-                  (void*)ctr, (void*)final_, (void*)vstate, (void*)cross})
+                  (void*)ctr, (void*)final_, (void*)vstate, (void*)cross, (void*)xcol, (void*)cand_x})
     dev_free(h, p);
   return FP_OK;
 }
