@@ -71,6 +71,7 @@ struct fp_handle {
   int32_t* node_begin = nullptr;  // [nnodes]
   int32_t* node_size = nullptr;   // [nnodes]
   int64_t node_cap = 0;           // allocated length of node arrays
+  std::vector<int32_t> level_nodes;   // non-empty tree nodes per depth (host)
 
   int32_t* d_status = nullptr;    // device status word
   int32_t* h_status = nullptr;    // pinned mirror

@@ -879,9 +879,11 @@ fp_status run_local_order(fp_handle* h) {
   // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3], early;
   int mmax[3] = {0, 0, 0};
+  h->level_nodes.assign(h->D + 1, 0);
   for (int64_t t = 0; t < nn; ++t) {
     const int m = hs[t];
     if (m == 0) continue;
+    ++h->level_nodes[63 - __builtin_clzll((unsigned long long)t + 1)];
     if (m > MD_MAX) return fail(h, FP_ERR_UNSUPPORTED, "a tree node has more than 32768 vertices");
     if (t < h->early_nodes && sparse_smem(m) <= SMEM_MAX) {
       early.push_back((int32_t)t);     // ordered during the dissection

@@ -183,27 +183,29 @@ __device__ __forceinline__ uint32_t popc_range(uint32_t s, int w, int32_t lo, in
   return __popc(s & mk);
 }
 
-// Column sweep of one node by one warp (step 3). NCH > 0: rows of at most
-// 32*NCH words; the current column's structure is kept in registers (carry)
-// while the etree parent is the next column, and the next row is loaded one
-// column ahead (a merge from column i never lands in row i+1 except through
-// the carry, so the early load sees its final contents). NCH = 0: rows of any
-// width, merged through memory. Returns the column where the dense tail
-// starts (its structure written back to its row), or m.
+// Column sweep of one node by one warp (step 3). Column i's parent is the first
+// set bit of its row (struct(i)), its count the popcount; the row minus the
+// parent bit is merged into the parent's row. Returns the column where the
+// dense tail starts (its structure written back to its row), or m.
+//
+// Rows of at most 32*NCH words (NCH > 0): lane l holds words l, l+32, ...
+// of the current row in registers. While the parent is the next column the
+// merged structure stays in registers (carry); any other merge is an atomic OR
+// into the parent's row. The next row is loaded one column ahead: a merge
+// from column i never lands in row i+1 except through the carry, so the early
+// load sees its final contents. The rare cases (an empty column, a parent
+// above the node, the start of the dense tail) leave the common path in one
+// branch.
 template <int NCH>
 __device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t* upos, int32_t m, int32_t W,
                                  int32_t b, bool tail_ok, unsigned long long& nnz, unsigned long long& fl) {
   const int lane = threadIdx.x & 31;
-  constexpr int NC = NCH > 0 ? NCH : 1;
-  uint32_t carry[NC], nxt[NC];
+  uint32_t carry[NCH], nxt[NCH];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) carry[c] = nxt[c] = 0u;
-  if constexpr (NCH > 0) {
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      const int w = lane + 32 * c;
-      nxt[c] = w < W ? rows[w] : 0u;
-    }
+  for (int c = 0; c < NCH; ++c) {
+    const int w = lane + 32 * c;
+    carry[c] = 0u;
+    nxt[c] = w < W ? rows[w] : 0u;
   }
   // column i's parent and count are held by lane i % 32 and stored 32 at a time
   int32_t my_par = -1, my_cc = 1;
@@ -216,39 +218,125 @@ __device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t
       fl += (unsigned long long)my_cc * (unsigned long long)my_cc;
     }
   };
-  bool cv = false;
+  int64_t off = 0;                                // tri_off(i, W)
+  for (int32_t i = 0; i < m; ++i) {
+    const int i0 = i >> 5;
+    uint32_t* ri = rows + off - i0;               // word w of row i at ri[w], w >= i0
+    off += W - i0;
+    uint32_t cur[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) cur[c] = nxt[c] | carry[c];
+    if (i + 1 < m) {
+      const int i1 = (i + 1) >> 5;
+      const uint32_t* rn = rows + off - i1;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int w = lane + 32 * c;
+        nxt[c] = (w < W && w >= i1) ? rn[w] : 0u;
+      }
+    }
+    uint32_t f = 0xffffffffu, cnt = 0;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const uint32_t s = cur[c];
+      const uint32_t bt = s ? (uint32_t)((lane + 32 * c) * 32 + __ffs(s) - 1) : 0xffffffffu;
+      f = bt < f ? bt : f;
+      cnt += __popc(s);
+    }
+    f = __reduce_min_sync(0xffffffffu, f);
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    const bool inside = f < (uint32_t)m;          // false for an empty column too
+    const bool chain = f == (uint32_t)i + 1;
+    const int32_t rest = m - 1 - i;
+    if (lane == (i & 31)) {
+      my_par = inside ? b + (int32_t)f : -1;
+      my_cc = (int32_t)cnt + 1;
+    }
+    if (!inside || (tail_ok && chain && rest >= DENSE_MIN && cnt >= (uint32_t)rest)) {
+      if (!inside) {
+        if (cnt != 0) {
+          const int32_t pf = upos[f];
+          if (lane == (i & 31)) my_par = pf;
+          // fill mode: the structure goes nowhere
+          if (!a.node_fill)
+            export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t {
+              uint32_t s = 0u;
+#pragma unroll
+              for (int c = 0; c < NCH; ++c) if (c == (w >> 5)) s = cur[c];
+              return s;
+            });
+        }
+        if ((i & 31) == 31) flush(i);
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) carry[c] = 0u;
+        continue;
+      }
+      // dense tail? struct(i) must hold every later column of the node (cnt
+      // bounds that count from above, so most columns skip the exact test)
+      uint32_t cn = 0;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) cn += popc_range(cur[c], lane + 32 * c, i + 1, m);
+      cn = __reduce_add_sync(0xffffffffu, cn);
+      if (cn == (uint32_t)rest) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+          const int w = lane + 32 * c;
+          if (w < W && w >= i0) ri[w] = cur[c];
+        }
+        flush(i);
+        __syncwarp();
+        return i;
+      }
+    }
+    if ((i & 31) == 31) flush(i);
+    // merge struct(i) \ {f} into column f
+    const int f0 = (int)(f >> 5);
+    const uint32_t fb = 1u << (f & 31);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+      if (lane + 32 * c == f0) cur[c] &= ~fb;
+    if (chain) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) carry[c] = cur[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) carry[c] = 0u;
+      uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const int w = lane + 32 * c;
+        if (w < W && w >= f0 && cur[c]) atomicOr(&rf[w], cur[c]);
+      }
+    }
+  }
+  if (m & 31) flush(m - 1);
+  return m;
+}
+
+// Rows of any width (NCH = 0): the same steps with every row in memory.
+template <>
+__device__ int32_t sweep_columns<0>(const SymArgs& a, uint32_t* rows, const int32_t* upos, int32_t m, int32_t W,
+                                    int32_t b, bool tail_ok, unsigned long long& nnz, unsigned long long& fl) {
+  const int lane = threadIdx.x & 31;
+  int32_t my_par = -1, my_cc = 1;
+  auto flush = [&](int32_t i_last) {
+    const int32_t j = (i_last & ~31) + lane;
+    if (j <= i_last) {
+      a.parent[b + j] = my_par;
+      a.colcount[b + j] = my_cc;
+      nnz += (unsigned long long)my_cc;
+      fl += (unsigned long long)my_cc * (unsigned long long)my_cc;
+    }
+  };
   int64_t off = 0;                                // tri_off(i, W)
   for (int32_t i = 0; i < m; ++i) {
     const int i0 = i >> 5;
     uint32_t* ri = rows + off - i0;               // word w of row i at ri[w], w >= i0
     off += W - i0;
     uint32_t f = 0xffffffffu, cnt = 0;
-    if constexpr (NCH > 0) {
-      uint32_t cur[NCH];
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) cur[c] = nxt[c];
-      if (i + 1 < m) {
-        const int i1 = (i + 1) >> 5;
-        const uint32_t* rn = rows + off - i1;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          const int w = lane + 32 * c;
-          nxt[c] = (w < W && w >= i1) ? rn[w] : 0u;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        const int w = lane + 32 * c;
-        uint32_t s = cur[c];
-        if (cv) s |= carry[c];
-        carry[c] = s;
-        if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
-      }
-    } else {
-      for (int w = lane; w < W; w += 32) {
-        const uint32_t s = w >= i0 ? ri[w] : 0u;
-        if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
-      }
+    for (int w = lane; w < W; w += 32) {
+      const uint32_t s = w >= i0 ? ri[w] : 0u;
+      if (s) { const uint32_t bt = w * 32 + __ffs(s) - 1; f = bt < f ? bt : f; cnt += __popc(s); }
     }
     f = __reduce_min_sync(0xffffffffu, f);
     cnt = __reduce_add_sync(0xffffffffu, cnt);
@@ -260,45 +348,17 @@ __device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t
     }
     const bool flushed = (i & 31) == 31 || i + 1 == m;
     if (flushed) flush(i);
-    if (cnt == 0) {
-      cv = false;
-      continue;
-    }
+    if (cnt == 0) continue;
     if (!inside) {
-      if (a.node_fill) {
-        // fill mode: the structure goes nowhere
-      } else if constexpr (NCH > 0) {
-        export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t {
-          uint32_t s = 0u;
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) if (c == (w >> 5)) s = carry[c];
-          return s;
-        });
-      } else {
+      if (!a.node_fill)
         export_element(a, upos, W, cnt, pf, [&](int w) -> uint32_t { return w >= i0 ? ri[w] : 0u; });
-      }
-      cv = false;
       continue;
     }
-    // dense tail? struct(i) must hold every later column of the node (cnt
-    // bounds that count from above, so most columns skip the exact test)
     if (tail_ok && f == (uint32_t)i + 1 && m - 1 - i >= DENSE_MIN && cnt >= (uint32_t)(m - 1 - i)) {
       uint32_t cn = 0;
-      if constexpr (NCH > 0) {
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) cn += popc_range(carry[c], lane + 32 * c, i + 1, m);
-      } else {
-        for (int w = lane; w < W; w += 32) if (w >= i0) cn += popc_range(ri[w], w, i + 1, m);
-      }
+      for (int w = lane; w < W; w += 32) if (w >= i0) cn += popc_range(ri[w], w, i + 1, m);
       cn = __reduce_add_sync(0xffffffffu, cn);
       if (cn == (uint32_t)(m - 1 - i)) {
-        if constexpr (NCH > 0) {
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) {
-            const int w = lane + 32 * c;
-            if (w < W && w >= i0) ri[w] = carry[c];
-          }
-        }
         if (!flushed) flush(i);
         __syncwarp();
         return i;
@@ -306,31 +366,12 @@ __device__ int32_t sweep_columns(const SymArgs& a, uint32_t* rows, const int32_t
     }
     // merge struct(i) \ {f} into column f
     const int f0 = (int)(f >> 5);
-    if constexpr (NCH > 0) {
-#pragma unroll
-      for (int c = 0; c < NCH; ++c) {
-        const int w = lane + 32 * c;
-        if (w == f0) carry[c] &= ~(1u << (f & 31));
-      }
-      if (f == (uint32_t)i + 1) {
-        cv = true;
-      } else {
-        cv = false;
-        uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-          const int w = lane + 32 * c;
-          if (w < W && w >= f0 && carry[c]) rf[w] |= carry[c];
-        }
-      }
-    } else {
-      uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
-      for (int w = lane; w < W; w += 32) {
-        if (w < f0) continue;           // struct(i) \ {f} lies above f
-        uint32_t s = ri[w];
-        if (w == f0) s &= ~(1u << (f & 31));
-        if (s) rf[w] |= s;
-      }
+    uint32_t* rf = rows + tri_off((int32_t)f, W) - f0;
+    for (int w = lane; w < W; w += 32) {
+      if (w < f0) continue;           // struct(i) \ {f} lies above f
+      uint32_t s = ri[w];
+      if (w == f0) s &= ~(1u << (f & 31));
+      if (s) rf[w] |= s;
     }
   }
   return m;
@@ -594,16 +635,29 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     for (int32_t i = tid; i < m; i += nthr) upos[i] = b + i;
     for (int32_t w = tid; w < bw; w += nthr) {
       uint32_t x = bitmap[w];
+      if (!x) continue;
       int32_t r = m + wpre[w];
+      // the range of the word's first bit by binary search, later bits by
+      // stepping forward (ranges grow with the coordinate)
+      int32_t i = 0;
+      {
+        const int32_t c = w * 32 + __ffs(x) - 1;
+#pragma unroll
+        for (int st = 16; st; st >>= 1)
+          if (i + st < na && s_ao[i + st] <= c) i += st;
+      }
+      int32_t base = s_ab[i] - s_ao[i];
+      int32_t nb = i + 1 < na ? s_ao[i + 1] : INT_MAX;
       while (x) {
         const int bt = __ffs(x) - 1;
         x &= x - 1;
         const int32_t c = w * 32 + bt;
-        int32_t i = 0;
-#pragma unroll
-        for (int st = 16; st; st >>= 1)
-          if (i + st < na && s_ao[i + st] <= c) i += st;
-        upos[r++] = s_ab[i] + c - s_ao[i];
+        while (c >= nb) {
+          ++i;
+          base = s_ab[i] - s_ao[i];
+          nb = i + 1 < na ? s_ao[i + 1] : INT_MAX;
+        }
+        upos[r++] = base + c;
       }
     }
     __syncthreads();
@@ -690,9 +744,13 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
         // few nodes: one large CTA each
         FP_LAUNCH(h, k_symbolic_nodes, T, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 0, 0);
       } else {
-        // many small nodes: one warp each; the ones that do not fit go to the
-        // large CTAs afterwards
-        FP_LAUNCH(h, k_symbolic_nodes, T, 32, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+        // many small nodes: one small CTA each (its first warp sweeps the
+        // columns, all of them gather); the ones that do not fit go to the
+        // large CTAs afterwards. Four warps a node while every node of the
+        // level is resident at once (four such CTAs per SM), else two.
+        const int32_t ne = d < (int32_t)h->level_nodes.size() ? h->level_nodes[d] : T;
+        const int thr = ne <= NUM_SMS_B300 * 4 ? 128 : 64;
+        FP_LAUNCH(h, k_symbolic_nodes, T, thr, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
         FP_LAUNCH(h, k_symbolic_nodes, NUM_SMS_B300, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 1,
                   0);
       }
@@ -744,7 +802,7 @@ fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm,
     SymArgs sa{h->rowptr, h->col, perm, iperm, h->node_of, h->node_begin, h->node_size, 0, 0, scr, scr + n, ctr,
                head, nullptr, nullptr, 0, 0, ctr + 2, pool, pool_words, ctr + 4, big, big + count, h->d_status,
                d_nodes, count, d_fill};
-    FP_LAUNCH(h, k_symbolic_nodes, count, 32, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+    FP_LAUNCH(h, k_symbolic_nodes, count, 64, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
     sa.in_list = nullptr;
     FP_LAUNCH(h, k_symbolic_nodes, NUM_SMS_B300, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 1, 0);
     FP_CHECK_LAUNCH(h, "leaf fill");
