@@ -175,6 +175,86 @@ __device__ __forceinline__ void for_adjacency(const SymArgs& a, int32_t b, int32
   }
 }
 
+// Step 1's gather, done once: the upper adjacency entries (column i, position
+// pos > b + i) of the node's columns and the entries of its incoming elements
+// (column r0 = the element's smallest entry, with each later entry) become
+// (column, position) pairs of a list that grows down from `top` (pair s at
+// top[-1 - s]); ancestor positions are marked in the bitmap. The loops run in
+// step across each warp, so a round takes its list slots with one shared
+// atomic per warp. *cnt ends as the number of pairs, which may exceed cap:
+// then the pairs from cap on were not stored.
+__device__ void gather_entries(const SymArgs& a, int32_t t, int32_t b, int32_t m, const int32_t* ab,
+                               const int32_t* ao, int32_t na, uint32_t* bitmap, int2* top, int32_t cap,
+                               int32_t* cnt) {
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  const int32_t end = b + m;
+  auto keep = [&](int32_t i, int32_t pos, int32_t slot) {
+    if (pos >= end) {
+      const int32_t c = anc_coord(ab, ao, na, pos);
+      atomicOr(&bitmap[c >> 5], 1u << (c & 31));
+    }
+    if (slot < cap) top[-1 - slot] = make_int2(i, pos);
+  };
+  for (int32_t ib = tid - lane; ib < m; ib += GV * nthr) {
+    const int32_t i0 = ib + lane;
+    int32_t e[GV], f[GV];
+#pragma unroll
+    for (int v = 0; v < GV; ++v) {
+      const int32_t i = i0 + v * nthr;
+      const int32_t x = i < m ? a.perm[b + i] : -1;
+      e[v] = x >= 0 ? a.rowptr[x] : 0;
+      f[v] = x >= 0 ? a.rowptr[x + 1] : 0;
+    }
+    for (;;) {
+      bool more = false;
+#pragma unroll
+      for (int v = 0; v < GV; ++v) more |= e[v] < f[v];
+      if (!__any_sync(0xffffffffu, more)) break;
+      int32_t p[GV][GE];
+#pragma unroll
+      for (int v = 0; v < GV; ++v)
+#pragma unroll
+        for (int k = 0; k < GE; ++k) p[v][k] = e[v] + k < f[v] ? a.col[e[v] + k] : -1;
+#pragma unroll
+      for (int v = 0; v < GV; ++v)
+#pragma unroll
+        for (int k = 0; k < GE; ++k) p[v][k] = p[v][k] >= 0 ? a.iperm[p[v][k]] : -1;
+      int32_t nv = 0;
+#pragma unroll
+      for (int v = 0; v < GV; ++v)
+#pragma unroll
+        for (int k = 0; k < GE; ++k) {
+          if (p[v][k] <= b + i0 + v * nthr) p[v][k] = -1;     // not above the column (or no entry)
+          nv += p[v][k] >= 0;
+        }
+      const int32_t inc = warp_incl_scan_i32(nv);
+      int32_t base = 0;
+      if (lane == 31 && inc) base = atomicAdd(cnt, inc);
+      base = __shfl_sync(0xffffffffu, base, 31) + inc - nv;
+#pragma unroll
+      for (int v = 0; v < GV; ++v) {
+#pragma unroll
+        for (int k = 0; k < GE; ++k)
+          if (p[v][k] >= 0) keep(i0 + v * nthr, p[v][k], base++);
+        e[v] += GE;
+      }
+    }
+  }
+  for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
+    const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
+    const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
+    for (int32_t j0 = 1 + tid - lane; j0 < len; j0 += nthr) {
+      const int32_t j = j0 + lane;
+      const int32_t pos = j < len ? a.elem_data[off + j] : -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, pos >= 0);
+      int32_t base = 0;
+      if (lane == 0) base = atomicAdd(cnt, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0) + __popc(bal & lanemask_lt());
+      if (pos >= 0) keep(r0, pos, base);
+    }
+  }
+}
+
 // Popcount of the bits of word w that fall in columns [lo, hi).
 __device__ __forceinline__ uint32_t popc_range(uint32_t s, int w, int32_t lo, int32_t hi) {
   const int32_t l = max(lo - 32 * w, 0), h = min(hi - 32 * w, 32);
@@ -485,7 +565,7 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
                                                                int32_t may_defer) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int32_t s_ab[32], s_ao[32];
-  __shared__ int32_t s_na, s_atot, s_fail, s_is;
+  __shared__ int32_t s_na, s_atot, s_fail, s_is, s_cnt;
   __shared__ uint32_t* s_bitmap;
   __shared__ int32_t* s_wpre;
   __shared__ uint32_t* s_rows;
@@ -522,9 +602,10 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     __syncthreads();
     const int32_t na = s_na, atot = s_atot, bw = (atot + 31) >> 5;
     int32_t cur = 0;   // shared-memory words taken so far (every thread tracks it)
+    int32_t lim = smem_words;   // below the gathered list while it is in use
     auto take = [&](int64_t words, bool& in_smem) -> int64_t {
       words = (words + 3) & ~3ll;     // keep every region 16-byte aligned
-      if (cur + words <= smem_words) {
+      if (cur + words <= lim) {
         in_smem = true;
         const int64_t o = cur;
         cur += (int32_t)words;
@@ -538,6 +619,7 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     const int64_t bm_off = take(2 * (int64_t)bw, bm_smem);
     if (tid == 0) {
       s_fail = 0;
+      s_cnt = 0;
       if (bm_smem) {
         s_bitmap = sm + bm_off;
       } else if (may_defer) {
@@ -558,23 +640,14 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     int32_t* wpre = s_wpre;
     for (int32_t w = tid; w < bw; w += nthr) bitmap[w] = 0u;
     __syncthreads();
-    for_adjacency(a, b, m, tid, nthr, [&](int32_t, int32_t pos) {
-      if (pos >= end) {
-        const int32_t c = anc_coord(s_ab, s_ao, na, pos);
-        atomicOr(&bitmap[c >> 5], 1u << (c & 31));
-      }
-    });
-    for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
-      const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
-      for (int32_t j = tid; j < len; j += nthr) {
-        const int32_t pos = a.elem_data[off + j];
-        if (pos >= end) {
-          const int32_t c = anc_coord(s_ab, s_ao, na, pos);
-          atomicOr(&bitmap[c >> 5], 1u << (c & 31));
-        }
-      }
-    }
+    // the list of (column, position) pairs fills shared memory down from the
+    // top, above everything taken so far
+    const int32_t cur_bm = cur;
+    const int32_t cap = (smem_words - cur) / 2;
+    int2* top = reinterpret_cast<int2*>(sm + smem_words);
+    gather_entries(a, t, b, m, s_ab, s_ao, na, bitmap, top, cap, &s_cnt);
     __syncthreads();
+    const int32_t npairs = s_cnt;
     int32_t acnt = 0;
     for (int32_t w0 = 0; w0 < bw; w0 += nthr) {
       const int32_t w = w0 + tid;
@@ -587,12 +660,22 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     const int32_t U = m + acnt;
     const int32_t W = (U + 31) >> 5;
     const int64_t row_words = tri_off(m, W);
-    // 2. placement: the local->position map, the rows, the tail scratch
+    // 2. placement: the local->position map, the rows, the tail scratch --
+    // below the list when it is complete and they fit there, else the list is
+    // dropped and the seeding gathers again
+    bool use_list = npairs <= cap;
     bool up_smem = false, rw_smem = false, tl_smem = false;
-    const int64_t up_off = take(U, up_smem);
-    const int64_t rw_off = up_smem ? take(row_words, rw_smem) : (rw_smem = false, -1);
+    int64_t up_off = -1, rw_off = -1, tl_off = -1;
     const bool tail_in_bitmap = 2 * (int64_t)bw >= U && bm_smem;
-    const int64_t tl_off = tail_in_bitmap ? -1 : take(U, tl_smem);
+    for (int pass = use_list ? 0 : 1; pass < 2; ++pass) {
+      cur = cur_bm;
+      lim = pass == 0 ? (smem_words - 2 * npairs) & ~3 : smem_words;
+      up_off = take(U, up_smem);
+      rw_off = up_smem ? take(row_words, rw_smem) : (rw_smem = false, -1);
+      tl_off = tail_in_bitmap ? -1 : take(U, tl_smem);
+      if (pass == 0 && up_smem && rw_smem) break;
+      use_list = false;
+    }
     if (tid == 0) {
       if (may_defer && !(up_smem && rw_smem)) {
         s_fail = 2;
@@ -662,19 +745,27 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
     }
     __syncthreads();
     // seed the column rows: adjacency above the column, then the elements
-    for_adjacency(a, b, m, tid, nthr, [&](int32_t i, int32_t pos) {
-      if (pos > b + i) {
-        const int32_t l = local_of(pos);
-        atomicOr(&rows[tri_off(i, W) - (i >> 5) + (l >> 5)], 1u << (l & 31));
+    if (use_list) {
+      for (int32_t q = tid; q < npairs; q += nthr) {
+        const int2 e = top[-1 - q];
+        const int32_t l = local_of(e.y);
+        atomicOr(&rows[tri_off(e.x, W) - (e.x >> 5) + (l >> 5)], 1u << (l & 31));
       }
-    });
-    for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
-      const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
-      const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
-      uint32_t* r = rows + tri_off(r0, W) - (r0 >> 5);
-      for (int32_t j = 1 + tid; j < len; j += nthr) {
-        const int32_t l = local_of(a.elem_data[off + j]);
-        atomicOr(&r[l >> 5], 1u << (l & 31));
+    } else {
+      for_adjacency(a, b, m, tid, nthr, [&](int32_t i, int32_t pos) {
+        if (pos > b + i) {
+          const int32_t l = local_of(pos);
+          atomicOr(&rows[tri_off(i, W) - (i >> 5) + (l >> 5)], 1u << (l & 31));
+        }
+      });
+      for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
+        const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
+        const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
+        uint32_t* r = rows + tri_off(r0, W) - (r0 >> 5);
+        for (int32_t j = 1 + tid; j < len; j += nthr) {
+          const int32_t l = local_of(a.elem_data[off + j]);
+          atomicOr(&r[l >> 5], 1u << (l & 31));
+        }
       }
     }
     __syncthreads();
