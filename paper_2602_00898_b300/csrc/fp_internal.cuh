@@ -14,6 +14,14 @@ namespace fp {
 constexpr unsigned long long KEY_INF = ~0ull;
 constexpr int NUM_SMS_B300 = 148;
 
+// Grid for a grid-stride loop over n items: one item per thread, at most
+// per_sm CTAs per SM.
+inline int grid_for(int64_t n, int threads, int per_sm = 32) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > (int64_t)NUM_SMS_B300 * per_sm) g = (int64_t)NUM_SMS_B300 * per_sm;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // Device status word bits (set by kernels, read by the host at sync points).
 enum : int32_t {
   ST_BAD_INDEX = 1 << 0,       // an input index out of range
@@ -71,7 +79,7 @@ struct fp_handle {
   int32_t* node_begin = nullptr;  // [nnodes]
   int32_t* node_size = nullptr;   // [nnodes]
   int64_t node_cap = 0;           // allocated length of node arrays
-  std::vector<int32_t> level_nodes;   // non-empty tree nodes per depth (host)
+  std::vector<int32_t> node_size_host;   // host copy of node_size (set by the ordering stage)
 
   int32_t* d_status = nullptr;    // device status word
   int32_t* h_status = nullptr;    // pinned mirror

@@ -154,12 +154,6 @@ __global__ void k_iota(int32_t* p, int64_t n) {
     p[i] = (int32_t)i;
 }
 
-inline int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > NUM_SMS_B300 * 16) g = NUM_SMS_B300 * 16;
-  return (int)(g < 1 ? 1 : g);
-}
-
 }  // namespace
 
 int64_t scan_tmp_ints(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
@@ -193,12 +187,12 @@ void scan_exclusive_pair_zero(fp_handle* h, const int32_t* a, int32_t* oa, int32
 
 void fill_i32(fp_handle* h, int32_t* p, int32_t v, int64_t n) {
   if (n <= 0) return;
-  FP_LAUNCH(h, k_fill, grid_for(n, 256), 256, 0, p, v, n);
+  FP_LAUNCH(h, k_fill, grid_for(n, 256, 16), 256, 0, p, v, n);
 }
 
 void iota_i32(fp_handle* h, int32_t* p, int64_t n) {
   if (n <= 0) return;
-  FP_LAUNCH(h, k_iota, grid_for(n, 256), 256, 0, p, n);
+  FP_LAUNCH(h, k_iota, grid_for(n, 256, 16), 256, 0, p, n);
 }
 
 }  // namespace fp

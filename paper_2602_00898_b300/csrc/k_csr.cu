@@ -230,12 +230,6 @@ __global__ void k_check_symmetric(const int32_t* __restrict__ rowptr, const int3
   }
 }
 
-inline int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
-  return (int)(g < 1 ? 1 : g);
-}
-
 // Shared tail: raw rows [off] -> sorted unique CSR in h->rowptr / h->col. The
 // column array is sized for nraw entries (an upper bound of the unique ones);
 // one host sync at the end reads the entry count and the status word

@@ -46,12 +46,6 @@ constexpr int SP_GROUPS = 96;   // group minima the sparse kernel's arg-min read
 constexpr uint16_t DEG_DEAD = 0xffff;
 constexpr size_t SMEM_MAX = 225 * 1024;
 
-inline int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
-  return (int)(g < 1 ? 1 : g);
-}
-
 int pow2_host(int x) {
   int p = 32;
   while (p < x) p <<= 1;
@@ -879,11 +873,10 @@ fp_status run_local_order(fp_handle* h) {
   // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3], early;
   int mmax[3] = {0, 0, 0};
-  h->level_nodes.assign(h->D + 1, 0);
+  h->node_size_host = hs;
   for (int64_t t = 0; t < nn; ++t) {
     const int m = hs[t];
     if (m == 0) continue;
-    ++h->level_nodes[63 - __builtin_clzll((unsigned long long)t + 1)];
     if (m > MD_MAX) return fail(h, FP_ERR_UNSUPPORTED, "a tree node has more than 32768 vertices");
     if (t < h->early_nodes && sparse_smem(m) <= SMEM_MAX) {
       early.push_back((int32_t)t);     // ordered during the dissection

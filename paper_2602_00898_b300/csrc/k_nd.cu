@@ -38,12 +38,6 @@ constexpr int EARLY_LEVELS = 1;
 constexpr int EARLY_CTAS = (1 << EARLY_LEVELS) - 1;  // at most that many early ordering CTAs
 constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
 
-inline int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
-  return (int)(g < 1 ? 1 : g);
-}
-
 // ---- generic counting sort helpers ----------------------------------------------------
 __global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t* __restrict__ cnt) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

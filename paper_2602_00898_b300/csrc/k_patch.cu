@@ -32,12 +32,6 @@ constexpr int BFS_THREADS = 256;
 constexpr int BFS_BATCH = 8;
 constexpr int BFS_TAIL = 1024;   // frontiers up to this size run in one CTA
 
-inline int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > NUM_SMS_B300 * 32) g = NUM_SMS_B300 * 32;
-  return (int)(g < 1 ? 1 : g);
-}
-
 // Level-synchronous multi-source BFS on packed keys (dist << 32 | label).
 // ctr[0] holds the size of the initial frontier `fa`. Frontier entries are
 // (vertex, first edge, end edge, 0), so that a level's first round trip

@@ -33,6 +33,9 @@
 // rows in shared memory when they fit, else in a global scratch pool).
 // Positions of a node are contiguous in both schedules and ancestors always
 // come later, so bit order equals position order.
+#include <algorithm>
+#include <vector>
+
 #include "fp_device.cuh"
 
 namespace fp {
@@ -53,10 +56,9 @@ __device__ __forceinline__ int64_t tri_off(int32_t i, int32_t W) {
 }
 
 struct SymArgs {
-  const int32_t* rowptr;
-  const int32_t* col;
+  const int32_t* prow;             // [n + 1] slab of row p: prow[p] .. prow[p+1]
+  const int2* ppair;               // (p, q): position p adjacent to position q in B
   const int32_t* perm;
-  const int32_t* iperm;
   const int32_t* node_of;
   const int32_t* node_begin;
   const int32_t* node_size;
@@ -133,47 +135,7 @@ __device__ __forceinline__ void export_element(const SymArgs& a, const int32_t* 
   }
 }
 
-// Calls fn(i, pos) for every adjacency entry (new position pos) of the node's
-// columns i = tid, tid + nthr, ... The gathers perm -> rowptr -> col -> iperm
-// are dependent, so GV columns and up to GE neighbours each are loaded
-// together: a handful of round trips per GV columns instead of a chain per
-// neighbour.
-constexpr int GV = 4, GE = 8;
-template <class Fn>
-__device__ __forceinline__ void for_adjacency(const SymArgs& a, int32_t b, int32_t m, int tid, int nthr, Fn fn) {
-  for (int32_t i0 = tid; i0 < m; i0 += GV * nthr) {
-    int32_t e[GV], f[GV];
-#pragma unroll
-    for (int v = 0; v < GV; ++v) {
-      const int32_t i = i0 + v * nthr;
-      const int32_t x = i < m ? a.perm[b + i] : -1;
-      e[v] = x >= 0 ? a.rowptr[x] : 0;
-      f[v] = x >= 0 ? a.rowptr[x + 1] : 0;
-    }
-    for (;;) {
-      bool more = false;
-#pragma unroll
-      for (int v = 0; v < GV; ++v) more |= e[v] < f[v];
-      if (!more) break;
-      int32_t p[GV][GE];
-#pragma unroll
-      for (int v = 0; v < GV; ++v)
-#pragma unroll
-        for (int k = 0; k < GE; ++k) p[v][k] = e[v] + k < f[v] ? a.col[e[v] + k] : -1;
-#pragma unroll
-      for (int v = 0; v < GV; ++v)
-#pragma unroll
-        for (int k = 0; k < GE; ++k) p[v][k] = p[v][k] >= 0 ? a.iperm[p[v][k]] : -1;
-#pragma unroll
-      for (int v = 0; v < GV; ++v) {
-#pragma unroll
-        for (int k = 0; k < GE; ++k)
-          if (p[v][k] >= 0) fn(i0 + v * nthr, p[v][k]);
-        e[v] += GE;
-      }
-    }
-  }
-}
+constexpr int SLAB_ILP = 4;
 
 // Step 1's gather, done once: the upper adjacency entries (column i, position
 // pos > b + i) of the node's columns and the entries of its incoming elements
@@ -195,49 +157,24 @@ __device__ void gather_entries(const SymArgs& a, int32_t t, int32_t b, int32_t m
     }
     if (slot < cap) top[-1 - slot] = make_int2(i, pos);
   };
-  for (int32_t ib = tid - lane; ib < m; ib += GV * nthr) {
-    const int32_t i0 = ib + lane;
-    int32_t e[GV], f[GV];
+  // the node's columns own one contiguous slab of B's pattern: stream it,
+  // SLAB_ILP pairs a lane per round, all loads issued first
+  const int32_t e0 = a.prow[b], e1 = a.prow[b + m];
+  for (int32_t eb = e0 + SLAB_ILP * (tid - lane); eb < e1; eb += SLAB_ILP * nthr) {
+    int2 pq[SLAB_ILP];
 #pragma unroll
-    for (int v = 0; v < GV; ++v) {
-      const int32_t i = i0 + v * nthr;
-      const int32_t x = i < m ? a.perm[b + i] : -1;
-      e[v] = x >= 0 ? a.rowptr[x] : 0;
-      f[v] = x >= 0 ? a.rowptr[x + 1] : 0;
+    for (int u = 0; u < SLAB_ILP; ++u) {
+      const int32_t e = eb + 32 * u + lane;
+      pq[u] = e < e1 ? a.ppair[e] : make_int2(0, -1);
     }
-    for (;;) {
-      bool more = false;
 #pragma unroll
-      for (int v = 0; v < GV; ++v) more |= e[v] < f[v];
-      if (!__any_sync(0xffffffffu, more)) break;
-      int32_t p[GV][GE];
-#pragma unroll
-      for (int v = 0; v < GV; ++v)
-#pragma unroll
-        for (int k = 0; k < GE; ++k) p[v][k] = e[v] + k < f[v] ? a.col[e[v] + k] : -1;
-#pragma unroll
-      for (int v = 0; v < GV; ++v)
-#pragma unroll
-        for (int k = 0; k < GE; ++k) p[v][k] = p[v][k] >= 0 ? a.iperm[p[v][k]] : -1;
-      int32_t nv = 0;
-#pragma unroll
-      for (int v = 0; v < GV; ++v)
-#pragma unroll
-        for (int k = 0; k < GE; ++k) {
-          if (p[v][k] <= b + i0 + v * nthr) p[v][k] = -1;     // not above the column (or no entry)
-          nv += p[v][k] >= 0;
-        }
-      const int32_t inc = warp_incl_scan_i32(nv);
+    for (int u = 0; u < SLAB_ILP; ++u) {
+      const bool up = pq[u].y > pq[u].x;           // above the column (never the padding)
+      const unsigned bal = __ballot_sync(0xffffffffu, up);
       int32_t base = 0;
-      if (lane == 31 && inc) base = atomicAdd(cnt, inc);
-      base = __shfl_sync(0xffffffffu, base, 31) + inc - nv;
-#pragma unroll
-      for (int v = 0; v < GV; ++v) {
-#pragma unroll
-        for (int k = 0; k < GE; ++k)
-          if (p[v][k] >= 0) keep(i0 + v * nthr, p[v][k], base++);
-        e[v] += GE;
-      }
+      if (lane == 0 && bal) base = atomicAdd(cnt, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0) + __popc(bal & lanemask_lt());
+      if (up) keep(pq[u].x - b, pq[u].y, base);
     }
   }
   for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
@@ -752,12 +689,14 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
         atomicOr(&rows[tri_off(e.x, W) - (e.x >> 5) + (l >> 5)], 1u << (l & 31));
       }
     } else {
-      for_adjacency(a, b, m, tid, nthr, [&](int32_t i, int32_t pos) {
-        if (pos > b + i) {
-          const int32_t l = local_of(pos);
+      const int32_t e0 = a.prow[b], e1 = a.prow[b + m];
+      for (int32_t e = e0 + tid; e < e1; e += nthr) {
+        const int2 pq = a.ppair[e];
+        if (pq.y > pq.x) {
+          const int32_t i = pq.x - b, l = local_of(pq.y);
           atomicOr(&rows[tri_off(i, W) - (i >> 5) + (l >> 5)], 1u << (l & 31));
         }
-      });
+      }
       for (int32_t el = a.elem_head[t]; el >= 0; el = a.elem_hdr[3 * el]) {
         const int32_t off = a.elem_hdr[3 * el + 1], len = a.elem_hdr[3 * el + 2];
         const int32_t r0 = a.elem_data[off] - b;      // smallest entry: a column of this node
@@ -802,7 +741,63 @@ __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, int64_t 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
+// B's pattern by rows in position order (row p = the neighbours of vertex
+// perm[p], at their positions), so that the columns of a tree node, which
+// hold consecutive positions, own one contiguous slab. deg[p] = |adj(perm[p])|
+// for p < n and deg[n] = 0, for the exclusive scan that gives prow.
+__global__ void k_perm_degrees(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm, int32_t n,
+                               int32_t* __restrict__ deg) {
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += gridDim.x * blockDim.x) {
+    int32_t d = 0;
+    if (p < n) {
+      const int32_t x = perm[p];
+      d = rowptr[x + 1] - rowptr[x];
+    }
+    deg[p] = d;
+  }
+}
+
+// One thread per row: its neighbours' positions, PP_ILP at a time.
+constexpr int PP_ILP = 8;
+__global__ void k_perm_pairs(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
+                             const int32_t* __restrict__ prow, int32_t n, int2* __restrict__ ppair) {
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int32_t x = perm[p];
+    const int32_t e0 = rowptr[x], d = rowptr[x + 1] - e0, o = prow[p];
+    for (int32_t k0 = 0; k0 < d; k0 += PP_ILP) {
+      int32_t u[PP_ILP];
+#pragma unroll
+      for (int k = 0; k < PP_ILP; ++k) u[k] = k0 + k < d ? col[e0 + k0 + k] : -1;
+#pragma unroll
+      for (int k = 0; k < PP_ILP; ++k) u[k] = u[k] >= 0 ? iperm[u[k]] : -1;
+#pragma unroll
+      for (int k = 0; k < PP_ILP; ++k)
+        if (k0 + k < d) ppair[o + k0 + k] = make_int2(p, u[k]);
+    }
+  }
+}
+
 }  // namespace
+
+// Builds the position-ordered slab of B = P G P^T for perm/iperm; the caller
+// frees *prow and *ppair.
+static fp_status build_perm_pairs(fp_handle* h, const int32_t* perm, const int32_t* iperm, int32_t** prow,
+                                  int2** ppair) {
+  const int32_t n = h->n;
+  int32_t* deg = (int32_t*)dev_alloc(h, sizeof(int32_t) * ((int64_t)n + 1));
+  int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * (scan_tmp_ints((int64_t)n + 1) + 8));
+  *prow = (int32_t*)dev_alloc(h, sizeof(int32_t) * ((int64_t)n + 1));
+  *ppair = (int2*)dev_alloc(h, sizeof(int2) * (h->nnz > 0 ? h->nnz : 1));
+  if (!deg || !tmp || !*prow || !*ppair) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic pattern");
+  const int G = grid_for((int64_t)n + 1, 256);
+  FP_LAUNCH(h, k_perm_degrees, G, 256, 0, h->rowptr, perm, n, deg);
+  scan_exclusive(h, deg, *prow, (int64_t)n + 1, tmp);
+  FP_LAUNCH(h, k_perm_pairs, G, 256, 0, h->rowptr, h->col, perm, iperm, *prow, n, *ppair);
+  dev_free(h, deg);
+  dev_free(h, tmp);
+  return FP_OK;
+}
 
 fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops) {
   const int32_t n = h->n;
@@ -812,36 +807,83 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
   if (n == 0) return FP_OK;
   if (h->D + 1 > SYM_MAX_ANC) return fail(h, FP_ERR_UNSUPPORTED, "tree deeper than 31 levels");
   int64_t cap_hdr = (int64_t)n + 1024, cap_data = 8 * (int64_t)n + (1 << 20), pool_words = 4 * (int64_t)n + (1 << 22);
+  int32_t* prow = nullptr;
+  int2* ppair = nullptr;
+  FP_TRY(build_perm_pairs(h, h->perm, h->iperm, &prow, &ppair));
+  // launch lists: every leaf (no non-empty child; they need no other node's
+  // result), largest first, in one launch; then the inner nodes depth by
+  // depth, deepest first (a node's elements come from its descendants)
+  std::vector<int32_t> hsz = h->node_size_host;
+  if ((int64_t)hsz.size() != nn) {
+    hsz.assign(nn, 0);
+    cudaError_t e = cudaMemcpyAsync(hsz.data(), h->node_size, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
+    int32_t st0 = 0;
+    FP_TRY(sync_status(h, &st0));
+  }
+  // below[t]: some descendant of t holds vertices. A node with empty children
+  // can still have them (a child split with an empty separator), and such a
+  // node must wait for its descendants' elements.
+  std::vector<int32_t> flat, leaves;
+  std::vector<std::vector<int32_t>> inner(h->D + 1);
+  std::vector<uint8_t> below(nn, 0);
+  for (int64_t t = nn - 1; t >= 0; --t) {
+    const int64_t c = 2 * t + 1;
+    if (c < nn) below[t] = hsz[c] > 0 || hsz[c + 1] > 0 || below[c] || below[c + 1];
+  }
+  for (int64_t t = 0; t < nn; ++t) {
+    if (hsz[t] == 0) continue;
+    if (!below[t]) leaves.push_back((int32_t)t);
+    else inner[63 - __builtin_clzll((unsigned long long)t + 1)].push_back((int32_t)t);
+  }
+  std::stable_sort(leaves.begin(), leaves.end(), [&](int32_t x, int32_t y) { return hsz[x] > hsz[y]; });
+  std::vector<std::pair<int64_t, int32_t>> launches;     // (offset in flat, count)
+  launches.push_back({0, (int32_t)leaves.size()});
+  flat = leaves;
+  for (int32_t d = h->D; d >= 0; --d) {
+    if (inner[d].empty()) continue;
+    launches.push_back({(int64_t)flat.size(), (int32_t)inner[d].size()});
+    flat.insert(flat.end(), inner[d].begin(), inner[d].end());
+  }
+  int32_t* lst = (int32_t*)dev_alloc(h, sizeof(int32_t) * (flat.size() + 1));
+  if (!lst) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic node lists");
+  if (!flat.empty()) {
+    cudaError_t e = cudaMemcpyAsync(lst, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "symbolic node lists");
+  }
   for (int attempt = 0; attempt < 4; ++attempt) {
     int32_t* head = (int32_t*)dev_alloc(h, sizeof(int32_t) * nn);
     int32_t* big = (int32_t*)dev_alloc(h, sizeof(int32_t) * (nn + 64));
     int32_t* hdr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 3 * cap_hdr);
     int32_t* data = (int32_t*)dev_alloc(h, sizeof(int32_t) * cap_data);
     uint32_t* pool = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * pool_words);
-    // [0..1] sums, [2..3] element counters, [4 + d] the scratch-pool counter of level d
+    // [0..1] sums, [2..3] element counters, [4 + j] the scratch-pool counter of launch j
     unsigned long long* ctr = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (8 + 32));
     if (!head || !big || !hdr || !data || !pool || !ctr) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic workspace");
     fill_i32(h, head, -1, nn);
-    fill_i32(h, big + nn, 0, 64);                 // per-level deferred-node counts
+    fill_i32(h, big + nn, 0, 64);                 // per-launch deferred-node counts
     FP_LAUNCH(h, k_fill_u64, 1, 64, 0, ctr, 0ull, (int64_t)(8 + 32));
     allow_max_dynamic_smem(k_symbolic_nodes);
-    for (int32_t d = h->D; d >= 0; --d) {
-      const int32_t t0 = (1 << d) - 1, T = 1 << d;
-      SymArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_of, h->node_begin, h->node_size, t0, T,
+    for (size_t j = 0; j < launches.size(); ++j) {
+      const int64_t off = launches[j].first;
+      const int32_t c = launches[j].second;
+      if (c == 0) continue;
+      // deferred nodes of launch j reuse its own stretch of `big`
+      SymArgs sa{prow, ppair, h->perm, h->node_of, h->node_begin, h->node_size, 0, 0,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
-                 ctr + 4 + d, big + t0, big + nn + d, h->d_status, nullptr, 0, nullptr};
+                 ctr + 4 + j, big + off, big + nn + j, h->d_status, lst + off, c, nullptr};
       ProfScope ps(FP_PROF_SYMBOLIC, h->stream);
-      if (T <= NUM_SMS_B300) {
+      if (c <= NUM_SMS_B300) {
         // few nodes: one large CTA each
-        FP_LAUNCH(h, k_symbolic_nodes, T, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 0, 0);
+        FP_LAUNCH(h, k_symbolic_nodes, c, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 0, 0);
       } else {
         // many small nodes: one small CTA each (its first warp sweeps the
         // columns, all of them gather); the ones that do not fit go to the
         // large CTAs afterwards. Four warps a node while every node of the
-        // level is resident at once (four such CTAs per SM), else two.
-        const int32_t ne = d < (int32_t)h->level_nodes.size() ? h->level_nodes[d] : T;
-        const int thr = ne <= NUM_SMS_B300 * 4 ? 128 : 64;
-        FP_LAUNCH(h, k_symbolic_nodes, T, thr, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+        // launch is resident at once (four such CTAs per SM), else two.
+        const int thr = c <= NUM_SMS_B300 * 4 ? 128 : 64;
+        FP_LAUNCH(h, k_symbolic_nodes, c, thr, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
+        sa.in_list = nullptr;
         FP_LAUNCH(h, k_symbolic_nodes, NUM_SMS_B300, SB_THREADS, (size_t)SB_SMEM_WORDS * 4, sa, SB_SMEM_WORDS, 1,
                   0);
       }
@@ -862,6 +904,9 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     }
     *nnzL = (int64_t)hs[0];
     *flops = (int64_t)hs[1];
+    dev_free(h, prow);
+    dev_free(h, ppair);
+    dev_free(h, lst);
     return FP_OK;
   }
   return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic pools exhausted");
@@ -878,6 +923,9 @@ fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm,
   const int64_t nn = h->nnodes;
   if (h->D + 1 > SYM_MAX_ANC) return fail(h, FP_ERR_UNSUPPORTED, "tree deeper than 31 levels");
   int64_t pool_words = 4 * (int64_t)n + (1 << 22);
+  int32_t* prow = nullptr;
+  int2* ppair = nullptr;
+  FP_TRY(build_perm_pairs(h, perm, iperm, &prow, &ppair));
   for (int attempt = 0; attempt < 4; ++attempt) {
     int32_t* head = (int32_t*)dev_alloc(h, sizeof(int32_t) * nn);
     int32_t* big = (int32_t*)dev_alloc(h, sizeof(int32_t) * ((int64_t)count + 64));
@@ -890,7 +938,7 @@ fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm,
     FP_LAUNCH(h, k_fill_u64, 1, 32, 0, ctr, 0ull, (int64_t)8);
     allow_max_dynamic_smem(k_symbolic_nodes);
     // leaves export nothing and receive nothing: no element lists are needed
-    SymArgs sa{h->rowptr, h->col, perm, iperm, h->node_of, h->node_begin, h->node_size, 0, 0, scr, scr + n, ctr,
+    SymArgs sa{prow, ppair, perm, h->node_of, h->node_begin, h->node_size, 0, 0, scr, scr + n, ctr,
                head, nullptr, nullptr, 0, 0, ctr + 2, pool, pool_words, ctr + 4, big, big + count, h->d_status,
                d_nodes, count, d_fill};
     FP_LAUNCH(h, k_symbolic_nodes, count, 64, (size_t)SW_SMEM_WORDS * 4, sa, SW_SMEM_WORDS, 0, 1);
@@ -906,6 +954,8 @@ fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm,
       pool_words *= 4;
       continue;
     }
+    dev_free(h, prow);
+    dev_free(h, ppair);
     return FP_OK;
   }
   return fail(h, FP_ERR_OUT_OF_MEMORY, "leaf fill pools exhausted");
