@@ -461,6 +461,7 @@ namespace fp {
 // Copies a caller's patch map, flagging labels outside [0, k).
 __global__ void k_copy_labels(const int32_t* __restrict__ g, int32_t n, int32_t k, int32_t* __restrict__ out,
                               int32_t* status) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t p = g[v];
     if (p < 0 || p >= k) atomicOr(status, ST_BAD_INDEX);

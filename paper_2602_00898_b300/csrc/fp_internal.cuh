@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/fastperm.h"
@@ -213,9 +214,37 @@ void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32
 
 }  // namespace fp
 
+namespace fp {
+
+// Launches on the handle's stream allow programmatic dependent launch: the
+// next kernel's CTAs may be scheduled as soon as every CTA of the one before
+// has exited, without waiting for the grid's completion to be processed.
+// Every kernel of the library therefore starts with FP_PDL_WAIT(), which
+// holds it until the previous grid has completed and its writes are visible
+// (a no-op for a launch that did not allow the early start).
+template <class... KArgs, class... Args>
+inline void launch_pdl(cudaStream_t s, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace fp
+
+#define FP_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
 #define FP_LAUNCH(h, kernel, grid, block, smem, ...)                                  \
   do {                                                                                \
-    kernel<<<(grid), (block), (smem), (h)->stream>>>(__VA_ARGS__);                    \
+    fp::launch_pdl((h)->stream, kernel, dim3(grid), dim3(block), (size_t)(smem), __VA_ARGS__); \
     (h)->launches++;                                                                  \
   } while (0)
 

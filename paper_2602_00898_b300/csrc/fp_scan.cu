@@ -43,6 +43,7 @@ __device__ __forceinline__ int32_t block_excl_scan(int32_t x, int32_t* total) {
 }
 
 __global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+  FP_PDL_WAIT();
   int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int32_t s = 0;
 #pragma unroll
@@ -55,6 +56,7 @@ __global__ void k_tile_sums(const int32_t* __restrict__ in, int64_t n, int32_t* 
 
 // One CTA scans the tile sums in place (exclusive), chunk by chunk with a carry.
 __global__ void k_scan_sums(int32_t* sums, int64_t nt, int32_t* total_out) {
+  FP_PDL_WAIT();
   int32_t carry = 0;
   for (int64_t base = 0; base < nt; base += blockDim.x) {
     int64_t i = base + threadIdx.x;
@@ -69,6 +71,7 @@ __global__ void k_scan_sums(int32_t* sums, int64_t nt, int32_t* total_out) {
 
 __global__ void k_tile_scan(const int32_t* __restrict__ in, int64_t n, const int32_t* __restrict__ sums,
                             int32_t* __restrict__ out) {
+  FP_PDL_WAIT();
   int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int32_t v[SCAN_ITEMS];
   int32_t s = 0;
@@ -90,6 +93,7 @@ __global__ void k_tile_scan(const int32_t* __restrict__ in, int64_t n, const int
 // 1024 x 4 items with a carry, out[n] = total.
 __global__ void __launch_bounds__(1024) k_scan_small(const int32_t* __restrict__ in, int64_t n,
                                                      int32_t* __restrict__ out) {
+  FP_PDL_WAIT();
   int32_t carry = 0;
   for (int64_t c = 0; c < n; c += 1024 * SCAN_ITEMS) {
     const int64_t base = c + (int64_t)threadIdx.x * SCAN_ITEMS;
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(1024) k_scan_small(const int32_t* __restrict__
 // is zeroed (so that it can serve as the scatter cursors).
 __global__ void __launch_bounds__(1024) k_scan_pair_small(const int32_t* __restrict__ a, int32_t* __restrict__ oa,
                                                           int32_t* b, int32_t* __restrict__ ob, int64_t n) {
+  FP_PDL_WAIT();
   const int32_t* in = blockIdx.x == 0 ? a : b;
   int32_t* out = blockIdx.x == 0 ? oa : ob;
   int32_t carry = 0;
@@ -145,11 +150,13 @@ __global__ void __launch_bounds__(1024) k_scan_pair_small(const int32_t* __restr
 }
 
 __global__ void k_fill(int32_t* p, int32_t v, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
 }
 
 __global__ void k_iota(int32_t* p, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int32_t)i;
 }

@@ -25,6 +25,7 @@ constexpr int ROW_WARPS = 8;         // warps per CTA in the warp-per-row kernel
 // that the fill pass places entries without atomics.
 __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* __restrict__ cnt,
                              int2* __restrict__ slots, int32_t* status) {
+  FP_PDL_WAIT();
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) {
@@ -43,6 +44,7 @@ __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int3
 
 __global__ void k_face_fill(const int32_t* __restrict__ faces, int64_t nf, int32_t n, const int32_t* __restrict__ off,
                             const int2* __restrict__ slots, int32_t* __restrict__ raw) {
+  FP_PDL_WAIT();
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) continue;
@@ -61,6 +63,7 @@ __global__ void k_face_fill(const int32_t* __restrict__ faces, int64_t nf, int32
 
 __global__ void k_pat_count(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t nrows, int32_t b,
                             int32_t* __restrict__ cnt, int32_t* status) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
     int32_t u = i / b, c = 0;
     for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
@@ -74,6 +77,7 @@ __global__ void k_pat_count(const int32_t* __restrict__ rp, const int32_t* __res
 
 __global__ void k_pat_fill(const int32_t* __restrict__ rp, const int32_t* __restrict__ col, int32_t nrows, int32_t b,
                            const int32_t* __restrict__ off, int32_t* __restrict__ fill, int32_t* __restrict__ raw) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x) {
     int32_t u = i / b, c = 0;
     for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
@@ -117,6 +121,7 @@ __device__ __forceinline__ int32_t dedupe_row_regs(int32_t* __restrict__ raw, in
 // ucnt. Longer rows are listed for the warp kernel.
 __global__ void k_rows_dedupe_thread(const int32_t* __restrict__ off, int32_t n, int32_t* __restrict__ raw,
                                      int32_t* __restrict__ ucnt, int32_t* __restrict__ mid_rows, int32_t* n_mid) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t b = off[v], L = off[v + 1] - b;
     if (L > 32) {
@@ -135,6 +140,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_dedupe_warp(const int32
                                                                       const int32_t* n_mid, int32_t* __restrict__ raw,
                                                                       int32_t* __restrict__ ucnt,
                                                                       int32_t* __restrict__ long_rows, int32_t* n_long) {
+  FP_PDL_WAIT();
   __shared__ int32_t sbuf[ROW_WARPS][WARP_ROW_CAP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* buf = sbuf[wid];
@@ -166,6 +172,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_dedupe_warp(const int32
 __global__ void k_rows_dedupe_block(const int32_t* __restrict__ off, const int32_t* __restrict__ long_rows,
                                     const int32_t* n_long, int32_t* __restrict__ raw, int32_t* __restrict__ ucnt,
                                     int32_t* status) {
+  FP_PDL_WAIT();
   extern __shared__ int32_t buf[];
   __shared__ int32_t warp_cnt[32];
   for (int32_t r = blockIdx.x; r < *n_long; r += gridDim.x) {
@@ -206,6 +213,7 @@ __global__ void k_rows_dedupe_block(const int32_t* __restrict__ off, const int32
 // hold about six entries).
 __global__ void k_rows_compact(const int32_t* __restrict__ off, const int32_t* __restrict__ raw, int32_t n,
                                const int32_t* __restrict__ rowptr, int32_t* __restrict__ col) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t s = off[v], d = rowptr[v], L = rowptr[v + 1] - d;
     for (int32_t i = 0; i < L; ++i) col[d + i] = raw[s + i];
@@ -216,6 +224,7 @@ __global__ void k_rows_compact(const int32_t* __restrict__ off, const int32_t* _
 // search in the sorted row of v.
 __global__ void k_check_symmetric(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, int32_t n,
                                   int32_t* status) {
+  FP_PDL_WAIT();
   const int lane = threadIdx.x & 31;
   for (int32_t u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += (gridDim.x * blockDim.x) >> 5) {
     for (int32_t e = rowptr[u] + lane; e < rowptr[u + 1]; e += 32) {

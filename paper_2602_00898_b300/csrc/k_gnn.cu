@@ -172,6 +172,7 @@ __device__ __forceinline__ void leaf_neighbours(const ScoreArgs& a, int32_t b, i
 }
 
 __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
@@ -363,6 +364,7 @@ __global__ void k_choose(const int32_t* __restrict__ leaves, int32_t nl, const i
                          const int32_t* __restrict__ node_size, const int64_t* __restrict__ fill_p,
                          const int64_t* __restrict__ fill_l, const int32_t* __restrict__ perm_l,
                          int32_t* __restrict__ perm, unsigned long long* __restrict__ stats) {
+  FP_PDL_WAIT();
   const int32_t t = leaves[blockIdx.x];
   const bool keep = fill_l[t] < fill_p[t];
   if (keep) {
@@ -377,6 +379,7 @@ __global__ void k_choose(const int32_t* __restrict__ leaves, int32_t nl, const i
 }
 
 __global__ void k_scatter_inverse(const int32_t* __restrict__ perm, int32_t n, int32_t* __restrict__ iperm) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
 }
 

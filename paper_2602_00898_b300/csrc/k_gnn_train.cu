@@ -56,6 +56,7 @@ __device__ __forceinline__ float xval(const uint8_t* x, int64_t p, int k) { retu
 __global__ void k_train_fwd1(const float* __restrict__ P, const uint8_t* __restrict__ x,
                              const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                              const uint8_t* __restrict__ mask, int32_t n, TrainBufs b) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     if (mask[p]) atomicAdd(b.count, 1);
     float m0[6] = {0, 0, 0, 0, 0, 0};
@@ -78,6 +79,7 @@ __global__ void k_train_fwd1(const float* __restrict__ P, const uint8_t* __restr
 __global__ void k_train_fwd2(const float* __restrict__ P, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ col, const uint8_t* __restrict__ mask,
                              const float* __restrict__ target, int32_t n, TrainBufs b) {
+  FP_PDL_WAIT();
   const float N = fmaxf((float)*b.count, 1.0f);
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     float m1[32];
@@ -122,6 +124,7 @@ __global__ void k_train_fwd2(const float* __restrict__ P, const int32_t* __restr
 // layer 1 backward rows
 __global__ void k_train_bwd1(const float* __restrict__ P, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ col, int32_t n, TrainBufs b) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     float dh[32];
     for (int k = 0; k < 32; ++k) {
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_train_partial(const uint8_t* __r
                                                               const uint8_t* __restrict__ mask,
                                                               const float* __restrict__ target,
                                                               const float* __restrict__ P, int32_t n, TrainBufs b) {
+  FP_PDL_WAIT();
   __shared__ float sx[GT_CHUNK][6], sm0[GT_CHUNK][6], sh1[GT_CHUNK][32], sm1[GT_CHUNK][32], sh2[GT_CHUNK][32],
       sdz2[GT_CHUNK][32], sdz1[GT_CHUNK][32], sds[GT_CHUNK];
   const int64_t c = blockIdx.x;
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_train_partial(const uint8_t* __r
 // sum of the partials in chunk order, the loss, and the update
 __global__ void k_train_reduce(float* __restrict__ P, float* __restrict__ grad, float lr, int64_t nch,
                                float* __restrict__ loss, TrainBufs b) {
+  FP_PDL_WAIT();
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P_COUNT; j += gridDim.x * blockDim.x) {
     float s = 0.0f;
     for (int64_t c = 0; c < nch; ++c) s += b.partial[c * P_COUNT + j];
@@ -221,6 +226,7 @@ __global__ void k_train_reduce(float* __restrict__ P, float* __restrict__ grad, 
 }
 
 __global__ void k_quantise(const float* __restrict__ P, int32_t* __restrict__ Q) {
+  FP_PDL_WAIT();
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P_COUNT; j += gridDim.x * blockDim.x) {
     const bool bias = (j >= P_B1 && j < P_W2S) || (j >= P_B2 && j < P_W3) || j == P_C;
     const float scale = bias ? 8192.0f : 128.0f;
@@ -232,10 +238,12 @@ __global__ void k_quantise(const float* __restrict__ P, int32_t* __restrict__ Q)
 // ---- samples -------------------------------------------------------------------
 
 __global__ void k_scatter_positions(const int32_t* __restrict__ perm, int32_t n, int32_t* __restrict__ iperm) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
 }
 
 __global__ void k_seed_keys(int32_t n, uint64_t r, uint32_t* __restrict__ key) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     key[v] = r == 0 ? 0u : (uint32_t)(splitmix64_state(r * 0x9E3779B97F4A7C15ull + (uint64_t)(uint32_t)v) >> 32);
 }
@@ -245,6 +253,7 @@ __global__ void k_keep_best(const int32_t* __restrict__ leaves, const int32_t* _
                             const int32_t* __restrict__ node_size, const int64_t* __restrict__ fill, int32_t r,
                             int64_t* __restrict__ best_fill, const int32_t* __restrict__ perm_r,
                             int32_t* __restrict__ best_perm) {
+  FP_PDL_WAIT();
   const int32_t t = leaves[blockIdx.x];
   const bool take = r == 0 || fill[t] < best_fill[t];
   if (take) {
@@ -259,6 +268,7 @@ __global__ void k_targets(const int32_t* __restrict__ leaves, const int32_t* __r
                           const int32_t* __restrict__ node_size, const int32_t* __restrict__ best_perm,
                           const int32_t* __restrict__ iperm, float* __restrict__ target, int32_t* __restrict__ rank,
                           uint8_t* __restrict__ mask) {
+  FP_PDL_WAIT();
   const int32_t t = leaves[blockIdx.x];
   const int32_t b = node_begin[t], m = node_size[t];
   for (int32_t k = threadIdx.x; k < m; k += blockDim.x) {
@@ -275,6 +285,7 @@ __global__ void k_leaf_degree(const int32_t* __restrict__ leaves, const int32_t*
                               const int32_t* __restrict__ iperm, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ col, int32_t* __restrict__ deg, int32_t* __restrict__ lcol,
                               const int32_t* __restrict__ lrowptr) {
+  FP_PDL_WAIT();
   const int32_t t = leaves[blockIdx.x];
   const int32_t b = node_begin[t], m = node_size[t];
   for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {

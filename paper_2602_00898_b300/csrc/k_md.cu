@@ -53,11 +53,13 @@ int pow2_host(int x) {
 }
 
 __global__ void k_node_sizes(const int32_t* __restrict__ node_of, int32_t n, int32_t* __restrict__ size) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) atomicAdd(&size[node_of[v]], 1);
 }
 
 __global__ void k_scatter_nodes(const int32_t* __restrict__ node_of, int32_t n, const int32_t* __restrict__ start,
                                 int32_t* __restrict__ fill, int32_t* __restrict__ list) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int32_t t = node_of[v];
     list[start[t] + atomicAdd(&fill[t], 1)] = v;
@@ -67,6 +69,7 @@ __global__ void k_scatter_nodes(const int32_t* __restrict__ node_of, int32_t n, 
 // Schedule layout (one CTA). sub: scratch [nnodes].
 __global__ void k_tree_layout(int32_t D, int64_t nnodes, const int32_t* __restrict__ size, int32_t* __restrict__ sub,
                               int32_t* __restrict__ begin, int32_t schedule) {
+  FP_PDL_WAIT();
   __shared__ int32_t red[40];
   for (int32_t d = D; d >= 0; --d) {
     const int64_t a = ((int64_t)1 << d) - 1, b = ((int64_t)1 << (d + 1)) - 1;
@@ -288,6 +291,7 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
 }
 
 __global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char* mine = smem + (size_t)wid * a.slice_bytes;
@@ -432,6 +436,7 @@ __device__ __forceinline__ uint32_t group_min_key(const uint32_t* deg2, int g, i
 // ---- sparse kernel (separators) --------------------------------------------------------
 
 __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int32_t s_ovf;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -605,6 +610,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
 // ---- global kernel -------------------------------------------------------------------
 
 __global__ void __launch_bounds__(MD_THREADS) k_md_global(MdArgs a) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t red32[40];
   __shared__ int32_t s_nnb;
@@ -704,11 +710,13 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_global(MdArgs a) {
 }
 
 __global__ void k_iperm(const int32_t* __restrict__ perm, int32_t n, int32_t* __restrict__ iperm) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
 }
 
 __global__ void k_dof_perm(const int32_t* __restrict__ perm, int32_t n, int32_t b, int32_t* __restrict__ perm_d,
                            int32_t* __restrict__ iperm_d) {
+  FP_PDL_WAIT();
   const int64_t N = (int64_t)n * b;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = (int32_t)(i / b), c = (int32_t)(i % b);
@@ -720,6 +728,7 @@ __global__ void k_dof_perm(const int32_t* __restrict__ perm, int32_t n, int32_t 
 
 __global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t* __restrict__ cc, int32_t n, int32_t b,
                                int32_t* __restrict__ parent_d, int32_t* __restrict__ cc_d) {
+  FP_PDL_WAIT();
   const int64_t N = (int64_t)n * b;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t j = (int32_t)(i / b), c = (int32_t)(i % b);
@@ -732,6 +741,7 @@ __global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t
 
 __global__ void k_early_count(const int32_t* __restrict__ node_of, int32_t n, int32_t t0, int32_t T,
                               int32_t* __restrict__ cnt) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t t = node_of[v];
     if (t >= t0 && t < t0 + T) atomicAdd(&cnt[t], 1);
@@ -741,6 +751,7 @@ __global__ void k_early_count(const int32_t* __restrict__ node_of, int32_t n, in
 // List offsets of the level's nodes after the lists of earlier levels (*base).
 __global__ void k_early_starts(const int32_t* __restrict__ cnt, int32_t t0, int32_t T, int32_t* base,
                                int32_t* __restrict__ start, int32_t* __restrict__ fill) {
+  FP_PDL_WAIT();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     int32_t b = *base;
     for (int32_t i = 0; i < T; ++i) {
@@ -755,6 +766,7 @@ __global__ void k_early_starts(const int32_t* __restrict__ cnt, int32_t t0, int3
 __global__ void k_early_scatter(const int32_t* __restrict__ node_of, int32_t n, int32_t t0, int32_t T,
                                 const int32_t* __restrict__ start, int32_t* __restrict__ fill,
                                 int32_t* __restrict__ list) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t t = node_of[v];
     if (t >= t0 && t < t0 + T) list[start[t] + atomicAdd(&fill[t], 1)] = v;
@@ -767,6 +779,7 @@ __global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, in
                               const int32_t* __restrict__ node_size, const int32_t* __restrict__ node_begin,
                               const int32_t* __restrict__ rank, const int32_t* __restrict__ ovf,
                               int32_t* __restrict__ perm, int64_t smem_max) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t t = node_of[v];
     if (t < NE && (int64_t)sparse_smem(node_size[t]) <= smem_max && !ovf[t]) perm[node_begin[t] + rank[v]] = v;

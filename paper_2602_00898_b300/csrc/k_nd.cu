@@ -40,6 +40,7 @@ constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
 
 // ---- generic counting sort helpers ----------------------------------------------------
 __global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t* __restrict__ cnt) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t c = key[i];
     if (c >= 0) atomicAdd(&cnt[c - koff], 1);
@@ -48,6 +49,7 @@ __global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t k
 
 __global__ void k_scatter_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, const int32_t* __restrict__ start,
                              int32_t* __restrict__ fill, int32_t* __restrict__ list) {
+  FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int32_t c = key[i];
     if (c >= 0) list[start[c - koff] + atomicAdd(&fill[c - koff], 1)] = i;
@@ -61,6 +63,7 @@ constexpr int GROUP_SMALL_MAX = 8192;
 __global__ void __launch_bounds__(1024) k_group_small(const int32_t* __restrict__ key, int32_t n, int32_t koff,
                                                       int32_t nk, int32_t* __restrict__ start,
                                                       int32_t* __restrict__ list, int32_t* __restrict__ zero4) {
+  FP_PDL_WAIT();
   extern __shared__ int32_t gsm[];
   __shared__ int32_t red[40];
   int32_t* cnt = gsm;          // [nk]
@@ -105,6 +108,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
                                                               const int32_t* __restrict__ gmap, int32_t k,
                                                               const int32_t* __restrict__ q_rowptr, int32_t* qdeg,
                                                               int32_t* q_col, int32_t* q_w, int32_t* status) {
+  FP_PDL_WAIT();
   __shared__ int32_t buf[QCAP];
   __shared__ int32_t starts[QCAP + 1];
   __shared__ int32_t red[40];
@@ -222,6 +226,7 @@ __device__ int block_bfs(const BisectView& v, int32_t src, int32_t* snext) {
 }
 
 __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(16) int32_t bsm[];
   __shared__ int64_t red64[40];
   __shared__ int32_t red[40];
@@ -473,6 +478,7 @@ struct LevelArgs {
 // a neighbour on the other side. Vertices of nodes that are leaves at this
 // depth become final.
 __global__ void k_nd_superset(LevelArgs a) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
     if (a.final_[v]) continue;
     const int32_t t = a.node_of[v];
@@ -531,6 +537,7 @@ __device__ __forceinline__ bool key_less(int32_t cu, int32_t u, int32_t cv, int3
 // separator) once a crossing neighbour is IN. Monotone, so concurrent updates
 // within a round only delay decisions; at most #candidates rounds.
 __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
+  FP_PDL_WAIT();
   cg::grid_group grid = cg::this_grid();
   const int32_t nc = __ldcg(&a.ctr[0]);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -577,6 +584,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
 // Separator bookkeeping (Section 5): the OUT vertices stay in node t as its
 // separator; patch weights and quotient edge weights lose them.
 __global__ void k_nd_apply(LevelArgs a) {
+  FP_PDL_WAIT();
   const int32_t nc = a.ctr[0];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     const int32_t v = a.cand[i];
@@ -652,6 +660,7 @@ __global__ void k_nd_apply(LevelArgs a) {
 // The patches follow: a split node's patch moves with its side, others drop out
 // (one launch, threads cover both ranges).
 __global__ void k_nd_move_patches(LevelArgs a) {
+  FP_PDL_WAIT();
   const int32_t span = a.n > a.k ? a.n : a.k;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < span; i += gridDim.x * blockDim.x) {
     if (i < a.n && !a.final_[i]) {
@@ -667,11 +676,13 @@ __global__ void k_nd_move_patches(LevelArgs a) {
 
 
 __global__ void k_patch_node_init(const int32_t* __restrict__ psize, int32_t k, int32_t* __restrict__ patch_node) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
     patch_node[p] = psize[p] > 0 ? 0 : -1;
 }
 
 __global__ void k_zero_i8(int8_t* p, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
 }
 

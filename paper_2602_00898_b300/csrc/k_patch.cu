@@ -39,6 +39,7 @@ constexpr int BFS_TAIL = 1024;   // frontiers up to this size run in one CTA
 // distance and the minimum label for every reached vertex.
 __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                                      unsigned long long* key, int4* fa, int4* fb, int32_t* ctr) {
+  FP_PDL_WAIT();
   cg::grid_group grid = cg::this_grid();
   int4* cur = fa;
   int4* nxt = fb;
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
 }
 
 __global__ void k_seed_flags(int32_t n, uint64_t kt, uint64_t seed, int32_t* __restrict__ flag) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     uint64_t h = splitmix64_state(seed * 0x9E3779B97F4A7C15ull + (uint64_t)(uint32_t)v);
     flag[v] = ((h >> 32) * (uint64_t)n) < (kt << 32) ? 1 : 0;
@@ -139,6 +141,7 @@ __global__ void k_seed_flags(int32_t n, uint64_t kt, uint64_t seed, int32_t* __r
 __global__ void k_seed_sources(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ flag,
                                const int32_t* __restrict__ rank, int32_t base, unsigned long long* __restrict__ key,
                                int32_t* __restrict__ seed_of, int4* __restrict__ frontier, int32_t* ctr) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     if (flag[v]) {
       int32_t r = rank[v];
@@ -155,10 +158,12 @@ __global__ void k_seed_sources(int32_t n, const int32_t* __restrict__ rowptr, co
 }
 
 __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
 __global__ void k_labels_of(const unsigned long long* __restrict__ key, int32_t n, int32_t* __restrict__ label) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     label[v] = key[v] == KEY_INF ? -1 : (int32_t)(uint32_t)key[v];
 }
@@ -168,6 +173,7 @@ __global__ void k_labels_of(const unsigned long long* __restrict__ key, int32_t 
 __global__ void k_labels_counts(const unsigned long long* __restrict__ key, const int32_t* __restrict__ rowptr,
                                 int32_t n, int32_t* __restrict__ label, int32_t* __restrict__ pcnt,
                                 int32_t* __restrict__ pdeg) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t p = (int32_t)(uint32_t)key[v];
     label[v] = p;
@@ -177,6 +183,7 @@ __global__ void k_labels_counts(const unsigned long long* __restrict__ key, cons
 }
 
 __global__ void k_zero2(int32_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     a[i] = 0;
     b[i] = 0;
@@ -184,6 +191,7 @@ __global__ void k_zero2(int32_t* __restrict__ a, int32_t* __restrict__ b, int64_
 }
 
 __global__ void k_count_unreached(const unsigned long long* __restrict__ key, int32_t n, int32_t* cnt) {
+  FP_PDL_WAIT();
   int32_t c = 0;
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) c += key[v] == KEY_INF;
   for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -197,6 +205,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_unreached_components(const int3
                                                                       const int32_t* __restrict__ col,
                                                                       const unsigned long long* __restrict__ key,
                                                                       int32_t n, int32_t* comp, int32_t* flags) {
+  FP_PDL_WAIT();
   cg::grid_group grid = cg::this_grid();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,11 +235,13 @@ __global__ void __launch_bounds__(BFS_THREADS) k_unreached_components(const int3
 }
 
 __global__ void k_component_seed_flags(const int32_t* __restrict__ comp, int32_t n, int32_t* __restrict__ flag) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
     flag[v] = comp[v] == v ? 1 : 0;
 }
 
 __global__ void k_lloyd_apply(const unsigned long long* __restrict__ best, int32_t k, int32_t* __restrict__ seed_of) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
     if (best[p]) seed_of[p] = (int32_t)(0xffffffffu - (uint32_t)best[p]);
 }
@@ -238,6 +249,7 @@ __global__ void k_lloyd_apply(const unsigned long long* __restrict__ best, int32
 // All k seeds become sources with their own rank.
 __global__ void k_all_seed_sources(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ seed_of, int32_t k,
                                    unsigned long long* __restrict__ key, int4* __restrict__ frontier, int32_t* ctr) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
     const int32_t v = seed_of[p];
     key[v] = (unsigned long long)(uint32_t)p;
@@ -247,6 +259,7 @@ __global__ void k_all_seed_sources(const int32_t* __restrict__ rowptr, const int
 }
 
 __global__ void k_oversize_flags(const int32_t* __restrict__ psize, int32_t k, int32_t cap, int32_t* __restrict__ over) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) over[p] = psize[p] > cap;
 }
 
@@ -254,6 +267,7 @@ __global__ void k_oversize_flags(const int32_t* __restrict__ psize, int32_t k, i
 // the new rank kbase + orank[p].
 __global__ void k_split_seeds(const unsigned long long* __restrict__ best, const int32_t* __restrict__ over,
                               const int32_t* __restrict__ orank, int32_t kbase, int32_t* __restrict__ seed_of) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < kbase; p += gridDim.x * blockDim.x)
     if (over[p]) seed_of[kbase + orank[p]] = (int32_t)(0xffffffffu - (uint32_t)best[p]);
 }
@@ -299,6 +313,7 @@ struct LocalArgs {
 // use more registers (four CTAs per SM) instead of spilling.
 template <int kMode>
 __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_local(LocalArgs a) {
+  FP_PDL_WAIT();
   __shared__ int32_t s_verts[LOCAL_SMEM_V];
   __shared__ int32_t s_lrow[LOCAL_SMEM_V + 1];
   __shared__ uint32_t s_dist[LOCAL_SMEM_V];
@@ -483,6 +498,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
 
 __global__ void k_patch_scatter(const int32_t* __restrict__ label, int32_t n, const int32_t* __restrict__ pstart,
                                 int32_t* __restrict__ fill, int32_t* __restrict__ pverts) {
+  FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     const int32_t p = label[v];
     pverts[pstart[p] + atomicAdd(&fill[p], 1)] = v;

@@ -41,6 +41,7 @@ enum : int32_t { SS_BAD_INDEX = 1, SS_ROW_TOO_LONG = 2, SS_COL_CAP = 4 };
 static __device__ __align__(256) int32_t g_static_scratch[SCRATCH_INTS];
 
 __global__ void ks_zero(int32_t* s, int32_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
     s[OFF_CNT + i] = 0;
     s[OFF_FILL + i] = 0;
@@ -50,6 +51,7 @@ __global__ void ks_zero(int32_t* s, int32_t n) {
 }
 
 __global__ void ks_count(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* s) {
+  FP_PDL_WAIT();
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) {
@@ -68,6 +70,7 @@ __global__ void ks_count(const int32_t* __restrict__ faces, int64_t nf, int32_t 
 
 // Exclusive scan of in[0..n) into out[0..n] by one CTA (n <= 65537).
 __global__ void ks_scan(const int32_t* in, int32_t* out, int32_t n) {
+  FP_PDL_WAIT();
   __shared__ int32_t red[40];
   int32_t carry = 0;
   for (int32_t base = 0; base < n; base += blockDim.x) {
@@ -82,6 +85,7 @@ __global__ void ks_scan(const int32_t* in, int32_t* out, int32_t n) {
 }
 
 __global__ void ks_fill(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* s) {
+  FP_PDL_WAIT();
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
     if (c[0] < 0 || c[0] >= n || c[1] < 0 || c[1] >= n || c[2] < 0 || c[2] >= n) continue;
@@ -97,6 +101,7 @@ __global__ void ks_fill(const int32_t* __restrict__ faces, int64_t nf, int32_t n
 
 // One warp per row: sort the raw row in shared memory, keep the unique prefix.
 __global__ void __launch_bounds__(256) ks_dedupe(int32_t n, int32_t* s) {
+  FP_PDL_WAIT();
   __shared__ int32_t sbuf[8][STATIC_ROW_CAP];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int32_t* buf = sbuf[wid];
@@ -125,6 +130,7 @@ __global__ void __launch_bounds__(256) ks_dedupe(int32_t n, int32_t* s) {
 
 __global__ void ks_compact(int32_t n, const int32_t* s, const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
                            int64_t col_cap, int32_t* status) {
+  FP_PDL_WAIT();
   const int lane = threadIdx.x & 31;
   for (int32_t v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += (gridDim.x * blockDim.x) >> 5) {
     const int32_t src = s[OFF_RAWOFF + v], dst = rowptr[v], L = rowptr[v + 1] - dst;

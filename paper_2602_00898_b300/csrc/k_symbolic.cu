@@ -500,6 +500,7 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
 // deferred list; rows that do not fit go to the global pool).
 __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_t smem_words, int32_t from_list,
                                                                int32_t may_defer) {
+  FP_PDL_WAIT();
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int32_t s_ab[32], s_ao[32];
   __shared__ int32_t s_na, s_atot, s_fail, s_is, s_cnt;
@@ -738,6 +739,7 @@ __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_
 }
 
 __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, int64_t n) {
+  FP_PDL_WAIT();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
@@ -747,6 +749,7 @@ __global__ void k_fill_u64(unsigned long long* p, unsigned long long v, int64_t 
 // for p < n and deg[n] = 0, for the exclusive scan that gives prow.
 __global__ void k_perm_degrees(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm, int32_t n,
                                int32_t* __restrict__ deg) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p <= n; p += gridDim.x * blockDim.x) {
     int32_t d = 0;
     if (p < n) {
@@ -762,6 +765,7 @@ constexpr int PP_ILP = 8;
 __global__ void k_perm_pairs(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                              const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
                              const int32_t* __restrict__ prow, int32_t n, int2* __restrict__ ppair) {
+  FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int32_t x = perm[p];
     const int32_t e0 = rowptr[x], d = rowptr[x + 1] - e0, o = prow[p];
