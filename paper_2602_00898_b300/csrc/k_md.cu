@@ -837,14 +837,14 @@ fp_status launch_early_md(fp_handle* h, int32_t d) {
   cudaStreamWaitEvent(s2, ax->fork, 0);
   const int G = grid_for(n, 256);
   ProfScope ps(FP_PROF_MD_MID, s2);
-  k_early_count<<<G, 256, 0, s2>>>(h->node_of, n, t0, T, h->early_cnt);
-  k_early_starts<<<1, 32, 0, s2>>>(h->early_cnt, t0, T, h->early_base, h->early_start, h->early_fill);
-  k_early_scatter<<<G, 256, 0, s2>>>(h->node_of, n, t0, T, h->early_start, h->early_fill, h->early_list);
+  launch_pdl(s2, k_early_count, G, 256, 0, h->node_of, n, t0, T, h->early_cnt);
+  launch_pdl(s2, k_early_starts, 1, 32, 0, h->early_cnt, t0, T, h->early_base, h->early_start, h->early_fill);
+  launch_pdl(s2, k_early_scatter, G, 256, 0, h->node_of, n, t0, T, h->early_start, h->early_fill, h->early_list);
   MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->early_start, h->early_list, h->early_loc,
            nullptr, nullptr, T, nullptr, nullptr, nullptr, nullptr, 0, h->early_ovf, nullptr, nullptr,
            t0, h->early_cnt, h->early_rank, (int64_t)SMEM_MAX};
   allow_max_dynamic_smem(k_md_sparse);
-  k_md_sparse<<<T, MD_THREADS, SMEM_MAX, s2>>>(a);
+  launch_pdl(s2, k_md_sparse, T, MD_THREADS, SMEM_MAX, a);
   h->launches += 4;
   return check_cuda(h, cudaGetLastError(), "early ordering launch");
 }
@@ -971,8 +971,8 @@ fp_status run_local_order(fp_handle* h) {
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
     ProfScope ps(FP_PROF_MD_LARGE, s2);
-    k_md_global<<<(unsigned)early.size(), MD_THREADS, smg, s2>>>(a);
-    k_early_place<<<G, 256, 0, s2>>>(h->node_of, n, h->early_nodes, h->node_size, h->node_begin, h->early_rank,
+    launch_pdl(s2, k_md_global, (unsigned)early.size(), MD_THREADS, smg, a);
+    launch_pdl(s2, k_early_place, G, 256, 0, h->node_of, n, h->early_nodes, h->node_size, h->node_begin, h->early_rank,
                                      h->early_ovf, h->perm, (int64_t)SMEM_MAX);
     h->launches += 2;
   }
@@ -985,14 +985,14 @@ fp_status run_local_order(fp_handle* h) {
     allow_max_dynamic_smem(k_md_sparse);
     {
       ProfScope ps(FP_PROF_MD_MID, s3);
-      k_md_sparse<<<(unsigned)ls[1].size(), MD_THREADS, sm, s3>>>(a);
+      launch_pdl(s3, k_md_sparse, (unsigned)ls[1].size(), MD_THREADS, sm, a);
       h->launches++;
     }
     // redo flagged nodes with global rows (grow_off/gsort_off index from 0 here)
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
     ProfScope ps(FP_PROF_MD_LARGE, s3);
-    k_md_global<<<(unsigned)ls[1].size(), MD_THREADS, smg, s3>>>(a);
+    launch_pdl(s3, k_md_global, (unsigned)ls[1].size(), MD_THREADS, smg, a);
     h->launches++;
   }
   if (!ls[2].empty()) {
@@ -1004,7 +1004,7 @@ fp_status run_local_order(fp_handle* h) {
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
     ProfScope ps(FP_PROF_MD_LARGE, s3);
-    k_md_global<<<(unsigned)ls[2].size(), MD_THREADS, smg, s3>>>(a);
+    launch_pdl(s3, k_md_global, (unsigned)ls[2].size(), MD_THREADS, smg, a);
     h->launches++;
   }
   if (!ls[0].empty()) {
@@ -1022,7 +1022,7 @@ fp_status run_local_order(fp_handle* h) {
     if (grid > cap) grid = cap;
     allow_max_dynamic_smem(k_md_leaf);
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
-    k_md_leaf<<<(unsigned)grid, 32 * nw, sm, h->stream>>>(a);
+    launch_pdl(h->stream, k_md_leaf, (unsigned)grid, 32 * nw, sm, a);
     h->launches++;
   }
   cudaEventRecord(ax->join, s2);
