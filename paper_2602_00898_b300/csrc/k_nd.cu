@@ -183,6 +183,8 @@ struct BisectArgs {
   int32_t* split;              // [T]
   int8_t* cross;               // [k] by patch id: some local neighbour lies on the other side
   int32_t mcap, ecap;          // shared-memory staging limits of this launch
+  int32_t k;                   // patches
+  int32_t smem_ints;           // dynamic shared memory of the launch, in ints
 };
 
 // Per-node working set: in shared memory when the node has <= mcap patches and
@@ -192,35 +194,55 @@ struct BisectView {
   int32_t* L;
   int32_t *lvl, *qa, *qb, *hist, *rbeg, *rlen, *adj;
   int8_t* mark;
+  int8_t* sd;                  // side by local index (shared-memory layout only)
 };
 
 // Level-synchronous BFS over the node's local quotient graph from local `src`.
-// lvl must be -1 on the component. Returns the number of levels.
-__device__ int block_bfs(const BisectView& v, int32_t src, int32_t* snext) {
+// lvl must be -1 on the component. Returns the number of levels. One barrier
+// per level: level l reads its frontier size from scnt[l % 3], appends to
+// scnt[(l + 1) % 3] and clears scnt[(l + 2) % 3], which nobody touches during
+// level l. Each frontier patch claims its neighbours BFS_CLAIM at a time and
+// appends its claims with one shared atomic.
+constexpr int BFS_CLAIM = 8;
+__device__ int block_bfs(const BisectView& v, int32_t src, int32_t* scnt) {
   int32_t* fa = v.qa;
   int32_t* fb = v.qb;
   if (threadIdx.x == 0) {
     v.lvl[src] = 0;
     fa[0] = src;
+    scnt[0] = 1;
+    scnt[1] = 0;
+    scnt[2] = 0;
   }
   __syncthreads();
-  int32_t nf = 1, level = 0;
-  while (nf > 0) {
-    if (threadIdx.x == 0) *snext = 0;
-    __syncthreads();
+  int level = 0;
+  for (;;) {
+    const int32_t nf = scnt[level % 3];
+    if (nf == 0) break;
+    if (threadIdx.x == 0) scnt[(level + 2) % 3] = 0;
+    int32_t* nxt_cnt = &scnt[(level + 1) % 3];
     for (int32_t i = threadIdx.x; i < nf; i += blockDim.x) {
       const int32_t u = fa[i];
-      const int32_t e0 = v.rbeg[u], e1 = e0 + v.rlen[u];
-      for (int32_t e = e0; e < e1; ++e) {
-        const int32_t w = v.adj[e];
-        if (atomicCAS(&v.lvl[w], -1, level + 1) == -1) fb[atomicAdd(snext, 1)] = w;
+      const int32_t e0 = v.rbeg[u], len = v.rlen[u];
+      for (int32_t eb = 0; eb < len; eb += BFS_CLAIM) {
+        int32_t w[BFS_CLAIM];
+        uint32_t got = 0;
+#pragma unroll
+        for (int k = 0; k < BFS_CLAIM; ++k) w[k] = eb + k < len ? v.adj[e0 + eb + k] : -1;
+#pragma unroll
+        for (int k = 0; k < BFS_CLAIM; ++k)
+          if (w[k] >= 0 && atomicCAS(&v.lvl[w[k]], -1, level + 1) == -1) got |= 1u << k;
+        if (got) {
+          int32_t o = atomicAdd(nxt_cnt, __popc(got));
+#pragma unroll
+          for (int k = 0; k < BFS_CLAIM; ++k)
+            if (got >> k & 1u) fb[o++] = w[k];
+        }
       }
     }
     __syncthreads();
-    nf = *snext;
     int32_t* t = fa; fa = fb; fb = t;
     ++level;
-    __syncthreads();
   }
   return level;
 }
@@ -230,7 +252,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
   extern __shared__ __align__(16) int32_t bsm[];
   __shared__ int64_t red64[40];
   __shared__ int32_t red[40];
-  __shared__ int32_t snext;
+  __shared__ int32_t scnt[3];
   __shared__ int32_t s_lstar, s_rem;
   for (int32_t ni = blockIdx.x; ni < a.T; ni += gridDim.x) {
     const int32_t t = a.t0 + ni;
@@ -242,8 +264,42 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       continue;
     }
     if (threadIdx.x == 0) a.split[ni] = 1;
-    // sort the node's patches by id (local index order = id order)
-    {
+    // sort the node's patches by id (local index order = id order): marks in
+    // a bitmap over all patch ids, read back in order through prefix
+    // popcounts, when it fits in shared memory; else a bitonic sort
+    const int32_t kw = (a.k + 31) >> 5;
+    if (2 * (int64_t)kw <= a.smem_ints) {
+      uint32_t* bm = reinterpret_cast<uint32_t*>(bsm);
+      int32_t* pre = bsm + kw;
+      for (int32_t w = threadIdx.x; w < kw; w += blockDim.x) bm[w] = 0u;
+      __syncthreads();
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const int32_t p = Lg[i];
+        atomicOr(&bm[p >> 5], 1u << (p & 31));
+      }
+      __syncthreads();
+      int32_t carry = 0;
+      for (int32_t w0 = 0; w0 < kw; w0 += blockDim.x) {
+        const int32_t w = w0 + threadIdx.x;
+        const int32_t c = w < kw ? __popc(bm[w]) : 0;
+        int32_t tot;
+        const int32_t ex = block_excl_scan_i32(c, &tot, red);
+        if (w < kw) pre[w] = carry + ex;
+        carry += tot;
+      }
+      __syncthreads();
+      for (int32_t w = threadIdx.x; w < kw; w += blockDim.x) {
+        uint32_t x = bm[w];
+        int32_t r = pre[w];
+        while (x) {
+          const int32_t id = w * 32 + __ffs(x) - 1;
+          x &= x - 1;
+          Lg[r] = id;
+          a.loc[id] = r++;
+        }
+      }
+      __syncthreads();
+    } else {
       int32_t* sb = (m <= a.mcap) ? bsm : a.sortbuf + 2 * (int64_t)base;
       const int N = pow2_at_least(m, 2);
       for (int32_t i = threadIdx.x; i < N; i += blockDim.x) sb[i] = i < m ? Lg[i] : INT_MAX;
@@ -251,9 +307,9 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       bitonic_sort<true>(sb, N, threadIdx.x, blockDim.x);
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x) Lg[i] = sb[i];
       __syncthreads();
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.loc[Lg[i]] = i;
+      __syncthreads();
     }
-    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) a.loc[Lg[i]] = i;
-    __syncthreads();
     // local quotient subgraph: neighbours in this node with remaining edge weight
     int32_t E = 0;
     for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
@@ -300,6 +356,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       v.rlen = a.ldeg + base;        // read once below into the compact rows
       v.adj = q;
       v.mark = (int8_t*)(q + a.ecap);
+      v.sd = v.mark + a.mcap;
       // compact CSR in shared memory
       int32_t carry = 0;
       for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
@@ -329,6 +386,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       v.rbeg = a.lbeg + base;
       v.rlen = a.ldeg + base;
       v.adj = a.ladj;
+      v.sd = nullptr;
     }
     for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
       v.lvl[i] = -1;
@@ -355,7 +413,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
           best = key < best ? key : best;
         }
       const int32_t ra = (int32_t)(block_min(best, red64) & 0xffffffff);
-      int32_t nl0 = block_bfs(v, ra, &snext);
+      int32_t nl0 = block_bfs(v, ra, scnt);
       if (v.lvl[c0] >= 0) {
         // ra's component is c0's: its levels are those of the sweep from r0 = ra
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
@@ -366,7 +424,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
           if (v.mark[i] == 0 && v.lvl[i] >= 0) v.lvl[i] = -1;
         __syncthreads();
         // sweep 0: discover c0's component
-        block_bfs(v, c0, &snext);
+        block_bfs(v, c0, scnt);
         best = INT64_MAX;
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
           if (v.mark[i] == 0 && v.lvl[i] >= 0) {
@@ -377,7 +435,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
           }
         const int32_t r0 = (int32_t)(block_min(best, red64) & 0xffffffff);
         // sweep 1: from r0 (minimum degree, then id)
-        nl0 = block_bfs(v, r0, &snext);
+        nl0 = block_bfs(v, r0, scnt);
       }
       // r1 = min (degree, id) on the last level of the sweep from r0
       best = INT64_MAX;
@@ -391,14 +449,18 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
         if (v.mark[i] == 2) v.lvl[i] = -1;
       __syncthreads();
       // sweep 2: the order of the component is (level from r1, id)
-      block_bfs(v, r1, &snext);
+      block_bfs(v, r1, scnt);
       int32_t cs = 0;
       for (int32_t i = threadIdx.x; i < m; i += blockDim.x) cs += v.mark[i] == 2;
       cs = block_sum(cs, red);
       if (pos + cs <= half || pos >= half) {
         const int32_t sd = pos >= half ? 1 : 0;
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
-          if (v.mark[i] == 2) { a.side[v.L[i]] = sd; v.mark[i] = 1; }
+          if (v.mark[i] == 2) {
+            a.side[v.L[i]] = sd;
+            if (v.sd) v.sd[i] = (int8_t)sd;
+            v.mark[i] = 1;
+          }
       } else {
         // levels histogram in the frontier buffer qa (free after the sweeps)
         const int32_t need = half - pos;
@@ -427,6 +489,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
           if (mk == 2) {
             const int32_t sd = (lv < lstar || (lv == lstar && ex < rem)) ? 0 : 1;
             a.side[v.L[i]] = sd;
+            if (v.sd) v.sd[i] = (int8_t)sd;
             v.mark[i] = 1;
           }
           before += tot;
@@ -437,11 +500,17 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
     }
     // crossing patches: a neighbour of positive weight in this node on the
     // other side (only their vertices can be superset vertices)
+    if (v.sd) __syncthreads();     // the shared sides are complete
     for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const int32_t si = a.side[v.L[i]];
       int8_t c = 0;
       const int32_t rb = v.rbeg[i], re = rb + v.rlen[i];
-      for (int32_t e = rb; e < re; ++e) c |= (int8_t)(a.side[v.L[v.adj[e]]] != si);
+      if (v.sd) {
+        const int8_t si = v.sd[i];
+        for (int32_t e = rb; e < re; ++e) c |= (int8_t)(v.sd[v.adj[e]] != si);
+      } else {
+        const int32_t si = a.side[v.L[i]];
+        for (int32_t e = rb; e < re; ++e) c |= (int8_t)(a.side[v.L[v.adj[e]]] != si);
+      }
       a.cross[v.L[i]] = c;
     }
     __syncthreads();
@@ -772,13 +841,13 @@ fp_status run_nested_dissection(fp_handle* h) {
     // nodes at depth d hold at most ceil(k / 2^d) patches (left = ceil(|S|/2)):
     // stage that many in shared memory with 7 adjacency entries per patch
     // (quotient graphs of meshes have degree ~6), up to what fits in a CTA
-    constexpr int32_t MCAP_MAX = (225 * 1024 - 64) / (4 * 12 + 1);
+    constexpr int32_t MCAP_MAX = (225 * 1024 - 64) / (4 * 12 + 2);
     int32_t mcap = (int32_t)(((int64_t)k + T - 1) / T);
     mcap = mcap < 32 ? 32 : (mcap > MCAP_MAX ? MCAP_MAX : mcap);
     const int32_t ecap = 7 * mcap;
-    const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + (size_t)mcap;
+    const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + 2 * (size_t)mcap;
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
-                  lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap};
+                  lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4)};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
     allow_max_dynamic_smem(k_nd_bisect);
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
