@@ -599,6 +599,8 @@ __device__ __forceinline__ bool key_less(int32_t cu, int32_t u, int32_t cv, int3
   return u < v;
 }
 
+constexpr int MIS_CACHE = 2, MIS_NB = 8;
+
 // RefineSeparator (Algorithm 2 step 4): lexicographically-first maximal
 // independent set of the crossing graph in increasing (cdeg, tie_hash, id).
 // A candidate joins (IN = released to its side) when no crossing neighbour is IN
@@ -612,21 +614,65 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t0 == 0) { a.ctr[1] = 0; a.ctr[2] = 0; a.ctr[3] = 0; }
+  // The thread's first MIS_CACHE candidates with at most MIS_NB crossing
+  // neighbours keep, for every round, their neighbours and which of them
+  // precede them in the key order in registers (a candidate's own state is
+  // written by its thread only): a round then reads just the neighbours'
+  // states. The others re-read everything each round.
+  int32_t cv[MIS_CACHE], nb[MIS_CACHE][MIS_NB];
+  uint32_t before[MIS_CACHE];
+  bool cached[MIS_CACHE], und[MIS_CACHE];
+#pragma unroll
+  for (int c = 0; c < MIS_CACHE; ++c) {
+    const int64_t i = t0 + c * stride;
+    cv[c] = i < nc ? __ldcg(&a.cand[i]) : -1;
+    const int2 x = i < nc ? __ldcg(&a.cand_x[i]) : make_int2(0, MIS_NB + 1);
+    cached[c] = x.y <= MIS_NB;
+    und[c] = cached[c];
+#pragma unroll
+    for (int k = 0; k < MIS_NB; ++k) nb[c][k] = cached[c] && k < x.y ? __ldcg(&a.xcol[x.x + k]) : -1;
+    int32_t cd[MIS_NB];
+#pragma unroll
+    for (int k = 0; k < MIS_NB; ++k) cd[k] = nb[c][k] >= 0 ? a.cdeg[nb[c][k]] : 0;
+    before[c] = 0;
+#pragma unroll
+    for (int k = 0; k < MIS_NB; ++k)
+      if (nb[c][k] >= 0 && key_less(cd[k], nb[c][k], x.y, cv[c])) before[c] |= 1u << k;
+  }
   grid.sync();
   for (int32_t round = 0; round <= nc; ++round) {
     if (t0 == 0) a.ctr[1 + (round + 1) % 3] = 0;
     int32_t undecided = 0;
-    for (int64_t i = t0; i < nc; i += stride) {
+#pragma unroll
+    for (int c = 0; c < MIS_CACHE; ++c) {
+      if (!und[c]) continue;
+      int8_t st[MIS_NB];
+#pragma unroll
+      for (int k = 0; k < MIS_NB; ++k)
+        st[k] = nb[c][k] >= 0 ? *(volatile int8_t*)&a.vstate[nb[c][k]] : (int8_t)VS_NONE;
+      bool any_in = false, is_min = true;
+#pragma unroll
+      for (int k = 0; k < MIS_NB; ++k) {
+        if (st[k] == VS_IN) any_in = true;
+        else if (st[k] == VS_UND && (before[c] >> k & 1u)) is_min = false;
+      }
+      if (any_in) { a.vstate[cv[c]] = VS_OUT; und[c] = false; }
+      else if (is_min) { a.vstate[cv[c]] = VS_IN; und[c] = false; }
+      else ++undecided;
+    }
+    int32_t c = 0;
+    for (int64_t i = t0; i < nc; i += stride, ++c) {
+      if (c < MIS_CACHE && cached[c]) continue;
       const int32_t v = __ldcg(&a.cand[i]);
       const int2 x = __ldcg(&a.cand_x[i]);
       if (*(volatile int8_t*)&a.vstate[v] != VS_UND) continue;
-      const int32_t cv = x.y;
+      const int32_t cdv = x.y;
       bool any_in = false, is_min = true;
       // the crossing neighbours listed by k_nd_superset, ND_BATCH at a time
-      for (int32_t j = 0; j < cv && !any_in; j += ND_BATCH) {
+      for (int32_t j = 0; j < cdv && !any_in; j += ND_BATCH) {
         int32_t u[ND_BATCH];
 #pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) u[k] = j + k < cv ? __ldcg(&a.xcol[x.x + j + k]) : -1;
+        for (int k = 0; k < ND_BATCH; ++k) u[k] = j + k < cdv ? __ldcg(&a.xcol[x.x + j + k]) : -1;
         int8_t st[ND_BATCH];
         int32_t cd[ND_BATCH];
 #pragma unroll
@@ -637,7 +683,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
 #pragma unroll
         for (int k = 0; k < ND_BATCH; ++k) {
           if (st[k] == VS_IN) any_in = true;
-          else if (st[k] == VS_UND && key_less(cd[k], u[k], cv, v)) is_min = false;
+          else if (st[k] == VS_UND && key_less(cd[k], u[k], cdv, v)) is_min = false;
         }
       }
       if (any_in) a.vstate[v] = VS_OUT;
