@@ -396,36 +396,100 @@ __device__ int32_t sweep_columns<0>(const SymArgs& a, uint32_t* rows, const int3
 
 // Step 4 for columns is+1 .. m-1 (see the file comment). scratch holds
 // U - m + (m - is) ints. All threads of the CTA call.
+// The count of ancestor columns first met in each row comes from a prefix OR
+// down the rows, word by word: the rows are cut into ch chunks, each (chunk,
+// word) pair ORs its rows, an exclusive OR-scan over the chunks gives each
+// pair the words met above it, and a second pass counts every row's new bits.
+// When the rows are in shared memory and that scratch fits; else (rows in
+// the global pool, or very few ancestor columns) each ancestor column takes
+// the first row holding it by an atomicMin per bit.
 __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t* upos, int32_t m, int32_t U,
                            int32_t W, int32_t b, int32_t is, int32_t* scratch, int32_t* red,
                            unsigned long long& nnz, unsigned long long& fl) {
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
   const int32_t nab = U - m, L = m - is;
-  int32_t* first = scratch;          // [nab]: first row in is..m-1 holding each ancestor column
-  int32_t* hist = scratch + nab;     // [L]: ancestor columns first met in row is + l
-  for (int32_t j = is + 1 + tid; j < m - 1; j += nthr) a.parent[b + j] = b + j + 1;
-  for (int32_t u = tid; u < nab; u += nthr) first[u] = NO_ROW;
-  for (int32_t l = tid; l < L; l += nthr) hist[l] = 0;
-  __syncthreads();
   const int32_t wa = m >> 5, nwa = W - wa;
   const uint32_t amask0 = 0xffffffffu << (m & 31);
-  if (nab > 0) {
+  // (rows in the global pool keep the atomicMin form: its single pass of
+  // loads beats two passes there)
+  int32_t ch = 0;
+  if (nab > 0 && __isShared(rows)) {
+    ch = nwa <= nthr ? nthr / nwa : 1;
+    const int32_t chmax = (is + nab) / nwa - 1;
+    if (ch > chmax) ch = chmax;
+    if (ch > L) ch = L;
+  }
+  const bool por = ch >= 1;
+  int32_t* hist;                     // [L]: ancestor columns first met in row is + l
+  int32_t* first = nullptr;          // [nab]: first row holding each ancestor column (atomicMin form)
+  uint32_t* part = nullptr;          // [ch * nwa]: OR of a chunk's rows, then of the rows above it
+  uint32_t* tot = nullptr;           // [nwa]: OR of all rows
+  if (por) {
+    hist = scratch;
+    part = reinterpret_cast<uint32_t*>(scratch + L);
+    tot = part + (int64_t)ch * nwa;
+  } else {
+    first = scratch;
+    hist = scratch + nab;
+    for (int32_t u = tid; u < nab; u += nthr) first[u] = NO_ROW;
+  }
+  for (int32_t j = is + 1 + tid; j < m - 1; j += nthr) a.parent[b + j] = b + j + 1;
+  for (int32_t l = tid; l < L; l += nthr) hist[l] = 0;
+  __syncthreads();
+  if (por) {
+    const int32_t R = (L + ch - 1) / ch;
+    auto word = [&](int32_t l, int32_t w) -> uint32_t {
+      const uint32_t x = rows[tri_off(l, W) - (l >> 5) + wa + w];
+      return w == 0 ? x & amask0 : x;
+    };
+    for (int32_t x = tid; x < ch * nwa; x += nthr) {
+      const int32_t c = x / nwa, w = x - c * nwa;
+      const int32_t l0 = is + c * R, l1 = min(l0 + R, m);
+      uint32_t acc = 0u;
+#pragma unroll 8
+      for (int32_t l = l0; l < l1; ++l) acc |= word(l, w);
+      part[x] = acc;
+    }
+    __syncthreads();
+    for (int32_t w = tid; w < nwa; w += nthr) {
+      uint32_t run = 0u;
+      for (int32_t c = 0; c < ch; ++c) {
+        const uint32_t t = part[c * nwa + w];
+        part[c * nwa + w] = run;
+        run |= t;
+      }
+      tot[w] = run;
+    }
+    __syncthreads();
+    for (int32_t x = tid; x < ch * nwa; x += nthr) {
+      const int32_t c = x / nwa, w = x - c * nwa;
+      const int32_t l0 = is + c * R, l1 = min(l0 + R, m);
+      uint32_t run = part[x];
+#pragma unroll 8
+      for (int32_t l = l0; l < l1; ++l) {
+        const uint32_t v = word(l, w);
+        const uint32_t nw = v & ~run;
+        if (nw) atomicAdd(&hist[l - is], __popc(nw));
+        run |= v;
+      }
+    }
+  } else if (nab > 0) {
     // every (row, ancestor word) pair independently, TAIL_ILP pairs a thread
     // per round with all their loads issued first, so that many loads are in
     // flight; thread tid starts at pair tid and steps nthr pairs (dl rows and
     // dw words) at a time
     constexpr int TAIL_ILP = 8;
-    const int64_t tot = (int64_t)L * nwa;
+    const int64_t npair = (int64_t)L * nwa;
     const int32_t dl = nthr / nwa, dw = nthr % nwa;
     int32_t l = is + tid / nwa, w = wa + tid % nwa;
-    for (int64_t x0 = tid; x0 < tot; x0 += (int64_t)TAIL_ILP * nthr) {
+    for (int64_t x0 = tid; x0 < npair; x0 += (int64_t)TAIL_ILP * nthr) {
       uint32_t s[TAIL_ILP];
       int32_t ls[TAIL_ILP], ws[TAIL_ILP];
 #pragma unroll
       for (int k = 0; k < TAIL_ILP; ++k) {
         ls[k] = l;
         ws[k] = w;
-        s[k] = x0 + (int64_t)k * nthr < tot ? rows[tri_off(l, W) - (l >> 5) + w] : 0u;
+        s[k] = x0 + (int64_t)k * nthr < npair ? rows[tri_off(l, W) - (l >> 5) + w] : 0u;
         l += dl;
         w += dw;
         if (w >= W) {
@@ -444,19 +508,19 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
         }
       }
     }
-  }
-  __syncthreads();
-  for (int32_t u = tid; u < nab; u += nthr) {
-    const int32_t f = first[u];
-    if (f != NO_ROW) atomicAdd(&hist[f - is], 1);
+    __syncthreads();
+    for (int32_t u = tid; u < nab; u += nthr) {
+      const int32_t f = first[u];
+      if (f != NO_ROW) atomicAdd(&hist[f - is], 1);
+    }
   }
   __syncthreads();
   int32_t run = 0;
   for (int32_t l0 = 0; l0 < L; l0 += nthr) {
     const int32_t l = l0 + tid;
     const int32_t hcount = l < L ? hist[l] : 0;
-    int32_t tot;
-    const int32_t ex = block_excl_scan_i32(hcount, &tot, red);
+    int32_t total;
+    const int32_t ex = block_excl_scan_i32(hcount, &total, red);
     if (l >= 1 && l < L) {
       const int32_t j = is + l;
       const int32_t cc = (m - 1 - j) + run + ex + hcount + 1;
@@ -464,12 +528,29 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
       nnz += (unsigned long long)cc;
       fl += (unsigned long long)cc * (unsigned long long)cc;
     }
-    run += tot;
+    run += total;
   }
   // the last column: its structure is every ancestor column met
   if (tid < 32) {
     if (run == 0) {
       if (lane == 0) a.parent[b + m - 1] = -1;
+    } else if (por) {
+      int32_t cmin = 0;
+      for (int32_t w0 = 0; w0 < nwa; w0 += 32) {
+        const int32_t w = w0 + lane;
+        const uint32_t x = w < nwa ? tot[w] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, x != 0u);
+        if (bal) {
+          const int src = __ffs(bal) - 1;
+          const uint32_t xs = __shfl_sync(0xffffffffu, x, src);
+          cmin = (wa + w0 + src) * 32 + __ffs(xs) - 1;
+          break;
+        }
+      }
+      const int32_t pf = upos[cmin];
+      if (lane == 0) a.parent[b + m - 1] = pf;
+      if (!a.node_fill)
+        export_element(a, upos, W, (uint32_t)run, pf, [&](int w) -> uint32_t { return w >= wa ? tot[w - wa] : 0u; });
     } else {
       int32_t umin = 0;
       for (int32_t u0 = 0; u0 < nab; u0 += 32) {
