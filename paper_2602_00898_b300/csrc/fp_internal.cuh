@@ -118,6 +118,26 @@ void dev_free(fp_handle* h, void* p);
 fp_status fail(fp_handle* h, fp_status s, const std::string& msg);
 fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what);
 fp_status sync_status(fp_handle* h, int32_t* status_out);   // sync stream, read status word
+// Many workspace arrays from one allocation: a layout function calls get()
+// for every array twice, first to size the block (pointers come back null),
+// then, after alloc(), to hand out 256-byte aligned pieces of it. One
+// stream-ordered allocation and one free instead of one per array.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* get(int64_t count) {
+    const size_t bytes = ((size_t)(count > 0 ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+  bool alloc(fp_handle* h) {
+    base = (char*)dev_alloc(h, off);
+    off = 0;
+    return base != nullptr;
+  }
+};
 // Per-thread pinned host scratch of 256 ints (allocated once per thread).
 int32_t* pinned_scratch();
 // Per-thread, per-device auxiliary streams (which = 0 or 1) with a fork and a

@@ -808,18 +808,20 @@ fp_status early_md_begin(fp_handle* h, int32_t levels) {
   h->early_nodes = 0;
   if (levels <= 0 || h->n == 0) return FP_OK;
   const int32_t NE = (1 << levels) - 1, n = h->n;
-  auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
-  h->early_rank = I(n);
-  h->early_list = I(n);
-  h->early_loc = I(n);
-  h->early_start = I(NE + 1);
-  h->early_cnt = I(NE);
-  h->early_fill = I(NE);
-  h->early_ovf = I(NE);
-  h->early_base = I(1);
-  if (!h->early_rank || !h->early_list || !h->early_loc || !h->early_start || !h->early_cnt || !h->early_fill ||
-      !h->early_ovf || !h->early_base)
-    return fail(h, FP_ERR_OUT_OF_MEMORY, "early ordering workspace");
+  Arena ar;
+  auto layout = [&]() {
+    h->early_rank = ar.get<int32_t>(n);
+    h->early_list = ar.get<int32_t>(n);
+    h->early_loc = ar.get<int32_t>(n);
+    h->early_start = ar.get<int32_t>(NE + 1);
+    h->early_cnt = ar.get<int32_t>(NE);
+    h->early_fill = ar.get<int32_t>(NE);
+    h->early_ovf = ar.get<int32_t>(NE);
+    h->early_base = ar.get<int32_t>(1);
+  };
+  layout();
+  if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "early ordering workspace");
+  layout();      // early_rank is the block's base: early_md_release frees it
   fill_i32(h, h->early_cnt, 0, NE);
   fill_i32(h, h->early_ovf, 0, NE);
   fill_i32(h, h->early_base, 0, 1);
@@ -850,11 +852,10 @@ fp_status launch_early_md(fp_handle* h, int32_t d) {
 }
 
 void early_md_release(fp_handle* h) {
+  dev_free(h, h->early_rank);       // the base of the one block holding all eight arrays
   for (int32_t** p : {&h->early_rank, &h->early_list, &h->early_loc, &h->early_start, &h->early_cnt, &h->early_fill,
-                      &h->early_ovf, &h->early_base}) {
-    dev_free(h, *p);
+                      &h->early_ovf, &h->early_base})
     *p = nullptr;
-  }
   h->early_nodes = 0;
 }
 

@@ -823,21 +823,28 @@ fp_status run_nested_dissection(fp_handle* h) {
   if (Dsplit == 0) { FP_CHECK_LAUNCH(h, "nd init"); return FP_OK; }
 
   const int64_t kk = (int64_t)k + 64;
-  auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
-  int32_t *psize = I(kk), *pstart = I(kk), *pfill = I(kk), *pverts = I(n), *qdeg = I(kk), *q_rowptr = I(kk);
-  int32_t *q_col = I(Q), *q_w = I(Q), *ladj = I(Q), *tmp = I(scan_tmp_ints(kk) + 8);
-  int32_t *patch_node = I(kk), *w = I(kk), *side = I(kk), *loc = I(kk), *ldeg = I(kk), *lvl = I(kk), *lbeg = I(kk);
-  int32_t *qa = I(kk), *qb = I(kk), *mark = I(kk), *hist = I(kk), *sortbuf = I(2 * kk + 64);
-  int32_t *npcount = I(kk), *npstart = I(kk + 1), *npfill = I(kk), *nplist = I(kk), *split = I(kk);
-  int32_t *cdeg = I(n), *cand = I(n), *ctr = I(8), *xcol = I(Q);
-  int2* cand_x = (int2*)dev_alloc(h, sizeof(int2) * (n > 0 ? n : 1));
-  int8_t* final_ = (int8_t*)dev_alloc(h, n);
-  int8_t* vstate = (int8_t*)dev_alloc(h, n);
-  int8_t* cross = (int8_t*)dev_alloc(h, kk);
-  if (!psize || !pstart || !pfill || !pverts || !qdeg || !q_rowptr || !q_col || !q_w || !ladj || !tmp || !patch_node ||
-      !w || !side || !loc || !ldeg || !lvl || !lbeg || !qa || !qb || !mark || !hist || !sortbuf || !npcount || !npstart ||
-      !npfill || !nplist || !split || !cdeg || !cand || !ctr || !final_ || !vstate || !cross || !xcol || !cand_x)
-    return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
+  int32_t *psize, *pstart, *pfill, *pverts, *qdeg, *q_rowptr, *q_col, *q_w, *ladj, *tmp, *patch_node, *w, *side, *loc;
+  int32_t *ldeg, *lvl, *lbeg, *qa, *qb, *mark, *hist, *sortbuf, *npcount, *npstart, *npfill, *nplist, *split, *cdeg;
+  int32_t *cand, *ctr, *xcol;
+  int2* cand_x;
+  int8_t *final_, *vstate, *cross;
+  Arena ar;
+  auto layout = [&]() {
+    psize = ar.get<int32_t>(kk); pstart = ar.get<int32_t>(kk); pfill = ar.get<int32_t>(kk);
+    pverts = ar.get<int32_t>(n); qdeg = ar.get<int32_t>(kk); q_rowptr = ar.get<int32_t>(kk);
+    q_col = ar.get<int32_t>(Q); q_w = ar.get<int32_t>(Q); ladj = ar.get<int32_t>(Q);
+    tmp = ar.get<int32_t>(scan_tmp_ints(kk) + 8); patch_node = ar.get<int32_t>(kk); w = ar.get<int32_t>(kk);
+    side = ar.get<int32_t>(kk); loc = ar.get<int32_t>(kk); ldeg = ar.get<int32_t>(kk); lvl = ar.get<int32_t>(kk);
+    lbeg = ar.get<int32_t>(kk); qa = ar.get<int32_t>(kk); qb = ar.get<int32_t>(kk); mark = ar.get<int32_t>(kk);
+    hist = ar.get<int32_t>(kk); sortbuf = ar.get<int32_t>(2 * kk + 64); npcount = ar.get<int32_t>(kk);
+    npstart = ar.get<int32_t>(kk + 1); npfill = ar.get<int32_t>(kk); nplist = ar.get<int32_t>(kk);
+    split = ar.get<int32_t>(kk); cdeg = ar.get<int32_t>(n); cand = ar.get<int32_t>(n); ctr = ar.get<int32_t>(8);
+    xcol = ar.get<int32_t>(Q); cand_x = ar.get<int2>(n); final_ = ar.get<int8_t>(n); vstate = ar.get<int8_t>(n);
+    cross = ar.get<int8_t>(kk);
+  };
+  layout();
+  if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
+  layout();
 
   const int G = grid_for(n, 256), GK = grid_for(k, 256);
   ProfScope ps_q(FP_PROF_QUOTIENT, h->stream);
@@ -924,12 +931,7 @@ fp_status run_nested_dissection(fp_handle* h) {
   // no host sync here: a quotient overflow (ST_QUOTIENT_TOO_BIG, the patch
   // keeps no quotient edges, every node index stays in range) is reported by
   // the ordering stage's first sync, before any ordering kernel runs
-  for (void* p : {(void*)psize, (void*)pstart, (void*)pfill, (void*)pverts, (void*)qdeg, (void*)q_rowptr, (void*)q_col,
-                  (void*)q_w, (void*)ladj, (void*)tmp, (void*)patch_node, (void*)w, (void*)side, (void*)loc,
-                  (void*)ldeg, (void*)lvl, (void*)lbeg, (void*)qa, (void*)qb, (void*)mark, (void*)hist, (void*)sortbuf,
-                  (void*)npcount, (void*)npstart, (void*)npfill, (void*)nplist, (void*)split, (void*)cdeg, (void*)cand,
-                  (void*)ctr, (void*)final_, (void*)vstate, (void*)cross, (void*)xcol, (void*)cand_x})
-    dev_free(h, p);
+  dev_free(h, ar.base);
   return FP_OK;
 }
 

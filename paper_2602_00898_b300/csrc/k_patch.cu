@@ -548,21 +548,27 @@ fp_status run_patching(fp_handle* h) {
   BfsLauncher L;
   FP_TRY(L.init(h));
 
-  size_t ints = (size_t)n + 8;
-  unsigned long long* key = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * n);
-  unsigned long long* key2 = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * n);
-  unsigned long long* best = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (n + 1));
-  int32_t* group = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int4* fa = (int4*)dev_alloc(h, sizeof(int4) * ints);      // frontier queues
-  int4* fb = (int4*)dev_alloc(h, sizeof(int4) * ints);
-  int32_t* flag = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* rank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* seed_of = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));
-  int32_t* ctr = (int32_t*)dev_alloc(h, sizeof(int32_t) * 8);
+  const int64_t ints = (int64_t)n + 8;
+  unsigned long long *key, *best;
+  int4 *fa, *fb;      // frontier queues
+  int32_t *group, *flag, *rank, *seed_of, *tmp, *ctr, *pcnt, *pdeg, *pstart, *pedge, *pverts, *loc, *g_adj, *g_vtx;
+  int32_t* orank;
+  Arena ar;
+  auto layout = [&]() {
+    key = ar.get<unsigned long long>(n); best = ar.get<unsigned long long>((int64_t)n + 1);
+    fa = ar.get<int4>(ints); fb = ar.get<int4>(ints);
+    group = ar.get<int32_t>(ints); flag = ar.get<int32_t>(ints); rank = ar.get<int32_t>(ints);
+    seed_of = ar.get<int32_t>(ints); tmp = ar.get<int32_t>(scan_tmp_ints((int64_t)n + 1)); ctr = ar.get<int32_t>(8);
+    // vertex lists by patch (for the searches inside patches)
+    pcnt = ar.get<int32_t>(ints); pdeg = ar.get<int32_t>(ints); pstart = ar.get<int32_t>(ints);
+    pedge = ar.get<int32_t>(ints); pverts = ar.get<int32_t>(ints); loc = ar.get<int32_t>(ints);
+    g_adj = ar.get<int32_t>(h->nnz + 8); g_vtx = ar.get<int32_t>(5 * (int64_t)n + 8); orank = ar.get<int32_t>(ints);
+  };
+  layout();
+  if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "patching workspace");
+  layout();
   int32_t* hbuf = pinned_scratch();
-  if (!key || !key2 || !best || !group || !fa || !fb || !flag || !rank || !seed_of || !tmp || !ctr || !hbuf)
-    return fail(h, FP_ERR_OUT_OF_MEMORY, "patching workspace");
+  if (!hbuf) return fail(h, FP_ERR_OUT_OF_MEMORY, "patching workspace");
 
   const int G = grid_for(n, 256);
   // R1 seeds
@@ -606,18 +612,6 @@ fp_status run_patching(fp_handle* h) {
     FP_TRY(sync_status(h, &st));
     k += hbuf[0];
   }
-  // vertex lists by patch (for the searches inside patches)
-  int32_t* pcnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* pdeg = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* pstart = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* pedge = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* pverts = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* loc = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  int32_t* g_adj = (int32_t*)dev_alloc(h, sizeof(int32_t) * (h->nnz + 8));
-  int32_t* g_vtx = (int32_t*)dev_alloc(h, sizeof(int32_t) * (5 * (size_t)n + 8));
-  int32_t* orank = (int32_t*)dev_alloc(h, sizeof(int32_t) * ints);
-  if (!pcnt || !pdeg || !pstart || !pedge || !pverts || !loc || !g_adj || !g_vtx || !orank)
-    return fail(h, FP_ERR_OUT_OF_MEMORY, "patch lists");
   // vertex lists by patch: labels and counts, their scans (pdeg is cleared to
   // serve as the scatter cursors), the scatter
   auto patch_lists = [&](int32_t kk) {
@@ -699,10 +693,7 @@ fp_status run_patching(fp_handle* h) {
   }
   FP_CHECK_LAUNCH(h, "labels");
   h->k = k;
-  for (void* p : {(void*)key, (void*)key2, (void*)best, (void*)group, (void*)fa, (void*)fb, (void*)flag,
-                  (void*)rank, (void*)seed_of, (void*)tmp, (void*)ctr, (void*)orank, (void*)pcnt, (void*)pdeg,
-                  (void*)pstart, (void*)pedge, (void*)pverts, (void*)loc, (void*)g_adj, (void*)g_vtx})
-    dev_free(h, p);
+  dev_free(h, ar.base);
   return FP_OK;
 }
 
