@@ -929,11 +929,19 @@ fp_status run_local_order(fp_handle* h) {
     for (int32_t t : *L) up32[o++] = t;
   const int64_t off64 = (nlist + 1) / 2;
   for (int64_t i = 0; i < nsg; ++i) { up[off64 + i] = goff[i]; up[off64 + nsg + i] = soff[i]; }
-  int64_t* dup = (int64_t*)dev_alloc(h, sizeof(int64_t) * (up.size() + 1));
-  uint32_t* grows = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * (gwords > 0 ? gwords : 1));
-  int32_t* gs = I(gsort);
-  int32_t* ovf = I((int64_t)ls[1].size() + 2);        // + the leaf kernel's node queue
-  if (!dup || !grows || !gs || !ovf) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
+  int64_t* dup;
+  uint32_t* grows;
+  int32_t *gs, *ovf;
+  Arena ar;
+  auto layout = [&]() {
+    dup = ar.get<int64_t>((int64_t)up.size() + 1);
+    grows = ar.get<uint32_t>(gwords);
+    gs = ar.get<int32_t>(gsort);
+    ovf = ar.get<int32_t>((int64_t)ls[1].size() + 2);      // + the leaf kernel's node queue
+  };
+  layout();
+  if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
+  layout();      // dup is the block's base
   e = cudaMemcpyAsync(dup, up.data(), sizeof(int64_t) * up.size(), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return check_cuda(h, e, "upload node lists");
   fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 2);
@@ -1037,8 +1045,7 @@ fp_status run_local_order(fp_handle* h) {
     FP_LAUNCH(h, k_iperm, G, 256, 0, h->perm, n, h->iperm);
   }
   FP_CHECK_LAUNCH(h, "iperm");
-  for (void* p : {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup,
-                  (void*)grows, (void*)gs, (void*)ovf})
+  for (void* p : {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup})
     dev_free(h, p);
   return FP_OK;
 }
