@@ -160,6 +160,35 @@ int32_t* pinned_scratch() {
   return buf;
 }
 
+int32_t* pinned_ints(int64_t count) {
+  thread_local int32_t* buf = nullptr;
+  thread_local int64_t cap = 0;
+  if (count > cap) {
+    if (buf) cudaFreeHost(buf);
+    int64_t want = count > 2 * cap ? count : 2 * cap;
+    if (want < 1024) want = 1024;
+    buf = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&buf, sizeof(int32_t) * want) != cudaSuccess) {
+      cudaGetLastError();
+      buf = nullptr;
+      return nullptr;
+    }
+    cap = want;
+  }
+  return buf;
+}
+
+cudaEvent_t mark_event(int device) {
+  thread_local cudaEvent_t ev[128] = {};
+  if (device < 0 || device >= 128) return nullptr;
+  if (!ev[device] && cudaEventCreateWithFlags(&ev[device], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ev[device] = nullptr;
+  }
+  return ev[device];
+}
+
 AuxStream* aux_stream(int device, int which) {
   thread_local AuxStream cache[128][2];
   if (device < 0 || device >= 128 || which < 0 || which > 1) return nullptr;

@@ -140,6 +140,12 @@ struct Arena {
 };
 // Per-thread pinned host scratch of 256 ints (allocated once per thread).
 int32_t* pinned_scratch();
+// Per-thread pinned host buffer of at least `count` ints (grown on demand;
+// the contents do not survive a growth). nullptr on failure.
+int32_t* pinned_ints(int64_t count);
+// Per-thread, per-device event without timing, for a host wait on part of a
+// stream (the work queued after it keeps the GPU busy meanwhile).
+cudaEvent_t mark_event(int device);
 // Per-thread, per-device auxiliary streams (which = 0 or 1) with a fork and a
 // join event each, created once and reused (stage kernels that overlap run on
 // them).

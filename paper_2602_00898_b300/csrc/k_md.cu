@@ -866,10 +866,18 @@ fp_status run_local_order(fp_handle* h) {
   auto I = [&](int64_t c) { return (int32_t*)dev_alloc(h, sizeof(int32_t) * (c > 0 ? c : 1)); };
   int32_t *sub = I(nn), *nvstart = I(nn + 1), *nvfill = I(nn), *nvlist = I(n), *loc = I(n), *tmp = I(scan_tmp_ints(nn) + 8);
   if (!sub || !nvstart || !nvfill || !nvlist || !loc || !tmp) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering workspace");
+  // the node sizes (and the status word) go to the host as soon as they are
+  // known; the host waits for them while the layout kernels still run
+  int32_t* hsp = pinned_ints(nn);
+  cudaEvent_t ev = mark_event(h->device);
+  if (!hsp || !ev) return fail(h, FP_ERR_OUT_OF_MEMORY, "node size transfer");
   {
     ProfScope ps(FP_PROF_LAYOUT, h->stream);
     fill_i32(h, h->node_size, 0, nn);
     if (n > 0) FP_LAUNCH(h, k_node_sizes, G, 256, 0, h->node_of, n, h->node_size);
+    cudaMemcpyAsync(hsp, h->node_size, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    cudaEventRecord(ev, h->stream);
     FP_LAUNCH(h, k_tree_layout, 1, 1024, 0, h->D, nn, h->node_size, sub, h->node_begin, h->opt.schedule);
     scan_exclusive(h, h->node_size, nvstart, nn, tmp);
     fill_i32(h, nvfill, 0, nn);
@@ -877,11 +885,10 @@ fp_status run_local_order(fp_handle* h) {
   }
   FP_CHECK_LAUNCH(h, "tree layout");
   // plan the ordering launches from the node sizes
-  std::vector<int32_t> hs(nn);
-  cudaError_t e = cudaMemcpyAsync(hs.data(), h->node_size, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaEventSynchronize(ev);
   if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
-  int32_t st = 0;
-  FP_TRY(sync_status(h, &st));
+  const int32_t st = *h->h_status;
+  std::vector<int32_t> hs(hsp, hsp + nn);
   if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
   // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
   // only if their adjacency lists overflow.
