@@ -234,11 +234,15 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
   }
   __syncwarp();
   warp_sort_smem(sb, N, lane);
+  // sorted by id alone (no keys): a neighbour's local index and whether it
+  // lies in the node come from a binary search of the sorted list in shared
+  // memory; with keys, from the global local-index and node arrays
+  const bool by_id = a.key == nullptr;
   for (int i = lane; i < m; i += 32) {
     const int32_t v = (int32_t)(uint32_t)sb[i];
     lv[i] = v;
     verts[i] = v;
-    a.loc[v] = i;
+    if (!by_id) a.loc[v] = i;
   }
   __syncwarp();
   {
@@ -250,6 +254,63 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
   const int M64 = (m + 63) & ~63;
   for (int i = m + lane; i < M64; i += 32) deg[i] = DEG_DEAD;
   __syncwarp();
+  if (by_id) {
+    // LEAF_GV vertices a lane per round: their edge ranges, their neighbours
+    // (LEAF_GE at a time), then the searches, all independent
+    constexpr int LEAF_GV = 4, LEAF_GE = 8;
+    for (int i0 = lane; i0 < m; i0 += 32 * LEAF_GV) {
+      int32_t b[LEAF_GV], e[LEAF_GV], c[LEAF_GV];
+#pragma unroll
+      for (int s = 0; s < LEAF_GV; ++s) {
+        const int i = i0 + 32 * s;
+        const int32_t v = i < m ? lv[i] : 0;
+        b[s] = i < m ? a.rowptr[v] : 0;
+        e[s] = i < m ? a.rowptr[v + 1] : 0;
+        c[s] = 0;
+      }
+      for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int s = 0; s < LEAF_GV; ++s) more |= b[s] < e[s];
+        if (!more) break;
+        int32_t u[LEAF_GV][LEAF_GE], lo[LEAF_GV][LEAF_GE];
+#pragma unroll
+        for (int s = 0; s < LEAF_GV; ++s)
+#pragma unroll
+          for (int k = 0; k < LEAF_GE; ++k) {
+            u[s][k] = b[s] + k < e[s] ? a.col[b[s] + k] : -1;
+            lo[s][k] = 0;
+          }
+        // lower bound: lo = number of list entries below u
+#pragma unroll
+        for (int st = MD_LEAF / 2; st > 0; st >>= 1)
+#pragma unroll
+          for (int s = 0; s < LEAF_GV; ++s)
+#pragma unroll
+            for (int k = 0; k < LEAF_GE; ++k) {
+              const int j = lo[s][k] + st;
+              if (j <= m && lv[j - 1] < u[s][k]) lo[s][k] = j;
+            }
+#pragma unroll
+        for (int s = 0; s < LEAF_GV; ++s) {
+          const int i = i0 + 32 * s;
+#pragma unroll
+          for (int k = 0; k < LEAF_GE; ++k) {
+            const int j = lo[s][k];
+            if (u[s][k] >= 0 && j < m && lv[j] == u[s][k]) {
+              R[(j >> 5) * S + i] |= 1u << (j & 31);
+              ++c[s];
+            }
+          }
+          b[s] += LEAF_GE;
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < LEAF_GV; ++s)
+        if (i0 + 32 * s < m) deg[i0 + 32 * s] = (uint16_t)c[s];
+    }
+    return;
+  }
   for (int i0 = lane; i0 < m; i0 += 64) {
     int32_t b[2], e[2], c[2] = {0, 0};
 #pragma unroll
