@@ -657,16 +657,20 @@ fp_status run_patching(fp_handle* h) {
   }
   cudaMemcpyAsync(hbuf, orank + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
   FP_CHECK_LAUNCH(h, "sizes");
-  FP_TRY(sync_status(h, &st));
-  int32_t nover = hbuf[0];
-  for (int32_t round = 0; round < n && nover > 0; ++round) {
+  // the first round is queued before its count is known (with no oversize
+  // patch its kernels find nothing to do); one sync then reads both counts
+  int32_t nover = -1;
+  for (int32_t round = 0; round < n; ++round) {
     const int GKr = grid_for(k, 256);
     la.k = k;
     la.over = over;
     la.kbase = k;
     la.next_over = over_next;
     la.next_cnt = ocnt;
-    fill_i32(h, over_next, 0, (int64_t)k + nover);
+    // the halves take the new ids k .. k+nover-1 (nover <= k, and k + nover
+    // <= n as every patch keeps a vertex)
+    const int64_t nclear = nover >= 0 ? (int64_t)k + nover : (2 * (int64_t)k < n ? 2 * (int64_t)k : (int64_t)n);
+    fill_i32(h, over_next, 0, nclear);
     fill_i32(h, ocnt, 0, 1);
     {
       ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
@@ -674,11 +678,12 @@ fp_status run_patching(fp_handle* h) {
       FP_LAUNCH(h, k_split_seeds, GKr, 256, 0, best, over, orank, k, seed_of);
       FP_LAUNCH(h, k_patch_local<2>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
     }
-    cudaMemcpyAsync(hbuf, ocnt, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(hbuf + 1, ocnt, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
     FP_CHECK_LAUNCH(h, "split");
     FP_TRY(sync_status(h, &st));
+    if (nover < 0) nover = hbuf[0];
     k += nover;
-    nover = hbuf[0];
+    nover = hbuf[1];
     if (nover == 0) break;
     std::swap(over, over_next);
     {
