@@ -11,10 +11,15 @@
 // descendant -- the structure of a column whose etree parent lies above its own
 // node (merged into that parent, as in the column-merge rule
 //   struct(j) = adj(j)_{>j}  u  U_{c : parent(c) = j} struct(c) \ {j}).
-// Nodes are processed level by level from the deepest:
-//   1. mark A_t in a bitmap over the concatenated ancestor ranges and compact
-//      it (prefix popcounts), so U_t gets dense local indices in position order;
-//   2. seed one bit row per column with its adjacency and the elements whose
+// A node runs once all its descendants have (their elements are complete):
+// every leaf (no non-empty descendant) in one launch, largest first, then the
+// inner nodes depth by depth, deepest first. Per node:
+//   1. stream the node's slab of B's pattern (rows in position order, built
+//      once per call by k_perm_pairs): mark A_t in a bitmap over the
+//      concatenated ancestor ranges and keep the (column, position) pairs
+//      above the diagonal in shared memory; compact the bitmap (prefix
+//      popcounts), so U_t gets dense local indices in position order;
+//   2. seed one bit row per column from those pairs and the elements whose
 //      smallest entry is in V_t;
 //   3. one warp sweeps the columns in order: parent = first set bit, count =
 //      popc; the row is merged into its parent's row, kept in registers when the
@@ -22,15 +27,16 @@
 //      as an element to the node holding its parent;
 //   4. dense tail: once struct(i) holds every later column of the node, the
 //      rest of the node is a chain (parent(j) = j+1) and struct(j) is
-//      {j+1..m-1} plus the ancestor columns met in the rows i..j. Each ancestor
-//      column is counted from the first row that holds it (an atomicMin per
-//      bit, then a histogram and a prefix sum), all in parallel. The top
-//      separators of a mesh reach this point within a few columns.
-// Small nodes (the deep levels: thousands of nodes of at most a few hundred
-// columns) run one node per single-warp CTA in 30 KB of shared memory, seven
-// CTAs per SM; a node that does not fit is deferred to the block kernel, which
-// also takes every node of the shallow levels (one 256-thread CTA per node,
-// rows in shared memory when they fit, else in a global scratch pool).
+//      {j+1..m-1} plus the ancestor columns met in the rows i..j, counted per
+//      row by a chunked prefix OR down the rows (rows in shared memory) or by
+//      the first row of each ancestor column (an atomicMin per bit), then a
+//      prefix sum. The top separators of a mesh reach this point within a
+//      few columns.
+// Launches of many small nodes run one node per small CTA (64 or 128
+// threads, 30 KB of shared memory, the first warp sweeping); a node that does
+// not fit is deferred to the block kernel, which also takes launches of at
+// most 148 nodes (one 512-thread CTA per node, rows in shared memory when they
+// fit, else in a global scratch pool).
 // Positions of a node are contiguous in both schedules and ancestors always
 // come later, so bit order equals position order.
 #include <algorithm>
@@ -43,7 +49,7 @@ namespace {
 
 constexpr int SYM_MAX_ANC = 32;
 constexpr int SW_SMEM_WORDS = 7680;        // single-warp CTAs: 30 KB each
-constexpr int SB_THREADS = 256;
+constexpr int SB_THREADS = 512;
 constexpr int SB_SMEM_WORDS = 54 * 1024;   // block CTAs: 216 KB each
 constexpr int DENSE_MIN = 16;              // shortest chain worth the parallel tail
 constexpr int32_t NO_ROW = INT_MAX;
