@@ -52,6 +52,10 @@ STAGES = ["graph", "patch_bfs", "patch_other", "quotient", "nd_bisect", "nd_sepa
 BYTES_PER_VERTEX = {"graph": 52, "patch_bfs": 60, "quotient": 52, "nd_separator": 60, "md_small": 32,
                     "md_mid": 32, "md_large": 32, "perm": 8, "symbolic": 60, "layout": 12}
 PER_LAUNCH_UNITS = {"patch_bfs"}   # bytes per vertex are per launch, not per step
+# nd_bisect (one launch per tree level) reads the live quotient graph: about 6
+# entries per patch, each read as column, weight, node and local index (16 B),
+# plus 24 B per patch of list, side and flags = 120 B per patch per launch
+BYTES_PER_PATCH = {"nd_bisect": 120}
 
 
 def peaks():
@@ -344,10 +348,13 @@ def run_ours(args):
     dom = max((s for s in stage_ms if s not in ("md_mid", "md_large")), key=lambda s: stage_ms[s])
     peak, peak_kind = peaks()
     roof = None
-    if dom in BYTES_PER_VERTEX and stage_n[dom] > 0:
+    if (dom in BYTES_PER_VERTEX or dom in BYTES_PER_PATCH) and stage_n[dom] > 0:
         per_launch_ms = stage_ms[dom] / stage_n[dom]
-        units = n if dom in PER_LAUNCH_UNITS else n / stage_n[dom]
-        bytes_launch = BYTES_PER_VERTEX[dom] * units
+        if dom in BYTES_PER_PATCH:
+            bytes_launch = BYTES_PER_PATCH[dom] * k
+        else:
+            units = n if dom in PER_LAUNCH_UNITS else n / stage_n[dom]
+            bytes_launch = BYTES_PER_VERTEX[dom] * units
         achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": measured_traffic(dom, args.workload),
