@@ -48,7 +48,7 @@ namespace fp {
 namespace {
 
 constexpr int SYM_MAX_ANC = 32;
-constexpr int SW_SMEM_WORDS = 7680;        // single-warp CTAs: 30 KB each
+constexpr int SW_SMEM_WORDS = 7680;        // small-node CTAs: 30 KB each
 constexpr int SB_THREADS = 512;
 constexpr int SB_SMEM_WORDS = 54 * 1024;   // block CTAs: 216 KB each
 constexpr int DENSE_MIN = 16;              // shortest chain worth the parallel tail
@@ -581,10 +581,11 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
   }
 }
 
-// One node per CTA. Used with 32 threads (single-warp CTAs for the small nodes
-// of deep levels; a node that does not fit in shared memory is deferred to
-// a.big_list) and with SB_THREADS threads (whole levels of few nodes, or the
-// deferred list; rows that do not fit go to the global pool).
+// One node per CTA. Used with 64 or 128 threads for launches of many small
+// nodes (the first warp sweeps, all gather; a node that does not fit in
+// shared memory is deferred to a.big_list) and with SB_THREADS threads
+// (launches of at most 148 nodes, or the deferred list; rows that do not fit
+// go to the global pool).
 __global__ void __launch_bounds__(SB_THREADS) k_symbolic_nodes(SymArgs a, int32_t smem_words, int32_t from_list,
                                                                int32_t may_defer) {
   FP_PDL_WAIT();
