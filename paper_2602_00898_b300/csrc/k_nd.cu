@@ -98,21 +98,22 @@ __global__ void __launch_bounds__(1024) k_group_small(const int32_t* __restrict_
 
 // ---- a3 quotient graph --------------------------------------------------------------
 // One CTA per patch: gather the patch ids across its cross edges, sort them on
-// chip and run-length encode. kWrite = false counts the distinct neighbours;
-// kWrite = true writes the sorted row (q_col) with its edge weights (q_w).
-template <bool kWrite>
+// chip and run-length encode, in one pass: the row (neighbour patches and edge
+// weights) goes to a scratch stretch taken with one atomic, its length to
+// qdeg; after the scan of qdeg, k_quotient_pack moves every row into place.
 __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __restrict__ pstart,
                                                               const int32_t* __restrict__ pverts,
                                                               const int32_t* __restrict__ rowptr,
                                                               const int32_t* __restrict__ col,
                                                               const int32_t* __restrict__ gmap, int32_t k,
-                                                              const int32_t* __restrict__ q_rowptr, int32_t* qdeg,
-                                                              int32_t* q_col, int32_t* q_w, int32_t* status) {
+                                                              int32_t* __restrict__ qdeg, int32_t* __restrict__ qtoff,
+                                                              int32_t* __restrict__ tcol, int32_t* __restrict__ tw,
+                                                              int32_t* tctr, int32_t* status) {
   FP_PDL_WAIT();
   __shared__ int32_t buf[QCAP];
   __shared__ int32_t starts[QCAP + 1];
   __shared__ int32_t red[40];
-  __shared__ int32_t cnt;
+  __shared__ int32_t cnt, s_off;
   for (int32_t p = blockIdx.x; p < k; p += gridDim.x) {
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
@@ -127,7 +128,11 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
     __syncthreads();
     const int32_t L = cnt;
     if (L > QCAP) {
-      if (threadIdx.x == 0) { atomicOr(status, ST_QUOTIENT_TOO_BIG); if (!kWrite) qdeg[p] = 0; }
+      if (threadIdx.x == 0) {
+        atomicOr(status, ST_QUOTIENT_TOO_BIG);
+        qdeg[p] = 0;
+        qtoff[p] = 0;
+      }
       __syncthreads();
       continue;
     }
@@ -144,18 +149,37 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
       if (f) starts[base + ex] = i;
       base += tot;
     }
-    if (threadIdx.x == 0) starts[base] = L;
-    __syncthreads();
-    if (!kWrite) {
-      if (threadIdx.x == 0) qdeg[p] = base;
-    } else {
-      const int32_t o = q_rowptr[p];
-      for (int32_t j = threadIdx.x; j < base; j += blockDim.x) {
-        q_col[o + j] = buf[starts[j]];
-        q_w[o + j] = starts[j + 1] - starts[j];
-      }
+    if (threadIdx.x == 0) {
+      starts[base] = L;
+      qdeg[p] = base;
+      s_off = base > 0 ? atomicAdd(tctr, base) : 0;
+      qtoff[p] = s_off;
     }
     __syncthreads();
+    const int32_t o = s_off;
+    for (int32_t j = threadIdx.x; j < base; j += blockDim.x) {
+      tcol[o + j] = buf[starts[j]];
+      tw[o + j] = starts[j + 1] - starts[j];
+    }
+    __syncthreads();
+  }
+}
+
+// Rows from the scratch stretches to their places q_rowptr[p]: one warp per
+// patch.
+__global__ void k_quotient_pack(const int32_t* __restrict__ q_rowptr, const int32_t* __restrict__ qdeg,
+                                const int32_t* __restrict__ qtoff, const int32_t* __restrict__ tcol,
+                                const int32_t* __restrict__ tw, int32_t k, int32_t* __restrict__ q_col,
+                                int32_t* __restrict__ q_w) {
+  FP_PDL_WAIT();
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < k; p += nwarps) {
+    const int32_t d = qdeg[p], o = q_rowptr[p], t = qtoff[p];
+    for (int32_t j = lane; j < d; j += 32) {
+      q_col[o + j] = tcol[t + j];
+      q_w[o + j] = tw[t + j];
+    }
   }
 }
 
@@ -856,11 +880,13 @@ fp_status run_nested_dissection(fp_handle* h) {
   FP_LAUNCH(h, k_scatter_by, G, 256, 0, h->gmap, n, 0, pstart, pfill, pverts);
   // quotient graph (a3)
   const int GQ = k < NUM_SMS_B300 * 8 ? k : NUM_SMS_B300 * 8;
-  FP_LAUNCH(h, k_quotient_rows<false>, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, q_rowptr, qdeg,
-            q_col, q_w, h->d_status);
+  // (ladj, xcol and lbeg serve as scratch here; the dissection uses them later)
+  fill_i32(h, ctr, 0, 8);
+  FP_LAUNCH(h, k_quotient_rows, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, qdeg, lbeg,
+            ladj, xcol, ctr + 7, h->d_status);
   scan_exclusive(h, qdeg, q_rowptr, k, tmp);
-  FP_LAUNCH(h, k_quotient_rows<true>, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, q_rowptr, qdeg,
-            q_col, q_w, h->d_status);
+  FP_LAUNCH(h, k_quotient_pack, grid_for((int64_t)k * 32, 256), 256, 0, q_rowptr, qdeg, lbeg, ladj, xcol, k, q_col,
+            q_w);
   // state: every patch with vertices starts in the root; an empty one (a
   // label of a supplied patch map that no vertex carries) takes no part
   FP_LAUNCH(h, k_patch_node_init, GK, 256, 0, psize, k, patch_node);
