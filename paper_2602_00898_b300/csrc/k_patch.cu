@@ -285,6 +285,7 @@ __global__ void k_split_seeds(const unsigned long long* __restrict__ best, const
 constexpr int LOCAL_THREADS = 256;
 constexpr int LOCAL_SMEM_V = 1024;
 constexpr int LOCAL_SMEM_E = 8192;
+constexpr int PL_SLOTS = 8;      // neighbour slots a frontier vertex gets in the pair sweep
 
 struct LocalArgs {
   int32_t k;
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
   __shared__ int32_t red[40];
   __shared__ unsigned long long red64[40];
   __shared__ int32_t s_cnt[3];
+  __shared__ int32_t s_long;     // some vertex has more than PL_SLOTS internal neighbours
   const int tid = threadIdx.x;
   for (int32_t p = blockIdx.x; p < a.k; p += gridDim.x) {
     if (kMode != 0 && !a.over[p]) continue;
@@ -335,6 +337,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
     uint32_t* dist = small ? s_dist : (uint32_t*)(gv + m + 1);
     int32_t* fa = small ? s_fa : gv + 2 * m + 1;
     int32_t* fb = small ? s_fb : gv + 3 * m + 1;
+    if (tid == 0) s_long = 0;
     for (int32_t i = tid; i < m; i += LOCAL_THREADS) {
       const int32_t v = a.pverts[v0 + i];
       if (small) s_verts[i] = v;
@@ -354,6 +357,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
           if (lu == p) ++c;
           else bnd = true;
         });
+      if (c > PL_SLOTS) s_long = 1;
       int32_t tot;
       const int32_t ex = block_excl_scan_i32(c, &tot, red);
       if (i < m) {
@@ -414,10 +418,38 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
     // and keeps the minimum
     const int lane = tid & 31;
     const unsigned lt = lanemask_lt();
+    const bool long_rows = s_long != 0;
     for (uint32_t level = 0;; ++level) {
       const int32_t nf = s_cnt[level % 3];
       if (nf == 0) break;
       if (tid == 0) s_cnt[(level + 2) % 3] = 0;
+      if (!long_rows) {
+        // one (frontier vertex, neighbour slot) pair a thread, every row
+        // having at most PL_SLOTS internal neighbours: a thread makes one
+        // claim, a warp appends its claims with one atomicAdd
+        const int32_t np = nf * PL_SLOTS;
+        for (int32_t x0 = 0; x0 < np; x0 += LOCAL_THREADS) {
+          const int32_t x = x0 + tid;
+          int32_t w = -1;
+          uint32_t cand = 0;
+          if (x < np) {
+            const int32_t u = fa[x / PL_SLOTS];
+            const int32_t r = lrow[u] + x % PL_SLOTS;
+            if (r < lrow[u + 1]) w = small ? (int32_t)s_adj[r] : a.g_adj[e0 + r];
+            cand = kMode == 2 ? (((level + 1) << 1) | (dist[u] & 1u)) : level + 1;
+          }
+          bool cl = false;
+          if (w >= 0) {
+            if (kMode == 2) cl = (dist[w] >> 1) > level && atomicMin(&dist[w], cand) == 0xffffffffu;
+            else cl = atomicCAS(&dist[w], 0xffffffffu, cand) == 0xffffffffu;
+          }
+          const unsigned bb = __ballot_sync(0xffffffffu, cl);
+          int32_t base = 0;
+          if (lane == 0 && bb) base = atomicAdd(&s_cnt[(level + 1) % 3], __popc(bb));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (cl) fb[base + __popc(bb & lt)] = w;
+        }
+      } else
       for (int32_t i0 = 0; i0 < nf; i0 += LOCAL_THREADS) {
         const int32_t i = i0 + tid;
         int32_t r0 = 0, r1 = 0;
