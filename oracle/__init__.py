@@ -70,6 +70,16 @@ def lib():
                                                 P(ctypes.c_uint32), i32p]
         L.oracle_tie_key.restype = ctypes.c_uint32
         L.oracle_tie_key.argtypes = [ctypes.c_uint64, ctypes.c_int32]
+        L.oracle_patches_from_seeds.restype = ctypes.c_int32
+        L.oracle_patches_from_seeds.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32,
+                                                ctypes.c_int32, i32p, i32p]
+        L.oracle_order_trace.restype = ctypes.c_int32
+        L.oracle_order_trace.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_void_p, i32p, ctypes.c_int32,
+                                         i32p, i32p, i32p, i32p, i32p, i32p, ctypes.c_int32, i32p, i32p, i32p,
+                                         i32p, i32p, i32p, i32p, ctypes.c_int32]
+        L.oracle_quotient.restype = ctypes.c_int64
+        L.oracle_quotient.argtypes = [i32p, i32p, ctypes.c_int32, i32p, ctypes.c_int32, i32p, i32p, i32p, i32p,
+                                      ctypes.c_int64]
         L.oracle_dof_expand.restype = None
         L.oracle_dof_expand.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p, i32p, i32p, i32p]
         _lib = L
@@ -297,3 +307,75 @@ def dof_expand(b: int, perm, parent, colcount):
     pd = np.zeros(max(n * b, 1), np.int32); ad = np.zeros_like(pd); cd = np.zeros_like(pd)
     lib().oracle_dof_expand(n, b, _p(perm), _p(parent), _p(colcount), _p(pd), _p(ad), _p(cd))
     return pd[:n * b], ad[:n * b], cd[:n * b]
+
+
+def patches_from_seeds(g: Graph, seeds, cap: int, lloyd_rounds: int = 0) -> tuple[np.ndarray, np.ndarray, int]:
+    """Contract R2-R5 from explicit seeds (rank = position in `seeds`): returns
+    (labels, seed of every final rank, k)."""
+    s = _i32(seeds) if len(seeds) else np.zeros(1, np.int32)
+    lab = np.zeros(max(g.n, 1), np.int32)
+    so = np.zeros(max(g.n, 1), np.int32)
+    rp, cp, _keep = _gp(g)
+    k = lib().oracle_patches_from_seeds(rp, cp, g.n, len(seeds), _p(s), cap, lloyd_rounds, _p(lab), _p(so))
+    if k < 0:
+        raise ValueError("bad seeds or options")
+    return lab[:g.n], so[:k], int(k)
+
+
+@dataclass
+class Trace:
+    """Intermediate stages of Algorithm 1 (see oracle_order_trace)."""
+    ordering: Ordering
+    seeds0: np.ndarray            # seed of every rank after R1 + R3
+    lloyd_seeds: list             # per Lloyd round: seed of every rank
+    labels: list                  # labels after the first labelling and after each Lloyd relabel
+    side_at: np.ndarray           # [D, k]: side of each patch in the node bisected at depth d, -1 if none
+    child_at: np.ndarray          # [D, k]: child node each patch moved to at depth d, -1 if none
+
+
+def order_trace(g: Graph, cap: int = 512, seed: int = 0, lloyd_rounds: int = 2, nd_level: int = 0,
+                schedule: int = 0, given=None, k: int = 0) -> Trace:
+    """oracle.order (or, with `given` labels in [0, k), oracle.order_given)
+    with its stage boundaries recorded."""
+    n = g.n
+    o = _Opts(cap, seed, lloyd_rounds, nd_level, schedule)
+    gv = _i32(given) if given is not None else None
+    N = max(n, 1)
+    lab = np.zeros(N, np.int32); nod = np.zeros(N, np.int32)
+    perm = np.zeros(N, np.int32); iperm = np.zeros(N, np.int32)
+    tree_cap = 4 * N + 8
+    if nd_level > 0:
+        tree_cap = max(tree_cap, (1 << (nd_level + 1)))
+    nb = np.zeros(tree_cap, np.int32); ns = np.zeros(tree_cap, np.int32)
+    depth = np.zeros(1, np.int32); k0 = np.zeros(1, np.int32)
+    max_levels = max(nd_level, 32)
+    seeds0 = np.zeros(N, np.int32)
+    ls = np.zeros((max(lloyd_rounds, 1), N), np.int32)
+    labels = np.zeros((lloyd_rounds + 1, N), np.int32)
+    side = np.full((max_levels, N), -1, np.int32); child = np.full((max_levels, N), -1, np.int32)
+    rp, cp, _keep = _gp(g)
+    if gv is not None:
+        tree_cap = max(tree_cap, 4 * max(k, 1) + 8)
+        nb = np.zeros(tree_cap, np.int32); ns = np.zeros(tree_cap, np.int32)
+    k = lib().oracle_order_trace(rp, cp, n, ctypes.byref(o), _p(gv) if gv is not None and n else None, int(k),
+                                 _p(lab), _p(nod), _p(perm), _p(iperm), _p(nb), _p(ns), tree_cap, _p(depth),
+                                 _p(seeds0), _p(k0), _p(ls), _p(labels), _p(side), _p(child), max_levels)
+    if k < 0:
+        raise ValueError(f"oracle_order_trace failed ({k})")
+    D = int(depth[0]); nn = (1 << (D + 1)) - 1; kz = int(k0[0])
+    ordering = Ordering(int(k), D, lab[:n], nod[:n], perm[:n], iperm[:n], nb[:nn].copy(), ns[:nn].copy(),
+                        np.full(nn, -1, np.int64))
+    return Trace(ordering, seeds0[:kz].copy(), [ls[r, :kz].copy() for r in range(lloyd_rounds)],
+                 [labels[r, :n].copy() for r in range(lloyd_rounds + 1)], side[:D, :k].copy(), child[:D, :k].copy())
+
+
+def quotient(g: Graph, label, k: int):
+    """Quotient graph of a patch map (contract R6): (w, q_rowptr, q_col, q_w),
+    rows in increasing neighbour id."""
+    lab = _i32(label) if g.n else np.zeros(1, np.int32)
+    rp, cp, _keep = _gp(g)
+    m = lib().oracle_quotient(rp, cp, g.n, _p(lab), k, None, None, None, None, 0)
+    w = np.zeros(max(k, 1), np.int32); qr = np.zeros(k + 1, np.int32)
+    qc = np.zeros(max(m, 1), np.int32); qw = np.zeros(max(m, 1), np.int32)
+    lib().oracle_quotient(rp, cp, g.n, _p(lab), k, _p(w), _p(qr), _p(qc), _p(qw), m)
+    return w[:k], qr, qc[:m], qw[:m]

@@ -155,14 +155,23 @@ struct Patching {
   int32_t k = 0;
 };
 
-// Full patching: seeds, Voronoi cells, unreached components, R Lloyd rounds,
-// cap splitting (contract R1-R5).
-Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_rounds) {
+// What the patching stage passes through, for tests that check each step
+// (and the library's stage dump) rather than only the final labels.
+struct PatchTrace {
+  std::vector<int32_t> seeds0;                     // seed of every rank after R1 + R3
+  std::vector<std::vector<int32_t>> lloyd_seeds;   // seed of every rank after each Lloyd round
+  std::vector<std::vector<int32_t>> labels;        // labels after the first labelling and each Lloyd relabel
+};
+
+// Patching from given seeds (rank = position in `seeds`): Voronoi cells,
+// unreached components, R Lloyd rounds, cap splitting (contract R2-R5).
+Patching patches_from_seeds(const Adj& adj, const std::vector<int32_t>& seeds, int32_t cap, int32_t lloyd_rounds,
+                            PatchTrace* tr) {
   int32_t n = (int32_t)adj.size();
   Patching P;
   P.label.assign(n, -1);
   std::vector<int32_t> dist(n, INF);
-  select_seeds(n, cap, seed, P.seed_of);
+  P.seed_of = seeds;
   std::vector<int32_t> ranks(P.seed_of.size());
   for (size_t r = 0; r < ranks.size(); ++r) ranks[r] = (int32_t)r;
   voronoi(adj, P.seed_of, ranks, nullptr, dist, P.label);
@@ -189,6 +198,7 @@ Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_r
     }
   }
   P.k = (int32_t)P.seed_of.size();
+  if (tr) { tr->seeds0 = P.seed_of; tr->labels.push_back(P.label); }
 
   // R4 Lloyd rounds: the new seed of a patch is its vertex farthest (in hops
   // inside the patch) from the patch boundary, ties to the lowest id; a patch
@@ -212,6 +222,7 @@ Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_r
     std::vector<int32_t> all(P.k);
     for (int32_t p = 0; p < P.k; ++p) all[p] = p;
     voronoi(adj, P.seed_of, all, nullptr, dist, P.label);
+    if (tr) { tr->lloyd_seeds.push_back(P.seed_of); tr->labels.push_back(P.label); }
   }
 
   // R5 cap: while some patch is larger than cap, each such patch gets a second
@@ -251,11 +262,24 @@ Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_r
   return P;
 }
 
+// Full patching (contract R1-R5): seeds by the hash rule, then as above.
+Patching get_patches(const Adj& adj, int32_t cap, uint64_t seed, int32_t lloyd_rounds, PatchTrace* tr = nullptr) {
+  std::vector<int32_t> seeds;
+  select_seeds((int32_t)adj.size(), cap, seed, seeds);
+  return patches_from_seeds(adj, seeds, cap, lloyd_rounds, tr);
+}
+
 // ---------------------------------------------------------------------------
 // Section 4.2 BuildEtree with Algorithm 2 GetSeparator, quotient graph built
 // once and updated by weight decrements (Section 5, "Quotient graph
 // computation").
 // ---------------------------------------------------------------------------
+
+int32_t ceil_log2_of(int64_t k) {
+  int32_t d = 0;
+  while (((int64_t)1 << d) < k) ++d;
+  return d;
+}
 
 struct NDTree {
   int32_t D = 0;
@@ -274,6 +298,12 @@ struct ND {
   std::vector<char> here, released, newsep, inS, sideS, done;
   std::vector<int32_t> cdeg;
   std::map<int32_t, int64_t> qsum_at;     // node -> sum of w(p,q), p,q in S (trace)
+  // stage trace (filled when `trace` is set): per depth d and patch p, the
+  // side (0 left, 1 right) p took in the node bisected at depth d, and the
+  // child node p moved to (-1 once it has no remaining vertex); -1 where p
+  // took part in no bisection at depth d
+  bool trace = false;
+  std::vector<std::vector<int32_t>> side_at, child_at;
 
   ND(const Adj& a, const std::vector<int32_t>& p, int32_t k, int32_t d)
       : adj(a), patch(p), D(d), w(k, 0), qw(k), removed(a.size(), 0), node_of(a.size(), -1),
@@ -308,13 +338,22 @@ struct ND {
     return lv;
   }
 
-  // Contract R8, BiPartition (Algorithm 2 step 2; METIS in the paper): order S
-  // component by component (components by their smallest patch id); inside a
-  // component, r0 = min (degree, id), r1 = min (degree, id) on the last BFS
-  // level from r0, and the patches are ordered by (BFS level from r1, id).
-  // Left = the first ceil(|S|/2) patches of that order.
+  // Contract R8, BiPartition (Algorithm 2 step 2; METIS with its balance
+  // constraint in the paper, which balances the quotient graph's vertex
+  // weights): order S component by component (components by their smallest
+  // patch id); inside a component, r0 = min (degree, id), r1 = min (degree,
+  // id) on the last BFS level from r0, and the patches are ordered by (BFS
+  // level from r1, id). With o_1..o_m that order, W the summed weight w(p) of
+  // S and P_j the weight of o_1..o_j, Left = o_1..o_j for the j in J whose
+  // |2 P_j - W| is smallest (ties to the smaller j): the cut of the order that
+  // best halves the remaining vertices. J keeps each child within the patch
+  // capacity of its subtree, so that with the default depth every leaf is a
+  // single patch: with D' = min(D, ceil(log2 k)) and c = 2^(D' - depth - 1),
+  // J = [max(1, m - c), min(m - 1, c)], or [1, m - 1] when that is empty
+  // (only when an explicit depth below ceil(log2 k) makes leaves hold
+  // several patches anyway).
   // Returns with sideS[p] set for p in S (0 left, 1 right); inS marks S.
-  void bipartition(const std::vector<int32_t>& S) {
+  void bipartition(const std::vector<int32_t>& S, int32_t depth) {
     for (int32_t p : S) { inS[p] = 1; sideS[p] = 0; done[p] = 0; }
     std::vector<int32_t> order;
     std::vector<int32_t> sorted = S;
@@ -340,8 +379,27 @@ struct ND {
         for (int32_t p : s) { order.push_back(p); done[p] = 1; }
       }
     }
-    size_t nl = (order.size() + 1) / 2;
-    for (size_t i = nl; i < order.size(); ++i) sideS[order[i]] = 1;
+    const int64_t m = (int64_t)order.size();
+    const int32_t Dp = std::min(D, ceil_log2_of((int64_t)w.size()));
+    int64_t lo = 1, hi = m - 1;
+    if (Dp - depth - 1 >= 0 && Dp - depth - 1 < 62) {
+      const int64_t c = (int64_t)1 << (Dp - depth - 1);
+      if (std::max<int64_t>(1, m - c) <= std::min<int64_t>(m - 1, c)) {
+        lo = std::max<int64_t>(1, m - c);
+        hi = std::min<int64_t>(m - 1, c);
+      }
+    }
+    int64_t W = 0;
+    for (int32_t p : order) W += w[p];
+    int64_t nl = lo;
+    int64_t P = 0, best_gap = INT64_MAX;
+    for (int64_t j = 1; j <= hi; ++j) {
+      P += w[order[j - 1]];
+      if (j < lo) continue;
+      const int64_t gap = 2 * P > W ? 2 * P - W : W - 2 * P;
+      if (gap < best_gap) { best_gap = gap; nl = j; }
+    }
+    for (int64_t i = nl; i < m; ++i) sideS[order[i]] = 1;
   }
 
   void node(int32_t t, int32_t depth, std::vector<int32_t> S, const std::vector<int32_t>& verts) {
@@ -353,8 +411,15 @@ struct ND {
       for (int32_t v : verts) node_of[v] = t;
       return;
     }
-    bipartition(S);
+    bipartition(S, depth);
     const std::vector<char>& side = sideS;
+    if (trace) {
+      if ((int32_t)side_at.size() <= depth) {
+        side_at.resize(depth + 1, std::vector<int32_t>(w.size(), -1));
+        child_at.resize(depth + 1, std::vector<int32_t>(w.size(), -1));
+      }
+      for (int32_t p : S) side_at[depth][p] = side[p];
+    }
     int64_t qs = 0;
     for (int32_t p : S)
       for (auto& e : qw[p]) if (inS[e.first]) qs += e.second;
@@ -403,6 +468,8 @@ struct ND {
       }
     }
     for (int32_t v : verts) if (newsep[v]) removed[v] = 1;
+    if (trace)
+      for (int32_t p : S) child_at[depth][p] = w[p] > 0 ? 2 * t + 1 + side[p] : -1;
 
     // Algorithm 2 step 5, LeftRight: children 2t+1 (left) and 2t+2 (right).
     std::vector<int32_t> SL, SR, VL, VR;
@@ -653,11 +720,13 @@ uint32_t oracle_tie_key(uint64_t r, int32_t v) { return (uint32_t)(seed_hash(r, 
 static int32_t order_from_patches(const Adj& a, int32_t n, const Patching& P, const oracle_opts* o,
                                   int32_t* label, int32_t* node_of, int32_t* perm, int32_t* iperm,
                                   int32_t* node_begin, int32_t* node_size, int32_t tree_cap, int32_t* depth_out,
-                                  int64_t* node_qsum) {
+                                  int64_t* node_qsum, ND** keep_nd = nullptr) {
   int32_t D = o->nd_level > 0 ? o->nd_level : ceil_log2(P.k);
   int64_t nnodes = ((int64_t)1 << (D + 1)) - 1;
   if (nnodes > tree_cap) return -3;
-  ND nd(a, P.label, P.k, D);
+  ND* ndp = new ND(a, P.label, P.k, D);
+  ND& nd = *ndp;
+  nd.trace = keep_nd != nullptr;
   std::vector<int32_t> S(P.k), V(n);
   for (int32_t p = 0; p < P.k; ++p) S[p] = p;
   for (int32_t v = 0; v < n; ++v) V[v] = v;
@@ -686,6 +755,7 @@ static int32_t order_from_patches(const Adj& a, int32_t n, const Patching& P, co
       auto it = nd.qsum_at.find((int32_t)t);
       node_qsum[t] = it == nd.qsum_at.end() ? -1 : it->second;
     }
+  if (keep_nd) *keep_nd = ndp; else delete ndp;
   return P.k;
 }
 
@@ -753,6 +823,110 @@ void oracle_dof_expand(int32_t n, int32_t b, const int32_t* perm, const int32_t*
       else parent_d[i] = parent[k] < 0 ? -1 : b * parent[k];
       colcount_d[i] = b * colcount[k] - c;
     }
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Patching from explicit seeds (test infrastructure): seeds[0..nseeds) are
+// the sources in rank order; then R3 (unreached components), R lloyd_rounds
+// and the cap splits follow as in the full method. label_out [n] receives the
+// final patch ids, seed_out [n] the seed of every final rank. Returns k.
+int32_t oracle_patches_from_seeds(const int32_t* rowptr, const int32_t* col, int32_t n, int32_t nseeds,
+                                  const int32_t* seeds, int32_t cap, int32_t lloyd_rounds, int32_t* label_out,
+                                  int32_t* seed_out) {
+  if (cap < 1 || lloyd_rounds < 0) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> s(seeds, seeds + nseeds);
+  for (int32_t v : s) if (v < 0 || v >= n) return -1;
+  Patching P = patches_from_seeds(a, s, cap, lloyd_rounds, nullptr);
+  std::copy(P.label.begin(), P.label.end(), label_out);
+  std::copy(P.seed_of.begin(), P.seed_of.end(), seed_out);
+  return P.k;
+}
+
+// Algorithm 1 with its intermediate stages recorded (test infrastructure).
+// given (may be NULL): a supplied patch map with labels in [0, kgiven), as in
+// oracle_order_given; the patching rows below are then left untouched.
+// Outputs as oracle_order, plus (rows of n ints; entries past the row's
+// count are left untouched):
+//   seeds0 [n]            seed of every rank after R1 + R3 (*k0_out ranks)
+//   lloyd_seeds [R][n]    seed of every rank after each Lloyd round
+//   labels [R+1][n]       labels after the first labelling and after each
+//                         Lloyd relabel (before the cap splits)
+//   side_at, child_at [max_levels][n]: per depth d < D and patch p, the side
+//                         p took in the node bisected at depth d and the child
+//                         node it moved to (-1 when it has no remaining vertex);
+//                         -1 where p took part in no bisection at depth d
+// Returns k, or -1 / -3 as oracle_order, or -4 when D > max_levels.
+int32_t oracle_order_trace(const int32_t* rowptr, const int32_t* col, int32_t n, const oracle_opts* o,
+                           const int32_t* given, int32_t kgiven, int32_t* label, int32_t* node_of, int32_t* perm,
+                           int32_t* iperm, int32_t* node_begin, int32_t* node_size, int32_t tree_cap,
+                           int32_t* depth_out, int32_t* seeds0, int32_t* k0_out, int32_t* lloyd_seeds,
+                           int32_t* labels, int32_t* side_at, int32_t* child_at, int32_t max_levels) {
+  if (o->patch_cap < 1 || o->nd_level < 0 || o->lloyd_rounds < 0) return -1;
+  Adj a = adj_from_csr(rowptr, col, n);
+  PatchTrace tr;
+  Patching P;
+  if (given) {          // patches supplied: no patching stage to record
+    if (kgiven < 1) return -1;
+    for (int32_t v = 0; v < n; ++v)
+      if (given[v] < 0 || given[v] >= kgiven) return -1;
+    P.k = kgiven;
+    P.label.assign(given, given + n);
+  } else {
+    P = get_patches(a, o->patch_cap, o->seed, o->lloyd_rounds, &tr);
+  }
+  ND* nd = nullptr;
+  int32_t k = order_from_patches(a, n, P, o, label, node_of, perm, iperm, node_begin, node_size, tree_cap, depth_out,
+                                 nullptr, &nd);
+  if (k < 0) return k;
+  int32_t D = *depth_out;
+  int rc = k;
+  if (D > max_levels) rc = -4;
+  *k0_out = (int32_t)tr.seeds0.size();
+  std::copy(tr.seeds0.begin(), tr.seeds0.end(), seeds0);
+  for (size_t r = 0; r < tr.lloyd_seeds.size(); ++r)
+    std::copy(tr.lloyd_seeds[r].begin(), tr.lloyd_seeds[r].end(), lloyd_seeds + r * (size_t)n);
+  for (size_t r = 0; r < tr.labels.size(); ++r)
+    std::copy(tr.labels[r].begin(), tr.labels[r].end(), labels + r * (size_t)n);
+  for (int32_t d = 0; d < D && d < max_levels; ++d)
+    for (int32_t p = 0; p < k; ++p) {
+      bool has = d < (int32_t)nd->side_at.size();
+      side_at[(size_t)d * n + p] = has ? nd->side_at[d][p] : -1;
+      child_at[(size_t)d * n + p] = has ? nd->child_at[d][p] : -1;
+    }
+  delete nd;
+  return rc;
+}
+
+// Quotient graph of a patch map (contract R6, Section 3 definition): node
+// weights w[p] = |p|; q_rowptr [k+1], q_col / q_w [cap] list, for every
+// patch in increasing neighbour id, the neighbouring patches and the number
+// of G-edges between the two. Returns the number of entries (-3 if > cap;
+// with q_col NULL only the count).
+int64_t oracle_quotient(const int32_t* rowptr, const int32_t* col, int32_t n, const int32_t* label, int32_t k,
+                        int32_t* w, int32_t* q_rowptr, int32_t* q_col, int32_t* q_w, int64_t cap) {
+  std::vector<std::map<int32_t, int32_t>> q(k);
+  std::vector<int32_t> wt(k, 0);
+  for (int32_t v = 0; v < n; ++v) {
+    wt[label[v]]++;
+    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e)
+      if (label[col[e]] != label[v]) q[label[v]][label[col[e]]]++;
+  }
+  int64_t m = 0;
+  for (auto& r : q) m += (int64_t)r.size();
+  if (!q_col) return m;
+  if (m > cap) return -3;
+  int64_t e = 0;
+  q_rowptr[0] = 0;
+  for (int32_t p = 0; p < k; ++p) {
+    w[p] = wt[p];
+    for (auto& kv : q[p]) { q_col[e] = kv.first; q_w[e] = kv.second; ++e; }
+    q_rowptr[p + 1] = (int32_t)e;
+  }
+  return m;
 }
 
 }  // extern "C"
