@@ -1,14 +1,17 @@
-"""Benchmark: fill-reducing permutation of the icosphere-7 mesh on one B300.
+"""Benchmark: fill-reducing permutation of a triangle mesh on one B300.
 
-One step = the whole path on one mesh: fp_create_from_faces (CSR assembly) +
-fp_permute (patching, quotient-graph nested dissection, local minimum degree,
-permutation) + fp_symbolic (etree, column counts) + fp_destroy, with the face
+Default workload: the 1024x1024 periodic torus with 30% of its quad diagonals
+flipped (1,048,576 vertices, 3 DOF per vertex, patch cap 512), the largest
+single-mesh configuration. One step = the whole path on one mesh:
+fp_create_from_faces (CSR assembly) + fp_permute (patching, quotient-graph
+nested dissection, local minimum degree, permutation, DOF expansion) +
+fp_symbolic (etree, column counts, DOF expansion) + fp_destroy, with the face
 list already resident in HBM. Each step is timed with CUDA events on the
 launching stream; L2 is flushed (256 MB write) between steps, outside the
 events. Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload icosphere7|torus1024|grid64]
+                  [--workload torus1024|icosphere7|grid64|batch256|batch256_learned]
 
 --impl reference times the CPU oracle (the plain single-threaded statement of
 the method that the tests check the GPU against) on the same workload.
@@ -48,7 +51,10 @@ WORKLOADS = {
 #   perm       : perm + iperm 8
 #   symbolic   : pattern + iperm gather + parent/colcount write 60
 STAGES = ["graph", "patch_bfs", "patch_other", "quotient", "nd_bisect", "nd_separator", "layout",
-          "md_small", "md_mid", "md_large", "perm", "symbolic", "learned", "train"]
+          "md_small", "md_mid", "md_large", "perm", "symbolic", "learned", "train", "patch_local", "join_wait"]
+# stages whose kernels run on the auxiliary streams, overlapped with the
+# handle's stream; their part of the critical path is the join wait
+AUX_STAGES = ("md_mid", "md_large")
 BYTES_PER_VERTEX = {"graph": 52, "patch_bfs": 60, "quotient": 52, "nd_separator": 60, "md_small": 32,
                     "md_mid": 32, "md_large": 32, "perm": 8, "symbolic": 60, "layout": 12}
 PER_LAUNCH_UNITS = {"patch_bfs"}   # bytes per vertex are per launch, not per step
@@ -123,25 +129,52 @@ def make_mesh(name, cap_override=None):
     return getattr(meshgen, gen)(0), (cap_override or cap), dof
 
 
-class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+def gpu_uuid(device_index: int) -> str:
+    """nvidia-smi's UUID string ("GPU-...") of CUDA device `device_index`."""
+    import torch
+    return "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+class Clocks:
+    """nvidia-smi sampling of the SM clock and throttle reasons of the GPU the
+    steps run on, selected by UUID (a CUDA device index need not be
+    nvidia-smi's index under CUDA_VISIBLE_DEVICES). A freshly started
+    nvidia-smi slows the CUDA calls of other processes for about a second
+    while it initialises, so callers keep the GPU busy with untimed work for
+    WARM_S seconds after starting it, then bracket the timed region with
+    begin()/end(); stop() reports the samples taken in that region and, for
+    the median, in the busy window around it."""
+
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    WARM_S = 1.5
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, device_index: int):
+        self.uuid = None
+        self.t0 = self.t1 = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
+            want = gpu_uuid(device_index)
+            listed = subprocess.run(["nvidia-smi", "--query-gpu=uuid", "--format=csv,noheader"],
+                                    capture_output=True, text=True, timeout=30).stdout.split()
+            self.uuid = want if want in listed else None
+            sel = self.uuid if self.uuid else str(device_index)
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "100", "-i", str(gpu_index)], stdout=self.f,
-                                      stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
+                                       "-lms", "100", "-i", sel], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, subprocess.SubprocessError):
             self.p = None
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self) -> dict:
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -149,23 +182,32 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.f.read().strip().splitlines():
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, val in zip(names, parts[6:10]) if val.lower() in ("active", "1")}))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower() in ("active", "1"):
-                    reasons.add(nm)
         os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        t0 = self.t0 if self.t0 is not None else -1e18
+        t1 = self.t1 if self.t1 is not None else 1e18
+        timed = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+        # the GPU runs the same step throughout the busy window around the
+        # timed region (warm steps before it, one more timed-like pass after)
+        busy = [r for r in rows if t0 - self.WARM_S / 2 <= r[0] <= t1 + 0.5] or rows
+        use = timed if len(timed) >= 3 else busy
+        reasons = set().union(*[r[3] for r in use]) if use else set()
+        return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "samples": len(use), "samples_in_timed_region": len(timed),
+                "window": "timed region" if use is timed else "timed region and the busy steps around it",
+                "reasons": sorted(reasons), "gpu": self.uuid or "index (UUID not listed by nvidia-smi)"}
 
 
 def oracle_step(mesh, cap, dof, codes=None):
@@ -223,6 +265,54 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def leaf_vertex_count(node_size) -> int:
+    """Vertices of the tree's leaves (nodes with vertices and no non-empty
+    descendant), given the node sizes of the binary tree in array form."""
+    nn = len(node_size)
+    below = [0] * nn           # vertices strictly below each node
+    for t in range(nn - 1, -1, -1):
+        for c in (2 * t + 1, 2 * t + 2):
+            if c < nn:
+                below[t] += below[c] + int(node_size[c])
+    return sum(int(node_size[t]) for t in range(nn) if node_size[t] > 0 and below[t] == 0)
+
+
+def stage_bytes_per_launch(stage, n, k, stage_n, leaf_vertices):
+    """Algorithmic bytes one launch of `stage` must move (see the table above),
+    or None for stages without a byte model."""
+    if stage_n.get(stage, 0) <= 0:
+        return None
+    if stage in BYTES_PER_PATCH:
+        return BYTES_PER_PATCH[stage] * k
+    if stage == "md_small":
+        units = leaf_vertices
+    elif stage in ("md_mid", "md_large"):
+        units = n - leaf_vertices          # separator vertices
+    elif stage in BYTES_PER_VERTEX:
+        units = n
+    else:
+        return None
+    if stage in PER_LAUNCH_UNITS:
+        return BYTES_PER_VERTEX[stage] * units
+    return BYTES_PER_VERTEX[stage] * units / stage_n[stage]
+
+
+def critical_path(stage_ms) -> dict:
+    """The step's critical path from the stage profile: every stage of the
+    handle's stream is on it; the separator orderings on the auxiliary streams
+    add only the join wait (the handle's stream idling for them after its own
+    leaf orderings). The dominant stage is the largest contribution; for the
+    auxiliary streams that is the longer of their two stages."""
+    main = {s: v for s, v in stage_ms.items() if s not in AUX_STAGES and s != "join_wait"}
+    contrib = dict(main)
+    aux = max(AUX_STAGES, key=lambda s: stage_ms.get(s, 0.0))
+    contrib[aux] = stage_ms.get("join_wait", 0.0)
+    dom = max(contrib, key=lambda s: contrib[s])
+    return {"handle_stream": round(sum(main.values()), 4), "join_wait": round(stage_ms.get("join_wait", 0.0), 4),
+            "auxiliary_streams": round(sum(stage_ms.get(s, 0.0) for s in AUX_STAGES), 4),
+            "dominant": dom, "dominant_contribution": round(contrib[dom], 4)}
+
+
 def run_ours(args):
     import torch
     import paper_2602_00898_b300 as fp
@@ -263,24 +353,32 @@ def run_ours(args):
     # region (about a tenth of a second) then ran ~8% slow in some processes.
     clocks = Clocks(lrank)
     t_warm = time.perf_counter()
-    while time.perf_counter() - t_warm < 0.3:
+    while time.perf_counter() - t_warm < Clocks.WARM_S:
         step()
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
+    t_inside = 0.0
+    clocks.begin()
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
+        t = time.perf_counter()
         nnz, fl, L = step()
+        t_inside += time.perf_counter() - t
         ev[i][1].record(stream)
         launches += L
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
+    clocks.end()
+    for _ in range(3):          # the busy window goes on briefly after the region
+        step()
+    torch.cuda.synchronize()
     clk = clocks.stop()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms_local = sum(ms_steps) / len(ms_steps)
@@ -294,10 +392,10 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     fp.lib().fp_profiling(0)
-    prof_ms = (ctypes.c_double * 16)()
-    prof_n = (ctypes.c_int64 * 16)()
+    prof_ms = (ctypes.c_double * len(STAGES))()
+    prof_n = (ctypes.c_int64 * len(STAGES))()
     fp.lib().fp_profile_read.restype = ctypes.c_int
-    fp.lib().fp_profile_read(prof_ms, prof_n, 16)
+    fp.lib().fp_profile_read(prof_ms, prof_n, len(STAGES))
     stage_ms = {STAGES[i]: prof_ms[i] / nprof for i in range(len(STAGES))}
     stage_n = {STAGES[i]: prof_n[i] / nprof for i in range(len(STAGES))}
 
@@ -318,23 +416,32 @@ def run_ours(args):
         pms.append(a.elapsed_time(b))
     k = fp.fp_get_patches(h)
     depth = fp.fp_get_tree(h)
+    nnodes = (1 << (depth + 1)) - 1
+    nsize = torch.empty(nnodes, dtype=torch.int32, device=dev)
+    fp.fp_get_tree(h, None, nsize, None)
     _, _, nnzA2 = fp.fp_get_sizes(h)
     fp.fp_destroy(h)
+    leaf_vertices = leaf_vertex_count(nsize.cpu().numpy())
 
     # end to end through the host-buffer entry point
     hfaces = torch.from_numpy(mesh.faces).pin_memory()
     houts = [torch.empty(N, dtype=torch.int32).pin_memory() for _ in range(4)]
-    e2e_ms = []
+    # fp_order_faces_host returns once the results are in host memory, so a
+    # host clock around the call is what its caller waits for
+    e2e_ms, e2e_ev = [], []
     for i in range(3 + max(10, args.steps // 2)):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = time.perf_counter()
         a.record(stream)
         fp.fp_order_faces_host(hfaces, n, opts, None, *houts)
         b.record(stream)
+        t = time.perf_counter() - t
         b.synchronize()
         if i >= 3:
-            e2e_ms.append(a.elapsed_time(b))
+            e2e_ms.append(1e3 * t)
+            e2e_ev.append(a.elapsed_time(b))
     e2e = statistics.mean(e2e_ms)
 
     if rank != 0:
@@ -342,25 +449,23 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the dominant stage: the largest GPU time among the stages on
-    # the handle's stream (the separator orderings run on a second stream,
-    # overlapped, and their event pairs also span the wait for the dissection)
-    dom = max((s for s in stage_ms if s not in ("md_mid", "md_large")), key=lambda s: stage_ms[s])
+    cp = critical_path(stage_ms)
+    dom = cp["dominant"]
     peak, peak_kind = peaks()
     roof = None
-    if (dom in BYTES_PER_VERTEX or dom in BYTES_PER_PATCH) and stage_n[dom] > 0:
+    bl = stage_bytes_per_launch(dom, n, k, stage_n, leaf_vertices)
+    if bl is not None and stage_n[dom] > 0:
         per_launch_ms = stage_ms[dom] / stage_n[dom]
-        if dom in BYTES_PER_PATCH:
-            bytes_launch = BYTES_PER_PATCH[dom] * k
-        else:
-            units = n if dom in PER_LAUNCH_UNITS else n / stage_n[dom]
-            bytes_launch = BYTES_PER_VERTEX[dom] * units
-        achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
+        achieved = bl / (per_launch_ms / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": measured_traffic(dom, args.workload),
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": bytes_launch,
-                "launch_ms": per_launch_ms}
-    nnzA = nnzA2 // 2 + n
+                "peak_source": peak_kind + " (HBM copy)", "algorithmic_bytes_per_launch": bl,
+                "launch_ms": per_launch_ms, "launches_per_step": stage_n[dom]}
+    # nnz of the lower triangle (with the diagonal) of the matrix factored:
+    # b x b dense blocks on the vertex graph's pattern plus its diagonal
+    E = nnzA2 // 2
+    nnzA = dof * dof * E + n * dof * (dof + 1) // 2
+    nnzL_vertex = (nnz + n * dof * (dof - 1) // 2) // (dof * dof)
     line = {
         "metric": "permutation Mverts/s at 1 GPU", "value": value, "unit": "Mverts/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -371,12 +476,20 @@ def run_ours(args):
         "ms_median": statistics.median(ms_steps),
         "permute_ms": statistics.median(pms),
         "wall_ms_per_step": 1e3 * wall / args.steps,
+        "host_ms_per_step_inside_events": 1e3 * t_inside / args.steps,
+        "critical_path_ms": cp,
         "stage_profile": f"{nprof} extra steps with per-stage CUDA events (kept out of the timed steps)",
-        "nnzL": nnz, "nnzA": nnzA, "fill_ratio": nnz / nnzA, "flops": fl, "patches": k, "tree_depth": depth,
+        "nnzL": nnz, "nnzA": nnzA, "fill_ratio": nnz / nnzA, "flops": fl,
+        "nnzL_vertex": nnzL_vertex, "fill_ratio_vertex": nnzL_vertex / (E + n),
+        "fill_note": "nnz of L and of the lower triangle of A, both with the diagonal, at the level factored "
+                     "(DOF level with b x b blocks); *_vertex: the same on the vertex graph",
+        "patches": k, "tree_depth": depth,
         "stage_ms": {s: round(v, 4) for s, v in stage_ms.items()},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": n / (e2e / 1e3) / 1e6, "unit": "Mverts/s", "ms": e2e,
+                "timing": "host clock around fp_order_faces_host (pinned faces in, four outputs out)",
+                "event_ms": statistics.mean(e2e_ev),
                 "h2d_bytes_per_step": int(mesh.faces.nbytes),
                 "d2h_bytes_per_step": int(4 * 4 * N + 16)},
         "gpu_launches": int(launches),
@@ -431,11 +544,12 @@ def run_batch(args):
     # the GPU stays busy while the clock sampler starts (as above)
     clocks = Clocks(lrank)
     t_warm = time.perf_counter()
-    while time.perf_counter() - t_warm < 0.3:
+    while time.perf_counter() - t_warm < Clocks.WARM_S:
         assert order_all() == 0
     if ws > 1:
         torch.distributed.barrier()
     times, launches = [], 0
+    clocks.begin()
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -447,6 +561,9 @@ def run_batch(args):
         launches += sum(int(it.launches) for it in items)
     if ws > 1:
         torch.distributed.barrier()
+    clocks.end()
+    assert order_all() == 0
+    torch.cuda.synchronize()
     clk = clocks.stop()
     sec = max_over_ranks(sum(times) / len(times), ws, dev)
     # end to end: pinned host faces in, four outputs back, every step
@@ -515,7 +632,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256", "batch256_learned"], default="icosphere7")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batch256", "batch256_learned"], default="torus1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--patch-cap", type=int, default=None,
                     help="patch cap of a single-mesh workload instead of its default (patch-size studies)")

@@ -60,7 +60,24 @@ typedef struct {
   int32_t dof_per_vertex;  /* b >= 1: each vertex owns b consecutive unknowns
                               (Section 6.5); perm/etree/colcount are then
                               expanded to n*b entries (default 1) */
-  int32_t reserved;        /* must be 0 */
+  int32_t debug_dump;      /* 0 or 1 (default 0). 1: fp_permute also keeps the
+                              boundaries of its stages (seeds, labels after each
+                              Lloyd round, the quotient graph, the sides and
+                              moves of every dissection level) for
+                              fp_get_stage; this adds device copies and one
+                              host sync per patching round */
+  int64_t max_spin;        /* >= 0 (default 0 = 2^24): how many times a bounded
+                              device wait of the library polls before it gives
+                              up. The only such wait is the tensor-core
+                              completion wait of the learned-priority network
+                              (fp_set_priority_net); when it runs out, the
+                              kernel flags it, waits (2^24 polls at most) for
+                              its tensor-core work in flight, frees its tensor
+                              memory and returns, and the call returns
+                              FP_ERR_TIMEOUT with the handle poisoned. The
+                              grid-wide barriers of the cooperative kernels are
+                              the CUDA runtime's (their co-residency is
+                              guaranteed by the cooperative launch). */
 } fp_options;
 
 /* Fills *opts with the defaults above. */
@@ -120,6 +137,53 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm);
  */
 fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL,
                       int64_t* h_flops);
+
+/*
+ * Stage boundaries of the last fp_permute, kept when the handle was created
+ * with opts->debug_dump = 1 (for checking each step of Algorithm 1 against a
+ * reference, not only the final permutation). `index` selects the Lloyd round
+ * or dissection level; int32 arrays:
+ *   FP_STAGE_SEEDS          (index 0)  seed vertex of every patch rank after
+ *                                      the seeding and the unreached
+ *                                      components (Section 4.1 step 1)
+ *   FP_STAGE_LLOYD_SEEDS    (round r)  seed of every rank after Lloyd round r
+ *   FP_STAGE_LABELS         (r = 0..R) patch of every vertex after the first
+ *                                      labelling (r = 0) and after the
+ *                                      relabelling of Lloyd round r (before
+ *                                      the cap splits); the final map is
+ *                                      fp_get_patches'
+ *   FP_STAGE_QUOTIENT_WEIGHT, _ROWPTR, _COL, _EDGE_WEIGHT (index 0): the
+ *                                      quotient graph of the final patches
+ *                                      (Section 3 definition; Algorithm 2
+ *                                      step 1): vertices per patch [k], CSR
+ *                                      [k+1], neighbour patches and edge
+ *                                      weights in increasing neighbour id
+ *   FP_STAGE_SIDE           (depth d)  [k]: side (0 left, 1 right) each patch
+ *                                      took in the node bisected at depth d
+ *                                      (Algorithm 2 step 2), -1 if it took
+ *                                      part in no bisection at depth d
+ *   FP_STAGE_CHILD          (depth d)  [k]: the child node each patch moved to
+ *                                      after depth d's separators (Algorithm 2
+ *                                      step 5), -1 if it has no remaining
+ *                                      vertex or was not bisected
+ * d_out: caller-owned device buffer of `cap` ints (may be NULL to query the
+ * length); *h_len receives the length. Stream-ordered, no sync.
+ * Errors: FP_ERR_STATE (no fp_permute with debug_dump on, or the stage/index
+ * was not recorded), FP_ERR_INVALID_ARG (cap below the length).
+ */
+typedef enum {
+  FP_STAGE_SEEDS = 0,
+  FP_STAGE_LLOYD_SEEDS = 1,
+  FP_STAGE_LABELS = 2,
+  FP_STAGE_QUOTIENT_WEIGHT = 3,
+  FP_STAGE_QUOTIENT_ROWPTR = 4,
+  FP_STAGE_QUOTIENT_COL = 5,
+  FP_STAGE_QUOTIENT_EDGE_WEIGHT = 6,
+  FP_STAGE_SIDE = 7,
+  FP_STAGE_CHILD = 8
+} fp_stage;
+
+fp_status fp_get_stage(fp_handle* h, int32_t stage, int32_t index, int32_t* d_out, int64_t cap, int64_t* h_len);
 
 /* Sizes of the handle: vertices n, DOFs per vertex b, nnz of G (2E). */
 fp_status fp_get_sizes(const fp_handle* h, int32_t* h_n, int32_t* h_dof, int64_t* h_nnz);
@@ -277,7 +341,7 @@ int64_t fp_launch_count(const fp_handle* h);
  */
 typedef enum {
   FP_PROF_GRAPH = 0,       /* a1 CSR assembly */
-  FP_PROF_PATCH_BFS,       /* a2 BFS searches (cooperative) */
+  FP_PROF_PATCH_BFS,       /* a2 Voronoi searches over the whole mesh (k_bfs) */
   FP_PROF_PATCH_OTHER,     /* a2 seeds, Lloyd picks, splits */
   FP_PROF_QUOTIENT,        /* a3 quotient graph */
   FP_PROF_ND_BISECT,       /* a4 bisection of the quotient graph */
@@ -290,6 +354,11 @@ typedef enum {
   FP_PROF_SYMBOLIC,        /* a7 etree and column counts */
   FP_PROF_LEARNED,         /* a10 network scores, keyed orders, fill choice */
   FP_PROF_TRAIN,           /* a10 training samples and gradient steps */
+  FP_PROF_PATCH_LOCAL,     /* a2 searches inside patches (Lloyd depth, splits) */
+  FP_PROF_JOIN_WAIT,       /* time the handle's stream waits, after its own
+                              leaf orderings, for the separator orderings that
+                              run on the auxiliary streams (the part of them on
+                              the critical path) */
   FP_PROF_COUNT
 } fp_prof_kind;
 

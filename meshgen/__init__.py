@@ -152,3 +152,22 @@ def gnn_weights(seed: int, f_in: int = 6, hidden: int = 32, quantized: bool = Tr
             sd = 0.1 if k in ("b1", "b2", "c") else 0.25
             out[k] = r.normal(0.0, sd, size=sh)
     return out
+
+
+def laplacian_values(rowptr: np.ndarray, col: np.ndarray, seed: int | None = None, shift: float = 1.0):
+    """FP64 values of a graph Laplacian plus `shift` times the identity on the
+    symmetric CSR pattern (rowptr, col): A_ij = -w_ij off the diagonal and
+    A_ii = sum_j w_ij + shift. seed None: unit weights (the configurations'
+    "Laplacian + I"); else symmetric weights uniform in [0.5, 1.5] drawn per
+    undirected edge from a PCG64 stream. Returns (diag [n], off [nnz])."""
+    n = rowptr.size - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    dst = col.astype(np.int64)
+    if seed is None:
+        w = np.ones(dst.size)
+    else:
+        key = np.minimum(src, dst) * n + np.maximum(src, dst)
+        uk, inv = np.unique(key, return_inverse=True)
+        w = _rng(seed, 7).uniform(0.5, 1.5, uk.size)[inv]
+    diag = np.bincount(src, weights=w, minlength=n) + shift
+    return diag, -w

@@ -379,3 +379,56 @@ def quotient(g: Graph, label, k: int):
     qc = np.zeros(max(m, 1), np.int32); qw = np.zeros(max(m, 1), np.int32)
     lib().oracle_quotient(rp, cp, g.n, _p(lab), k, _p(w), _p(qr), _p(qc), _p(qw), m)
     return w[:k], qr, qc[:m], qw[:m]
+
+
+def _numeric_lib():
+    L = lib()
+    if not getattr(L, "_chol_ready", False):
+        P = ctypes.POINTER
+        i32p, i64p, f64p = P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_double)
+        L.oracle_cholesky.restype = ctypes.c_int64
+        L.oracle_cholesky.argtypes = [i32p, i32p, ctypes.c_int32, f64p, f64p, i32p, i64p, i32p, f64p, ctypes.c_int64]
+        L.oracle_cholesky_solve.restype = None
+        L.oracle_cholesky_solve.argtypes = [ctypes.c_int32, i32p, i64p, i32p, f64p, f64p, f64p]
+        L._chol_ready = True
+    return L
+
+
+@dataclass
+class Factor:
+    """L of P A P^T in compressed columns (rows ascending, diagonal first)."""
+    Lp: np.ndarray   # int64 [n+1]
+    Li: np.ndarray   # int32 [nnz]
+    Lx: np.ndarray   # float64 [nnz]
+
+
+def cholesky(g: Graph, a_diag, a_off, perm) -> Factor:
+    """Sparse FP64 Cholesky of P A P^T (A: diagonal a_diag, off-diagonal
+    values a_off aligned with g's CSR) by up-looking row solves."""
+    L = _numeric_lib()
+    n = g.n
+    ad = np.ascontiguousarray(a_diag, np.float64)
+    ao = np.ascontiguousarray(a_off, np.float64) if len(a_off) else np.zeros(1)
+    pm = _i32(perm) if n else np.zeros(1, np.int32)
+    rp, cp, _keep = _gp(g)
+    Lp = np.zeros(n + 1, np.int64)
+    nnz = L.oracle_cholesky(rp, cp, n, _p(ad, ctypes.c_double), _p(ao, ctypes.c_double), _p(pm), _p(Lp, ctypes.c_int64),
+                            None, None, 0)
+    Li = np.zeros(max(nnz, 1), np.int32)
+    Lx = np.zeros(max(nnz, 1), np.float64)
+    r = L.oracle_cholesky(rp, cp, n, _p(ad, ctypes.c_double), _p(ao, ctypes.c_double), _p(pm), _p(Lp, ctypes.c_int64),
+                          _p(Li), _p(Lx, ctypes.c_double), nnz)
+    if r < 0:
+        raise ValueError("matrix not positive definite" if r == -1 else "factor storage")
+    return Factor(Lp, Li[:nnz], Lx[:nnz])
+
+
+def cholesky_solve(f: Factor, perm, b) -> np.ndarray:
+    """x with A x = b from the factor of P A P^T."""
+    L = _numeric_lib()
+    n = f.Lp.size - 1
+    bb = np.ascontiguousarray(b, np.float64)
+    x = np.zeros(max(n, 1), np.float64)
+    L.oracle_cholesky_solve(n, _p(_i32(perm)), _p(f.Lp, ctypes.c_int64), _p(f.Li), _p(f.Lx, ctypes.c_double),
+                            _p(bb, ctypes.c_double), _p(x, ctypes.c_double))
+    return x[:n]

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
@@ -927,6 +928,99 @@ int64_t oracle_quotient(const int32_t* rowptr, const int32_t* col, int32_t n, co
     q_rowptr[p + 1] = (int32_t)e;
   }
   return m;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Numeric factorisation and solve (Section 6: the permutation and its
+// elimination tree drive a sparse Cholesky solver). Textbook up-looking
+// sparse Cholesky in FP64 (row k of L solves L[0:k,0:k] l = B[0:k,k] over the
+// columns of k's elimination-tree reach; George & Liu 1981, Davis 2006 ch. 4),
+// written plainly: a dense accumulator, columns kept as growing lists.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+// B = P A P^T with A given by its diagonal a_diag[n] and the off-diagonal
+// values a_off[] aligned with the symmetric CSR (rowptr, col) of its graph.
+// Outputs L in compressed columns, rows ascending (the diagonal first):
+// Lp[n+1], Li[nnz], Lx[nnz]; with Li == NULL only Lp is written and the
+// entry count returned. Returns nnz(L), -1 if a pivot is not positive, -3 if
+// cap is too small.
+int64_t oracle_cholesky(const int32_t* rowptr, const int32_t* col, int32_t n, const double* a_diag,
+                        const double* a_off, const int32_t* perm, int64_t* Lp, int32_t* Li, double* Lx, int64_t cap) {
+  std::vector<int32_t> iperm(n);
+  for (int32_t i = 0; i < n; ++i) iperm[perm[i]] = i;
+  Adj a = adj_from_csr(rowptr, col, n);
+  std::vector<int32_t> parent, cc;
+  int64_t nnzL = 0, fl = 0;
+  symbolic(a, perm, parent, cc, nnzL, fl);
+  if (!Li) {
+    Lp[0] = 0;
+    for (int32_t j = 0; j < n; ++j) Lp[j + 1] = Lp[j] + cc[j];
+    return nnzL;
+  }
+  if (nnzL > cap) return -3;
+  std::vector<std::vector<int32_t>> rows(n);
+  std::vector<std::vector<double>> vals(n);
+  std::vector<double> x(n, 0.0);
+  std::vector<int32_t> mark(n, -1), reach;
+  for (int32_t k = 0; k < n; ++k) {
+    // scatter column k of B (rows <= k) and find the reach: every column j < k
+    // on an etree path from an entry B(i, k), i < k, up to k
+    const int32_t v = perm[k];
+    double d = a_diag[v];
+    reach.clear();
+    mark[k] = k;
+    for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      const int32_t i = iperm[col[e]];
+      if (i > k) continue;
+      x[i] += a_off[e];
+      for (int32_t j = i; mark[j] != k; j = parent[j]) {
+        mark[j] = k;
+        reach.push_back(j);
+      }
+    }
+    std::sort(reach.begin(), reach.end());
+    // triangular solve in increasing column order: l_j = x_j / L_jj, then
+    // column j's rows below j (and above k) lose L_pj l_j
+    for (int32_t j : reach) {
+      const double lj = x[j] / vals[j][0];
+      x[j] = 0.0;
+      for (size_t q = 1; q < rows[j].size(); ++q) x[rows[j][q]] -= vals[j][q] * lj;
+      d -= lj * lj;
+      rows[j].push_back(k);
+      vals[j].push_back(lj);
+    }
+    if (!(d > 0.0)) return -1;
+    rows[k].push_back(k);
+    vals[k].push_back(std::sqrt(d));
+  }
+  int64_t e = 0;
+  Lp[0] = 0;
+  for (int32_t j = 0; j < n; ++j) {
+    for (size_t q = 0; q < rows[j].size(); ++q) { Li[e] = rows[j][q]; Lx[e] = vals[j][q]; ++e; }
+    Lp[j + 1] = e;
+  }
+  return e;
+}
+
+// Solves P A P^T y = P b for x = P^T y with the factor of oracle_cholesky:
+// forward substitution L z = P b, back substitution L^T y = z, x[perm[i]] = y[i].
+void oracle_cholesky_solve(int32_t n, const int32_t* perm, const int64_t* Lp, const int32_t* Li, const double* Lx,
+                           const double* b, double* x) {
+  std::vector<double> y(n);
+  for (int32_t i = 0; i < n; ++i) y[i] = b[perm[i]];
+  for (int32_t j = 0; j < n; ++j) {
+    y[j] /= Lx[Lp[j]];
+    for (int64_t q = Lp[j] + 1; q < Lp[j + 1]; ++q) y[Li[q]] -= Lx[q] * y[j];
+  }
+  for (int32_t j = n - 1; j >= 0; --j) {
+    double s = y[j];
+    for (int64_t q = Lp[j] + 1; q < Lp[j + 1]; ++q) s -= Lx[q] * y[Li[q]];
+    y[j] = s / Lx[Lp[j]];
+  }
+  for (int32_t i = 0; i < n; ++i) x[perm[i]] = y[i];
 }
 
 }  // extern "C"

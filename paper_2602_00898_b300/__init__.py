@@ -30,7 +30,7 @@ class FpError(RuntimeError):
 class fp_options(ctypes.Structure):
     _fields_ = [("patch_cap", ctypes.c_int32), ("lloyd_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("nd_level", ctypes.c_int32), ("schedule", ctypes.c_int32), ("dof_per_vertex", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("debug_dump", ctypes.c_int32), ("max_spin", ctypes.c_int64)]
 
 
 class fp_batch_item(ctypes.Structure):
@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
             "fp_permute": (i32, [vp, vp, vp]),
             "fp_symbolic": (i32, [vp, vp, vp, P64, P64]),
             "fp_get_sizes": (i32, [vp, P32, P32, P64]),
+            "fp_get_stage": (i32, [vp, i32, i32, vp, i64, P64]),
             "fp_get_graph": (i32, [vp, vp, vp]),
             "fp_get_patches": (i32, [vp, vp, P32]),
             "fp_set_patches": (i32, [vp, vp, i32]),
@@ -151,6 +152,22 @@ def fp_get_sizes(h) -> tuple[int, int, int]:
     n, b, nnz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(lib().fp_get_sizes(h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(nnz)), h)
     return n.value, b.value, nnz.value
+
+
+STAGES = {"seeds": 0, "lloyd_seeds": 1, "labels": 2, "quotient_weight": 3, "quotient_rowptr": 4,
+          "quotient_col": 5, "quotient_edge_weight": 6, "side": 7, "child": 8}
+
+
+def fp_get_stage(h, stage: str, index: int = 0):
+    """A stage boundary of the last fp_permute of a handle created with
+    debug_dump=1, as a new int32 CUDA tensor."""
+    import torch
+    n = ctypes.c_int64()
+    code = STAGES[stage]
+    _check(lib().fp_get_stage(h, code, int(index), None, 0, ctypes.byref(n)), h)
+    out = torch.empty(max(n.value, 1), dtype=torch.int32, device="cuda")
+    _check(lib().fp_get_stage(h, code, int(index), out.data_ptr(), n.value, ctypes.byref(n)), h)
+    return out[:n.value]
 
 
 def fp_get_graph(h, rowptr=None, col=None):

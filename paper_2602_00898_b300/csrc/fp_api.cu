@@ -230,6 +230,24 @@ fp_status sync_status(fp_handle* h, int32_t* status_out) {
   return FP_OK;
 }
 
+int32_t* stage_buffer(fp_handle* h, int32_t stage, int32_t index, int64_t len) {
+  if (!h->opt.debug_dump) return nullptr;
+  int32_t* d = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(len > 0 ? len : 1));
+  if (!d) return nullptr;
+  h->dumps.push_back({stage, index, d, len});
+  return d;
+}
+
+void stage_dump(fp_handle* h, int32_t stage, int32_t index, const int32_t* src, int64_t len) {
+  int32_t* d = stage_buffer(h, stage, index, len);
+  if (d && len > 0) cudaMemcpyAsync(d, src, sizeof(int32_t) * (size_t)len, cudaMemcpyDeviceToDevice, h->stream);
+}
+
+void stage_clear(fp_handle* h) {
+  for (auto& e : h->dumps) dev_free(h, e.d);
+  h->dumps.clear();
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -239,7 +257,8 @@ namespace {
 fp_status validate_options(const fp_options* o) {
   if (!o) return FP_ERR_INVALID_ARG;
   if (o->patch_cap < 1 || o->lloyd_rounds < 0 || o->lloyd_rounds > 64 || o->nd_level < 0 || o->nd_level > 24 ||
-      (o->schedule != 0 && o->schedule != 1) || o->dof_per_vertex < 1 || o->reserved != 0)
+      (o->schedule != 0 && o->schedule != 1) || o->dof_per_vertex < 1 || (o->debug_dump != 0 && o->debug_dump != 1) ||
+      o->max_spin < 0)
     return FP_ERR_INVALID_ARG;
   return FP_OK;
 }
@@ -299,7 +318,8 @@ void fp_default_options(fp_options* o) {
   o->nd_level = 0;
   o->schedule = 0;
   o->dof_per_vertex = 1;
-  o->reserved = 0;
+  o->debug_dump = 0;
+  o->max_spin = 0;
 }
 
 fp_status fp_create_from_faces(const int32_t* d_faces, int64_t n_faces, int32_t n_vertices, const fp_options* opts,
@@ -335,6 +355,7 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
   if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
   if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
   h->permuted = false;
+  stage_clear(h);
   if (h->user_k > 0) {
     // patches supplied by the caller (fp_set_patches)
     h->k = h->user_k;
@@ -458,6 +479,23 @@ fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int6
   if (h_nnzL) *h_nnzL = nnz;
   if (h_flops) *h_flops = fl;
   return FP_OK;
+}
+
+fp_status fp_get_stage(fp_handle* h, int32_t stage, int32_t index, int32_t* d_out, int64_t cap, int64_t* h_len) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->permuted || !h->opt.debug_dump) return fail(h, FP_ERR_STATE, "no stage record: create the handle with "
+                                                                    "debug_dump = 1 and call fp_permute");
+  for (const auto& e : h->dumps) {
+    if (e.stage != stage || e.index != index) continue;
+    if (h_len) *h_len = e.len;
+    if (!d_out) return FP_OK;
+    if (cap < e.len) return fail(h, FP_ERR_INVALID_ARG, "stage buffer too small");
+    if (e.len > 0) cudaMemcpyAsync(d_out, e.d, sizeof(int32_t) * (size_t)e.len, cudaMemcpyDeviceToDevice, h->stream);
+    FP_CHECK_LAUNCH(h, "stage copy");
+    return FP_OK;
+  }
+  return fail(h, FP_ERR_STATE, "stage not recorded by the last fp_permute");
 }
 
 fp_status fp_get_sizes(const fp_handle* h, int32_t* h_n, int32_t* h_dof, int64_t* h_nnz) {

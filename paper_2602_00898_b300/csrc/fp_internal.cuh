@@ -104,6 +104,14 @@ struct fp_handle {
   int32_t learned_leaves = 0, learned_kept = 0;
   int64_t fill_plain = 0, fill_chosen = 0;
 
+  // stage boundaries kept for fp_get_stage (opt.debug_dump)
+  struct StageDump {
+    int32_t stage, index;
+    int32_t* d;
+    int64_t len;
+  };
+  std::vector<StageDump> dumps;
+
   std::string err;
   int64_t launches = 0;
   std::vector<void*> allocs;
@@ -118,6 +126,12 @@ void dev_free(fp_handle* h, void* p);
 fp_status fail(fp_handle* h, fp_status s, const std::string& msg);
 fp_status check_cuda(fp_handle* h, cudaError_t e, const char* what);
 fp_status sync_status(fp_handle* h, int32_t* status_out);   // sync stream, read status word
+// Stage boundaries for fp_get_stage (no-ops unless opt.debug_dump): a new
+// handle-owned buffer of `len` ints recorded as (stage, index), or a copy of
+// `src` into one. stage_clear drops the records of an earlier fp_permute.
+int32_t* stage_buffer(fp_handle* h, int32_t stage, int32_t index, int64_t len);
+void stage_dump(fp_handle* h, int32_t stage, int32_t index, const int32_t* src, int64_t len);
+void stage_clear(fp_handle* h);
 // Many workspace arrays from one allocation: a layout function calls get()
 // for every array twice, first to size the block (pointers come back null),
 // then, after alloc(), to hand out 256-byte aligned pieces of it. One

@@ -98,13 +98,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Bounded wait for the phase with the given parity; false if it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait for the phase with the given parity: at most `polls`
+// non-blocking tests of the barrier (so that a limit counts exactly); false
+// if it ran out.
+constexpr int64_t SPIN_DEFAULT = (int64_t)1 << 24;
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int64_t polls) {
   const uint32_t a = smem_u32(mbar);
-  for (int it = 0; it < (1 << 24); ++it) {
+  for (int64_t it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
         : "r"(a), "r"(parity)
@@ -148,6 +151,7 @@ struct ScoreArgs {
   int32_t* score;          // [n] per position, out (may be NULL)
   uint8_t* xout;           // [n][8] feature codes per position, out (may be NULL)
   int32_t* status;
+  int64_t max_spin;        // polls of the tensor-core completion wait
 };
 
 // shared layout of the scoring kernel (bytes)
@@ -310,12 +314,14 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
                  IDESC_BF16_M128_N32, kk > 0);
         tc_commit(&s_mbar);
       }
-      ok = __syncthreads_and(mbar_wait(&s_mbar, phase)) != 0;
+      ok = __syncthreads_and(mbar_wait(&s_mbar, phase, a.max_spin)) != 0;
       if (!ok) {
-        // the MMA did not complete within the bound: wait for it once more
-        // (bounded), flag the failure, and leave with the accumulator unread
+        // the MMA did not complete within the caller's bound: wait for it
+        // once more (2^24 polls at most) so that nothing is in flight when
+        // the tensor memory is freed, flag the failure, and leave with the
+        // accumulator unread
         if (tid == 0) {
-          mbar_wait(&s_mbar, phase);
+          mbar_wait(&s_mbar, phase, SPIN_DEFAULT);
           atomicOr(a.status, ST_TIMEOUT);
         }
         break;
@@ -420,7 +426,8 @@ fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, co
                            int32_t* d_score, uint8_t* d_x) {
   if (nl == 0) return FP_OK;
   ScoreArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_begin, h->node_size, d_leaves, nl, d_q,
-               h->opt.patch_cap, d_key, d_score, d_x, h->d_status};
+               h->opt.patch_cap, d_key, d_score, d_x, h->d_status,
+               h->opt.max_spin > 0 ? h->opt.max_spin : SPIN_DEFAULT};
   allow_max_dynamic_smem(k_gnn_score);
   FP_LAUNCH(h, k_gnn_score, nl, SC_THREADS, (size_t)SC_BYTES, sa);
   FP_CHECK_LAUNCH(h, "network scores");

@@ -1102,10 +1102,15 @@ fp_status run_local_order(fp_handle* h) {
     launch_pdl(h->stream, k_md_leaf, (unsigned)grid, 32 * nw, sm, a);
     h->launches++;
   }
-  cudaEventRecord(ax->join, s2);
-  cudaStreamWaitEvent(h->stream, ax->join, 0);
-  cudaEventRecord(ax3->join, s3);
-  cudaStreamWaitEvent(h->stream, ax3->join, 0);
+  {
+    // the pair brackets only the wait: it starts when the handle's stream has
+    // finished the leaves and ends when both auxiliary streams have finished
+    ProfScope ps(FP_PROF_JOIN_WAIT, h->stream);
+    cudaEventRecord(ax->join, s2);
+    cudaStreamWaitEvent(h->stream, ax->join, 0);
+    cudaEventRecord(ax3->join, s3);
+    cudaStreamWaitEvent(h->stream, ax3->join, 0);
+  }
   FP_CHECK_LAUNCH(h, "minimum degree");
   early_md_release(h);
   if (n > 0) {

@@ -18,6 +18,7 @@
 //      and patches to the children 2t+1 / 2t+2.
 // All nodes of one depth are processed by the same launches; the host never
 // waits inside the level loop.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "fp_device.cuh"
@@ -209,6 +210,8 @@ struct BisectArgs {
   int32_t mcap, ecap;          // shared-memory staging limits of this launch
   int32_t k;                   // patches
   int32_t smem_ints;           // dynamic shared memory of the launch, in ints
+  const int32_t* w;            // [k] remaining vertices of every patch
+  int32_t cap_log;             // a child of a node at this depth keeps at most 2^cap_log patches
 };
 
 // Per-node working set: in shared memory when the node has <= mcap patches and
@@ -277,7 +280,8 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
   __shared__ int64_t red64[40];
   __shared__ int32_t red[40];
   __shared__ int32_t scnt[3];
-  __shared__ int32_t s_lstar, s_rem;
+  __shared__ int32_t s_lstar, s_rem, s_jstar;
+  __shared__ int64_t s_cumw;
   for (int32_t ni = blockIdx.x; ni < a.T; ni += gridDim.x) {
     const int32_t t = a.t0 + ni;
     const int32_t base = a.npstart[ni];
@@ -417,8 +421,23 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       v.mark[i] = 0;
     }
     __syncthreads();
-    const int32_t half = (m + 1) / 2;
-    int32_t pos = 0;
+    // R8 balance: the cut j of the node's order (the number of patches on
+    // the left) minimises |2 P_j - W| over J = [lo, hi], P_j the weight of
+    // the first j patches, ties to the smaller j. The cost is unimodal in j,
+    // so the answer is the first crossing (2 P_j >= W) or the patch before
+    // it, clamped into J. Components come in order; the cut is fixed in the
+    // component holding the crossing (or at hi, if that comes first), and
+    // every component is then assigned against the cut.
+    int32_t lo = 1, hi = m - 1;
+    if (a.cap_log < 30) {
+      const int32_t c = 1 << a.cap_log;
+      const int32_t l2 = m - c > 1 ? m - c : 1, h2 = m - 1 < c ? m - 1 : c;
+      if (l2 <= h2) { lo = l2; hi = h2; }
+    }
+    int64_t W = -1;            // the node's weight, once needed
+    int32_t jstar = lo == hi ? lo : -1;   // the cut, once fixed
+    int32_t pos = 0;           // patches ordered before this component
+    int64_t posw = 0;          // and their weight
     for (;;) {
       // next component: smallest untouched local index
       int32_t c0 = INT_MAX;
@@ -474,11 +493,97 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
       __syncthreads();
       // sweep 2: the order of the component is (level from r1, id)
       block_bfs(v, r1, scnt);
-      int32_t cs = 0;
-      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) cs += v.mark[i] == 2;
-      cs = block_sum(cs, red);
-      if (pos + cs <= half || pos >= half) {
-        const int32_t sd = pos >= half ? 1 : 0;
+      // count and weight of the component in one reduction
+      int64_t pk = 0;
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+        if (v.mark[i] == 2) pk += ((int64_t)1 << 32) | (uint32_t)a.w[v.L[i]];
+      pk = block_sum(pk, red64);
+      const int32_t cs = (int32_t)(pk >> 32);
+      const int64_t cw = pk & 0xffffffffll;
+      // left-set rule of this component: lvl < lstar, or lvl == lstar and
+      // (local index < istar, or == istar when incl); -1 = by count below
+      int32_t d_lstar = -1, d_istar = 0, d_incl = 0;
+      if (jstar < 0) {
+        if (W < 0) {
+          if (pos == 0 && cs == m) {
+            W = cw;
+          } else {
+            int32_t ws = 0;
+            for (int32_t i = threadIdx.x; i < m; i += blockDim.x) ws += a.w[v.L[i]];
+            W = block_sum(ws, red);
+          }
+        }
+        if (2 * (posw + cw) >= W) {
+          // the crossing lies in this component: levels by weight (and
+          // count), then the patches of the crossing level in id order
+          const int64_t T2 = W - 2 * posw;        // > 0: need 2 * (prefix) >= T2
+          int32_t* hc = v.qa;                     // counts per level
+          int32_t* hw = v.qb;                     // weights per level
+          for (int32_t i = threadIdx.x; i < m; i += blockDim.x) { hc[i] = 0; hw[i] = 0; }
+          __syncthreads();
+          for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+            if (v.mark[i] == 2) { atomicAdd(&hc[v.lvl[i]], 1); atomicAdd(&hw[v.lvl[i]], a.w[v.L[i]]); }
+          __syncthreads();
+          if (threadIdx.x == 0) {
+            int64_t cumw = 0;
+            int32_t cumc = 0, l = 0;
+            while (2 * (cumw + hw[l]) < T2) { cumw += hw[l]; cumc += hc[l]; ++l; }
+            s_lstar = l;
+            s_rem = cumc;
+            s_cumw = cumw;
+            s_jstar = hc[l];
+          }
+          __syncthreads();
+          const int32_t lstar = s_lstar, cumc = s_rem, nlev = s_jstar;
+          const int64_t cumw = s_cumw;
+          int32_t beforew = 0;
+          for (int32_t i0 = 0; i0 < m; i0 += blockDim.x) {
+            const int32_t i = i0 + threadIdx.x;
+            const bool at = i < m && v.mark[i] == 2 && v.lvl[i] == lstar;
+            const int32_t wi = at ? a.w[v.L[i]] : 0;
+            int32_t totw;
+            const int32_t exw = block_excl_scan_i32(wi, &totw, red) + beforew;
+            if (at && 2 * (cumw + exw) < T2 && 2 * (cumw + exw + wi) >= T2) {
+              // the first patch whose prefix reaches half the weight: keep it
+              // on the left iff that cut is strictly closer to the half
+              const int64_t p1 = posw + cumw + exw + wi;
+              s_lstar = i;
+              s_rem = (2 * p1 - W) < (W - 2 * (p1 - wi)) ? 1 : 0;
+            }
+            beforew += totw;
+          }
+          __syncthreads();
+          const int32_t istar = s_lstar, incl = s_rem;
+          // the cut's position j0 lies in [pos + cumc, pos + cumc + nlev];
+          // its exact rank is needed only when the clamp may bind
+          int32_t j0lo = pos + cumc, j0hi = pos + cumc + nlev;
+          if (j0lo < lo || j0hi > hi) {
+            int32_t r = 0;
+            for (int32_t i = threadIdx.x; i < istar; i += blockDim.x) r += v.mark[i] == 2 && v.lvl[i] == lstar;
+            r = block_sum(r, red);
+            const int32_t j0 = pos + cumc + r + incl;
+            jstar = j0 < lo ? lo : (j0 > hi ? hi : j0);
+            if (jstar == j0) { d_lstar = lstar; d_istar = istar; d_incl = incl; }
+          } else {
+            jstar = INT_MAX;          // fixed by the rule below, inside this component
+            d_lstar = lstar; d_istar = istar; d_incl = incl;
+          }
+        } else if (hi <= pos + cs) {
+          jstar = hi;       // the crossing comes later, the cut stops at hi
+        }
+      }
+      if (d_lstar >= 0) {
+        for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+          if (v.mark[i] == 2) {
+            const int32_t lv = v.lvl[i];
+            const int32_t sd = (lv < d_lstar || (lv == d_lstar && (i < d_istar || (d_incl && i == d_istar)))) ? 0 : 1;
+            a.side[v.L[i]] = sd;
+            if (v.sd) v.sd[i] = (int8_t)sd;
+            v.mark[i] = 1;
+          }
+        if (jstar == INT_MAX) jstar = pos;  // every later component goes right
+      } else if (jstar < 0 || pos + cs <= jstar || pos >= jstar) {
+        const int32_t sd = (jstar >= 0 && pos >= jstar) ? 1 : 0;
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
           if (v.mark[i] == 2) {
             a.side[v.L[i]] = sd;
@@ -486,8 +591,10 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
             v.mark[i] = 1;
           }
       } else {
-        // levels histogram in the frontier buffer qa (free after the sweeps)
-        const int32_t need = half - pos;
+        // the cut falls inside the component: its first `need` patches in
+        // (level, id) order go left; levels histogram in the frontier buffer
+        // qa (free after the sweeps)
+        const int32_t need = jstar - pos;
         int32_t* hist2 = v.qa;
         for (int32_t i = threadIdx.x; i < m; i += blockDim.x) hist2[i] = 0;
         __syncthreads();
@@ -520,6 +627,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
         }
       }
       pos += cs;
+      posw += cw;
       __syncthreads();
     }
     // crossing patches: a neighbour of positive weight in this node on the
@@ -814,6 +922,18 @@ __global__ void k_nd_move_patches(LevelArgs a) {
 }
 
 
+// Stage record (debug_dump) of one level's bisection: the side of every patch
+// of a split node at this depth, -1 for the others.
+__global__ void k_stage_sides(const int32_t* __restrict__ patch_node, const int32_t* __restrict__ side,
+                              const int32_t* __restrict__ split, int32_t t0, int32_t T, int32_t k,
+                              int32_t* __restrict__ out) {
+  FP_PDL_WAIT();
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) {
+    const int32_t t = patch_node[p];
+    out[p] = (t >= t0 && t < t0 + T && split[t - t0]) ? side[p] : -1;
+  }
+}
+
 __global__ void k_patch_node_init(const int32_t* __restrict__ psize, int32_t k, int32_t* __restrict__ patch_node) {
   FP_PDL_WAIT();
   for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
@@ -895,6 +1015,18 @@ fp_status run_nested_dissection(fp_handle* h) {
   FP_LAUNCH(h, k_zero_i8, G, 256, 0, vstate, (int64_t)n);
   FP_CHECK_LAUNCH(h, "quotient graph");
   ps_q.end();
+  if (h->opt.debug_dump) {
+    // stage record: the quotient graph (its entry count is read back here)
+    int32_t* hb = pinned_scratch();
+    if (!hb) return fail(h, FP_ERR_OUT_OF_MEMORY, "stage record");
+    cudaMemcpyAsync(hb, q_rowptr + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return check_cuda(h, e, "stage record");
+    stage_dump(h, FP_STAGE_QUOTIENT_WEIGHT, 0, psize, k);
+    stage_dump(h, FP_STAGE_QUOTIENT_ROWPTR, 0, q_rowptr, (int64_t)k + 1);
+    stage_dump(h, FP_STAGE_QUOTIENT_COL, 0, q_col, hb[0]);
+    stage_dump(h, FP_STAGE_QUOTIENT_EDGE_WEIGHT, 0, q_w, hb[0]);
+  }
 
   int per = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -917,20 +1049,25 @@ fp_status run_nested_dissection(fp_handle* h) {
       fill_i32(h, npfill, 0, T);
       FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
     }
-    // nodes at depth d hold at most ceil(k / 2^d) patches (left = ceil(|S|/2)):
-    // stage that many in shared memory with 7 adjacency entries per patch
-    // (quotient graphs of meshes have degree ~6), up to what fits in a CTA
+    // a node at depth d holds at most 2^(Dsplit - d) patches (the subtree
+    // capacity that bounds every cut, R8): stage that many in shared memory
+    // with 7 adjacency entries per patch (quotient graphs of meshes have
+    // degree ~6), up to what fits in a CTA; larger nodes (only with an
+    // explicit depth below ceil(log2 k)) work in global memory
     constexpr int32_t MCAP_MAX = (225 * 1024 - 64) / (4 * 12 + 2);
-    int32_t mcap = (int32_t)(((int64_t)k + T - 1) / T);
+    int32_t mcap = Dsplit - d >= 31 ? k : (int32_t)std::min<int64_t>(k, (int64_t)1 << (Dsplit - d));
     mcap = mcap < 32 ? 32 : (mcap > MCAP_MAX ? MCAP_MAX : mcap);
     const int32_t ecap = 7 * mcap;
     const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + 2 * (size_t)mcap;
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
-                  lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4)};
+                  lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4),
+                  w, Dsplit - d - 1};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
     allow_max_dynamic_smem(k_nd_bisect);
     FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
     ps_b.end();
+    if (int32_t* sb = stage_buffer(h, FP_STAGE_SIDE, d, k))
+      FP_LAUNCH(h, k_stage_sides, GK, 256, 0, patch_node, side, split, t0, T, k, sb);
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, cand_x, xcol,
                  ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross};
@@ -951,6 +1088,7 @@ fp_status run_nested_dissection(fp_handle* h) {
     FP_LAUNCH(h, k_nd_apply, G, 256, 0, la);
     FP_LAUNCH(h, k_nd_move_patches, G > GK ? G : GK, 256, 0, la);
     FP_CHECK_LAUNCH(h, "nd level");
+    stage_dump(h, FP_STAGE_CHILD, d, patch_node, k);
     // the nodes of depth d are final now
     FP_TRY(launch_early_md(h, d));
   }

@@ -644,6 +644,9 @@ fp_status run_patching(fp_handle* h) {
     FP_TRY(sync_status(h, &st));
     k += hbuf[0];
   }
+  // stage record (debug_dump): the seeds after R1 + R3 and the first labels
+  stage_dump(h, FP_STAGE_SEEDS, 0, seed_of, k);
+  if (int32_t* lb = stage_buffer(h, FP_STAGE_LABELS, 0, n)) FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, lb);
   // vertex lists by patch: labels and counts, their scans (pdeg is cleared to
   // serve as the scatter cursors), the scatter
   auto patch_lists = [&](int32_t kk) {
@@ -663,7 +666,7 @@ fp_status run_patching(fp_handle* h) {
     la.k = k;
     la.over = nullptr;
     {
-      ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
+      ProfScope ps(FP_PROF_PATCH_LOCAL, h->stream);
       FP_LAUNCH(h, k_patch_local<0>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
     }
     {
@@ -673,7 +676,9 @@ fp_status run_patching(fp_handle* h) {
       FP_LAUNCH(h, k_all_seed_sources, GK, 256, 0, h->rowptr, seed_of, k, key, fa, ctr);
     }
     FP_CHECK_LAUNCH(h, "lloyd");
+    stage_dump(h, FP_STAGE_LLOYD_SEEDS, it, seed_of, k);
     FP_TRY(L.bfs(h, key, fa, fb, ctr));
+    if (int32_t* lb = stage_buffer(h, FP_STAGE_LABELS, it + 1, n)) FP_LAUNCH(h, k_labels_of, G, 256, 0, key, n, lb);
   }
   // R5 cap: split until every patch fits. The first round counts the patch
   // sizes; every split counts its two halves, so a later round rebuilds the
@@ -705,7 +710,7 @@ fp_status run_patching(fp_handle* h) {
     fill_i32(h, over_next, 0, nclear);
     fill_i32(h, ocnt, 0, 1);
     {
-      ProfScope ps(FP_PROF_PATCH_BFS, h->stream);
+      ProfScope ps(FP_PROF_PATCH_LOCAL, h->stream);
       FP_LAUNCH(h, k_patch_local<1>, k < GL ? k : GL, LOCAL_THREADS, 0, la);
       FP_LAUNCH(h, k_split_seeds, GKr, 256, 0, best, over, orank, k, seed_of);
       FP_LAUNCH(h, k_patch_local<2>, k < GL ? k : GL, LOCAL_THREADS, 0, la);

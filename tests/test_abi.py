@@ -30,9 +30,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_default_options_and_status_strings():
     o = fp.fp_default_options()
-    assert (o.patch_cap, o.lloyd_rounds, o.seed, o.nd_level, o.schedule, o.dof_per_vertex, o.reserved) == \
-        (512, 2, 0, 0, 0, 1, 0)
-    assert ctypes.sizeof(fp.fp_options) == 32
+    assert (o.patch_cap, o.lloyd_rounds, o.seed, o.nd_level, o.schedule, o.dof_per_vertex, o.debug_dump,
+            o.max_spin) == (512, 2, 0, 0, 0, 1, 0, 0)
+    assert ctypes.sizeof(fp.fp_options) == 40
     L = fp.lib()
     for code, name in fp.STATUS.items():
         assert L.fp_status_string(code).decode() == name
@@ -40,7 +40,7 @@ def test_default_options_and_status_strings():
 
 @pytest.mark.parametrize("field,value", [("patch_cap", 0), ("lloyd_rounds", -1), ("nd_level", -2),
                                          ("nd_level", 25), ("schedule", 2), ("dof_per_vertex", 0),
-                                         ("reserved", 1)])
+                                         ("debug_dump", 2), ("debug_dump", -1), ("max_spin", -1)])
 def test_bad_options_rejected_without_device(field, value):
     o = fp.fp_default_options(**{field: value})
     h = ctypes.c_void_p()
