@@ -51,7 +51,8 @@ WORKLOADS = {
 #   perm       : perm + iperm 8
 #   symbolic   : pattern + iperm gather + parent/colcount write 60
 STAGES = ["graph", "patch_bfs", "patch_other", "quotient", "nd_bisect", "nd_separator", "layout",
-          "md_small", "md_mid", "md_large", "perm", "symbolic", "learned", "train", "patch_local", "join_wait"]
+          "md_small", "md_mid", "md_large", "perm", "symbolic", "learned", "train", "patch_local", "join_wait",
+          "numeric"]
 # stages whose kernels run on the auxiliary streams, overlapped with the
 # handle's stream; their part of the critical path is the join wait
 AUX_STAGES = ("md_mid", "md_large")

@@ -316,6 +316,54 @@ fp_status fp_graph_from_faces_static(const int32_t* d_faces, int64_t n_faces, in
                                      int32_t* d_rowptr, int32_t* d_col, int64_t col_cap, int64_t* h_nnz,
                                      void* stream);
 
+/* ---- numeric factorisation driven by the permutation ----------------------------
+ *
+ * The paper's purpose for the permutation is a sparse Cholesky solver
+ * (Section 6: the permutation and its elimination tree are handed to cuDSS or
+ * MKL). These calls factor and solve on the GPU with the handle's ordering:
+ * a multifrontal Cholesky with one dense front per tree node of Section 4.2
+ * (the node's columns plus the ancestor rows its subtree reaches), FP64.
+ * Scalar matrices only (dof_per_vertex = 1).
+ */
+
+/*
+ * Numeric Cholesky L L^T = P A P^T after fp_permute. A is symmetric positive
+ * definite with the pattern of the handle's graph plus the diagonal:
+ * d_diag [n] its diagonal by vertex, d_offdiag [nnz] its off-diagonal values
+ * aligned with the CSR that fp_get_graph returns (entry e of row v is
+ * A[v, col[e]]; both triangles, equal values). Device buffers, read during the
+ * call. The factor stays in the handle until the next fp_permute or
+ * fp_destroy. Synchronises the stream. Errors: FP_ERR_STATE (no fp_permute),
+ * FP_ERR_UNSUPPORTED (dof_per_vertex > 1, or a front beyond the kernels'
+ * limits: a node with more than 1.6M ancestor columns or an update matrix
+ * above 51,200 rows), FP_ERR_INVALID_ARG (NULL values with n > 0, or a pivot
+ * that is not positive: A is not positive definite), FP_ERR_OUT_OF_MEMORY.
+ */
+fp_status fp_factor(fp_handle* h, const double* d_diag, const double* d_offdiag);
+
+/*
+ * Solves A x = b with the factor of fp_factor: d_b [n] by vertex (read),
+ * d_x [n] by vertex (written; may equal d_b). Stream-ordered, no sync.
+ * Errors: FP_ERR_STATE (no factor), FP_ERR_INVALID_ARG, FP_ERR_OUT_OF_MEMORY.
+ */
+fp_status fp_solve(fp_handle* h, const double* d_b, double* d_x);
+
+/*
+ * The factor in compressed columns indexed by new position: d_colptr [n+1]
+ * (int64), d_rows / d_vals [*h_nnz] (rows ascending, the diagonal first). The
+ * rows of column j are those of its front: every later position of j's tree
+ * node (where L is structurally zero the value is exactly 0.0) and the
+ * ancestor rows of the node's front. Call with NULL buffers to get *h_nnz.
+ * Synchronises the stream. Errors: FP_ERR_STATE (no factor),
+ * FP_ERR_INVALID_ARG (cap below *h_nnz).
+ */
+fp_status fp_factor_export(fp_handle* h, int64_t* d_colptr, int32_t* d_rows, double* d_vals, int64_t cap,
+                           int64_t* h_nnz);
+
+/* Sizes of the factor: doubles held by the fronts, flops of their partial
+ * factorisations, and entries of L as stored (each may be NULL). */
+fp_status fp_factor_stats(const fp_handle* h, int64_t* h_front_doubles, int64_t* h_flops, int64_t* h_nnz);
+
 /* Releases the handle and its workspace (stream-ordered). NULL is a no-op. */
 fp_status fp_destroy(fp_handle* h);
 
@@ -359,6 +407,7 @@ typedef enum {
                               leaf orderings, for the separator orderings that
                               run on the auxiliary streams (the part of them on
                               the critical path) */
+  FP_PROF_NUMERIC,         /* numeric factorisation and solves (fp_factor, fp_solve) */
   FP_PROF_COUNT
 } fp_prof_kind;
 

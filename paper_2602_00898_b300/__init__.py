@@ -62,6 +62,10 @@ def lib() -> ctypes.CDLL:
             "fp_symbolic": (i32, [vp, vp, vp, P64, P64]),
             "fp_get_sizes": (i32, [vp, P32, P32, P64]),
             "fp_get_stage": (i32, [vp, i32, i32, vp, i64, P64]),
+            "fp_factor": (i32, [vp, vp, vp]),
+            "fp_solve": (i32, [vp, vp, vp]),
+            "fp_factor_export": (i32, [vp, vp, vp, vp, i64, P64]),
+            "fp_factor_stats": (i32, [vp, P64, P64, P64]),
             "fp_get_graph": (i32, [vp, vp, vp]),
             "fp_get_patches": (i32, [vp, vp, P32]),
             "fp_set_patches": (i32, [vp, vp, i32]),
@@ -168,6 +172,41 @@ def fp_get_stage(h, stage: str, index: int = 0):
     out = torch.empty(max(n.value, 1), dtype=torch.int32, device="cuda")
     _check(lib().fp_get_stage(h, code, int(index), out.data_ptr(), n.value, ctypes.byref(n)), h)
     return out[:n.value]
+
+
+def fp_factor(h, diag, offdiag):
+    """Numeric Cholesky of P A P^T (A: FP64 CUDA tensors, diag [n] by vertex,
+    offdiag [nnz] aligned with fp_get_graph's CSR)."""
+    _check(lib().fp_factor(h, _ptr(diag), _ptr(offdiag)), h)
+
+
+def fp_solve(h, b, x=None):
+    """x with A x = b (FP64 CUDA tensors by vertex); returns x."""
+    import torch
+    if x is None:
+        x = torch.empty_like(b)
+    _check(lib().fp_solve(h, _ptr(b), _ptr(x)), h)
+    return x
+
+
+def fp_factor_export(h):
+    """The factor as (colptr int64, rows int32, vals float64) CUDA tensors."""
+    import torch
+    nnz = ctypes.c_int64()
+    _check(lib().fp_factor_export(h, None, None, None, 0, ctypes.byref(nnz)), h)
+    n, _, _ = fp_get_sizes(h)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ri = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    rx = torch.empty(max(nnz.value, 1), dtype=torch.float64, device=dev)
+    _check(lib().fp_factor_export(h, _ptr(cp), _ptr(ri), _ptr(rx), nnz.value, ctypes.byref(nnz)), h)
+    return cp, ri[:nnz.value], rx[:nnz.value]
+
+
+def fp_factor_stats(h) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fp_factor_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
 
 
 def fp_get_graph(h, rowptr=None, col=None):

@@ -356,6 +356,7 @@ fp_status fp_permute(fp_handle* h, int32_t* d_perm, int32_t* d_iperm) {
   if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
   h->permuted = false;
   stage_clear(h);
+  numeric_release(h);
   if (h->user_k > 0) {
     // patches supplied by the caller (fp_set_patches)
     h->k = h->user_k;
@@ -611,8 +612,42 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
   return st;
 }
 
+fp_status fp_factor(fp_handle* h, const double* d_diag, const double* d_offdiag) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "fp_factor before fp_permute");
+  if (h->b != 1) return fail(h, FP_ERR_UNSUPPORTED, "fp_factor: dof_per_vertex > 1");
+  if (h->n > 0 && (!d_diag || (h->nnz > 0 && !d_offdiag))) return fail(h, FP_ERR_INVALID_ARG, "NULL values");
+  if (h->n == 0) return FP_OK;
+  return run_factor(h, d_diag, d_offdiag);
+}
+
+fp_status fp_solve(fp_handle* h, const double* d_b, double* d_x) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->numeric) return fail(h, FP_ERR_STATE, "fp_solve before fp_factor");
+  if (h->n > 0 && (!d_b || !d_x)) return fail(h, FP_ERR_INVALID_ARG, "NULL vector");
+  if (h->n == 0) return FP_OK;
+  return run_solve(h, d_b, d_x);
+}
+
+fp_status fp_factor_export(fp_handle* h, int64_t* d_colptr, int32_t* d_rows, double* d_vals, int64_t cap,
+                           int64_t* h_nnz) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->numeric) return fail(h, FP_ERR_STATE, "fp_factor_export before fp_factor");
+  return run_factor_export(h, d_colptr, d_rows, d_vals, cap, h_nnz);
+}
+
+fp_status fp_factor_stats(const fp_handle* h, int64_t* h_front_doubles, int64_t* h_flops, int64_t* h_nnz) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  numeric_stats(h, h_front_doubles, h_flops, h_nnz);
+  return FP_OK;
+}
+
 fp_status fp_destroy(fp_handle* h) {
   if (!h) return FP_OK;
+  numeric_release(h);
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   h->allocs.clear();
   // stream-ordered frees only: every copy into the status word was waited

@@ -31,7 +31,8 @@ enum : int32_t {
   ST_POOL_OVERFLOW = 1 << 3,   // a device bump pool ran out (host retries bigger)
   ST_NODE_TOO_BIG = 1 << 4,    // a tree node beyond the ordering kernel's limit
   ST_QUOTIENT_TOO_BIG = 1 << 5, // a patch with more cross edges than the sort capacity
-  ST_TIMEOUT = 1 << 6           // a bounded device wait ran out
+  ST_TIMEOUT = 1 << 6,          // a bounded device wait ran out
+  ST_NOT_SPD = 1 << 7           // a Cholesky pivot was not positive
 };
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output for generator state s
@@ -44,6 +45,7 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_state(uint64_t s) {
 }
 
 struct Workspace;   // per-handle device scratch (fp_api.cu)
+struct NumericFactor;   // numeric Cholesky factor of a handle (k_numeric.cu)
 
 // a10 priority network: packed parameter layout (codes or floats)
 // w1s[32][6] w1n[32][6] b1[32] w2s[32][32] w2n[32][32] b2[32] w3[32] c
@@ -103,6 +105,9 @@ struct fp_handle {
   int32_t* scores = nullptr;      // optional per-position score output of the learned pass
   int32_t learned_leaves = 0, learned_kept = 0;
   int64_t fill_plain = 0, fill_chosen = 0;
+
+  // numeric factor (fp_factor), released by fp_permute and fp_destroy
+  fp::NumericFactor* numeric = nullptr;
 
   // stage boundaries kept for fp_get_stage (opt.debug_dump)
   struct StageDump {
@@ -247,6 +252,13 @@ fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count,
                             int32_t* loc, const uint32_t* key, int32_t* perm_out);
 fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm, const int32_t* d_nodes,
                         int32_t count, int64_t* d_fill);
+// f4: numeric Cholesky of P A P^T over the tree (k_numeric.cu).
+fp_status run_factor(fp_handle* h, const double* d_diag, const double* d_off);
+fp_status run_solve(fp_handle* h, const double* d_b, double* d_x);
+fp_status run_factor_export(fp_handle* h, int64_t* d_colptr, int32_t* d_rows, double* d_vals, int64_t cap,
+                            int64_t* h_nnz);
+void numeric_stats(const fp_handle* h, int64_t* front_doubles, int64_t* flops, int64_t* nnz);
+void numeric_release(fp_handle* h);
 // a8: DOF expansion of perm/iperm/parent/colcount (b > 1).
 void launch_dof_expand_perm(fp_handle* h, const int32_t* perm, int32_t* perm_d, int32_t* iperm_d);
 void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32_t* colcount, int32_t* parent_d,
