@@ -104,9 +104,12 @@ fp_status fp_create_from_faces(const int32_t* d_faces, int64_t n_faces, int32_t 
  * pattern is the unknown-level pattern of n_rows = b*n unknowns and every
  * b x b block is merged into one vertex (Section 6.5): vertices u != v are
  * adjacent iff any entry of block (u, v) exists. The vertex graph must be
- * structurally symmetric. Errors as fp_create_from_faces, plus
- * FP_ERR_NOT_SYMMETRIC, and FP_ERR_INVALID_ARG if n_rows is not a multiple of
- * b or an index is out of range. Synchronises `stream` once.
+ * structurally symmetric. d_rowptr must start at 0 and not decrease (checked
+ * first: FP_ERR_INVALID_ARG), and d_col must hold d_rowptr[n_rows] entries (the
+ * caller's contract: a shorter buffer cannot be detected). Errors as
+ * fp_create_from_faces, plus FP_ERR_NOT_SYMMETRIC, and FP_ERR_INVALID_ARG if
+ * n_rows is not a multiple of b or an index is out of range. Synchronises
+ * `stream` twice.
  */
 fp_status fp_create_from_csr(const int32_t* d_rowptr, const int32_t* d_col, int32_t n_rows,
                              const fp_options* opts, void* stream, fp_handle** out);
@@ -307,7 +310,10 @@ fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, const fp_option
  * fp_last_error(NULL)). FP_ERR_INVALID_ARG for NULL pointers, negative sizes,
  * a corner out of range, or col_cap smaller than the number of entries.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the process; make that first call
+ * before any stream capture. The kept address does not survive a reset of the
+ * device's primary context (cudaDeviceReset): do not call this entry point
+ * after one.
  * Every call on a device shares the one scratch array: calls that may overlap
  * on the GPU (other streams, other host threads) race and must be serialised
  * by the caller. Synchronises `stream`.

@@ -32,7 +32,8 @@ enum : int32_t {
   ST_NODE_TOO_BIG = 1 << 4,    // a tree node beyond the ordering kernel's limit
   ST_QUOTIENT_TOO_BIG = 1 << 5, // a patch with more cross edges than the sort capacity
   ST_TIMEOUT = 1 << 6,          // a bounded device wait ran out
-  ST_NOT_SPD = 1 << 7           // a Cholesky pivot was not positive
+  ST_NOT_SPD = 1 << 7,          // a Cholesky pivot was not positive
+  ST_BAD_ROWPTR = 1 << 8        // a CSR row pointer array that is not a valid prefix
 };
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output for generator state s

@@ -324,8 +324,29 @@ fp_status build_graph_from_faces(fp_handle* h, const int32_t* d_faces, int64_t n
   return FP_OK;
 }
 
+// A caller's row pointers must start at 0 and never decrease (checked before
+// any kernel reads a column index through them).
+__global__ void k_check_rowptr(const int32_t* __restrict__ rowptr, int32_t nrows, int32_t* status) {
+  FP_PDL_WAIT();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nrows; i += gridDim.x * blockDim.x)
+    if ((i == 0 && rowptr[0] != 0) || rowptr[i] > rowptr[i + 1]) atomicOr(status, ST_BAD_ROWPTR);
+}
+
 fp_status build_graph_from_csr(fp_handle* h, const int32_t* d_rowptr, const int32_t* d_col, int32_t nrows) {
   const int32_t n = h->n, b = h->b;
+  if (nrows > 0) {
+    FP_LAUNCH(h, k_check_rowptr, grid_for(nrows, 256), 256, 0, d_rowptr, nrows, h->d_status);
+    FP_CHECK_LAUNCH(h, "row pointer check");
+    int32_t st0 = 0;
+    FP_TRY(sync_status(h, &st0));
+    if (st0 & ST_BAD_ROWPTR) return fail(h, FP_ERR_INVALID_ARG, "row pointers must start at 0 and not decrease");
+    if (!d_col) {
+      int32_t last = 0;
+      cudaError_t e0 = cudaMemcpy(&last, d_rowptr + nrows, sizeof(int32_t), cudaMemcpyDeviceToHost);
+      if (e0 != cudaSuccess) return check_cuda(h, e0, "row pointers");
+      if (last != 0) return fail(h, FP_ERR_INVALID_ARG, "NULL column array with entries");
+    }
+  }
   int32_t* cnt = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* off = (int32_t*)dev_alloc(h, sizeof(int32_t) * (n + 1));
   int32_t* tmp = (int32_t*)dev_alloc(h, sizeof(int32_t) * scan_tmp_ints(n + 1));

@@ -423,7 +423,6 @@ __global__ void k_scatter_perm(const double* __restrict__ y, const int32_t* __re
 // L[U_t, t] x_t joins the update vector.
 __global__ void __launch_bounds__(NT) k_solve_forward(SolveArgs a) {
   FP_PDL_WAIT();
-  __shared__ double s_x;
   const int32_t t = a.nodes[blockIdx.x];
   const int32_t b = a.node_begin[t], m = a.node_size[t], r = a.r[t];
   const int64_t f = (int64_t)m + r;
@@ -450,15 +449,31 @@ __global__ void __launch_bounds__(NT) k_solve_forward(SolveArgs a) {
     }
     __syncthreads();
   }
-  for (int32_t k = 0; k < m; ++k) {
-    if (threadIdx.x == 0) {
-      s_x = y[k] / F[k + k * f];
-      y[k] = s_x;
+  // blocks of 64 columns: warp 0 solves the diagonal block (lanes own rows
+  // k0 + lane and k0 + 32 + lane, the solved entry passed by shuffle), then
+  // every thread subtracts the block's contribution from one row below it
+  const int32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t k0 = 0; k0 < m; k0 += 64) {
+    const int32_t nb = min(64, m - k0);
+    if (warp == 0) {
+      double y0 = lane < nb ? y[k0 + lane] : 0.0, y1 = 32 + lane < nb ? y[k0 + 32 + lane] : 0.0;
+      for (int32_t k = 0; k < nb; ++k) {
+        const double* colk = F + (int64_t)(k0 + k) * f + k0;
+        const double yk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
+        const double xk = yk / colk[k];
+        if (lane == (k & 31)) { if (k < 32) y0 = xk; else y1 = xk; }
+        if (lane > k && lane < nb) y0 -= colk[lane] * xk;
+        if (32 + lane > k && 32 + lane < nb) y1 -= colk[32 + lane] * xk;
+      }
+      if (lane < nb) y[k0 + lane] = y0;
+      if (32 + lane < nb) y[k0 + 32 + lane] = y1;
     }
     __syncthreads();
-    const double xk = s_x;
-    const double* colk = F + k * f;
-    for (int32_t i = k + 1 + threadIdx.x; i < m; i += NT) y[i] -= colk[i] * xk;
+    for (int32_t i = k0 + nb + threadIdx.x; i < m; i += NT) {
+      double s = 0.0;
+      for (int32_t k = 0; k < nb; ++k) s += F[i + (int64_t)(k0 + k) * f] * y[k0 + k];
+      y[i] -= s;
+    }
     __syncthreads();
   }
   for (int32_t i = threadIdx.x; i < r; i += NT) {
@@ -473,7 +488,6 @@ __global__ void __launch_bounds__(NT) k_solve_forward(SolveArgs a) {
 // transposed diagonal block.
 __global__ void __launch_bounds__(NT) k_solve_backward(SolveArgs a) {
   FP_PDL_WAIT();
-  __shared__ double s_x;
   const int32_t t = a.nodes[blockIdx.x];
   const int32_t b = a.node_begin[t], m = a.node_size[t], r = a.r[t];
   const int64_t f = (int64_t)m + r;
@@ -487,14 +501,32 @@ __global__ void __launch_bounds__(NT) k_solve_backward(SolveArgs a) {
     y[k] -= s;
   }
   __syncthreads();
-  for (int32_t k = m - 1; k >= 0; --k) {
-    if (threadIdx.x == 0) {
-      s_x = y[k] / F[k + k * f];
-      y[k] = s_x;
+  // blocks of 64 columns from the last: warp 0 solves the transposed
+  // diagonal block, then every thread subtracts the block's contribution
+  // from one entry above it
+  const int32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t k1 = m; k1 > 0; k1 -= 64) {
+    const int32_t k0 = k1 > 64 ? k1 - 64 : 0, nb = k1 - k0;
+    if (warp == 0) {
+      double y0 = lane < nb ? y[k0 + lane] : 0.0, y1 = 32 + lane < nb ? y[k0 + 32 + lane] : 0.0;
+      for (int32_t k = nb - 1; k >= 0; --k) {
+        // row k of the block: L[k0 + k][k0 + i] = F[(k0 + k) + (k0 + i) f]
+        const double yk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
+        const double xk = yk / F[(k0 + k) + (int64_t)(k0 + k) * f];
+        if (lane == (k & 31)) { if (k < 32) y0 = xk; else y1 = xk; }
+        if (lane < k) y0 -= F[(k0 + k) + (int64_t)(k0 + lane) * f] * xk;
+        if (32 + lane < k) y1 -= F[(k0 + k) + (int64_t)(k0 + 32 + lane) * f] * xk;
+      }
+      if (lane < nb) y[k0 + lane] = y0;
+      if (32 + lane < nb) y[k0 + 32 + lane] = y1;
     }
     __syncthreads();
-    const double xk = s_x;
-    for (int32_t i = threadIdx.x; i < k; i += NT) y[i] -= F[k + i * f] * xk;
+    for (int32_t i = threadIdx.x; i < k0; i += NT) {
+      const double* coli = F + (int64_t)i * f + k0;
+      double s = 0.0;
+      for (int32_t k = 0; k < nb; ++k) s += coli[k] * y[k0 + k];
+      y[i] -= s;
+    }
     __syncthreads();
   }
 }

@@ -5,6 +5,8 @@ nested-dissection tree (node of every vertex, node begin/size), the
 permutation and its inverse, the elimination tree and the column counts must
 be bit-exact, at small sizes spanning many patches and tree levels and at the
 full benchmark sizes."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -356,3 +358,21 @@ def test_supplied_patches_errors_and_reuse():
         assert np.array_equal(np_(perm), O.order_given(g, lab, 3).perm)
     finally:
         fp.fp_destroy(h)
+
+
+def test_csr_bad_row_pointers_rejected():
+    """Row pointers that do not start at 0 or that decrease are rejected
+    before any column is read through them."""
+    L = fp.lib()
+    o = fp.fp_default_options()
+    col = torch.tensor([1, 0, 2, 1], dtype=torch.int32, device="cuda")
+    h = ctypes.c_void_p()
+    for bad in ([0, 1, 3, 2], [1, 1, 3, 4], [0, 3, 1, 4]):
+        rp = torch.tensor(bad, dtype=torch.int32, device="cuda")
+        st = L.fp_create_from_csr(rp.data_ptr(), col.data_ptr(), 3, ctypes.byref(o), None, ctypes.byref(h))
+        assert st == 1 and not h.value, bad
+        assert "row pointers" in fp.fp_last_error(None)
+    rp = torch.tensor([0, 1, 3, 4], dtype=torch.int32, device="cuda")
+    assert L.fp_create_from_csr(rp.data_ptr(), None, 3, ctypes.byref(o), None, ctypes.byref(h)) == 1
+    assert L.fp_create_from_csr(rp.data_ptr(), col.data_ptr(), 3, ctypes.byref(o), None, ctypes.byref(h)) == 0
+    fp.fp_destroy(h)

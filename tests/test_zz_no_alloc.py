@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import meshgen as M
+import oracle as O
 import paper_2602_00898_b300 as fp
 
 pytestmark = pytest.mark.gpu
@@ -55,12 +56,15 @@ def _static_csr(faces, n, cap):
 def test_static_matches_allocating_path_twice(mesh):
     faces = torch.from_numpy(mesh.faces).cuda()
     rp_ref, col_ref = _reference_csr(faces, mesh.n)
+    g = O.graph_from_faces(mesh.faces, mesh.n)          # the definition, on the CPU
+    np.testing.assert_array_equal(rp_ref, g.rowptr)
+    np.testing.assert_array_equal(col_ref, g.col)
     for call in range(2):     # the second call sees the first call's leftovers in the scratch array
         st, rp, col, nnz = _static_csr(faces, mesh.n, col_ref.size + 5)
         assert st == 0, fp.fp_last_error(None)
         assert nnz == col_ref.size
-        np.testing.assert_array_equal(rp, rp_ref)
-        np.testing.assert_array_equal(col, col_ref)
+        np.testing.assert_array_equal(rp, g.rowptr)
+        np.testing.assert_array_equal(col, g.col)
 
 
 def test_static_alternating_sizes():
@@ -98,3 +102,25 @@ def test_static_limits_and_errors():
     assert st == 0
     np.testing.assert_array_equal(rp2, rp_ref)
     np.testing.assert_array_equal(col2, col_ref)
+
+
+def test_static_row_limit_and_no_faces():
+    """A vertex with more than 256 face-edge entries (a fan of 130 triangles
+    around vertex 0) is rejected with a message naming the limit, and the next
+    valid call still matches; a mesh without faces gives empty rows."""
+    fan = np.array([[0, i, i + 1] for i in range(1, 131)], np.int32)
+    faces = torch.from_numpy(fan).cuda()
+    st, _, _, _ = _static_csr(faces, 132, 1024)
+    assert st == 7
+    assert "256" in fp.fp_last_error(None)
+    mesh = M.shuffle(M.grid(30, 20), 4)
+    fc = torch.from_numpy(mesh.faces).cuda()
+    g = O.graph_from_faces(mesh.faces, mesh.n)
+    st, rp, col, nnz = _static_csr(fc, mesh.n, g.col.size)
+    assert st == 0 and nnz == g.col.size
+    np.testing.assert_array_equal(rp, g.rowptr)
+    np.testing.assert_array_equal(col, g.col)
+    empty = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    st, rp, col, nnz = _static_csr(empty, 10, 0)
+    assert st == 0 and nnz == 0
+    np.testing.assert_array_equal(rp, np.zeros(11, np.int32))
