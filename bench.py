@@ -680,6 +680,7 @@ def run_factor(args):
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks.begin()
+    l0 = fp.fp_launch_count(h)
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()
@@ -690,6 +691,7 @@ def run_factor(args):
         ev[i][2].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
+    launches = fp.fp_launch_count(h) - l0
     clocks.end()
     fp.fp_factor(h, diag, off)
     torch.cuda.synchronize()
@@ -738,7 +740,7 @@ def run_factor(args):
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": None, "peak_source": "nominal FP64 rate of the part (no measured FP64 peak)"},
         "clocks": clk,
-        "gpu_launches": None,
+        "gpu_launches": int(launches),
     }
     if not args.no_cpu_baseline:
         import oracle as O
