@@ -594,13 +594,24 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
   fp_handle* h = nullptr;
   fp_status st = fp_create_from_faces(d_faces, n_faces, n_vertices, opts, stream, &h);
   if (st == FP_OK) st = fp_permute(h, d_out, d_out + N);
+  // perm and iperm are final here: their copies to the host run on an
+  // auxiliary stream while the symbolic factorisation runs on `stream`
+  AuxStream* ax = st == FP_OK && N > 0 ? aux_stream(dev, 1) : nullptr;
+  int32_t* hs[4] = {h_perm, h_iperm, h_parent, h_colcount};
+  if (ax) {
+    cudaEventRecord(ax->fork, s);
+    cudaStreamWaitEvent(ax->s, ax->fork, 0);
+    for (int i = 0; i < 2; ++i)
+      if (hs[i]) cudaMemcpyAsync(hs[i], d_out + i * N, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ax->s);
+    cudaEventRecord(ax->join, ax->s);
+  }
   int64_t nnz = 0, fl = 0;
   if (st == FP_OK) st = fp_symbolic(h, d_out + 2 * N, d_out + 3 * N, &nnz, &fl);
   if (st == FP_OK && N > 0) {
-    int32_t* hs[4] = {h_perm, h_iperm, h_parent, h_colcount};
-    for (int i = 0; i < 4; ++i)
+    for (int i = 2; i < 4; ++i)
       if (hs[i]) cudaMemcpyAsync(hs[i], d_out + i * N, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s);
   }
+  if (ax) cudaStreamWaitEvent(s, ax->join, 0);     // d_out is freed on `stream` below
   if (st != FP_OK && h) g_create_err = h->err;
   fp_destroy(h);
   cudaFreeAsync(d_faces, s);

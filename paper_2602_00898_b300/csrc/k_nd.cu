@@ -274,7 +274,7 @@ __device__ int block_bfs(const BisectView& v, int32_t src, int32_t* scnt) {
   return level;
 }
 
-__global__ void __launch_bounds__(ND_THREADS) k_nd_bisect(BisectArgs a) {
+__global__ void __launch_bounds__(1024) k_nd_bisect(BisectArgs a) {
   FP_PDL_WAIT();
   extern __shared__ __align__(16) int32_t bsm[];
   __shared__ int64_t red64[40];
@@ -1063,8 +1063,12 @@ fp_status run_nested_dissection(fp_handle* h) {
                   lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4),
                   w, Dsplit - d - 1};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
+    // the top levels have a few large nodes, one CTA each: 1024 threads make
+    // their gathers of the quotient rows (dependent L2 loads, one round per
+    // blockDim patches) four times shorter
+    const int bt = T <= 16 ? 1024 : ND_THREADS;
     allow_max_dynamic_smem(k_nd_bisect);
-    FP_LAUNCH(h, k_nd_bisect, GB, ND_THREADS, bsmem, ba);
+    FP_LAUNCH(h, k_nd_bisect, GB, bt, bsmem, ba);
     ps_b.end();
     if (int32_t* sb = stage_buffer(h, FP_STAGE_SIDE, d, k))
       FP_LAUNCH(h, k_stage_sides, GK, 256, 0, patch_node, side, split, t0, T, k, sb);

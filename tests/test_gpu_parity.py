@@ -224,6 +224,27 @@ def test_host_buffer_entry_point():
     assert (nnz, fl) == (s.nnzL, s.flops)
 
 
+def test_host_buffer_entry_point_dof3():
+    """The host-buffer form with 3 DOF per vertex (the end-to-end benchmark's
+    call): perm and iperm come back while the symbolic factorisation runs."""
+    mesh = M.shuffle(M.torus(120, 90, 0.3, 8), 8)
+    g, o, s = oracle_all(mesh, 512, 0)
+    n, N = mesh.n, 3 * mesh.n
+    pd, ad, cd = O.dof_expand(3, o.perm, s.parent, s.colcount)
+    ipd = np.empty_like(pd)
+    ipd[pd] = np.arange(N, dtype=np.int32)
+    faces = torch.from_numpy(mesh.faces).pin_memory()
+    for _ in range(2):
+        outs = [torch.full((N,), -1, dtype=torch.int32).pin_memory() for _ in range(4)]
+        nnz, fl = fp.fp_order_faces_host(faces, n, fp.fp_default_options(patch_cap=512, dof_per_vertex=3), None,
+                                         *outs)
+        np.testing.assert_array_equal(outs[0].numpy(), pd)
+        np.testing.assert_array_equal(outs[1].numpy(), ipd)
+        np.testing.assert_array_equal(outs[2].numpy(), ad)
+        np.testing.assert_array_equal(outs[3].numpy(), cd)
+        assert nnz == 9 * s.nnzL - 3 * n
+
+
 def _sym_rows(n, edges):
     adj = [set() for _ in range(n)]
     for u, v in edges:
