@@ -21,6 +21,7 @@ does not shard); value counts the vertices of all ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -266,6 +267,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def warm_event(stream, flush=None):
+    """Runs, once and untimed, the work the timed loop adds around the steps:
+    the L2 flush (PyTorch's fill kernel: the first launch of a PyTorch kernel
+    in a process loads its module, a one-time host stall of ~0.3 s measured
+    between two steps of a first timed block) and a timing event record."""
+    import torch
+    if flush is not None:
+        flush.zero_()
+    e = torch.cuda.Event(enable_timing=True)
+    e.record(stream)
+    e.synchronize()
+
+
 def leaf_vertex_count(node_size) -> int:
     """Vertices of the tree's leaves (nodes with vertices and no non-empty
     descendant), given the node sizes of the binary tree in array form."""
@@ -362,9 +376,16 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
     t_inside = 0.0
+    host_steps = []
+    # one-time costs of the loop's own work (the flush's first launch) and
+    # Python's collector are kept out of the region
+    warm_event(stream, flush)
+    gc.collect()
+    gc.disable()
     clocks.begin()
     t_wall = time.perf_counter()
     for i in range(args.steps):
+        t0 = time.perf_counter()
         flush.zero_()
         ev[i][0].record(stream)
         t = time.perf_counter()
@@ -372,10 +393,12 @@ def run_ours(args):
         t_inside += time.perf_counter() - t
         ev[i][1].record(stream)
         launches += L
+        host_steps.append(time.perf_counter() - t0)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     wall = time.perf_counter() - t_wall
+    gc.enable()
     clocks.end()
     for _ in range(3):          # the busy window goes on briefly after the region
         step()
@@ -478,6 +501,8 @@ def run_ours(args):
         "permute_ms": statistics.median(pms),
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "host_ms_per_step_inside_events": 1e3 * t_inside / args.steps,
+        "host_ms_per_step_median": 1e3 * statistics.median(host_steps),
+        "host_ms_per_step_max": 1e3 * max(host_steps),
         "critical_path_ms": cp,
         "stage_profile": f"{nprof} extra steps with per-stage CUDA events (kept out of the timed steps)",
         "nnzL": nnz, "nnzA": nnzA, "fill_ratio": nnz / nnzA, "flops": fl,
@@ -550,6 +575,7 @@ def run_batch(args):
     if ws > 1:
         torch.distributed.barrier()
     times, launches = [], 0
+    warm_event(torch.cuda.current_stream(), flush)
     clocks.begin()
     for _ in range(args.steps):
         flush.zero_()
@@ -679,6 +705,7 @@ def run_factor(args):
         fp.fp_factor(h, diag, off)
     torch.cuda.synchronize()
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    warm_event(stream, flush)
     clocks.begin()
     l0 = fp.fp_launch_count(h)
     t_wall = time.perf_counter()
