@@ -238,16 +238,31 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
  * Batched ordering of many independent meshes (a library service; the paper
  * orders one mesh at a time). Each item is one mesh: device faces in, device
  * outputs (caller-owned, each may be NULL, DOF-expanded when
- * opts->dof_per_vertex > 1) and host results out. The meshes are spread over
- * `n_workers` host threads (1..64; 0 = 8), each with its own CUDA stream on
- * the current device, which run create + permute + symbolic + destroy for one
- * mesh after another; the per-mesh pipelines are latency bound, so running
- * many at once fills the GPU. Items are taken in order of decreasing size.
- * Synchronous: returns when every item is done. Returns FP_OK if every item
- * succeeded, else the first failing item's status (each item's own status is
- * in item->status). A patch_cap of 0 in an item selects the autotuned cap of
- * its size class (see fp_batch_autotune); item->chosen_cap reports the cap
- * used, so that a result can be reproduced with the single-mesh calls.
+ * opts->dof_per_vertex > 1) and host results out. Every item's results equal
+ * those of the single-mesh calls (create + permute + symbolic) on that mesh
+ * with its chosen_cap.
+ *
+ * n_workers = 0 (fused): the batch is ordered as ONE graph, the disjoint union
+ * of its meshes, by one pipeline whose every launch covers all meshes (each
+ * mesh's dissection tree hangs below an empty super-tree; its cap, seed
+ * threshold and tie hashes stay its own). Taken when opts has
+ * dof_per_vertex 1, nd_level 0 and debug_dump 0 and the totals fit int32
+ * (sum of n_vertices, 6 x sum of n_faces); otherwise, and when the fused
+ * pipeline fails (an input error, out of memory), the items are ordered one
+ * by one as below, so that each item gets its own status. The fused form
+ * counts the batch's kernel launches on the first item (0 on the others).
+ * n_workers = 1..64 (pool): the meshes are spread over that many host
+ * threads, each with its own CUDA stream on the current device, which run
+ * create + permute + symbolic + destroy for one mesh after another, largest
+ * first (each item counts its own launches).
+ *
+ * The device faces must be complete before the call (it runs on streams of
+ * its own). Synchronous: returns when every item is done. Returns FP_OK if
+ * every item succeeded, else the first failing item's status (each item's own
+ * status is in item->status). A patch_cap of 0 in an item selects the
+ * autotuned cap of its size class (see fp_batch_autotune); item->chosen_cap
+ * reports the cap used, so that a result can be reproduced with the
+ * single-mesh calls.
  */
 typedef struct {
   const int32_t* d_faces;   /* int32 [n_faces][3] on the device */
@@ -262,7 +277,7 @@ typedef struct {
   int64_t flops;            /* out */
   int32_t chosen_cap;       /* out */
   int32_t status;           /* out: fp_status of this item */
-  int64_t launches;         /* out: kernel launches issued for this item */
+  int64_t launches;         /* out: kernel launches issued for this item (fused: the batch's, on item 0) */
   int32_t learned_leaves;   /* out (fp_batch_order_learned): leaves considered */
   int32_t learned_kept;     /* out: leaves whose learned order was kept */
   int64_t fill_plain;       /* out: summed leaf fills under plain minimum degree */
@@ -276,8 +291,9 @@ fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* 
  * (FP_GNN_NPARAMS codes, see fp_set_priority_net) attached before its
  * fp_permute, so each leaf keeps the lower-fill of its learned and plain
  * orders; the per-item learned_* and fill_* fields report the choices.
- * h_codes NULL is fp_batch_order. Errors as fp_batch_order, plus
- * FP_ERR_INVALID_ARG for a code out of range.
+ * Always the pool form (n_workers 0 = 8 workers). h_codes NULL is the pool
+ * form of fp_batch_order. Errors as fp_batch_order, plus FP_ERR_INVALID_ARG
+ * for a code out of range.
  */
 fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers,
                                  const int32_t* h_codes);

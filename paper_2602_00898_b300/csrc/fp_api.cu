@@ -665,6 +665,7 @@ fp_status fp_destroy(fp_handle* h) {
   // for when it was made, and the auxiliary streams' work was joined into
   // the handle's stream before the call that launched it returned
   if (h->h_status) status_word_give(h->h_status);
+  delete h->seg;
   delete h;
   return FP_OK;
 }

@@ -194,4 +194,9 @@ __device__ __forceinline__ uint32_t tie_hash(int32_t v) {
   return (uint32_t)(splitmix64_state((uint64_t)(uint32_t)v) >> 32);
 }
 
+// A union vertex's number inside its own mesh (fused batch), or v itself.
+__device__ __forceinline__ int32_t seg_local(const SegView& s, int32_t v) {
+  return s.vmesh ? v - s.voff[s.vmesh[v]] : v;
+}
+
 }  // namespace fp

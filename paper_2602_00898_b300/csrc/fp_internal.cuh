@@ -46,6 +46,33 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_state(uint64_t s) {
 }
 
 struct Workspace;   // per-handle device scratch (fp_api.cu)
+
+// A batch of meshes ordered as one graph, their disjoint union (the fused
+// batch ordering, k_batch.cu). Mesh m owns the union's vertices
+// [voff[m], voff[m+1]); no edge, patch or tree node joins two meshes. The few
+// kernels whose result depends on a mesh's own size, cap or vertex numbering
+// (the seed threshold, the cap splits, the separator tie hash) read them here;
+// a single-mesh handle passes the empty view (vmesh == nullptr).
+struct SegView {
+  const int32_t* vmesh = nullptr;   // [n] mesh of every union vertex
+  const int32_t* voff = nullptr;    // [M+1] first union vertex of every mesh
+  const int32_t* mcap = nullptr;    // [M] patch cap of every mesh
+};
+// Host side of the union (owned by the handle). Every mesh's dissection tree
+// hangs below an empty super-tree at depth D - h_m, h_m = ceil(log2 k_m), so
+// that all leaves lie at depth D (a canonical prefix code of the meshes,
+// largest subtree first): every node at depth d then has the cut bound
+// 2^(D-d-1) of a single mesh dissected to depth D.
+struct Segments {
+  int32_t M = 0;
+  SegView v;                         // device arrays
+  int32_t* mroot = nullptr;          // [M] device: root node of every mesh's subtree
+  std::vector<int32_t> h_voff;       // [M+1]
+  std::vector<int32_t> h_root;       // [M] root node (-1: an empty mesh)
+  std::vector<int32_t> h_k;          // [M] patches of every mesh
+  std::vector<int32_t> h_posoff;     // [M] first position of every mesh in the union's order
+  int32_t dmin = 0;                  // shallowest root depth
+};
 struct NumericFactor;   // numeric Cholesky factor of a handle (k_numeric.cu)
 
 // a10 priority network: packed parameter layout (codes or floats)
@@ -109,6 +136,9 @@ struct fp_handle {
 
   // numeric factor (fp_factor), released by fp_permute and fp_destroy
   fp::NumericFactor* numeric = nullptr;
+
+  // the disjoint union of a fused batch (null for one mesh)
+  fp::Segments* seg = nullptr;
 
   // stage boundaries kept for fp_get_stage (opt.debug_dump)
   struct StageDump {

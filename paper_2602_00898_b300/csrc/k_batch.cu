@@ -3,11 +3,17 @@
 //
 // One mesh's pipeline is a chain of latency-bound launches separated by a few
 // host read-backs of data-dependent sizes (patch count, tree depth, node
-// sizes), so it occupies a small part of the GPU. Independent meshes are
-// therefore run concurrently: a pool of host workers, each with its own CUDA
-// stream on the caller's device, drains a shared queue of meshes (largest
-// first, so that the longest pipelines start early), and the GPU interleaves
-// the kernels of all streams.
+// sizes), so it occupies a small part of the GPU, and a host pool running
+// many meshes' pipelines at once is bound by the launch rate of one CUDA
+// context (about 143 launches a mesh). The fused form orders the whole batch
+// as one graph instead, the disjoint union of its meshes: every stage is one
+// pipeline over all meshes (the same launches as one mesh, each covering
+// every mesh's vertices, patches and tree nodes), and the union's tree puts
+// every mesh's dissection tree below an empty super-tree (Segments). A mesh's
+// patches, separators, orders and symbolic counts depend only on its own
+// vertices, with its own cap, seed threshold and vertex numbering, so each
+// result equals the mesh ordered alone. The pool remains for the learned form
+// and on request (n_workers > 0).
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -63,12 +69,230 @@ fp_status run_one(const fp_batch_item& it, fp_options o, cudaStream_t s, int32_t
   return st;
 }
 
+// ---- fused batch: one pipeline over the disjoint union ----------------------------
+
+struct FaceSeg {
+  const int32_t* faces;
+  int64_t foff;      // first union face
+  int32_t voff;      // first union vertex
+  int32_t n;         // vertices of the mesh
+};
+
+struct OutSeg {
+  int32_t* perm;
+  int32_t* iperm;
+  int32_t* parent;
+  int32_t* colcount;
+};
+
+// Union faces: every mesh's corners shifted by its first vertex. A corner out
+// of its own mesh's range becomes -1, which the CSR build reports as a bad
+// index (it would otherwise join two meshes).
+__global__ void k_union_faces(const FaceSeg* __restrict__ seg, int32_t M, int64_t F, int32_t* __restrict__ out) {
+  FP_PDL_WAIT();
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = M - 1;        // the last mesh whose first face is <= f
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (seg[mid].foff <= f) lo = mid; else hi = mid - 1;
+    }
+    const FaceSeg s = seg[lo];
+    const int32_t* src = s.faces + 3 * (f - s.foff);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int32_t x = src[c];
+      out[3 * f + c] = (x >= 0 && x < s.n) ? x + s.voff : -1;
+    }
+  }
+}
+
+__global__ void k_vertex_mesh(const int32_t* __restrict__ voff, int32_t M, int32_t n, int32_t* __restrict__ vmesh) {
+  FP_PDL_WAIT();
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int32_t lo = 0, hi = M - 1;        // the last mesh whose first vertex is <= v
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (voff[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    vmesh[v] = lo;
+  }
+}
+
+// Per-mesh outputs from the union's: position p holds union vertex v of mesh
+// m; both are renumbered inside the mesh (its positions start at posoff[m],
+// its vertices at voff[m]); the elimination tree never leaves a mesh. nnz(L)
+// and flops per mesh are the sums of colcount and colcount^2 over its
+// positions (a warp's positions usually lie in one mesh: one atomic a warp).
+__global__ void k_batch_out(const int32_t* __restrict__ perm, const int32_t* __restrict__ parent,
+                            const int32_t* __restrict__ colcount, int32_t n, const int32_t* __restrict__ vmesh,
+                            const int32_t* __restrict__ voff, const int32_t* __restrict__ posoff,
+                            const OutSeg* __restrict__ outs, unsigned long long* __restrict__ sums) {
+  FP_PDL_WAIT();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t p = base + threadIdx.x;
+    const bool live = p < n;
+    int32_t m = -1;
+    unsigned long long c = 0, c2 = 0;
+    if (live) {
+      const int32_t v = perm[p];
+      m = vmesh[v];
+      const int32_t lp = (int32_t)p - posoff[m], lv = v - voff[m];
+      const OutSeg o = outs[m];
+      const int32_t cc = colcount[p];
+      if (o.perm) o.perm[lp] = lv;
+      if (o.iperm) o.iperm[lv] = lp;
+      if (o.parent) {
+        const int32_t q = parent[p];
+        o.parent[lp] = q < 0 ? -1 : q - posoff[m];
+      }
+      if (o.colcount) o.colcount[lp] = cc;
+      c = (unsigned long long)cc;
+      c2 = c * c;
+    }
+    const int32_t m0 = __shfl_sync(0xffffffffu, m, 0);
+    if (__all_sync(0xffffffffu, !live || m == m0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        c2 += __shfl_down_sync(0xffffffffu, c2, o);
+      }
+      if ((threadIdx.x & 31) == 0 && m0 >= 0) {
+        atomicAdd(&sums[2 * m0], c);
+        atomicAdd(&sums[2 * m0 + 1], c2);
+      }
+    } else if (live) {
+      atomicAdd(&sums[2 * m], c);
+      atomicAdd(&sums[2 * m + 1], c2);
+    }
+  }
+}
+
+// Whether the fused form takes the batch (else the pool): one DOF per vertex,
+// no explicit depth, totals within int32.
+bool fused_ok(const fp_batch_item* items, int32_t count, const fp_options& o) {
+  if (o.dof_per_vertex != 1 || o.nd_level != 0 || o.debug_dump != 0) return false;
+  int64_t N = 0, F = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    const fp_batch_item& it = items[i];
+    if (it.n_vertices < 0 || it.n_faces < 0 || (it.n_faces > 0 && !it.d_faces)) return false;
+    N += it.n_vertices;
+    F += it.n_faces;
+  }
+  return N <= INT32_MAX && F <= INT32_MAX / 6;
+}
+
+fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s) {
+  int device = 0;
+  cudaGetDevice(&device);
+  std::vector<int32_t> voff(M + 1, 0), caps(M);
+  std::vector<FaceSeg> fs(M);
+  int64_t F = 0;
+  for (int32_t m = 0; m < M; ++m) {
+    caps[m] = cap_for(items[m], base);
+    fs[m] = {items[m].d_faces, F, voff[m], items[m].n_vertices};
+    F += items[m].n_faces;
+    voff[m + 1] = voff[m] + items[m].n_vertices;
+  }
+  const int32_t N = voff[M];
+  cudaMemPool_t pool = library_pool(device);
+  int32_t* d_faces = nullptr;
+  FaceSeg* d_fs = nullptr;
+  if (cudaMallocFromPoolAsync((void**)&d_faces, sizeof(int32_t) * 3 * (size_t)(F > 0 ? F : 1), pool, s) != cudaSuccess ||
+      cudaMallocFromPoolAsync((void**)&d_fs, sizeof(FaceSeg) * (size_t)M, pool, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (d_faces) cudaFreeAsync(d_faces, s);
+    return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "batch union faces");
+  }
+  // pageable source: the call returns once the table is staged
+  cudaMemcpyAsync(d_fs, fs.data(), sizeof(FaceSeg) * (size_t)M, cudaMemcpyHostToDevice, s);
+  int64_t launches = 0;
+  if (F > 0) {
+    launch_pdl(s, k_union_faces, grid_for(F, 256), 256, 0, (const FaceSeg*)d_fs, M, F, d_faces);
+    ++launches;
+  }
+  fp_options o = base;
+  o.patch_cap = caps[0];
+  fp_handle* h = nullptr;
+  fp_status st = fp_create_from_faces(d_faces, F, N, &o, s, &h);
+  cudaFreeAsync(d_faces, s);
+  cudaFreeAsync(d_fs, s);
+  if (st != FP_OK) return st;
+  Segments* sg = new Segments();
+  h->seg = sg;
+  sg->M = M;
+  sg->h_voff = voff;
+  int32_t* d_voff = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(M + 1));
+  int32_t* d_cap = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
+  int32_t* d_vmesh = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  sg->mroot = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
+  int32_t* parent = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  int32_t* colcount = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  if (!d_voff || !d_cap || !d_vmesh || !sg->mroot || !parent || !colcount) {
+    fp_destroy(h);
+    return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "batch union arrays");
+  }
+  cudaMemcpyAsync(d_voff, voff.data(), sizeof(int32_t) * (size_t)(M + 1), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_cap, caps.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, s);
+  if (N > 0) FP_LAUNCH(h, k_vertex_mesh, grid_for(N, 256), 256, 0, (const int32_t*)d_voff, M, N, d_vmesh);
+  sg->v = SegView{d_vmesh, d_voff, d_cap};
+  int64_t nnz = 0, fl = 0;
+  st = fp_permute(h, nullptr, nullptr);
+  if (st == FP_OK) st = fp_symbolic(h, parent, colcount, &nnz, &fl);
+  if (st == FP_OK) {
+    std::vector<OutSeg> outs(M);
+    for (int32_t m = 0; m < M; ++m) outs[m] = {items[m].d_perm, items[m].d_iperm, items[m].d_parent, items[m].d_colcount};
+    OutSeg* d_outs = (OutSeg*)dev_alloc(h, sizeof(OutSeg) * (size_t)M);
+    int32_t* d_pos = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
+    unsigned long long* d_sums = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 2 * (size_t)M);
+    std::vector<unsigned long long> sums(2 * (size_t)M, 0ull);
+    if (!d_outs || !d_pos || !d_sums) {
+      st = fail(h, FP_ERR_OUT_OF_MEMORY, "batch outputs");
+    } else {
+      cudaMemcpyAsync(d_outs, outs.data(), sizeof(OutSeg) * (size_t)M, cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(d_pos, sg->h_posoff.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, s);
+      cudaMemsetAsync(d_sums, 0, sizeof(unsigned long long) * 2 * (size_t)M, s);
+      if (N > 0)
+        FP_LAUNCH(h, k_batch_out, grid_for(N, 256), 256, 0, (const int32_t*)h->perm, (const int32_t*)parent,
+                  (const int32_t*)colcount, N, (const int32_t*)d_vmesh, (const int32_t*)d_voff,
+                  (const int32_t*)d_pos, (const OutSeg*)d_outs, d_sums);
+      cudaMemcpyAsync(sums.data(), d_sums, sizeof(unsigned long long) * 2 * (size_t)M, cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = check_cuda(h, e, "batch outputs");
+    }
+    if (st == FP_OK)
+      for (int32_t m = 0; m < M; ++m) {
+        fp_batch_item& it = items[m];
+        it.status = FP_OK;
+        it.chosen_cap = caps[m];
+        it.nnzL = (int64_t)sums[2 * m];
+        it.flops = (int64_t)sums[2 * m + 1];
+        it.launches = 0;
+        it.learned_leaves = it.learned_kept = 0;
+        it.fill_plain = it.fill_chosen = 0;
+      }
+    if (st == FP_OK) items[0].launches = launches + fp_launch_count(h);
+  }
+  fp_destroy(h);
+  return st;
+}
+
 }  // namespace
 }  // namespace fp
 
 using namespace fp;
 
 extern "C" fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers) {
+  if (count > 0 && items && opts && n_workers == 0 && fused_ok(items, count, *opts)) {
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return fail(nullptr, FP_ERR_CUDA, cudaGetErrorString(e));
+    cudaStream_t s = worker_stream(device);
+    if (!s) return fail(nullptr, FP_ERR_CUDA, "batch stream");
+    const fp_status st = run_fused(items, count, *opts, s);
+    if (st == FP_OK) return FP_OK;
+    // a failure: every item's own status comes from ordering it alone
+  }
   return fp_batch_order_learned(items, count, opts, n_workers, nullptr);
 }
 

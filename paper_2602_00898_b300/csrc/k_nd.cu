@@ -40,20 +40,24 @@ constexpr int EARLY_CTAS = (1 << EARLY_LEVELS) - 1;  // at most that many early 
 constexpr int8_t VS_NONE = 0, VS_UND = 1, VS_IN = 2, VS_OUT = 3;
 
 // ---- generic counting sort helpers ----------------------------------------------------
-__global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t* __restrict__ cnt) {
+// Keys outside [koff, koff + nk) are skipped (-1, or a tree node at another
+// depth: in a fused batch the meshes' subtrees start at different depths).
+__global__ void k_count_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t nk,
+                           int32_t* __restrict__ cnt) {
   FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int32_t c = key[i];
-    if (c >= 0) atomicAdd(&cnt[c - koff], 1);
+    const uint32_t c = (uint32_t)(key[i] - koff);
+    if (c < (uint32_t)nk) atomicAdd(&cnt[c], 1);
   }
 }
 
-__global__ void k_scatter_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, const int32_t* __restrict__ start,
-                             int32_t* __restrict__ fill, int32_t* __restrict__ list) {
+__global__ void k_scatter_by(const int32_t* __restrict__ key, int32_t n, int32_t koff, int32_t nk,
+                             const int32_t* __restrict__ start, int32_t* __restrict__ fill,
+                             int32_t* __restrict__ list) {
   FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int32_t c = key[i];
-    if (c >= 0) list[start[c - koff] + atomicAdd(&fill[c - koff], 1)] = i;
+    const uint32_t c = (uint32_t)(key[i] - koff);
+    if (c < (uint32_t)nk) list[start[c] + atomicAdd(&fill[c], 1)] = i;
   }
 }
 
@@ -73,8 +77,8 @@ __global__ void __launch_bounds__(1024) k_group_small(const int32_t* __restrict_
   for (int32_t i = threadIdx.x; i < nk; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const int32_t c = key[i];
-    if (c >= 0) atomicAdd(&cnt[c - koff], 1);
+    const uint32_t c = (uint32_t)(key[i] - koff);
+    if (c < (uint32_t)nk) atomicAdd(&cnt[c], 1);
   }
   __syncthreads();
   int32_t carry = 0;
@@ -92,8 +96,8 @@ __global__ void __launch_bounds__(1024) k_group_small(const int32_t* __restrict_
   if (threadIdx.x == 0) start[nk] = carry;
   __syncthreads();
   for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const int32_t c = key[i];
-    if (c >= 0) list[atomicAdd(&pos[c - koff], 1)] = i;
+    const uint32_t c = (uint32_t)(key[i] - koff);
+    if (c < (uint32_t)nk) list[atomicAdd(&pos[c], 1)] = i;
   }
 }
 
@@ -294,9 +298,10 @@ __global__ void __launch_bounds__(1024) k_nd_bisect(BisectArgs a) {
     if (threadIdx.x == 0) a.split[ni] = 1;
     // sort the node's patches by id (local index order = id order): marks in
     // a bitmap over all patch ids, read back in order through prefix
-    // popcounts, when it fits in shared memory; else a bitonic sort
+    // popcounts, when it fits in shared memory and is not much longer than
+    // the node (a fused batch has many patch ids); else a bitonic sort
     const int32_t kw = (a.k + 31) >> 5;
-    if (2 * (int64_t)kw <= a.smem_ints) {
+    if (2 * (int64_t)kw <= a.smem_ints && (kw <= 1024 || kw <= 8 * m)) {
       uint32_t* bm = reinterpret_cast<uint32_t*>(bsm);
       int32_t* pre = bsm + kw;
       for (int32_t w = threadIdx.x; w < kw; w += blockDim.x) bm[w] = 0u;
@@ -673,6 +678,7 @@ struct LevelArgs {
   int32_t* patch_node;
   int32_t k;
   const int8_t* cross;         // [k] crossing patches of this level (k_nd_bisect)
+  SegView sv;                  // fused batch: tie hashes of mesh-local vertex numbers
 };
 
 // SuperSeparator (Algorithm 2 step 3): remaining vertices of a split node with
@@ -683,6 +689,7 @@ __global__ void k_nd_superset(LevelArgs a) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
     if (a.final_[v]) continue;
     const int32_t t = a.node_of[v];
+    if ((uint32_t)(t - a.t0) >= (uint32_t)a.T) continue;     // a subtree that starts deeper
     if (!a.split[t - a.t0]) { a.final_[v] = 1; continue; }
     const int32_t pv = a.gmap[v];
     // no neighbour across in its patch's quotient row: not a candidate (its
@@ -724,9 +731,9 @@ __global__ void k_nd_superset(LevelArgs a) {
   }
 }
 
-__device__ __forceinline__ bool key_less(int32_t cu, int32_t u, int32_t cv, int32_t v) {
+__device__ __forceinline__ bool key_less(int32_t cu, int32_t u, int32_t cv, int32_t v, const SegView& sv) {
   if (cu != cv) return cu < cv;
-  const uint32_t hu = tie_hash(u), hv = tie_hash(v);
+  const uint32_t hu = tie_hash(seg_local(sv, u)), hv = tie_hash(seg_local(sv, v));
   if (hu != hv) return hu < hv;
   return u < v;
 }
@@ -769,7 +776,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
     before[c] = 0;
 #pragma unroll
     for (int k = 0; k < MIS_NB; ++k)
-      if (nb[c][k] >= 0 && key_less(cd[k], nb[c][k], x.y, cv[c])) before[c] |= 1u << k;
+      if (nb[c][k] >= 0 && key_less(cd[k], nb[c][k], x.y, cv[c], a.sv)) before[c] |= 1u << k;
   }
   grid.sync();
   for (int32_t round = 0; round <= nc; ++round) {
@@ -815,7 +822,7 @@ __global__ void __launch_bounds__(ND_THREADS) k_nd_mis(LevelArgs a) {
 #pragma unroll
         for (int k = 0; k < ND_BATCH; ++k) {
           if (st[k] == VS_IN) any_in = true;
-          else if (st[k] == VS_UND && key_less(cd[k], u[k], cdv, v)) is_min = false;
+          else if (st[k] == VS_UND && key_less(cd[k], u[k], cdv, v, a.sv)) is_min = false;
         }
       }
       if (any_in) a.vstate[v] = VS_OUT;
@@ -912,11 +919,12 @@ __global__ void k_nd_move_patches(LevelArgs a) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < span; i += gridDim.x * blockDim.x) {
     if (i < a.n && !a.final_[i]) {
       const int32_t t = a.node_of[i];
-      a.node_of[i] = 2 * t + 1 + a.side[a.gmap[i]];
+      if ((uint32_t)(t - a.t0) < (uint32_t)a.T) a.node_of[i] = 2 * t + 1 + a.side[a.gmap[i]];
     }
     if (i < a.k) {
       const int32_t t = a.patch_node[i];
-      if (t >= 0) a.patch_node[i] = (a.split[t - a.t0] && a.w[i] > 0) ? 2 * t + 1 + a.side[i] : -1;
+      if ((uint32_t)(t - a.t0) < (uint32_t)a.T)
+        a.patch_node[i] = (a.split[t - a.t0] && a.w[i] > 0) ? 2 * t + 1 + a.side[i] : -1;
     }
   }
 }
@@ -951,20 +959,121 @@ int ceil_log2(int64_t k) {
   return d;
 }
 
+// ---- fused batch: the meshes' subtrees -------------------------------------------------
+// pmesh[p]: the mesh of patch p (every vertex of a patch lies in one mesh).
+__global__ void k_patch_mesh(const int32_t* __restrict__ gmap, const int32_t* __restrict__ vmesh, int32_t n,
+                             int32_t* __restrict__ pmesh) {
+  FP_PDL_WAIT();
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) pmesh[gmap[v]] = vmesh[v];
+}
+
+__global__ void k_mesh_patch_count(const int32_t* __restrict__ pmesh, int32_t k, int32_t* __restrict__ kcount) {
+  FP_PDL_WAIT();
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+    atomicAdd(&kcount[pmesh[p]], 1);
+}
+
+// Every vertex and every patch starts at the root of its mesh's subtree.
+__global__ void k_seg_roots(const int32_t* __restrict__ vmesh, const int32_t* __restrict__ pmesh,
+                            const int32_t* __restrict__ psize, const int32_t* __restrict__ mroot, int32_t n, int32_t k,
+                            int32_t* __restrict__ node_of, int32_t* __restrict__ patch_node) {
+  FP_PDL_WAIT();
+  const int32_t span = n > k ? n : k;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < span; i += gridDim.x * blockDim.x) {
+    if (i < n) node_of[i] = mroot[vmesh[i]];
+    if (i < k) patch_node[i] = psize[i] > 0 ? mroot[pmesh[i]] : -1;
+  }
+}
+
+// Places the meshes' subtrees of a fused batch (after patching): mesh m with
+// k_m patches needs a subtree of height h_m = ceil(log2 k_m), the depth one
+// mesh alone is dissected to. Its root goes to depth l_m = D - h_m, with D the
+// smallest depth whose Kraft sum sum_m 2^(h_m - D) is at most 1, as the
+// canonical prefix code of the lengths l_m (largest subtree first, then mesh
+// index); every leaf then lies at depth D. Leaves pmesh [k] on the device
+// for the root initialisation, sets h->D, the roots and the meshes' position
+// ranges (their left-to-right order in the tree).
+fp_status seg_plan(fp_handle* h, int32_t** pmesh_out) {
+  Segments* sg = h->seg;
+  const int32_t n = h->n, k = h->k, M = sg->M;
+  int32_t* pmesh = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(k > 0 ? k : 1));
+  int32_t* kc = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(M > 0 ? M : 1));
+  int32_t* hk = pinned_ints(M);
+  if (!pmesh || !kc || !hk) return fail(h, FP_ERR_OUT_OF_MEMORY, "batch plan");
+  fill_i32(h, kc, 0, M);
+  fill_i32(h, pmesh, 0, k);          // (every patch has a vertex; kept in range regardless)
+  FP_LAUNCH(h, k_patch_mesh, grid_for(n, 256), 256, 0, h->gmap, sg->v.vmesh, n, pmesh);
+  FP_LAUNCH(h, k_mesh_patch_count, grid_for(k, 256), 256, 0, pmesh, k, kc);
+  cudaMemcpyAsync(hk, kc, sizeof(int32_t) * (size_t)M, cudaMemcpyDeviceToHost, h->stream);
+  FP_CHECK_LAUNCH(h, "batch plan");
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  dev_free(h, kc);
+  sg->h_k.assign(hk, hk + M);
+  std::vector<int32_t> hm(M, -1), order;
+  int64_t S = 0;
+  for (int32_t m = 0; m < M; ++m)
+    if (sg->h_k[m] > 0) {
+      hm[m] = ceil_log2(sg->h_k[m]);
+      S += (int64_t)1 << hm[m];
+      order.push_back(m);
+    }
+  const int32_t D = ceil_log2(S > 0 ? S : 1);
+  if (D > 24) return fail(h, FP_ERR_UNSUPPORTED, "fused batch tree deeper than 24 levels");
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return hm[a] > hm[b]; });
+  sg->h_root.assign(M, -1);
+  sg->h_posoff.assign(M, 0);
+  int64_t code = -1;
+  int32_t lprev = 0, pos = 0;
+  sg->dmin = order.empty() ? D : D - hm[order[0]];
+  for (int32_t m : order) {
+    const int32_t l = D - hm[m];
+    code = code < 0 ? 0 : (code + 1) << (l - lprev);
+    lprev = l;
+    sg->h_root[m] = (int32_t)(((int64_t)1 << l) - 1 + code);
+    sg->h_posoff[m] = pos;
+    pos += sg->h_voff[m + 1] - sg->h_voff[m];
+  }
+  h->D = D;
+  int32_t* hr = pinned_ints(M);
+  if (!hr) return fail(h, FP_ERR_OUT_OF_MEMORY, "batch plan");
+  for (int32_t m = 0; m < M; ++m) hr[m] = sg->h_root[m] < 0 ? 0 : sg->h_root[m];
+  cudaMemcpyAsync(sg->mroot, hr, sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, h->stream);
+  // the pinned buffer is reused by the next call on this thread: wait here
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return check_cuda(h, e, "batch roots");
+  *pmesh_out = pmesh;
+  return FP_OK;
+}
+
 }  // namespace
 
 fp_status run_nested_dissection(fp_handle* h) {
   const int32_t n = h->n, k = h->k;
   const int64_t Q = h->nnz > 0 ? h->nnz : 1;
+  Segments* sg = h->seg;
+  if (sg && h->opt.nd_level > 0) return fail(h, FP_ERR_UNSUPPORTED, "a fused batch takes nd_level 0");
   int32_t D = h->opt.nd_level > 0 ? h->opt.nd_level : ceil_log2(k);
   if (D > 24) return fail(h, FP_ERR_UNSUPPORTED, "nd_level above 24");
   h->D = D;
   if (n == 0) return FP_OK;
-  fill_i32(h, h->node_of, 0, n);
-  const int32_t Dsplit = D < ceil_log2(k) ? D : ceil_log2(k);   // deeper nodes hold <= 1 patch
+  // a fused batch: every mesh's subtree has its leaves at depth D; the levels
+  // above the shallowest root hold no vertex
+  int32_t* pmesh = nullptr;
+  int32_t dmin = 0;
+  if (sg) {
+    FP_TRY(seg_plan(h, &pmesh));
+    D = h->D;
+    dmin = sg->dmin;
+  } else {
+    fill_i32(h, h->node_of, 0, n);
+  }
+  const int32_t Dsplit = sg ? D : (D < ceil_log2(k) ? D : ceil_log2(k));   // deeper nodes hold <= 1 patch
   // the separators of the top levels are ordered while deeper levels are cut
-  FP_TRY(early_md_begin(h, Dsplit < EARLY_LEVELS ? Dsplit : EARLY_LEVELS));
-  if (Dsplit == 0) { FP_CHECK_LAUNCH(h, "nd init"); return FP_OK; }
+  FP_TRY(early_md_begin(h, sg ? 0 : (Dsplit < EARLY_LEVELS ? Dsplit : EARLY_LEVELS)));
+  if (Dsplit == 0 && !sg) { FP_CHECK_LAUNCH(h, "nd init"); return FP_OK; }
+  // per-level arrays hold one entry per node of the deepest cut level
+  const int64_t tl = std::max<int64_t>((int64_t)k + 64, Dsplit > 0 ? ((int64_t)1 << (Dsplit - 1)) + 64 : 64);
 
   const int64_t kk = (int64_t)k + 64;
   int32_t *psize, *pstart, *pfill, *pverts, *qdeg, *q_rowptr, *q_col, *q_w, *ladj, *tmp, *patch_node, *w, *side, *loc;
@@ -980,9 +1089,9 @@ fp_status run_nested_dissection(fp_handle* h) {
     tmp = ar.get<int32_t>(scan_tmp_ints(kk) + 8); patch_node = ar.get<int32_t>(kk); w = ar.get<int32_t>(kk);
     side = ar.get<int32_t>(kk); loc = ar.get<int32_t>(kk); ldeg = ar.get<int32_t>(kk); lvl = ar.get<int32_t>(kk);
     lbeg = ar.get<int32_t>(kk); qa = ar.get<int32_t>(kk); qb = ar.get<int32_t>(kk); mark = ar.get<int32_t>(kk);
-    hist = ar.get<int32_t>(kk); sortbuf = ar.get<int32_t>(2 * kk + 64); npcount = ar.get<int32_t>(kk);
-    npstart = ar.get<int32_t>(kk + 1); npfill = ar.get<int32_t>(kk); nplist = ar.get<int32_t>(kk);
-    split = ar.get<int32_t>(kk); cdeg = ar.get<int32_t>(n); cand = ar.get<int32_t>(n); ctr = ar.get<int32_t>(8);
+    hist = ar.get<int32_t>(kk); sortbuf = ar.get<int32_t>(2 * kk + 64); npcount = ar.get<int32_t>(tl);
+    npstart = ar.get<int32_t>(tl + 1); npfill = ar.get<int32_t>(tl); nplist = ar.get<int32_t>(kk);
+    split = ar.get<int32_t>(tl); cdeg = ar.get<int32_t>(n); cand = ar.get<int32_t>(n); ctr = ar.get<int32_t>(8);
     xcol = ar.get<int32_t>(Q); cand_x = ar.get<int2>(n); final_ = ar.get<int8_t>(n); vstate = ar.get<int8_t>(n);
     cross = ar.get<int8_t>(kk);
   };
@@ -994,10 +1103,10 @@ fp_status run_nested_dissection(fp_handle* h) {
   ProfScope ps_q(FP_PROF_QUOTIENT, h->stream);
   // patch vertex lists
   fill_i32(h, psize, 0, k);
-  FP_LAUNCH(h, k_count_by, G, 256, 0, h->gmap, n, 0, psize);
+  FP_LAUNCH(h, k_count_by, G, 256, 0, h->gmap, n, 0, k, psize);
   scan_exclusive(h, psize, pstart, k, tmp);
   fill_i32(h, pfill, 0, k);
-  FP_LAUNCH(h, k_scatter_by, G, 256, 0, h->gmap, n, 0, pstart, pfill, pverts);
+  FP_LAUNCH(h, k_scatter_by, G, 256, 0, h->gmap, n, 0, k, pstart, pfill, pverts);
   // quotient graph (a3)
   const int GQ = k < NUM_SMS_B300 * 8 ? k : NUM_SMS_B300 * 8;
   // (ladj, xcol and lbeg serve as scratch here; the dissection uses them later)
@@ -1009,7 +1118,13 @@ fp_status run_nested_dissection(fp_handle* h) {
             q_w);
   // state: every patch with vertices starts in the root; an empty one (a
   // label of a supplied patch map that no vertex carries) takes no part
-  FP_LAUNCH(h, k_patch_node_init, GK, 256, 0, psize, k, patch_node);
+  if (sg) {
+    FP_LAUNCH(h, k_seg_roots, G > GK ? G : GK, 256, 0, sg->v.vmesh, pmesh, psize, sg->mroot, n, k, h->node_of,
+              patch_node);
+    dev_free(h, pmesh);
+  } else {
+    FP_LAUNCH(h, k_patch_node_init, GK, 256, 0, psize, k, patch_node);
+  }
   cudaMemcpyAsync(w, psize, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, h->stream);
   FP_LAUNCH(h, k_zero_i8, G, 256, 0, final_, (int64_t)n);
   FP_LAUNCH(h, k_zero_i8, G, 256, 0, vstate, (int64_t)n);
@@ -1034,7 +1149,7 @@ fp_status run_nested_dissection(fp_handle* h) {
   const int gmis_max = sms * (per > 0 ? per : 1);
 
   allow_max_dynamic_smem(k_group_small);
-  for (int32_t d = 0; d < Dsplit; ++d) {
+  for (int32_t d = dmin; d < Dsplit; ++d) {
     const int32_t t0 = (1 << d) - 1, T = 1 << d;
     ProfScope ps_b(FP_PROF_ND_BISECT, h->stream);
     const bool grouped_small = T <= GROUP_SMALL_MAX;
@@ -1044,10 +1159,10 @@ fp_status run_nested_dissection(fp_handle* h) {
                 ctr);
     } else {
       fill_i32(h, npcount, 0, T);
-      FP_LAUNCH(h, k_count_by, GK, 256, 0, patch_node, k, t0, npcount);
+      FP_LAUNCH(h, k_count_by, GK, 256, 0, patch_node, k, t0, T, npcount);
       scan_exclusive(h, npcount, npstart, T, tmp);
       fill_i32(h, npfill, 0, T);
-      FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, npstart, npfill, nplist);
+      FP_LAUNCH(h, k_scatter_by, GK, 256, 0, patch_node, k, t0, T, npstart, npfill, nplist);
     }
     // a node at depth d holds at most 2^(Dsplit - d) patches (the subtree
     // capacity that bounds every cut, R8): stage that many in shared memory
@@ -1074,7 +1189,7 @@ fp_status run_nested_dissection(fp_handle* h) {
       FP_LAUNCH(h, k_stage_sides, GK, 256, 0, patch_node, side, split, t0, T, k, sb);
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, cand_x, xcol,
-                 ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross};
+                 ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross, sg ? sg->v : SegView{}};
     if (!grouped_small) fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {

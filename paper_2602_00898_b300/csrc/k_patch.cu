@@ -129,11 +129,23 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
   }
 }
 
-__global__ void k_seed_flags(int32_t n, uint64_t kt, uint64_t seed, int32_t* __restrict__ flag) {
+// In a fused batch every vertex draws with its number, vertex count and
+// k_target inside its own mesh.
+__global__ void k_seed_flags(int32_t n, uint64_t kt, uint64_t seed, int32_t* __restrict__ flag, SegView sv) {
   FP_PDL_WAIT();
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    uint64_t h = splitmix64_state(seed * 0x9E3779B97F4A7C15ull + (uint64_t)(uint32_t)v);
-    flag[v] = ((h >> 32) * (uint64_t)n) < (kt << 32) ? 1 : 0;
+    int32_t lv = v;
+    uint64_t nm = (uint64_t)n, ktm = kt;
+    if (sv.vmesh) {
+      const int32_t m = sv.vmesh[v], b = sv.voff[m];
+      const uint64_t c = (uint64_t)sv.mcap[m];
+      lv = v - b;
+      nm = (uint64_t)(sv.voff[m + 1] - b);
+      ktm = (2 * nm + c - 1) / c;
+      if (ktm < 1) ktm = 1;
+    }
+    uint64_t h = splitmix64_state(seed * 0x9E3779B97F4A7C15ull + (uint64_t)(uint32_t)lv);
+    flag[v] = ((h >> 32) * nm) < (ktm << 32) ? 1 : 0;
   }
 }
 
@@ -258,9 +270,11 @@ __global__ void k_all_seed_sources(const int32_t* __restrict__ rowptr, const int
   if (blockIdx.x == 0 && threadIdx.x == 0) { ctr[0] = k; ctr[1] = 0; ctr[2] = 0; }
 }
 
-__global__ void k_oversize_flags(const int32_t* __restrict__ psize, int32_t k, int32_t cap, int32_t* __restrict__ over) {
+__global__ void k_oversize_flags(const int32_t* __restrict__ psize, int32_t k, int32_t cap, int32_t* __restrict__ over,
+                                 const int32_t* __restrict__ seed_of, SegView sv) {
   FP_PDL_WAIT();
-  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x) over[p] = psize[p] > cap;
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < k; p += gridDim.x * blockDim.x)
+    over[p] = psize[p] > (sv.vmesh ? sv.mcap[sv.vmesh[seed_of[p]]] : cap);
 }
 
 // Cap split: the farthest vertex of every oversize patch p becomes the seed of
@@ -307,6 +321,7 @@ struct LocalArgs {
   int32_t* next_over;           // mode 2: the halves still above cap (flag by new patch id)
   int32_t* next_cnt;            // mode 2: how many
   int32_t cap;
+  SegView sv;                   // fused batch: the cap of the patch's own mesh
 };
 
 // Mode 0 visits every patch: five CTAs per SM keep one wave for a mesh of
@@ -510,8 +525,9 @@ __global__ void __launch_bounds__(LOCAL_THREADS, kMode == 0 ? 5 : 4) k_patch_loc
       // so every vertex is reached from one of the two seeds)
       c2 = block_sum(c2, red);
       if (tid == 0) {
-        if (m - c2 > a.cap) { a.next_over[p] = 1; atomicAdd(a.next_cnt, 1); }
-        if (c2 > a.cap) { a.next_over[p2] = 1; atomicAdd(a.next_cnt, 1); }
+        const int32_t cap = a.sv.vmesh ? a.sv.mcap[a.sv.vmesh[a.seed_of[p]]] : a.cap;
+        if (m - c2 > cap) { a.next_over[p] = 1; atomicAdd(a.next_cnt, 1); }
+        if (c2 > cap) { a.next_over[p2] = 1; atomicAdd(a.next_cnt, 1); }
       }
     } else {
       unsigned long long b = 0ull;
@@ -603,13 +619,14 @@ fp_status run_patching(fp_handle* h) {
   if (!hbuf) return fail(h, FP_ERR_OUT_OF_MEMORY, "patching workspace");
 
   const int G = grid_for(n, 256);
+  const SegView sv = h->seg ? h->seg->v : SegView{};
   // R1 seeds
   uint64_t kt = ((uint64_t)2 * (uint64_t)n + (uint64_t)cap - 1) / (uint64_t)cap;
   if (kt < 1) kt = 1;
   {
     ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
     FP_LAUNCH(h, k_fill_u64, G, 256, 0, key, KEY_INF, (int64_t)n);
-    FP_LAUNCH(h, k_seed_flags, G, 256, 0, n, kt, h->opt.seed, flag);
+    FP_LAUNCH(h, k_seed_flags, G, 256, 0, n, kt, h->opt.seed, flag, sv);
     scan_exclusive(h, flag, rank, n, tmp);
     FP_LAUNCH(h, k_seed_sources, G, 256, 0, n, h->rowptr, flag, rank, 0, key, seed_of, fa, ctr);
   }
@@ -657,7 +674,7 @@ fp_status run_patching(fp_handle* h) {
     FP_LAUNCH(h, k_patch_scatter, G, 256, 0, group, n, pstart, pdeg, pverts);
   };
   LocalArgs la{0, h->rowptr, h->col, group, pstart, pverts, pedge, g_adj, g_vtx, loc, nullptr, orank, 0,
-               seed_of, best, key, nullptr, nullptr, cap};
+               seed_of, best, key, nullptr, nullptr, cap, sv};
   const int GL = NUM_SMS_B300 * 8;
   // R4 Lloyd rounds
   const int GK = grid_for(k, 256);
@@ -689,7 +706,7 @@ fp_status run_patching(fp_handle* h) {
   patch_lists(k);
   {
     ProfScope ps(FP_PROF_PATCH_OTHER, h->stream);
-    FP_LAUNCH(h, k_oversize_flags, grid_for(k, 256), 256, 0, pcnt, k, cap, over);
+    FP_LAUNCH(h, k_oversize_flags, grid_for(k, 256), 256, 0, pcnt, k, cap, over, seed_of, sv);
     scan_exclusive(h, over, orank, k, tmp);
   }
   cudaMemcpyAsync(hbuf, orank + k, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);

@@ -135,3 +135,83 @@ def test_full_batch_256_sampled():
         assert (parent == -1).any() and ((parent == -1) | (parent > np.arange(m.n))).all()
         if i % 16 == 0:
             _check_item(m, it, outs)
+
+
+# ---- the fused form (n_workers = 0): the whole batch as one disjoint union ----
+
+def _tiny_meshes():
+    """Degenerate members: an empty mesh, one vertex, isolated vertices only, a
+    single triangle, and a mesh of two components plus isolated vertices."""
+    a = M.shuffle(M.torus(12, 10, 0.3, 1), 1)
+    b = M.shuffle(M.icosphere(2), 2)
+    two = np.concatenate([a.faces, b.faces + a.n]).astype(np.int32)
+    return [M.Mesh("empty", 0, np.zeros((0, 3), np.int32)),
+            M.Mesh("one", 1, np.zeros((0, 3), np.int32)),
+            M.Mesh("isolated", 9, np.zeros((0, 3), np.int32)),
+            M.Mesh("triangle", 3, np.array([[0, 1, 2]], np.int32)),
+            M.Mesh("two+isolated", a.n + b.n + 4, two)]
+
+
+def test_fused_explicit_caps_matches_oracle():
+    meshes = _mix(12, 7) + _tiny_meshes()
+    caps = [64, 128, 256, 512] * 3 + [16, 16, 4, 2, 40]
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes], caps)
+    st = fp.fp_batch_order(items, fp.fp_default_options(), n_workers=0)
+    torch.cuda.synchronize()
+    assert st == 0
+    assert [it.chosen_cap for it in items] == caps
+    assert items[0].launches > 0 and all(it.launches == 0 for it in list(items)[1:])
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        _check_item(m, it, outs)
+
+
+def test_fused_equals_pool():
+    """The same batch through the fused union and through the per-mesh pool:
+    every output and every count identical."""
+    meshes = _mix(20, 23, 1500, 40000)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    caps = [128, 192, 256, 384, 512] * 4
+    a = fp.make_batch(faces, [m.n for m in meshes], caps)
+    b = fp.make_batch(faces, [m.n for m in meshes], caps)
+    assert fp.fp_batch_order(a, fp.fp_default_options(), n_workers=0) == 0
+    assert fp.fp_batch_order(b, fp.fp_default_options(), n_workers=6) == 0
+    torch.cuda.synchronize()
+    for x, y, (_, ox), (_, oy) in zip(a, b, a.tensors, b.tensors):
+        assert (x.nnzL, x.flops, x.chosen_cap, x.status) == (y.nnzL, y.flops, y.chosen_cap, y.status)
+        for tx, ty in zip(ox, oy):
+            assert torch.equal(tx, ty)
+
+
+def test_fused_single_mesh_and_seeds():
+    """A batch of one mesh, and the seed option reaching every member."""
+    m = M.shuffle(M.icosphere(5), 8)
+    faces = [torch.from_numpy(m.faces).cuda()]
+    items = fp.make_batch(faces, [m.n], [300])
+    assert fp.fp_batch_order(items, fp.fp_default_options(), n_workers=0) == 0
+    _check_item(m, items[0], items.tensors[0][1])
+    meshes = _mix(5, 29)
+    faces = [torch.from_numpy(x.faces).cuda() for x in meshes]
+    items = fp.make_batch(faces, [x.n for x in meshes], [256] * 5)
+    assert fp.fp_batch_order(items, fp.fp_default_options(seed=5, lloyd_rounds=1), n_workers=0) == 0
+    torch.cuda.synchronize()
+    for x, it, (_, outs) in zip(meshes, items, items.tensors):
+        g = O.graph_from_faces(x.faces, x.n)
+        o = O.order(g, 256, seed=5, lloyd_rounds=1)
+        np.testing.assert_array_equal(outs[0].cpu().numpy(), o.perm)
+
+
+def test_fused_failure_reports_every_item():
+    """A corner outside its own mesh (though inside the union) fails the fused
+    pipeline; the items are then ordered one by one and each gets its own
+    status."""
+    meshes = _mix(4, 3)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    bad = torch.tensor([[0, 1, 12]], dtype=torch.int32, device="cuda")   # vertex 12 of a 10-vertex mesh
+    items = fp.make_batch(faces + [bad], [m.n for m in meshes] + [10], [200] * 5)
+    st = fp.fp_batch_order(items, fp.fp_default_options(), n_workers=0)
+    torch.cuda.synchronize()
+    assert st == 1
+    assert [it.status for it in items] == [0, 0, 0, 0, 1]
+    for m, it, (_, outs) in zip(meshes, list(items)[:4], items.tensors[:4]):
+        _check_item(m, it, outs)
