@@ -291,9 +291,8 @@ fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* 
  * (FP_GNN_NPARAMS codes, see fp_set_priority_net) attached before its
  * fp_permute, so each leaf keeps the lower-fill of its learned and plain
  * orders; the per-item learned_* and fill_* fields report the choices.
- * Always the pool form (n_workers 0 = 8 workers). h_codes NULL is the pool
- * form of fp_batch_order. Errors as fp_batch_order, plus FP_ERR_INVALID_ARG
- * for a code out of range.
+ * n_workers as in fp_batch_order (0: fused). h_codes NULL is fp_batch_order.
+ * Errors as fp_batch_order, plus FP_ERR_INVALID_ARG for a code out of range.
  */
 fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers,
                                  const int32_t* h_codes);

@@ -71,6 +71,9 @@ struct Segments {
   std::vector<int32_t> h_root;       // [M] root node (-1: an empty mesh)
   std::vector<int32_t> h_k;          // [M] patches of every mesh
   std::vector<int32_t> h_posoff;     // [M] first position of every mesh in the union's order
+  // learned form, per mesh: leaves considered, learned orders kept, summed
+  // plain and chosen leaf fills
+  std::vector<unsigned long long> h_learned;   // [M][4]
   int32_t dmin = 0;                  // shallowest root depth
 };
 struct NumericFactor;   // numeric Cholesky factor of a handle (k_numeric.cu)

@@ -12,8 +12,8 @@
 // every mesh's dissection tree below an empty super-tree (Segments). A mesh's
 // patches, separators, orders and symbolic counts depend only on its own
 // vertices, with its own cap, seed threshold and vertex numbering, so each
-// result equals the mesh ordered alone. The pool remains for the learned form
-// and on request (n_workers > 0).
+// result equals the mesh ordered alone. The pool runs on request
+// (n_workers > 0) and orders the items one by one when the fused form fails.
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -182,7 +182,7 @@ bool fused_ok(const fp_batch_item* items, int32_t count, const fp_options& o) {
   return N <= INT32_MAX && F <= INT32_MAX / 6;
 }
 
-fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s) {
+fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s, const int32_t* codes) {
   int device = 0;
   cudaGetDevice(&device);
   std::vector<int32_t> voff(M + 1, 0), caps(M);
@@ -237,7 +237,8 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
   if (N > 0) FP_LAUNCH(h, k_vertex_mesh, grid_for(N, 256), 256, 0, (const int32_t*)d_voff, M, N, d_vmesh);
   sg->v = SegView{d_vmesh, d_voff, d_cap};
   int64_t nnz = 0, fl = 0;
-  st = fp_permute(h, nullptr, nullptr);
+  if (codes) st = fp_set_priority_net(h, codes);
+  if (st == FP_OK) st = fp_permute(h, nullptr, nullptr);
   if (st == FP_OK) st = fp_symbolic(h, parent, colcount, &nnz, &fl);
   if (st == FP_OK) {
     std::vector<OutSeg> outs(M);
@@ -270,6 +271,13 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
         it.launches = 0;
         it.learned_leaves = it.learned_kept = 0;
         it.fill_plain = it.fill_chosen = 0;
+        if (codes && sg->h_learned.size() == 4 * (size_t)M) {
+          const unsigned long long* L = &sg->h_learned[4 * (size_t)m];
+          it.learned_kept = (int32_t)L[0];
+          it.fill_plain = (int64_t)L[1];
+          it.fill_chosen = (int64_t)L[2];
+          it.learned_leaves = (int32_t)L[3];
+        }
       }
     if (st == FP_OK) items[0].launches = launches + fp_launch_count(h);
   }
@@ -283,16 +291,6 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
 using namespace fp;
 
 extern "C" fp_status fp_batch_order(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t n_workers) {
-  if (count > 0 && items && opts && n_workers == 0 && fused_ok(items, count, *opts)) {
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return fail(nullptr, FP_ERR_CUDA, cudaGetErrorString(e));
-    cudaStream_t s = worker_stream(device);
-    if (!s) return fail(nullptr, FP_ERR_CUDA, "batch stream");
-    const fp_status st = run_fused(items, count, *opts, s);
-    if (st == FP_OK) return FP_OK;
-    // a failure: every item's own status comes from ordering it alone
-  }
   return fp_batch_order_learned(items, count, opts, n_workers, nullptr);
 }
 
@@ -304,12 +302,18 @@ extern "C" fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count,
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return fail(nullptr, FP_ERR_CUDA, cudaGetErrorString(e));
+  if (n_workers == 0 && fused_ok(items, count, *opts)) {
+    cudaStream_t s = worker_stream(device);
+    if (!s) return fail(nullptr, FP_ERR_CUDA, "batch stream");
+    if (run_fused(items, count, *opts, s, h_codes) == FP_OK) return FP_OK;
+    // a failure: every item's own status comes from ordering it alone
+  }
   std::vector<int32_t> order(count);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return items[a].n_vertices > items[b].n_vertices; });
-  // 8 workers measured best for a 256-mesh mix on B300 (more contend in the
-  // driver's launch path and for the cooperative grids)
+  // the fused form's fallback runs 8 workers (8-16 measured best for the
+  // pool on a 256-mesh mix: more contend in the driver's launch path)
   const int T = std::min<int>(n_workers > 0 ? n_workers : 8, count);
   std::atomic<int32_t> next(0);
   const fp_options base = *opts;

@@ -152,6 +152,7 @@ struct ScoreArgs {
   uint8_t* xout;           // [n][8] feature codes per position, out (may be NULL)
   int32_t* status;
   int64_t max_spin;        // polls of the tensor-core completion wait
+  SegView sv;              // fused batch: the cap of the leaf's own mesh
 };
 
 // shared layout of the scoring kernel (bytes)
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
   const int32_t t = a.leaves[blockIdx.x];
   const int32_t m = a.node_size[t], b = a.node_begin[t];
   if (m <= 0 || m > GNN_LEAF_MAX) return;      // uniform per CTA
+  const int32_t cap = a.sv.vmesh ? a.sv.mcap[a.sv.vmesh[a.perm[b]]] : a.cap;
 
   uint8_t* X = sm + SC_X;
   uint8_t* H = sm + SC_H;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
     const int32_t dp = depth[i] == INF_DEPTH ? dmax + 1 : (int32_t)depth[i];
     X[i * 8 + 0] = (uint8_t)min(8 * degh[i], 255);
     X[i * 8 + 3] = (uint8_t)min(rne_div(64 * dp, dmax + 1), 255);
-    X[i * 8 + 4] = (uint8_t)min(rne_div(64 * m, a.cap), 255);
+    X[i * 8 + 4] = (uint8_t)min(rne_div(64 * m, cap), 255);
     X[i * 8 + 5] = 64;
     X[i * 8 + 6] = X[i * 8 + 7] = 0;
     if (a.xout)
@@ -365,22 +367,25 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
   if (warp == 0) tc_dealloc32(tmem);
 }
 
-// Keeps the learned order of a leaf iff its fill is smaller.
+// Keeps the learned order of a leaf iff its fill is smaller. stats[4 m + 0..3]
+// of the leaf's mesh m (0 for one mesh): learned orders kept, summed plain
+// fills, summed chosen fills, leaves.
 __global__ void k_choose(const int32_t* __restrict__ leaves, int32_t nl, const int32_t* __restrict__ node_begin,
                          const int32_t* __restrict__ node_size, const int64_t* __restrict__ fill_p,
                          const int64_t* __restrict__ fill_l, const int32_t* __restrict__ perm_l,
-                         int32_t* __restrict__ perm, unsigned long long* __restrict__ stats) {
+                         int32_t* __restrict__ perm, unsigned long long* __restrict__ stats, SegView sv) {
   FP_PDL_WAIT();
   const int32_t t = leaves[blockIdx.x];
   const bool keep = fill_l[t] < fill_p[t];
-  if (keep) {
-    const int32_t b = node_begin[t], m = node_size[t];
+  const int32_t b = node_begin[t], m = node_size[t];
+  if (keep)
     for (int32_t i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = perm_l[b + i];
-  }
   if (threadIdx.x == 0) {
-    atomicAdd(&stats[0], keep ? 1ull : 0ull);
-    atomicAdd(&stats[1], (unsigned long long)fill_p[t]);
-    atomicAdd(&stats[2], (unsigned long long)(keep ? fill_l[t] : fill_p[t]));
+    unsigned long long* st = stats + (sv.vmesh ? 4 * (int64_t)sv.vmesh[perm_l[b]] : 0);
+    atomicAdd(&st[0], keep ? 1ull : 0ull);
+    atomicAdd(&st[1], (unsigned long long)fill_p[t]);
+    atomicAdd(&st[2], (unsigned long long)(keep ? fill_l[t] : fill_p[t]));
+    atomicAdd(&st[3], 1ull);
   }
 }
 
@@ -427,7 +432,7 @@ fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, co
   if (nl == 0) return FP_OK;
   ScoreArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_begin, h->node_size, d_leaves, nl, d_q,
                h->opt.patch_cap, d_key, d_score, d_x, h->d_status,
-               h->opt.max_spin > 0 ? h->opt.max_spin : SPIN_DEFAULT};
+               h->opt.max_spin > 0 ? h->opt.max_spin : SPIN_DEFAULT, h->seg ? h->seg->v : SegView{}};
   allow_max_dynamic_smem(k_gnn_score);
   FP_LAUNCH(h, k_gnn_score, nl, SC_THREADS, (size_t)SC_BYTES, sa);
   FP_CHECK_LAUNCH(h, "network scores");
@@ -452,12 +457,13 @@ fp_status run_learned(fp_handle* h) {
   int32_t* perm_l = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
   int32_t* iperm_l = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
   int64_t* fills = (int64_t*)dev_alloc(h, sizeof(int64_t) * 2 * nn);
-  unsigned long long* stats = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 4);
+  const int32_t nst = h->seg ? 4 * h->seg->M : 4;
+  unsigned long long* stats = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * nst);
   if (!key || !vlist || !loc || !perm_l || !iperm_l || !fills || !stats)
     return fail(h, FP_ERR_OUT_OF_MEMORY, "learned ordering workspace");
   cudaMemsetAsync(key, 0, sizeof(uint32_t) * n, h->stream);
   cudaMemsetAsync(fills, 0, sizeof(int64_t) * 2 * nn, h->stream);
-  cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * 4, h->stream);
+  cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * nst, h->stream);
   FP_TRY(launch_gnn_score(h, dl, nl, h->qnet, key, h->scores, nullptr));
   cudaMemcpyAsync(vlist, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(perm_l, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
@@ -466,19 +472,25 @@ fp_status run_learned(fp_handle* h) {
   FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, perm_l, n, iperm_l);
   FP_TRY(run_leaf_fill(h, h->perm, h->iperm, dl, nl, fills));
   FP_TRY(run_leaf_fill(h, perm_l, iperm_l, dl, nl, fills + nn));
-  if (nl > 0) FP_LAUNCH(h, k_choose, nl, 128, 0, dl, nl, h->node_begin, h->node_size, fills, fills + nn, perm_l, h->perm, stats);
+  if (nl > 0)
+    FP_LAUNCH(h, k_choose, nl, 128, 0, dl, nl, h->node_begin, h->node_size, fills, fills + nn, perm_l, h->perm, stats,
+              h->seg ? h->seg->v : SegView{});
   FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, h->perm, n, h->iperm);
   FP_CHECK_LAUNCH(h, "learned choice");
-  unsigned long long hs[4];
-  cudaError_t e = cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, h->stream);
+  std::vector<unsigned long long> hs(nst);
+  cudaError_t e = cudaMemcpyAsync(hs.data(), stats, sizeof(unsigned long long) * nst, cudaMemcpyDeviceToHost, h->stream);
   if (e != cudaSuccess) return check_cuda(h, e, "learned stats");
   int32_t st = 0;
   FP_TRY(sync_status(h, &st));
   if (st & ST_TIMEOUT) return fail(h, FP_ERR_TIMEOUT, "tensor-core wait ran out");
+  if (h->seg) h->seg->h_learned = hs;
+  unsigned long long tot[3] = {0, 0, 0};
+  for (int32_t i = 0; i < nst; i += 4)
+    for (int c = 0; c < 3; ++c) tot[c] += hs[i + c];
   h->learned_leaves = nl;
-  h->learned_kept = (int32_t)hs[0];
-  h->fill_plain = (int64_t)hs[1];
-  h->fill_chosen = (int64_t)hs[2];
+  h->learned_kept = (int32_t)tot[0];
+  h->fill_plain = (int64_t)tot[1];
+  h->fill_chosen = (int64_t)tot[2];
   for (void* p : {(void*)dl, (void*)key, (void*)vlist, (void*)loc, (void*)perm_l, (void*)iperm_l, (void*)fills,
                   (void*)stats})
     dev_free(h, p);

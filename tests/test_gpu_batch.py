@@ -215,3 +215,37 @@ def test_fused_failure_reports_every_item():
     assert [it.status for it in items] == [0, 0, 0, 0, 1]
     for m, it, (_, outs) in zip(meshes, list(items)[:4], items.tensors[:4]):
         _check_item(m, it, outs)
+
+
+def test_fused_learned_matches_oracle_and_pool():
+    """fp_batch_order_learned in the fused form: every mesh equals the oracle's
+    learned ordering of that mesh alone, the per-mesh choice statistics match,
+    and the pool form gives the same items."""
+    from oracle import gnn as G
+    meshes = _mix(6, 19, 1500, 12000) + _tiny_meshes()[2:]
+    caps = [128, 256, 512, 128, 256, 512, 4, 2, 40]
+    d = M.gnn_weights(31)
+    codes = fp.pack_params(d, np.int32)
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, [m.n for m in meshes], caps)
+    pool = fp.make_batch(faces, [m.n for m in meshes], caps)
+    assert fp.fp_batch_order_learned(items, codes, fp.fp_default_options(), n_workers=0) == 0
+    assert fp.fp_batch_order_learned(pool, codes, fp.fp_default_options(), n_workers=4) == 0
+    torch.cuda.synchronize()
+    for m, it, (_, outs), jt, (_, pouts) in zip(meshes, items, items.tensors, pool, pool.tensors):
+        g = O.graph_from_faces(m.faces, m.n)
+        o = O.order(g, it.chosen_cap, seed=0)
+        L = G.order_learned(g, o, G.QParams.from_dict(d), it.chosen_cap)
+        s = O.symbolic(g, L.perm)
+        perm, iperm, parent, colcount = [t.cpu().numpy()[:m.n] for t in outs]
+        np.testing.assert_array_equal(perm, L.perm)
+        np.testing.assert_array_equal(parent, s.parent)
+        np.testing.assert_array_equal(colcount, s.colcount)
+        assert (it.nnzL, it.flops) == (s.nnzL, s.flops)
+        assert it.learned_leaves == len(L.leaves) and it.learned_kept == int(L.kept.sum())
+        assert it.fill_plain == int(L.fill_plain.sum())
+        assert it.fill_chosen == int(np.where(L.kept, L.fill_learned, L.fill_plain).sum())
+        assert (it.learned_leaves, it.learned_kept, it.fill_plain, it.fill_chosen) == \
+            (jt.learned_leaves, jt.learned_kept, jt.fill_plain, jt.fill_chosen)
+        for tx, ty in zip(outs, pouts):
+            assert torch.equal(tx, ty)
