@@ -556,8 +556,11 @@ def run_batch(args):
     caps = fp.fp_batch_autotune(items, opts)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
-    def order_all():
-        return fp.fp_batch_order_learned(items, codes, opts) if learned else fp.fp_batch_order(items, opts)
+    def order_all(workers=0):
+        # workers 0: the fused form (the whole batch as one disjoint union)
+        if learned:
+            return fp.fp_batch_order_learned(items, codes, opts, n_workers=workers)
+        return fp.fp_batch_order(items, opts, n_workers=workers)
 
     plain_nnz = None
     if learned:
@@ -593,6 +596,25 @@ def run_batch(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     sec = max_over_ranks(sum(times) / len(times), ws, dev)
+    # stage breakdown of the fused pipeline (a separate profiled pass)
+    import ctypes
+    fp.lib().fp_profile_reset()
+    fp.lib().fp_profiling(1)
+    assert order_all() == 0
+    torch.cuda.synchronize()
+    fp.lib().fp_profiling(0)
+    prof_ms = (ctypes.c_double * len(STAGES))()
+    fp.lib().fp_profile_read.restype = ctypes.c_int
+    fp.lib().fp_profile_read(prof_ms, None, len(STAGES))
+    stage_ms = {STAGES[i]: round(prof_ms[i], 4) for i in range(len(STAGES)) if prof_ms[i] > 0}
+    # context: the same batch through the per-mesh pool of 8 host workers
+    pool_t = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        assert order_all(8) == 0
+        torch.cuda.synchronize()
+        pool_t.append(time.perf_counter() - t)
     # end to end: pinned host faces in, four outputs back, every step
     hfaces = [torch.from_numpy(m.faces).pin_memory() for m in meshes]
     houts = [[torch.empty(m.n, dtype=torch.int32).pin_memory() for _ in range(4)] for m in meshes]
@@ -619,10 +641,14 @@ def run_batch(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "meshes": len(meshes), "vertices": nverts,
-                   "caps_by_size_class": caps, "workers": 8, "l2": "flushed between steps (256 MB write)",
+                   "caps_by_size_class": caps, "form": "fused (one pipeline over the disjoint union)",
+                   "l2": "flushed between steps (256 MB write)",
                    "step": ("fp_batch_order_learned" if learned else "fp_batch_order")
-                           + " over all meshes (create+permute+symbolic each)"},
+                           + " over all meshes (create+permute+symbolic of the union, per-mesh outputs)"},
         "mverts_per_s": ws * nverts / sec / 1e6, "nnzL_total": nnz,
+        "stage_ms": stage_ms,
+        "pool_8_workers": {"meshes_per_s": len(meshes) / statistics.median(pool_t),
+                           "note": "the same batch, one mesh pipeline per host worker (context, not the value)"},
         "clocks": clk,
         "e2e": {"value": len(meshes) / statistics.median(e2e), "unit": "meshes/s",
                 "h2d_bytes_per_step": int(sum(m.faces.nbytes for m in meshes)),

@@ -496,6 +496,13 @@ __device__ __forceinline__ uint32_t group_min_key(const uint32_t* deg2, int g, i
 
 // ---- sparse kernel (separators) --------------------------------------------------------
 
+// kGlobal: a node too large for the lists in shared memory (above about 4.5k
+// vertices) keeps them in its stretch of the global row storage (L2
+// resident, 48 B a vertex) and sorts in its global sort scratch; the
+// degrees, pivots and group minima stay in shared memory. The same single
+// warp runs the elimination; a list overflow leaves the node to the dense
+// global kernel, as in shared memory.
+template <bool kGlobal>
 __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
   FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
@@ -509,12 +516,15 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
     const int32_t pbeg = a.rank_out ? 0 : a.node_begin[t];
     int32_t* verts = a.nvlist + a.nvstart[t];
     const int M64 = (m + 63) & ~63, NG = M64 >> 6;
-    uint16_t* adj = (uint16_t*)smem;                      // m x SP_CAP local ids (48 B rows)
-    uint16_t* deg = adj + (size_t)m * SP_CAP;             // [M64], padded with dead entries
-    uint16_t* order = deg + M64;                          // pivot of each step
-    uint32_t* gmin = (uint32_t*)(order + ((m + 1) & ~1)); // [NG] least key of each 64 vertices
-    // sort the node's vertices by original id (buffer overlaps the lists)
-    int32_t* sb = (int32_t*)smem;
+    // m x SP_CAP local ids (48 B rows), then [M64] degrees padded with dead
+    // entries, the pivot of each step and [NG] least keys of each 64 vertices
+    uint16_t* adj = kGlobal ? (uint16_t*)(a.grows + a.grow_off[li]) : (uint16_t*)smem;
+    uint16_t* deg = kGlobal ? (uint16_t*)smem : adj + (size_t)m * SP_CAP;
+    uint16_t* order = deg + M64;
+    uint32_t* gmin = (uint32_t*)(order + ((m + 1) & ~1));
+    // sort the node's vertices by original id (in shared memory the buffer
+    // overlaps the lists)
+    int32_t* sb = kGlobal ? a.gsort + a.gsort_off[li] : (int32_t*)smem;
     const int NS = pow2_at_least(m, 32);
     for (int i = tid; i < NS; i += blockDim.x) sb[i] = i < m ? verts[i] : INT_MAX;
     if (tid == 0) s_ovf = 0;
@@ -569,10 +579,14 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         // arg-min of the keys (degree << 16 | local index) over the group
         // minima; the key also gives the pivot's degree
         uint32_t best = 0xffffffffu;
+        if (kGlobal) {
+          for (int g = lane; g < NG; g += 32) best = min(best, gmin[g]);
+        } else {
 #pragma unroll
-        for (int r = 0; r < SP_GROUPS / 32; ++r) {
-          const int g = lane + 32 * r;
-          if (g < NG) best = min(best, gmin[g]);
+          for (int r = 0; r < SP_GROUPS / 32; ++r) {
+            const int g = lane + 32 * r;
+            if (g < NG) best = min(best, gmin[g]);
+          }
         }
         const uint32_t pkey = __reduce_min_sync(0xffffffffu, best);
         const int p = (int)(pkey & 0xffffu);
@@ -906,8 +920,8 @@ fp_status launch_early_md(fp_handle* h, int32_t d) {
   MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->early_start, h->early_list, h->early_loc,
            nullptr, nullptr, T, nullptr, nullptr, nullptr, nullptr, 0, h->early_ovf, nullptr, nullptr,
            t0, h->early_cnt, h->early_rank, (int64_t)SMEM_MAX};
-  allow_max_dynamic_smem(k_md_sparse);
-  launch_pdl(s2, k_md_sparse, T, MD_THREADS, SMEM_MAX, a);
+  allow_max_dynamic_smem(k_md_sparse<false>);
+  launch_pdl(s2, k_md_sparse<false>, T, MD_THREADS, SMEM_MAX, a);
   h->launches += 4;
   return check_cuda(h, cudaGetLastError(), "early ordering launch");
 }
@@ -984,7 +998,8 @@ fp_status run_local_order(fp_handle* h) {
     for (int32_t t : *L) {
       const int m = hs[t];
       goff.push_back(gwords);
-      gwords += (int64_t)m * ((m + 31) / 32);
+      // dense bit rows, or the sparse lists (12 words a vertex), 16 B aligned
+      gwords += (std::max<int64_t>((int64_t)m * ((m + 31) / 32), 12 * (int64_t)m) + 3) & ~(int64_t)3;
       soff.push_back(gsort);
       gsort += pow2_host(m);
     }
@@ -1005,14 +1020,16 @@ fp_status run_local_order(fp_handle* h) {
     dup = ar.get<int64_t>((int64_t)up.size() + 1);
     grows = ar.get<uint32_t>(gwords);
     gs = ar.get<int32_t>(gsort);
-    ovf = ar.get<int32_t>((int64_t)ls[1].size() + 2);      // + the leaf kernel's node queue
+    // flags of the sparse-list passes (ls[1], then ls[2] after the leaf
+    // kernel's node queue)
+    ovf = ar.get<int32_t>((int64_t)ls[1].size() + 2 + (int64_t)ls[2].size());
   };
   layout();
   if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "ordering rows");
   layout();      // dup is the block's base
   e = cudaMemcpyAsync(dup, up.data(), sizeof(int64_t) * up.size(), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return check_cuda(h, e, "upload node lists");
-  fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 2);
+  fill_i32(h, ovf, 0, (int64_t)ls[1].size() + 2 + (int64_t)ls[2].size());
   const int32_t* dnodes = (const int32_t*)dup;
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
               nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr, ovf + ls[1].size()};
@@ -1059,10 +1076,10 @@ fp_status run_local_order(fp_handle* h) {
     a.nnodes_launch = (int32_t)ls[1].size();
     a.overflow = ovf;
     const size_t sm = sparse_smem(mmax[1]);
-    allow_max_dynamic_smem(k_md_sparse);
+    allow_max_dynamic_smem(k_md_sparse<false>);
     {
       ProfScope ps(FP_PROF_MD_MID, s3);
-      launch_pdl(s3, k_md_sparse, (unsigned)ls[1].size(), MD_THREADS, sm, a);
+      launch_pdl(s3, k_md_sparse<false>, (unsigned)ls[1].size(), MD_THREADS, sm, a);
       h->launches++;
     }
     // redo flagged nodes with global rows (grow_off/gsort_off index from 0 here)
@@ -1078,11 +1095,18 @@ fp_status run_local_order(fp_handle* h) {
     a.nnodes_launch = (int32_t)ls[2].size();
     a.grow_off = dup + off64 + (int64_t)ls[1].size();
     a.gsort_off = dup + off64 + nsg + (int64_t)ls[1].size();
+    a.overflow = ovf + ls[1].size() + 2;
+    // first with sparse lists in global memory, then the dense kernel for the
+    // nodes whose lists overflowed
+    const size_t M64 = (size_t)((mmax[2] + 63) & ~63);
+    const size_t smsp = M64 * 2 + (size_t)((mmax[2] + 1) & ~1) * 2 + (M64 / 64) * 4;
+    allow_max_dynamic_smem(k_md_sparse<true>);
+    ProfScope ps(FP_PROF_MD_LARGE, s3);
+    launch_pdl(s3, k_md_sparse<true>, (unsigned)ls[2].size(), MD_THREADS, smsp, a);
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
-    ProfScope ps(FP_PROF_MD_LARGE, s3);
     launch_pdl(s3, k_md_global, (unsigned)ls[2].size(), MD_THREADS, smg, a);
-    h->launches++;
+    h->launches += 2;
   }
   if (!ls[0].empty()) {
     MdArgs a = base;
