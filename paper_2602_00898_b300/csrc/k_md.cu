@@ -351,7 +351,9 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
   }
 }
 
-__global__ void __launch_bounds__(MD_THREADS) k_md_leaf(MdArgs a) {
+// up to LEAF_WARPS warps a CTA, one leaf each (its registers allow 10)
+constexpr int LEAF_WARPS = 10;
+__global__ void __launch_bounds__(LEAF_WARPS * 32) k_md_leaf(MdArgs a) {
   FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1114,7 +1116,7 @@ fp_status run_local_order(fp_handle* h) {
     a.nnodes_launch = (int32_t)ls[0].size();
     const size_t slice = leaf_slice(mmax[0]);
     int nw = (int)(220 * 1024 / slice);
-    nw = nw < 1 ? 1 : (nw > MD_THREADS / 32 ? MD_THREADS / 32 : nw);
+    nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
     size_t sm = slice * nw;
     if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
     a.slice_bytes = (int64_t)slice;
@@ -1158,7 +1160,7 @@ fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count,
            d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key, queue};
   const size_t slice = leaf_slice(mmax);
   int nw = (int)(220 * 1024 / slice);
-  nw = nw < 1 ? 1 : (nw > MD_THREADS / 32 ? MD_THREADS / 32 : nw);
+  nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
   size_t sm = slice * nw;
   if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
   a.slice_bytes = (int64_t)slice;
