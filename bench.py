@@ -584,8 +584,12 @@ def run_batch(args):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
+        # an NVTX range per timed step lets a profiler select exactly these
+        # launches (ncu --nvtx --nvtx-include "batch_step/")
+        torch.cuda.nvtx.range_push("batch_step")
         st = order_all()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         times.append(time.perf_counter() - t)
         assert st == 0
         launches += sum(int(it.launches) for it in items)
