@@ -298,6 +298,34 @@ fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_o
                                  const int32_t* h_codes);
 
 /*
+ * The fused batch as a handle (the survey's batch create / permute /
+ * symbolic; the paper has no batch form): fp_batch_create builds ONE handle
+ * for the disjoint union of the items' meshes (device faces read on `stream`
+ * during the call; patch caps as in fp_batch_order: item->patch_cap, or the
+ * autotuned cap of its size class); fp_batch_permute orders it and writes
+ * every item's d_perm / d_iperm (mesh-local numbering, each may be NULL) and
+ * status, chosen_cap and, with a network attached by fp_set_priority_net,
+ * the learned_* and fill_* fields; fp_batch_symbolic writes every item's
+ * d_parent / d_colcount (indexed by the mesh's own positions, -1 for roots)
+ * and nnzL, flops. item 0's `launches` counts the handle's launches so far.
+ * `items` must be the array (and `count` its length) given to
+ * fp_batch_create; only their output pointers may differ. The handle's
+ * single-mesh calls see the union (fp_get_tree: the union's tree, with
+ * every mesh's subtree below an empty super-tree; fp_permute: the union's
+ * order); fp_destroy frees it. Synchronous (each call waits for its stream).
+ * Errors: FP_ERR_INVALID_ARG (count < 1, NULL items or options, an item
+ * with negative sizes or NULL faces, options other than dof_per_vertex 1,
+ * nd_level 0 and debug_dump 0, totals beyond int32, a corner outside its
+ * own mesh; permute/symbolic: not a batch handle of `count` items),
+ * FP_ERR_STATE (symbolic before permute; a poisoned handle), and those of
+ * fp_create_from_faces, fp_permute, fp_symbolic.
+ */
+fp_status fp_batch_create(const fp_batch_item* items, int32_t count, const fp_options* opts, void* stream,
+                          fp_handle** out);
+fp_status fp_batch_permute(fp_handle* h, fp_batch_item* items, int32_t count);
+fp_status fp_batch_symbolic(fp_handle* h, fp_batch_item* items, int32_t count);
+
+/*
  * Autotuner for fp_batch_order: for every size class of the items (vertex
  * counts below 8k, 32k, 128k, 512k, and above) it orders the class's largest
  * item once per candidate cap in {128, 256, 384, 512}, timing create +

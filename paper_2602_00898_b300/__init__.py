@@ -81,6 +81,10 @@ def lib() -> ctypes.CDLL:
             "fp_batch_order": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32]),
             "fp_batch_autotune": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, P32]),
             "fp_batch_order_learned": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, i32, P32]),
+            "fp_batch_create": (i32, [ctypes.POINTER(fp_batch_item), i32, opt, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+            "fp_batch_permute": (i32, [ctypes.c_void_p, ctypes.POINTER(fp_batch_item), i32]),
+            "fp_batch_symbolic": (i32, [ctypes.c_void_p, ctypes.POINTER(fp_batch_item), i32]),
             "fp_graph_from_faces_static": (i32, [vp, i64, i32, vp, vp, i64, P64, vp]),
             "fp_set_priority_net": (i32, [vp, P32]),
             "fp_learned_stats": (i32, [vp, P32, P32, P64, P64]),
@@ -271,6 +275,25 @@ def fp_batch_order_learned(items, codes, opts: fp_options | None = None, n_worke
     assert c.size == GNN_NPARAMS
     return int(lib().fp_batch_order_learned(items, len(items), ctypes.byref(opts), n_workers,
                                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+
+
+def fp_batch_create(items, opts: fp_options | None = None, stream=None):
+    """The fused batch as one handle over the disjoint union of the items'
+    meshes (items: a ctypes array of fp_batch_item). Returns the handle."""
+    opts = opts or fp_default_options()
+    h = ctypes.c_void_p()
+    _check(lib().fp_batch_create(items, len(items), ctypes.byref(opts), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def fp_batch_permute(h, items) -> None:
+    """Orders the union and writes every item's perm / iperm and host fields."""
+    _check(lib().fp_batch_permute(h, items, len(items)), h)
+
+
+def fp_batch_symbolic(h, items) -> None:
+    """Every item's parent / colcount, nnzL and flops."""
+    _check(lib().fp_batch_symbolic(h, items, len(items)), h)
 
 
 def fp_batch_autotune(items, opts: fp_options | None = None) -> list[int]:

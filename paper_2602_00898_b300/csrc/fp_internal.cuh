@@ -71,6 +71,9 @@ struct Segments {
   std::vector<int32_t> h_root;       // [M] root node (-1: an empty mesh)
   std::vector<int32_t> h_k;          // [M] patches of every mesh
   std::vector<int32_t> h_posoff;     // [M] first position of every mesh in the union's order
+  std::vector<int32_t> h_cap;        // [M] patch cap of every mesh
+  int32_t* d_posoff = nullptr;       // [M] device copy of h_posoff
+  void* d_outs = nullptr;            // [M] device table of the items' output pointers
   // learned form, per mesh: leaves considered, learned orders kept, summed
   // plain and chosen leaf fills
   std::vector<unsigned long long> h_learned;   // [M][4]

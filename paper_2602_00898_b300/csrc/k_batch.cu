@@ -120,13 +120,29 @@ __global__ void k_vertex_mesh(const int32_t* __restrict__ voff, int32_t M, int32
 
 // Per-mesh outputs from the union's: position p holds union vertex v of mesh
 // m; both are renumbered inside the mesh (its positions start at posoff[m],
-// its vertices at voff[m]); the elimination tree never leaves a mesh. nnz(L)
-// and flops per mesh are the sums of colcount and colcount^2 over its
-// positions (a warp's positions usually lie in one mesh: one atomic a warp).
-__global__ void k_batch_out(const int32_t* __restrict__ perm, const int32_t* __restrict__ parent,
-                            const int32_t* __restrict__ colcount, int32_t n, const int32_t* __restrict__ vmesh,
-                            const int32_t* __restrict__ voff, const int32_t* __restrict__ posoff,
-                            const OutSeg* __restrict__ outs, unsigned long long* __restrict__ sums) {
+// its vertices at voff[m]).
+__global__ void k_batch_perm_out(const int32_t* __restrict__ perm, int32_t n, const int32_t* __restrict__ vmesh,
+                                 const int32_t* __restrict__ voff, const int32_t* __restrict__ posoff,
+                                 const OutSeg* __restrict__ outs) {
+  FP_PDL_WAIT();
+  for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int32_t v = perm[p];
+    const int32_t m = vmesh[v];
+    const int32_t lp = p - posoff[m], lv = v - voff[m];
+    const OutSeg o = outs[m];
+    if (o.perm) o.perm[lp] = lv;
+    if (o.iperm) o.iperm[lv] = lp;
+  }
+}
+
+// The elimination tree never leaves a mesh (no union edge joins two
+// meshes): parents are renumbered like positions. nnz(L) and flops per mesh
+// are the sums of colcount and colcount^2 over its positions (a warp's
+// positions usually lie in one mesh: one atomic pair a warp).
+__global__ void k_batch_sym_out(const int32_t* __restrict__ perm, const int32_t* __restrict__ parent,
+                                const int32_t* __restrict__ colcount, int32_t n, const int32_t* __restrict__ vmesh,
+                                const int32_t* __restrict__ posoff, const OutSeg* __restrict__ outs,
+                                unsigned long long* __restrict__ sums) {
   FP_PDL_WAIT();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -135,13 +151,10 @@ __global__ void k_batch_out(const int32_t* __restrict__ perm, const int32_t* __r
     int32_t m = -1;
     unsigned long long c = 0, c2 = 0;
     if (live) {
-      const int32_t v = perm[p];
-      m = vmesh[v];
-      const int32_t lp = (int32_t)p - posoff[m], lv = v - voff[m];
+      m = vmesh[perm[p]];
+      const int32_t lp = (int32_t)p - posoff[m];
       const OutSeg o = outs[m];
       const int32_t cc = colcount[p];
-      if (o.perm) o.perm[lp] = lv;
-      if (o.iperm) o.iperm[lv] = lp;
       if (o.parent) {
         const int32_t q = parent[p];
         o.parent[lp] = q < 0 ? -1 : q - posoff[m];
@@ -168,8 +181,8 @@ __global__ void k_batch_out(const int32_t* __restrict__ perm, const int32_t* __r
   }
 }
 
-// Whether the fused form takes the batch (else the pool): one DOF per vertex,
-// no explicit depth, totals within int32.
+// Whether the fused form takes the batch: one DOF per vertex, no explicit
+// depth, no stage records, valid items, totals within int32.
 bool fused_ok(const fp_batch_item* items, int32_t count, const fp_options& o) {
   if (o.dof_per_vertex != 1 || o.nd_level != 0 || o.debug_dump != 0) return false;
   int64_t N = 0, F = 0;
@@ -182,7 +195,11 @@ bool fused_ok(const fp_batch_item* items, int32_t count, const fp_options& o) {
   return N <= INT32_MAX && F <= INT32_MAX / 6;
 }
 
-fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s, const int32_t* codes) {
+// The union handle: union faces gathered on `s`, the CSR built by the
+// single-mesh path, then the per-mesh lookups.
+fp_status fused_create(const fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s,
+                       fp_handle** out) {
+  *out = nullptr;
   int device = 0;
   cudaGetDevice(&device);
   std::vector<int32_t> voff(M + 1, 0), caps(M);
@@ -206,11 +223,7 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
   }
   // pageable source: the call returns once the table is staged
   cudaMemcpyAsync(d_fs, fs.data(), sizeof(FaceSeg) * (size_t)M, cudaMemcpyHostToDevice, s);
-  int64_t launches = 0;
-  if (F > 0) {
-    launch_pdl(s, k_union_faces, grid_for(F, 256), 256, 0, (const FaceSeg*)d_fs, M, F, d_faces);
-    ++launches;
-  }
+  if (F > 0) launch_pdl(s, k_union_faces, grid_for(F, 256), 256, 0, (const FaceSeg*)d_fs, M, F, d_faces);
   fp_options o = base;
   o.patch_cap = caps[0];
   fp_handle* h = nullptr;
@@ -218,17 +231,19 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
   cudaFreeAsync(d_faces, s);
   cudaFreeAsync(d_fs, s);
   if (st != FP_OK) return st;
+  if (F > 0) h->launches++;
   Segments* sg = new Segments();
   h->seg = sg;
   sg->M = M;
   sg->h_voff = voff;
+  sg->h_cap = caps;
   int32_t* d_voff = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(M + 1));
   int32_t* d_cap = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
   int32_t* d_vmesh = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
   sg->mroot = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
-  int32_t* parent = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
-  int32_t* colcount = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
-  if (!d_voff || !d_cap || !d_vmesh || !sg->mroot || !parent || !colcount) {
+  sg->d_posoff = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
+  sg->d_outs = dev_alloc(h, sizeof(OutSeg) * (size_t)M);
+  if (!d_voff || !d_cap || !d_vmesh || !sg->mroot || !sg->d_posoff || !sg->d_outs) {
     fp_destroy(h);
     return fail(nullptr, FP_ERR_OUT_OF_MEMORY, "batch union arrays");
   }
@@ -236,51 +251,88 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
   cudaMemcpyAsync(d_cap, caps.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, s);
   if (N > 0) FP_LAUNCH(h, k_vertex_mesh, grid_for(N, 256), 256, 0, (const int32_t*)d_voff, M, N, d_vmesh);
   sg->v = SegView{d_vmesh, d_voff, d_cap};
-  int64_t nnz = 0, fl = 0;
-  if (codes) st = fp_set_priority_net(h, codes);
-  if (st == FP_OK) st = fp_permute(h, nullptr, nullptr);
-  if (st == FP_OK) st = fp_symbolic(h, parent, colcount, &nnz, &fl);
-  if (st == FP_OK) {
-    std::vector<OutSeg> outs(M);
-    for (int32_t m = 0; m < M; ++m) outs[m] = {items[m].d_perm, items[m].d_iperm, items[m].d_parent, items[m].d_colcount};
-    OutSeg* d_outs = (OutSeg*)dev_alloc(h, sizeof(OutSeg) * (size_t)M);
-    int32_t* d_pos = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)M);
-    unsigned long long* d_sums = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 2 * (size_t)M);
-    std::vector<unsigned long long> sums(2 * (size_t)M, 0ull);
-    if (!d_outs || !d_pos || !d_sums) {
-      st = fail(h, FP_ERR_OUT_OF_MEMORY, "batch outputs");
-    } else {
-      cudaMemcpyAsync(d_outs, outs.data(), sizeof(OutSeg) * (size_t)M, cudaMemcpyHostToDevice, s);
-      cudaMemcpyAsync(d_pos, sg->h_posoff.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, s);
-      cudaMemsetAsync(d_sums, 0, sizeof(unsigned long long) * 2 * (size_t)M, s);
-      if (N > 0)
-        FP_LAUNCH(h, k_batch_out, grid_for(N, 256), 256, 0, (const int32_t*)h->perm, (const int32_t*)parent,
-                  (const int32_t*)colcount, N, (const int32_t*)d_vmesh, (const int32_t*)d_voff,
-                  (const int32_t*)d_pos, (const OutSeg*)d_outs, d_sums);
-      cudaMemcpyAsync(sums.data(), d_sums, sizeof(unsigned long long) * 2 * (size_t)M, cudaMemcpyDeviceToHost, s);
-      cudaError_t e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) st = check_cuda(h, e, "batch outputs");
-    }
-    if (st == FP_OK)
-      for (int32_t m = 0; m < M; ++m) {
-        fp_batch_item& it = items[m];
-        it.status = FP_OK;
-        it.chosen_cap = caps[m];
-        it.nnzL = (int64_t)sums[2 * m];
-        it.flops = (int64_t)sums[2 * m + 1];
-        it.launches = 0;
-        it.learned_leaves = it.learned_kept = 0;
-        it.fill_plain = it.fill_chosen = 0;
-        if (codes && sg->h_learned.size() == 4 * (size_t)M) {
-          const unsigned long long* L = &sg->h_learned[4 * (size_t)m];
-          it.learned_kept = (int32_t)L[0];
-          it.fill_plain = (int64_t)L[1];
-          it.fill_chosen = (int64_t)L[2];
-          it.learned_leaves = (int32_t)L[3];
-        }
-      }
-    if (st == FP_OK) items[0].launches = launches + fp_launch_count(h);
+  fp_status e = check_cuda(h, cudaGetLastError(), "batch union");
+  if (e != FP_OK) {
+    fp_destroy(h);
+    return e;
   }
+  *out = h;
+  return FP_OK;
+}
+
+// Uploads the items' output pointers (host vectors must stay alive until the
+// copy is staged: pageable memory, so the call returns after staging).
+void upload_outs(fp_handle* h, const fp_batch_item* items) {
+  Segments* sg = h->seg;
+  std::vector<OutSeg> outs(sg->M);
+  for (int32_t m = 0; m < sg->M; ++m) outs[m] = {items[m].d_perm, items[m].d_iperm, items[m].d_parent, items[m].d_colcount};
+  cudaMemcpyAsync(sg->d_outs, outs.data(), sizeof(OutSeg) * (size_t)sg->M, cudaMemcpyHostToDevice, h->stream);
+}
+
+fp_status fused_permute(fp_handle* h, fp_batch_item* items) {
+  Segments* sg = h->seg;
+  const int32_t M = sg->M, N = h->n;
+  FP_TRY(fp_permute(h, nullptr, nullptr));
+  upload_outs(h, items);
+  cudaMemcpyAsync(sg->d_posoff, sg->h_posoff.data(), sizeof(int32_t) * (size_t)M, cudaMemcpyHostToDevice, h->stream);
+  if (N > 0)
+    FP_LAUNCH(h, k_batch_perm_out, grid_for(N, 256), 256, 0, (const int32_t*)h->perm, N, sg->v.vmesh, sg->v.voff,
+              (const int32_t*)sg->d_posoff, (const OutSeg*)sg->d_outs);
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  for (int32_t m = 0; m < M; ++m) {
+    fp_batch_item& it = items[m];
+    it.status = FP_OK;
+    it.chosen_cap = sg->h_cap[m];
+    it.launches = 0;
+    it.learned_leaves = it.learned_kept = 0;
+    it.fill_plain = it.fill_chosen = 0;
+    if (h->qnet && sg->h_learned.size() == 4 * (size_t)M) {
+      const unsigned long long* L = &sg->h_learned[4 * (size_t)m];
+      it.learned_kept = (int32_t)L[0];
+      it.fill_plain = (int64_t)L[1];
+      it.fill_chosen = (int64_t)L[2];
+      it.learned_leaves = (int32_t)L[3];
+    }
+  }
+  items[0].launches = h->launches;
+  return FP_OK;
+}
+
+fp_status fused_symbolic(fp_handle* h, fp_batch_item* items) {
+  Segments* sg = h->seg;
+  const int32_t M = sg->M, N = h->n;
+  int32_t* parent = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  int32_t* colcount = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+  unsigned long long* d_sums = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * 2 * (size_t)M);
+  if (!parent || !colcount || !d_sums) return fail(h, FP_ERR_OUT_OF_MEMORY, "batch symbolic outputs");
+  int64_t nnz = 0, fl = 0;
+  FP_TRY(fp_symbolic(h, parent, colcount, &nnz, &fl));
+  upload_outs(h, items);
+  cudaMemsetAsync(d_sums, 0, sizeof(unsigned long long) * 2 * (size_t)M, h->stream);
+  if (N > 0)
+    FP_LAUNCH(h, k_batch_sym_out, grid_for(N, 256), 256, 0, (const int32_t*)h->perm, (const int32_t*)parent,
+              (const int32_t*)colcount, N, sg->v.vmesh, (const int32_t*)sg->d_posoff, (const OutSeg*)sg->d_outs,
+              d_sums);
+  std::vector<unsigned long long> sums(2 * (size_t)M, 0ull);
+  cudaMemcpyAsync(sums.data(), d_sums, sizeof(unsigned long long) * 2 * (size_t)M, cudaMemcpyDeviceToHost, h->stream);
+  int32_t st = 0;
+  FP_TRY(sync_status(h, &st));
+  for (void* p : {(void*)parent, (void*)colcount, (void*)d_sums}) dev_free(h, p);
+  for (int32_t m = 0; m < M; ++m) {
+    items[m].nnzL = (int64_t)sums[2 * m];
+    items[m].flops = (int64_t)sums[2 * m + 1];
+  }
+  items[0].launches = h->launches;
+  return FP_OK;
+}
+
+fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cudaStream_t s, const int32_t* codes) {
+  fp_handle* h = nullptr;
+  FP_TRY(fused_create(items, M, base, s, &h));
+  fp_status st = codes ? fp_set_priority_net(h, codes) : FP_OK;
+  if (st == FP_OK) st = fused_permute(h, items);
+  if (st == FP_OK) st = fused_symbolic(h, items);
   fp_destroy(h);
   return st;
 }
@@ -397,4 +449,30 @@ extern "C" fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, cons
   if (h_caps)
     for (int c = 0; c < N_CLASSES; ++c) h_caps[c] = chosen[c];
   return FP_OK;
+}
+
+extern "C" fp_status fp_batch_create(const fp_batch_item* items, int32_t count, const fp_options* opts, void* stream,
+                                     fp_handle** out) {
+  if (!out) return fail(nullptr, FP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !items || !opts) return fail(nullptr, FP_ERR_INVALID_ARG, "bad batch arguments");
+  if (!fused_ok(items, count, *opts))
+    return fail(nullptr, FP_ERR_INVALID_ARG,
+                "a batch handle takes dof_per_vertex 1, nd_level 0, debug_dump 0 and valid items within int32 totals");
+  return fused_create(items, count, *opts, (cudaStream_t)stream, out);
+}
+
+extern "C" fp_status fp_batch_permute(fp_handle* h, fp_batch_item* items, int32_t count) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (!h->seg || !items || count != h->seg->M) return fail(h, FP_ERR_INVALID_ARG, "not a batch handle of this many items");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  return fused_permute(h, items);
+}
+
+extern "C" fp_status fp_batch_symbolic(fp_handle* h, fp_batch_item* items, int32_t count) {
+  if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
+  if (!h->seg || !items || count != h->seg->M) return fail(h, FP_ERR_INVALID_ARG, "not a batch handle of this many items");
+  if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
+  if (!h->permuted) return fail(h, FP_ERR_STATE, "fp_batch_permute first");
+  return fused_symbolic(h, items);
 }

@@ -249,3 +249,86 @@ def test_fused_learned_matches_oracle_and_pool():
             (jt.learned_leaves, jt.learned_kept, jt.fill_plain, jt.fill_chosen)
         for tx, ty in zip(outs, pouts):
             assert torch.equal(tx, ty)
+
+
+# ---- the fused batch as a handle: fp_batch_create / permute / symbolic ----
+
+def test_batch_handle_trio_matches_fused_order():
+    """create + permute + symbolic on the union handle gives exactly what
+    fp_batch_order gives; the perms are out after permute, the symbolic
+    outputs after symbolic; with a network attached, the learned choices."""
+    meshes = _mix(10, 41, 1500, 30000) + _tiny_meshes()
+    caps = [128, 256, 384, 512, 200] * 2 + [16, 16, 4, 2, 40]
+    ns = [m.n for m in meshes]
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    a = fp.make_batch(faces, ns, caps)
+    b = fp.make_batch(faces, ns, caps)
+    assert fp.fp_batch_order(a, fp.fp_default_options(), n_workers=0) == 0
+    for _, outs in b.tensors:
+        outs[2].fill_(-7)
+    h = fp.fp_batch_create(b)
+    try:
+        fp.fp_batch_permute(h, b)
+        torch.cuda.synchronize()
+        for m, (_, ox), (_, oy) in zip(meshes, a.tensors, b.tensors):
+            assert torch.equal(ox[0][:m.n], oy[0][:m.n]) and torch.equal(ox[1][:m.n], oy[1][:m.n])
+            assert (oy[2] == -7).all()               # parents only after symbolic
+        fp.fp_batch_symbolic(h, b)
+        assert fp.fp_get_tree(h) >= 1                # the union's tree
+        assert b[0].launches > 0
+    finally:
+        fp.fp_destroy(h)
+    torch.cuda.synchronize()
+    for m, x, y, (_, ox), (_, oy) in zip(meshes, a, b, a.tensors, b.tensors):
+        assert (x.nnzL, x.flops, x.chosen_cap, x.status) == (y.nnzL, y.flops, y.chosen_cap, y.status)
+        for tx, ty in zip(ox, oy):
+            assert torch.equal(tx[:m.n], ty[:m.n])
+    _check_item(meshes[3], b[3], b.tensors[3][1])
+    # learned: the network attached to the union handle
+    codes = fp.pack_params(M.gnn_weights(31), np.int32)
+    c = fp.make_batch(faces, ns, caps)
+    d = fp.make_batch(faces, ns, caps)
+    assert fp.fp_batch_order_learned(c, codes, fp.fp_default_options(), n_workers=0) == 0
+    h = fp.fp_batch_create(d)
+    try:
+        fp.fp_set_priority_net(h, codes)
+        fp.fp_batch_permute(h, d)
+        fp.fp_batch_symbolic(h, d)
+    finally:
+        fp.fp_destroy(h)
+    torch.cuda.synchronize()
+    for m, x, y, (_, ox), (_, oy) in zip(meshes, c, d, c.tensors, d.tensors):
+        assert (x.nnzL, x.learned_leaves, x.learned_kept, x.fill_plain, x.fill_chosen) == \
+            (y.nnzL, y.learned_leaves, y.learned_kept, y.fill_plain, y.fill_chosen)
+        assert torch.equal(ox[0][:m.n], oy[0][:m.n])
+
+
+def test_batch_handle_errors():
+    meshes = _mix(3, 43)
+    ns = [m.n for m in meshes]
+    faces = [torch.from_numpy(m.faces).cuda() for m in meshes]
+    items = fp.make_batch(faces, ns, [256] * 3)
+    with pytest.raises(fp.FpError) as e:
+        fp.fp_batch_create(items, fp.fp_default_options(dof_per_vertex=3))
+    assert e.value.status == 1
+    bad = torch.tensor([[0, 1, 12]], dtype=torch.int32, device="cuda")   # vertex 12 of a 10-vertex mesh
+    with pytest.raises(fp.FpError) as e:
+        fp.fp_batch_create(fp.make_batch(faces + [bad], ns + [10], [256] * 4))
+    assert e.value.status == 1
+    h = fp.fp_batch_create(items)
+    try:
+        with pytest.raises(fp.FpError) as e:
+            fp.fp_batch_symbolic(h, items)                   # before permute
+        assert e.value.status == 6
+        assert fp.lib().fp_batch_permute(h, items, 2) == 1   # count differs from the create call
+        fp.fp_batch_permute(h, items)
+        fp.fp_batch_symbolic(h, items)
+    finally:
+        fp.fp_destroy(h)
+    for m, it, (_, outs) in zip(meshes, items, items.tensors):
+        _check_item(m, it, outs)
+    single = fp.fp_create_from_faces(faces[0], ns[0], fp.fp_default_options())
+    try:
+        assert fp.lib().fp_batch_permute(single, items, 3) == 1   # not a batch handle
+    finally:
+        fp.fp_destroy(single)
