@@ -21,8 +21,10 @@ constexpr int ROW_WARPS = 8;         // warps per CTA in the warp-per-row kernel
 // ---- faces ------------------------------------------------------------------------
 
 // Counts the raw entries of every row; the count each increment returns is the
-// entry's slot in its row, kept (6 per face: the two ends of each edge) so
-// that the fill pass places entries without atomics.
+// entry's slot in its row, kept (for every face edge, its slot in both end
+// rows) so that the fill pass places entries without atomics. Each corner
+// takes the slots of its two face edges (fewer where an edge is degenerate)
+// with one atomic: three a face.
 __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int32_t n, int32_t* __restrict__ cnt,
                              int2* __restrict__ slots, int32_t* status) {
   FP_PDL_WAIT();
@@ -32,12 +34,19 @@ __global__ void k_face_count(const int32_t* __restrict__ faces, int64_t nf, int3
       atomicOr(status, ST_BAD_INDEX);
       continue;
     }
+    // corner i owns edge i = (c[i], c[i+1]) first, then edge i-1 = (c[i-1], c[i])
+    int32_t out[3], base[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[i] = c[i] != c[(i + 1) % 3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int32_t k = out[i] + out[(i + 2) % 3];
+      base[i] = k ? atomicAdd(&cnt[c[i]], k) : 0;
+    }
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      const int32_t a = c[e], b = c[(e + 1) % 3];
-      int2 sl = make_int2(0, 0);
-      if (a != b) sl = make_int2(atomicAdd(&cnt[a], 1), atomicAdd(&cnt[b], 1));
-      slots[3 * f + e] = sl;
+      const int j = (e + 1) % 3;
+      slots[3 * f + e] = out[e] ? make_int2(base[e], base[j] + out[j]) : make_int2(0, 0);
     }
   }
 }
