@@ -269,7 +269,10 @@ void upload_outs(fp_handle* h, const fp_batch_item* items) {
   cudaMemcpyAsync(sg->d_outs, outs.data(), sizeof(OutSeg) * (size_t)sg->M, cudaMemcpyHostToDevice, h->stream);
 }
 
-fp_status fused_permute(fp_handle* h, fp_batch_item* items) {
+// wait: return only when the outputs are complete (the public call); the
+// fused batch goes straight on to the symbolic stage, whose host planning
+// then overlaps the ordering kernels, and waits there.
+fp_status fused_permute(fp_handle* h, fp_batch_item* items, bool wait) {
   Segments* sg = h->seg;
   const int32_t M = sg->M, N = h->n;
   FP_TRY(fp_permute(h, nullptr, nullptr));
@@ -278,8 +281,11 @@ fp_status fused_permute(fp_handle* h, fp_batch_item* items) {
   if (N > 0)
     FP_LAUNCH(h, k_batch_perm_out, grid_for(N, 256), 256, 0, (const int32_t*)h->perm, N, sg->v.vmesh, sg->v.voff,
               (const int32_t*)sg->d_posoff, (const OutSeg*)sg->d_outs);
-  int32_t st = 0;
-  FP_TRY(sync_status(h, &st));
+  FP_CHECK_LAUNCH(h, "batch permutation outputs");
+  if (wait) {
+    int32_t st = 0;
+    FP_TRY(sync_status(h, &st));
+  }
   for (int32_t m = 0; m < M; ++m) {
     fp_batch_item& it = items[m];
     it.status = FP_OK;
@@ -331,7 +337,7 @@ fp_status run_fused(fp_batch_item* items, int32_t M, const fp_options& base, cud
   fp_handle* h = nullptr;
   FP_TRY(fused_create(items, M, base, s, &h));
   fp_status st = codes ? fp_set_priority_net(h, codes) : FP_OK;
-  if (st == FP_OK) st = fused_permute(h, items);
+  if (st == FP_OK) st = fused_permute(h, items, false);
   if (st == FP_OK) st = fused_symbolic(h, items);
   fp_destroy(h);
   return st;
@@ -466,7 +472,7 @@ extern "C" fp_status fp_batch_permute(fp_handle* h, fp_batch_item* items, int32_
   if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
   if (!h->seg || !items || count != h->seg->M) return fail(h, FP_ERR_INVALID_ARG, "not a batch handle of this many items");
   if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
-  return fused_permute(h, items);
+  return fused_permute(h, items, true);
 }
 
 extern "C" fp_status fp_batch_symbolic(fp_handle* h, fp_batch_item* items, int32_t count) {

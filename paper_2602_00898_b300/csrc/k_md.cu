@@ -965,13 +965,13 @@ fp_status run_local_order(fp_handle* h) {
   cudaError_t e = cudaEventSynchronize(ev);
   if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
   const int32_t st = *h->h_status;
-  std::vector<int32_t> hs(hsp, hsp + nn);
+  h->node_size_host.assign(hsp, hsp + nn);
+  const std::vector<int32_t>& hs = h->node_size_host;
   if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
   // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
   // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3], early;
   int mmax[3] = {0, 0, 0};
-  h->node_size_host = hs;
   for (int64_t t = 0; t < nn; ++t) {
     const int m = hs[t];
     if (m == 0) continue;

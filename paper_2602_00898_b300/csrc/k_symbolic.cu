@@ -905,14 +905,15 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
   // launch lists: every leaf (no non-empty child; they need no other node's
   // result), largest first, in one launch; then the inner nodes depth by
   // depth, deepest first (a node's elements come from its descendants)
-  std::vector<int32_t> hsz = h->node_size_host;
-  if ((int64_t)hsz.size() != nn) {
-    hsz.assign(nn, 0);
-    cudaError_t e = cudaMemcpyAsync(hsz.data(), h->node_size, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, h->stream);
+  if ((int64_t)h->node_size_host.size() != nn) {
+    h->node_size_host.assign(nn, 0);
+    cudaError_t e = cudaMemcpyAsync(h->node_size_host.data(), h->node_size, sizeof(int32_t) * nn,
+                                    cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "node sizes");
     int32_t st0 = 0;
     FP_TRY(sync_status(h, &st0));
   }
+  const std::vector<int32_t>& hsz = h->node_size_host;
   // below[t]: some descendant of t holds vertices. A node with empty children
   // can still have them (a child split with an empty separator), and such a
   // node must wait for its descendants' elements.
@@ -928,7 +929,16 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     if (!below[t]) leaves.push_back((int32_t)t);
     else inner[63 - __builtin_clzll((unsigned long long)t + 1)].push_back((int32_t)t);
   }
-  std::stable_sort(leaves.begin(), leaves.end(), [&](int32_t x, int32_t y) { return hsz[x] > hsz[y]; });
+  {
+    // largest first, ties in node order: a counting sort by size
+    int32_t smax = 0;
+    for (int32_t t : leaves) smax = std::max(smax, hsz[t]);
+    std::vector<int32_t> cnt((size_t)smax + 2, 0), sorted(leaves.size());
+    for (int32_t t : leaves) ++cnt[(size_t)(smax - hsz[t]) + 1];
+    for (size_t i = 1; i < cnt.size(); ++i) cnt[i] += cnt[i - 1];
+    for (int32_t t : leaves) sorted[(size_t)cnt[(size_t)(smax - hsz[t])]++] = t;
+    leaves.swap(sorted);
+  }
   std::vector<std::pair<int64_t, int32_t>> launches;     // (offset in flat, count)
   launches.push_back({0, (int32_t)leaves.size()});
   flat = leaves;
