@@ -454,19 +454,91 @@ fp_status fp_gnn_scores(fp_handle* h, const int32_t* h_codes, int32_t* d_scores,
   return FP_OK;
 }
 
-fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL, int64_t* h_flops) {
+namespace {
+
+// Host destinations of the symbolic outputs (the host-buffer entry point):
+// the columns outside the tree's top EARLY_SYM_LEVELS levels are final before
+// those levels' launches run; they are expanded to DOFs and copied to the
+// host on an auxiliary stream while the top levels run, and only the top
+// nodes' column ranges follow at the end.
+struct SymbolicHost {
+  int32_t* parent;
+  int32_t* colcount;
+};
+constexpr int EARLY_SYM_LEVELS = 5;
+// below this many output bytes the copies are short and the early path's
+// extra copy calls cost more than they hide
+constexpr int64_t EARLY_SYM_MIN_BYTES = 16 << 20;
+
+fp_status symbolic_impl(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL, int64_t* h_flops,
+                        const SymbolicHost* ho) {
   if (!h) return fail(nullptr, FP_ERR_INVALID_ARG, "NULL handle");
   if (h->poisoned) return fail(h, FP_ERR_STATE, "handle poisoned by an earlier failure");
   if (!h->permuted) return fail(h, FP_ERR_STATE, "fp_symbolic before fp_permute");
   const int32_t n = h->n, b = h->b;
+  const int64_t N = (int64_t)n * b;
   int32_t* par = (b == 1 && d_parent) ? d_parent : (int32_t*)dev_alloc(h, sizeof(int32_t) * (n > 0 ? n : 1));
   int32_t* cc = (b == 1 && d_colcount) ? d_colcount : (int32_t*)dev_alloc(h, sizeof(int32_t) * (n > 0 ? n : 1));
   if (!par || !cc) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic outputs");
+  AuxStream* ax = nullptr;
+  int32_t* top_begin = nullptr;
+  int64_t ntop = 0;
+  bool queued = false;
+  if (ho && N > 0 && d_parent && d_colcount && 8 * N >= EARLY_SYM_MIN_BYTES) {
+    ax = aux_stream(h->device, 0);
+    top_begin = pinned_scratch();
+    if (!ax || !top_begin) return fail(h, FP_ERR_CUDA, "auxiliary stream");
+    ntop = std::min<int64_t>(h->nnodes, ((int64_t)1 << EARLY_SYM_LEVELS) - 1);
+    // read after run_symbolic's final sync
+    cudaMemcpyAsync(top_begin, h->node_begin, sizeof(int32_t) * ntop, cudaMemcpyDeviceToHost, h->stream);
+    h->sym_early_depth = EARLY_SYM_LEVELS;
+    h->sym_early = [&](cudaEvent_t ev) {
+      cudaStreamWaitEvent(ax->s, ev, 0);
+      if (b > 1) launch_dof_expand_symbolic(h, par, cc, d_parent, d_colcount, 0, n, ax->s);
+      if (ho->parent) cudaMemcpyAsync(ho->parent, d_parent, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ax->s);
+      if (ho->colcount) cudaMemcpyAsync(ho->colcount, d_colcount, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, ax->s);
+      cudaEventRecord(ax->join, ax->s);
+      queued = true;
+    };
+  }
   int64_t nnz = 0, fl = 0;
-  FP_TRY(run_symbolic(h, par, cc, &nnz, &fl));
+  fp_status st = run_symbolic(h, par, cc, &nnz, &fl);
+  h->sym_early = nullptr;
+  // the host copies of the early pass end before anything below writes the
+  // same host ranges (and before the caller frees the device buffers)
+  if (queued) cudaStreamWaitEvent(h->stream, ax->join, 0);
+  FP_TRY(st);
+  const bool top_only = queued && h->sym_early_fired;
+  auto finish = [&](int32_t v0, int32_t v1) {
+    if (b > 1) launch_dof_expand_symbolic(h, par, cc, d_parent, d_colcount, v0, v1);
+    if (!ho) return;
+    const size_t off = (size_t)v0 * b, len = (size_t)(v1 - v0) * b;
+    if (ho->parent && len)
+      cudaMemcpyAsync(ho->parent + off, d_parent + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, h->stream);
+    if (ho->colcount && len)
+      cudaMemcpyAsync(ho->colcount + off, d_colcount + off, sizeof(int32_t) * len, cudaMemcpyDeviceToHost, h->stream);
+  };
+  if (top_only) {
+    // the top nodes' column ranges, adjacent ones merged (in post-order a
+    // node's columns follow its right child's)
+    std::vector<std::pair<int32_t, int32_t>> r;
+    for (int64_t t = 0; t < ntop; ++t) {
+      const int32_t sz = h->node_size_host[t];
+      if (sz > 0) r.push_back({top_begin[t], top_begin[t] + sz});
+    }
+    std::sort(r.begin(), r.end());
+    for (size_t i = 0; i < r.size();) {
+      size_t j = i + 1;
+      int32_t end = r[i].second;
+      while (j < r.size() && r[j].first == end) end = r[j++].second;
+      finish(r[i].first, end);
+      i = j;
+    }
+  } else if (b > 1 || ho) {
+    finish(0, n);
+  }
+  FP_CHECK_LAUNCH(h, "dof expansion");
   if (b > 1) {
-    launch_dof_expand_symbolic(h, par, cc, d_parent, d_colcount);
-    FP_CHECK_LAUNCH(h, "dof expansion");
     const int64_t B = b;
     const int64_t nnz_d = B * B * nnz - (int64_t)n * B * (B - 1) / 2;
     const int64_t fl_d = B * B * B * fl - B * B * (B - 1) * nnz + (int64_t)n * (B - 1) * B * (2 * B - 1) / 6;
@@ -480,6 +552,12 @@ fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int6
   if (h_nnzL) *h_nnzL = nnz;
   if (h_flops) *h_flops = fl;
   return FP_OK;
+}
+
+}  // namespace
+
+fp_status fp_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* h_nnzL, int64_t* h_flops) {
+  return symbolic_impl(h, d_parent, d_colcount, h_nnzL, h_flops, nullptr);
 }
 
 fp_status fp_get_stage(fp_handle* h, int32_t stage, int32_t index, int32_t* d_out, int64_t cap, int64_t* h_len) {
@@ -606,11 +684,9 @@ fp_status fp_order_faces_host(const int32_t* h_faces, int64_t n_faces, int32_t n
     cudaEventRecord(ax->join, ax->s);
   }
   int64_t nnz = 0, fl = 0;
-  if (st == FP_OK) st = fp_symbolic(h, d_out + 2 * N, d_out + 3 * N, &nnz, &fl);
-  if (st == FP_OK && N > 0) {
-    for (int i = 2; i < 4; ++i)
-      if (hs[i]) cudaMemcpyAsync(hs[i], d_out + i * N, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s);
-  }
+  // parent and colcount reach the host as soon as their columns are final
+  const SymbolicHost ho{h_parent, h_colcount};
+  if (st == FP_OK) st = symbolic_impl(h, d_out + 2 * N, d_out + 3 * N, &nnz, &fl, &ho);
   if (ax) cudaStreamWaitEvent(s, ax->join, 0);     // d_out is freed on `stream` below
   if (st != FP_OK && h) g_create_err = h->err;
   fp_destroy(h);

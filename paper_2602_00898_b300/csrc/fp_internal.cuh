@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <utility>
 #include <vector>
@@ -145,6 +146,14 @@ struct fp_handle {
 
   // the disjoint union of a fused batch (null for one mesh)
   fp::Segments* seg = nullptr;
+
+  // run_symbolic calls sym_early(event) once, on its first pass, as soon as
+  // every column outside the tree's top sym_early_depth levels is final (the
+  // event marks that point on the handle's stream); sym_early_fired says
+  // whether that pass was the one that completed
+  std::function<void(cudaEvent_t)> sym_early;
+  int32_t sym_early_depth = 0;
+  bool sym_early_fired = false;
 
   // stage boundaries kept for fp_get_stage (opt.debug_dump)
   struct StageDump {
@@ -298,8 +307,9 @@ void numeric_stats(const fp_handle* h, int64_t* front_doubles, int64_t* flops, i
 void numeric_release(fp_handle* h);
 // a8: DOF expansion of perm/iperm/parent/colcount (b > 1).
 void launch_dof_expand_perm(fp_handle* h, const int32_t* perm, int32_t* perm_d, int32_t* iperm_d);
+// columns [v0, v1) (v1 < 0: to the end) on stream s (null: the handle's)
 void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32_t* colcount, int32_t* parent_d,
-                                int32_t* colcount_d);
+                                int32_t* colcount_d, int32_t v0 = 0, int32_t v1 = -1, cudaStream_t s = nullptr);
 
 }  // namespace fp
 

@@ -803,11 +803,13 @@ __global__ void k_dof_perm(const int32_t* __restrict__ perm, int32_t n, int32_t 
   }
 }
 
-__global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t* __restrict__ cc, int32_t n, int32_t b,
-                               int32_t* __restrict__ parent_d, int32_t* __restrict__ cc_d) {
+// Expands the columns [v0, v1) (vertex positions) to their DOF columns.
+__global__ void k_dof_symbolic(const int32_t* __restrict__ parent, const int32_t* __restrict__ cc, int32_t v0,
+                               int32_t v1, int32_t b, int32_t* __restrict__ parent_d, int32_t* __restrict__ cc_d) {
   FP_PDL_WAIT();
-  const int64_t N = (int64_t)n * b;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t N = (int64_t)v1 * b;
+  for (int64_t i = (int64_t)v0 * b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t j = (int32_t)(i / b), c = (int32_t)(i % b);
     if (parent_d) parent_d[i] = c < b - 1 ? (int32_t)(i + 1) : (parent[j] < 0 ? -1 : b * parent[j]);
     if (cc_d) cc_d[i] = b * cc[j] - c;
@@ -1184,11 +1186,14 @@ void launch_dof_expand_perm(fp_handle* h, const int32_t* perm, int32_t* perm_d, 
 }
 
 void launch_dof_expand_symbolic(fp_handle* h, const int32_t* parent, const int32_t* colcount, int32_t* parent_d,
-                                int32_t* colcount_d) {
-  const int64_t N = (int64_t)h->n * h->b;
-  if (N == 0) return;
-  ProfScope ps(FP_PROF_PERM, h->stream);
-  FP_LAUNCH(h, k_dof_symbolic, grid_for(N, 256), 256, 0, parent, colcount, h->n, h->b, parent_d, colcount_d);
+                                int32_t* colcount_d, int32_t v0, int32_t v1, cudaStream_t s) {
+  if (v1 < 0) v1 = h->n;
+  const int64_t N = (int64_t)(v1 - v0) * h->b;
+  if (N <= 0) return;
+  if (!s) s = h->stream;
+  ProfScope ps(FP_PROF_PERM, s);
+  launch_pdl(s, k_dof_symbolic, grid_for(N, 256), 256, 0, parent, colcount, v0, v1, h->b, parent_d, colcount_d);
+  h->launches++;
 }
 
 }  // namespace fp

@@ -940,13 +940,17 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     leaves.swap(sorted);
   }
   std::vector<std::pair<int64_t, int32_t>> launches;     // (offset in flat, count)
+  std::vector<int32_t> ldepth;                            // depth of each launch's nodes (leaves: past the tree)
   launches.push_back({0, (int32_t)leaves.size()});
+  ldepth.push_back(h->D + 1);
   flat = leaves;
   for (int32_t d = h->D; d >= 0; --d) {
     if (inner[d].empty()) continue;
     launches.push_back({(int64_t)flat.size(), (int32_t)inner[d].size()});
+    ldepth.push_back(d);
     flat.insert(flat.end(), inner[d].begin(), inner[d].end());
   }
+  h->sym_early_fired = false;
   int32_t* lst = (int32_t*)dev_alloc(h, sizeof(int32_t) * (flat.size() + 1));
   if (!lst) return fail(h, FP_ERR_OUT_OF_MEMORY, "symbolic node lists");
   if (!flat.empty()) {
@@ -966,10 +970,20 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
     fill_i32(h, big + nn, 0, 64);                 // per-launch deferred-node counts
     FP_LAUNCH(h, k_fill_u64, 1, 64, 0, ctr, 0ull, (int64_t)(8 + 32));
     allow_max_dynamic_smem(k_symbolic_nodes);
+    bool early = false;
+    auto fire_early = [&]() {
+      if (early || attempt > 0 || !h->sym_early) return;
+      cudaEvent_t ev = mark_event(h->device);
+      if (ev && cudaEventRecord(ev, h->stream) == cudaSuccess) {
+        h->sym_early(ev);
+        early = true;
+      }
+    };
     for (size_t j = 0; j < launches.size(); ++j) {
       const int64_t off = launches[j].first;
       const int32_t c = launches[j].second;
       if (c == 0) continue;
+      if (ldepth[j] < h->sym_early_depth) fire_early();
       // deferred nodes of launch j reuse its own stretch of `big`
       SymArgs sa{prow, ppair, h->perm, h->node_of, h->node_begin, h->node_size, 0, 0,
                  d_parent, d_colcount, ctr, head, hdr, data, cap_hdr, cap_data, ctr + 2, pool, pool_words,
@@ -991,6 +1005,7 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
       }
     }
     FP_CHECK_LAUNCH(h, "symbolic");
+    fire_early();          // no launch of the top levels: every column is final here
     unsigned long long hs[2] = {0, 0};
     cudaError_t e = cudaMemcpyAsync(hs, ctr, sizeof(hs), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return check_cuda(h, e, "read sums");
@@ -1004,6 +1019,7 @@ fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int
       cap_hdr *= 4; cap_data *= 4; pool_words *= 4;
       continue;
     }
+    h->sym_early_fired = early;
     *nnzL = (int64_t)hs[0];
     *flops = (int64_t)hs[1];
     dev_free(h, prow);
