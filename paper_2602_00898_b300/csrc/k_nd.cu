@@ -345,34 +345,48 @@ __global__ void __launch_bounds__(1024) k_nd_bisect(BisectArgs a) {
     }
     // local quotient subgraph: neighbours in this node with remaining edge weight
     int32_t E = 0;
-    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      const int32_t p = Lg[i];
-      int32_t c = 0;
-      const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
-      // ND_BATCH quotient edges per round: their ends and weights, then the
-      // ends' node and local index
-      for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
-        int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
-          wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          const bool live = q[k] >= 0 && wq[k] > 0;
-          nq[k] = live ? a.patch_node[q[k]] : -1;
-          lq[k] = live ? a.loc[q[k]] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k)
-          if (nq[k] == t) a.ladj[e0 + c++] = lq[k];
+    if (m == a.k) {
+      // the root holding every patch: its local graph is the quotient graph
+      // itself (local index = patch id, every patch in this node, and before
+      // the first separator every edge has weight), copied edge by edge
+      E = a.q_rowptr[m];
+      for (int32_t e = threadIdx.x; e < E; e += blockDim.x) a.ladj[e] = a.q_col[e];
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const int32_t e0 = a.q_rowptr[i];
+        a.ldeg[base + i] = a.q_rowptr[i + 1] - e0;
+        a.lbeg[base + i] = e0;
       }
-      a.ldeg[base + i] = c;
-      a.lbeg[base + i] = e0;
-      E += c;
+      __syncthreads();
+    } else {
+      for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
+        const int32_t p = Lg[i];
+        int32_t c = 0;
+        const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
+        // ND_BATCH quotient edges per round: their ends and weights, then the
+        // ends' node and local index
+        for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
+          int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k) {
+            q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
+            wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k) {
+            const bool live = q[k] >= 0 && wq[k] > 0;
+            nq[k] = live ? a.patch_node[q[k]] : -1;
+            lq[k] = live ? a.loc[q[k]] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k)
+            if (nq[k] == t) a.ladj[e0 + c++] = lq[k];
+        }
+        a.ldeg[base + i] = c;
+        a.lbeg[base + i] = e0;
+        E += c;
+      }
+      E = block_sum(E, red);
     }
-    E = block_sum(E, red);
     const bool sm = m <= a.mcap && E <= a.ecap;
     BisectView v;
     if (sm) {
