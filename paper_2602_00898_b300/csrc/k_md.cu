@@ -1113,22 +1113,40 @@ fp_status run_local_order(fp_handle* h) {
     h->launches += 2;
   }
   if (!ls[0].empty()) {
-    MdArgs a = base;
-    a.nodes = dnodes;
-    a.nnodes_launch = (int32_t)ls[0].size();
-    const size_t slice = leaf_slice(mmax[0]);
-    int nw = (int)(220 * 1024 / slice);
-    nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
-    size_t sm = slice * nw;
-    if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
-    a.slice_bytes = (int64_t)slice;
-    int64_t grid = ((int64_t)ls[0].size() + nw - 1) / nw;
-    const int64_t cap = sms - reserved > 1 ? sms - reserved : 1;
-    if (grid > cap) grid = cap;
-    allow_max_dynamic_smem(k_md_leaf);
+    // two launches when the leaves span both size classes and are many more
+    // than one launch's warps (several waves): those above LEAF_SPLIT
+    // vertices with slices for the largest, then the others with slices for
+    // at most LEAF_SPLIT, so that more warps fit on an SM. With few leaves
+    // one wave holds them all and a second launch would only add its own
+    // largest leaf to the time.
+    constexpr int LEAF_SPLIT = 256;
+    const int64_t nleaf = (int64_t)ls[0].size();
+    const int64_t cap_sms = sms - reserved > 1 ? sms - reserved : 1;
+    const int64_t warps1 = cap_sms * std::max(1, std::min<int>(LEAF_WARPS, (int)(220 * 1024 / leaf_slice(mmax[0]))));
+    int64_t cut = 0;
+    while (cut < nleaf && hs[ls[0][cut]] > LEAF_SPLIT) ++cut;
+    if (cut == 0 || cut == nleaf || nleaf <= 2 * warps1) cut = nleaf;
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
-    launch_pdl(h->stream, k_md_leaf, (unsigned)grid, 32 * nw, sm, a);
-    h->launches++;
+    allow_max_dynamic_smem(k_md_leaf);
+    for (int part = 0; part < 2; ++part) {
+      const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : (int64_t)ls[0].size();
+      if (hi <= lo) continue;
+      MdArgs a = base;
+      a.nodes = dnodes + lo;
+      a.nnodes_launch = (int32_t)(hi - lo);
+      a.queue = base.queue + part;
+      const size_t slice = leaf_slice(hs[ls[0][lo]]);
+      int nw = (int)(220 * 1024 / slice);
+      nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
+      size_t sm = slice * nw;
+      if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
+      a.slice_bytes = (int64_t)slice;
+      int64_t grid = (hi - lo + nw - 1) / nw;
+      const int64_t cap = sms - reserved > 1 ? sms - reserved : 1;
+      if (grid > cap) grid = cap;
+      launch_pdl(h->stream, k_md_leaf, (unsigned)grid, 32 * nw, sm, a);
+      h->launches++;
+    }
   }
   {
     // the pair brackets only the wait: it starts when the handle's stream has
