@@ -31,6 +31,11 @@ namespace {
 constexpr int BFS_THREADS = 256;
 constexpr int BFS_BATCH = 8;
 constexpr int BFS_TAIL = 1024;   // frontiers up to this size run in one CTA
+// frontiers above this size (only a batch's union reaches it) read the
+// neighbours' keys before claiming: a neighbour settled at an earlier level
+// needs no atomic (about half of them on a mesh), which pays where the level
+// is bound by atomic throughput rather than by its round trips
+constexpr int32_t BFS_PRECHECK_MIN = 1 << 18;
 
 // Level-synchronous multi-source BFS on packed keys (dist << 32 | label).
 // ctr[0] holds the size of the initial frontier `fa`. Frontier entries are
@@ -56,6 +61,7 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
   // ranges loaded meanwhile.
   auto sweep = [&](uint32_t level, int32_t ncur, int64_t first, int64_t stride) {
     const unsigned long long dnext = (unsigned long long)(level + 1) << 32;
+    const bool pre = ncur > BFS_PRECHECK_MIN;
     for (int64_t i0 = first - lane; i0 < ncur; i0 += stride) {
       const int64_t i = i0 + lane;
       int32_t u = 0, e = 0, e1 = 0;
@@ -71,6 +77,14 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
         unsigned long long old[BFS_BATCH];
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k) v[k] = e + k < e1 ? col[e + k] : -1;
+        if (pre) {
+          // settled at a level <= this one: its key cannot change
+#pragma unroll
+          for (int k = 0; k < BFS_BATCH; ++k) old[k] = v[k] >= 0 ? __ldcg(&key[v[k]]) : 0ull;
+#pragma unroll
+          for (int k = 0; k < BFS_BATCH; ++k)
+            if (v[k] >= 0 && old[k] < dnext) v[k] = -1;
+        }
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k) old[k] = v[k] >= 0 ? atomicMin(&key[v[k]], dnext | lab) : 0ull;
         uint32_t claim = 0;
