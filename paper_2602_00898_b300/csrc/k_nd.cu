@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
                                                               const int32_t* __restrict__ gmap, int32_t k,
                                                               int32_t* __restrict__ qdeg, int32_t* __restrict__ qtoff,
                                                               int32_t* __restrict__ tcol, int32_t* __restrict__ tw,
-                                                              int32_t* tctr, int32_t* status) {
+                                                              int32_t* tctr, int32_t* status,
+                                                              int8_t* __restrict__ bnd) {
   FP_PDL_WAIT();
   __shared__ int32_t buf[QCAP];
   __shared__ int32_t starts[QCAP + 1];
@@ -123,12 +124,16 @@ __global__ void __launch_bounds__(ND_THREADS) k_quotient_rows(const int32_t* __r
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
     for (int32_t i = pstart[p] + threadIdx.x; i < pstart[p + 1]; i += blockDim.x) {
-      for_row_gather<8>(rowptr, col, pverts[i], gmap, [&](int32_t, int32_t q) {
+      const int32_t v = pverts[i];
+      bool outside = false;
+      for_row_gather<8>(rowptr, col, v, gmap, [&](int32_t, int32_t q) {
         if (q != p) {
+          outside = true;
           int32_t s = atomicAdd(&cnt, 1);
           if (s < QCAP) buf[s] = q;
         }
       });
+      bnd[v] = outside;        // on its patch's boundary
     }
     __syncthreads();
     const int32_t L = cnt;
@@ -692,6 +697,7 @@ struct LevelArgs {
   int32_t* patch_node;
   int32_t k;
   const int8_t* cross;         // [k] crossing patches of this level (k_nd_bisect)
+  const int8_t* bnd;           // [n] the vertex has a neighbour in another patch
   SegView sv;                  // fused batch: tie hashes of mesh-local vertex numbers
 };
 
@@ -706,9 +712,10 @@ __global__ void k_nd_superset(LevelArgs a) {
     if ((uint32_t)(t - a.t0) >= (uint32_t)a.T) continue;     // a subtree that starts deeper
     if (!a.split[t - a.t0]) { a.final_[v] = 1; continue; }
     const int32_t pv = a.gmap[v];
-    // no neighbour across in its patch's quotient row: not a candidate (its
-    // cdeg and state are not read this level)
-    if (!a.cross[pv]) continue;
+    // no neighbour across in its patch's quotient row, or none of its own
+    // neighbours in another patch (those of its own patch are on its side):
+    // not a candidate (its cdeg and state are not read this level)
+    if (!a.cross[pv] || !a.bnd[v]) continue;
     const int32_t sv = a.side[pv];
     int32_t c = 0;
     // neighbours in batches of ND_BATCH: col, then node and patch, then side;
@@ -1094,7 +1101,7 @@ fp_status run_nested_dissection(fp_handle* h) {
   int32_t *ldeg, *lvl, *lbeg, *qa, *qb, *mark, *hist, *sortbuf, *npcount, *npstart, *npfill, *nplist, *split, *cdeg;
   int32_t *cand, *ctr, *xcol;
   int2* cand_x;
-  int8_t *final_, *vstate, *cross;
+  int8_t *final_, *vstate, *cross, *bnd;
   Arena ar;
   auto layout = [&]() {
     psize = ar.get<int32_t>(kk); pstart = ar.get<int32_t>(kk); pfill = ar.get<int32_t>(kk);
@@ -1107,7 +1114,7 @@ fp_status run_nested_dissection(fp_handle* h) {
     npstart = ar.get<int32_t>(tl + 1); npfill = ar.get<int32_t>(tl); nplist = ar.get<int32_t>(kk);
     split = ar.get<int32_t>(tl); cdeg = ar.get<int32_t>(n); cand = ar.get<int32_t>(n); ctr = ar.get<int32_t>(8);
     xcol = ar.get<int32_t>(Q); cand_x = ar.get<int2>(n); final_ = ar.get<int8_t>(n); vstate = ar.get<int8_t>(n);
-    cross = ar.get<int8_t>(kk);
+    cross = ar.get<int8_t>(kk); bnd = ar.get<int8_t>(n);
   };
   layout();
   if (!ar.alloc(h)) return fail(h, FP_ERR_OUT_OF_MEMORY, "nested dissection workspace");
@@ -1126,7 +1133,7 @@ fp_status run_nested_dissection(fp_handle* h) {
   // (ladj, xcol and lbeg serve as scratch here; the dissection uses them later)
   fill_i32(h, ctr, 0, 8);
   FP_LAUNCH(h, k_quotient_rows, GQ, ND_THREADS, 0, pstart, pverts, h->rowptr, h->col, h->gmap, k, qdeg, lbeg,
-            ladj, xcol, ctr + 7, h->d_status);
+            ladj, xcol, ctr + 7, h->d_status, bnd);
   scan_exclusive(h, qdeg, q_rowptr, k, tmp);
   FP_LAUNCH(h, k_quotient_pack, grid_for((int64_t)k * 32, 256), 256, 0, q_rowptr, qdeg, lbeg, ladj, xcol, k, q_col,
             q_w);
@@ -1203,7 +1210,7 @@ fp_status run_nested_dissection(fp_handle* h) {
       FP_LAUNCH(h, k_stage_sides, GK, 256, 0, patch_node, side, split, t0, T, k, sb);
     ProfScope ps_s(FP_PROF_ND_SEPARATOR, h->stream);
     LevelArgs la{n, t0, T, h->rowptr, h->col, h->gmap, h->node_of, final_, side, split, cdeg, vstate, cand, cand_x, xcol,
-                 ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross, sg ? sg->v : SegView{}};
+                 ctr, w, q_rowptr, q_col, q_w, patch_node, k, cross, bnd, sg ? sg->v : SegView{}};
     if (!grouped_small) fill_i32(h, ctr, 0, 4);
     FP_LAUNCH(h, k_nd_superset, G, 256, 0, la);
     {
