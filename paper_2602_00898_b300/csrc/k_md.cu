@@ -970,6 +970,7 @@ fp_status run_local_order(fp_handle* h) {
   h->node_size_host.assign(hsp, hsp + nn);
   const std::vector<int32_t>& hs = h->node_size_host;
   if (st & ST_QUOTIENT_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a patch has more than 4096 cross edges");
+  if (st & ST_NODE_TOO_BIG) return fail(h, FP_ERR_UNSUPPORTED, "a dissection node above the warp bisection's 32 patches");
   // kinds: 0 leaf, 1 sparse, 2 global. Sparse nodes also get global rows, used
   // only if their adjacency lists overflow.
   std::vector<int32_t> ls[3], early;

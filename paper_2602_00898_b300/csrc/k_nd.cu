@@ -221,6 +221,7 @@ struct BisectArgs {
   int32_t smem_ints;           // dynamic shared memory of the launch, in ints
   const int32_t* w;            // [k] remaining vertices of every patch
   int32_t cap_log;             // a child of a node at this depth keeps at most 2^cap_log patches
+  int32_t* status;             // k_nd_bisect_warp: ST_NODE_TOO_BIG for a node above 32 patches
 };
 
 // Per-node working set: in shared memory when the node has <= mcap patches and
@@ -951,6 +952,229 @@ __global__ void k_nd_move_patches(LevelArgs a) {
 }
 
 
+// Bisection of nodes of at most 32 patches (the deep levels, where the
+// subtree capacity bounds every node by 2^(Dsplit-d) <= 32 patches): one warp
+// a node, lane i = the node's i-th patch in id order, its local quotient
+// neighbours as a 32-bit mask, BFS levels by OR-reductions of the frontier's
+// masks. The same rule as k_nd_bisect (R8: components by smallest id, r0 and
+// r1 by (degree, id), order by (level from r1, id), the weighted cut clamped
+// to the subtree capacity), decided with warp votes and reductions instead
+// of CTA barriers.
+constexpr int BW_WARPS = 8;
+
+// (degree << 8 | lane) keys: the lane of the least key among `in`, -1 if none
+__device__ __forceinline__ int32_t warp_argmin_key(bool in, uint32_t key) {
+  const uint32_t k = __reduce_min_sync(0xffffffffu, in ? key : 0xffffffffu);
+  return k == 0xffffffffu ? -1 : (int32_t)(k & 0xffu);
+}
+
+// Level-synchronous BFS from lane src over the lanes with lvl == -1 (src
+// among them); sets their levels and returns the number of levels.
+__device__ __forceinline__ int32_t warp_bfs(uint32_t adj, int32_t& lvl, int32_t src) {
+  const int lane = threadIdx.x & 31;
+  uint32_t unvisited = __ballot_sync(0xffffffffu, lvl == -1);
+  if (lane == src) lvl = 0;
+  uint32_t front = 1u << src;
+  unvisited &= ~front;
+  int32_t level = 0;
+  while (front) {
+    const uint32_t nxt = __reduce_or_sync(0xffffffffu, (front >> lane & 1u) ? adj : 0u) & unvisited;
+    ++level;
+    if (nxt >> lane & 1u) lvl = level;
+    unvisited &= ~nxt;
+    front = nxt;
+  }
+  return level;
+}
+
+__global__ void __launch_bounds__(BW_WARPS * 32) k_nd_bisect_warp(BisectArgs a) {
+  FP_PDL_WAIT();
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ int32_t s_ids[BW_WARPS][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int32_t ni = blockIdx.x * BW_WARPS + wid; ni < a.T; ni += gridDim.x * BW_WARPS) {
+    const int32_t t = a.t0 + ni;
+    const int32_t base = a.npstart[ni];
+    const int32_t m = a.npstart[ni + 1] - base;
+    if (m < 2 || m > 32) {
+      // (above 32 patches the subtree capacity was not met: flagged, and the
+      // ordering stage reports it before any result is used)
+      if (lane == 0) {
+        a.split[ni] = 0;
+        if (m > 32) atomicOr(a.status, ST_NODE_TOO_BIG);
+      }
+      continue;
+    }
+    if (lane == 0) a.split[ni] = 1;
+    int32_t* Lg = a.nplist + base;
+    // id order: every lane's rank among the ids, then lane r takes rank r
+    const int32_t myid = lane < m ? Lg[lane] : INT_MAX;
+    int32_t rank = 0;
+    for (int j = 0; j < 32; ++j) rank += __shfl_sync(FULL, myid, j) < myid;
+    if (lane < m) s_ids[wid][rank] = myid;
+    __syncwarp();
+    const int32_t p = lane < m ? s_ids[wid][lane] : -1;
+    if (lane < m) {
+      Lg[lane] = p;
+      a.loc[p] = lane;
+    }
+    __syncwarp();
+    // neighbours in this node with remaining edge weight, ND_BATCH a round
+    uint32_t adj = 0u;
+    if (lane < m) {
+      const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
+      for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
+        int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
+          wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k) {
+          const bool live = q[k] >= 0 && wq[k] > 0;
+          nq[k] = live ? a.patch_node[q[k]] : -1;
+          lq[k] = live ? a.loc[q[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ND_BATCH; ++k)
+          if (nq[k] == t) adj |= 1u << lq[k];
+      }
+    }
+    const int32_t w = lane < m ? a.w[p] : 0;
+    const uint32_t key = ((uint32_t)__popc(adj) << 8) | (uint32_t)lane;
+    int32_t lvl = lane < m ? -1 : -2;
+    int32_t mark = lane < m ? 0 : 1;       // 0 untouched, 2 this component, 1 done
+    int32_t sd = 0;
+    int32_t lo = 1, hi = m - 1;
+    if (a.cap_log < 30) {
+      const int32_t c = 1 << a.cap_log;
+      const int32_t l2 = m - c > 1 ? m - c : 1, h2 = m - 1 < c ? m - 1 : c;
+      if (l2 <= h2) { lo = l2; hi = h2; }
+    }
+    int64_t W = -1;
+    int32_t jstar = lo == hi ? lo : -1;
+    int32_t pos = 0;
+    int64_t posw = 0;
+    for (;;) {
+      const uint32_t untouched = __ballot_sync(FULL, mark == 0);
+      if (!untouched) break;
+      const int32_t c0 = __ffs(untouched) - 1;
+      const int32_t ra = warp_argmin_key(mark == 0, key);
+      int32_t nl0 = warp_bfs(adj, lvl, ra);
+      if (__shfl_sync(FULL, lvl, c0) >= 0) {
+        if (mark == 0 && lvl >= 0) mark = 2;
+      } else {
+        if (mark == 0 && lvl >= 0) lvl = -1;
+        warp_bfs(adj, lvl, c0);
+        const bool comp = mark == 0 && lvl >= 0;
+        if (comp) {
+          mark = 2;
+          lvl = -1;
+        }
+        nl0 = warp_bfs(adj, lvl, warp_argmin_key(comp, key));
+      }
+      const int32_t r1 = warp_argmin_key(mark == 2 && lvl == nl0 - 1, key);
+      if (mark == 2) lvl = -1;
+      warp_bfs(adj, lvl, r1);
+      const bool cur = mark == 2;
+      const int32_t cs = __popc(__ballot_sync(FULL, cur));
+      const int64_t cw = (int64_t)__reduce_add_sync(FULL, cur ? (uint32_t)w : 0u);
+      int32_t d_lstar = -1, d_istar = 0, d_incl = 0;
+      if (jstar < 0) {
+        if (W < 0) W = (pos == 0 && cs == m) ? cw : (int64_t)__reduce_add_sync(FULL, (uint32_t)w);
+        if (2 * (posw + cw) >= W) {
+          // the crossing lies in this component: levels by weight (and
+          // count), then the patches of the crossing level in id order
+          const int64_t T2 = W - 2 * posw;
+          int64_t cumw = 0;
+          int32_t cumc = 0, l = 0, nlev = 0;
+          for (; l < 32; ++l) {                 // levels <= m <= 32
+            const bool at = cur && lvl == l;
+            const int64_t hw = (int64_t)__reduce_add_sync(FULL, at ? (uint32_t)w : 0u);
+            const int32_t hc = __popc(__ballot_sync(FULL, at));
+            if (2 * (cumw + hw) < T2) {
+              cumw += hw;
+              cumc += hc;
+            } else {
+              nlev = hc;
+              break;
+            }
+          }
+          const int32_t lstar = l;
+          const bool at = cur && lvl == lstar;
+          const int32_t wi = at ? w : 0;
+          int32_t inc = wi;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+          }
+          const int32_t exw = inc - wi;
+          const bool hit = at && 2 * (cumw + exw) < T2 && 2 * (cumw + exw + wi) >= T2;
+          const uint32_t hb = __ballot_sync(FULL, hit);
+          const int32_t istar = hb ? __ffs(hb) - 1 : 0;
+          int32_t incl = 0;
+          if (hit) {
+            // keep the crossing patch on the left iff that cut is strictly
+            // closer to the half
+            const int64_t p1 = posw + cumw + exw + wi;
+            incl = (2 * p1 - W) < (W - 2 * (p1 - wi)) ? 1 : 0;
+          }
+          incl = __shfl_sync(FULL, incl, istar);
+          const int32_t j0lo = pos + cumc, j0hi = pos + cumc + nlev;
+          if (j0lo < lo || j0hi > hi) {
+            const int32_t r = __popc(__ballot_sync(FULL, at && lane < istar));
+            const int32_t j0 = pos + cumc + r + incl;
+            jstar = j0 < lo ? lo : (j0 > hi ? hi : j0);
+            if (jstar == j0) { d_lstar = lstar; d_istar = istar; d_incl = incl; }
+          } else {
+            jstar = INT_MAX;          // fixed by the rule below, inside this component
+            d_lstar = lstar; d_istar = istar; d_incl = incl;
+          }
+        } else if (hi <= pos + cs) {
+          jstar = hi;                 // the crossing comes later, the cut stops at hi
+        }
+      }
+      if (d_lstar >= 0) {
+        if (cur) {
+          sd = (lvl < d_lstar || (lvl == d_lstar && (lane < d_istar || (d_incl && lane == d_istar)))) ? 0 : 1;
+          mark = 1;
+        }
+        if (jstar == INT_MAX) jstar = pos;   // every later component goes right
+      } else if (jstar < 0 || pos + cs <= jstar || pos >= jstar) {
+        if (cur) {
+          sd = (jstar >= 0 && pos >= jstar) ? 1 : 0;
+          mark = 1;
+        }
+      } else {
+        // the cut falls inside the component: its first `need` patches in
+        // (level, id) order go left
+        const int32_t need = jstar - pos;
+        int32_t cum = 0, l = 0;
+        for (; l < 32; ++l) {
+          const int32_t hc = __popc(__ballot_sync(FULL, cur && lvl == l));
+          if (cum + hc < need) cum += hc; else break;
+        }
+        const uint32_t atm = __ballot_sync(FULL, cur && lvl == l);
+        const int32_t ex = __popc(atm & ((1u << lane) - 1u));
+        if (cur) {
+          sd = (lvl < l || (lvl == l && ex < need - cum)) ? 0 : 1;
+          mark = 1;
+        }
+      }
+      pos += cs;
+      posw += cw;
+    }
+    // sides, and the crossing patches (a local neighbour on the other side)
+    const uint32_t right = __ballot_sync(FULL, lane < m && sd == 1);
+    if (lane < m) {
+      a.side[p] = sd;
+      a.cross[p] = (int8_t)((adj & (sd ? ~right : right)) != 0u);
+    }
+  }
+}
+
 // Stage record (debug_dump) of one level's bisection: the side of every patch
 // of a split node at this depth, -1 for the others.
 __global__ void k_stage_sides(const int32_t* __restrict__ patch_node, const int32_t* __restrict__ side,
@@ -1170,6 +1394,9 @@ fp_status run_nested_dissection(fp_handle* h) {
   const int gmis_max = sms * (per > 0 ? per : 1);
 
   allow_max_dynamic_smem(k_group_small);
+  // the subtree capacity 2^(Dsplit-d) bounds every node's patches when the
+  // depth is the patches' own (not an explicit smaller nd_level)
+  const bool cap_exact = sg || Dsplit == ceil_log2(k);
   for (int32_t d = dmin; d < Dsplit; ++d) {
     const int32_t t0 = (1 << d) - 1, T = 1 << d;
     ProfScope ps_b(FP_PROF_ND_BISECT, h->stream);
@@ -1197,14 +1424,20 @@ fp_status run_nested_dissection(fp_handle* h) {
     const size_t bsmem = sizeof(int32_t) * (5 * (size_t)mcap + 1 + (size_t)ecap) + 2 * (size_t)mcap;
     BisectArgs ba{t0, T, npstart, nplist, sortbuf, q_rowptr, q_col, q_w, patch_node, loc, ldeg, lbeg, ladj,
                   lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4),
-                  w, Dsplit - d - 1};
+                  w, Dsplit - d - 1, h->d_status};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
-    // the top levels have a few large nodes, one CTA each: 1024 threads make
-    // their gathers of the quotient rows (dependent L2 loads, one round per
-    // blockDim patches) four times shorter
-    const int bt = T <= 16 ? 1024 : ND_THREADS;
-    allow_max_dynamic_smem(k_nd_bisect);
-    FP_LAUNCH(h, k_nd_bisect, GB, bt, bsmem, ba);
+    if (cap_exact && Dsplit - d <= 5) {
+      // every node holds at most 2^(Dsplit-d) <= 32 patches: one warp a node
+      const int64_t gw = ((int64_t)T + BW_WARPS - 1) / BW_WARPS;
+      FP_LAUNCH(h, k_nd_bisect_warp, (int)std::min<int64_t>(gw, NUM_SMS_B300 * 16), BW_WARPS * 32, 0, ba);
+    } else {
+      // the top levels have a few large nodes, one CTA each: 1024 threads
+      // make their gathers of the quotient rows (dependent L2 loads, one
+      // round per blockDim patches) four times shorter
+      const int bt = T <= 16 ? 1024 : ND_THREADS;
+      allow_max_dynamic_smem(k_nd_bisect);
+      FP_LAUNCH(h, k_nd_bisect, GB, bt, bsmem, ba);
+    }
     ps_b.end();
     if (int32_t* sb = stage_buffer(h, FP_STAGE_SIDE, d, k))
       FP_LAUNCH(h, k_stage_sides, GK, 256, 0, patch_node, side, split, t0, T, k, sb);
