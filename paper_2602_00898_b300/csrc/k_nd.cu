@@ -952,100 +952,168 @@ __global__ void k_nd_move_patches(LevelArgs a) {
 }
 
 
-// Bisection of nodes of at most 32 patches (the deep levels, where the
-// subtree capacity bounds every node by 2^(Dsplit-d) <= 32 patches): one warp
-// a node, lane i = the node's i-th patch in id order, its local quotient
-// neighbours as a 32-bit mask, BFS levels by OR-reductions of the frontier's
-// masks. The same rule as k_nd_bisect (R8: components by smallest id, r0 and
-// r1 by (degree, id), order by (level from r1, id), the weighted cut clamped
-// to the subtree capacity), decided with warp votes and reductions instead
-// of CTA barriers.
+// Bisection of nodes of at most 32 K patches (the deep levels, where the
+// subtree capacity bounds every node by 2^(Dsplit-d) patches): one warp a
+// node, the node's patches in id order as local indices j * 32 + lane (lane
+// holds K of them), each one's local quotient neighbours as a K-word mask,
+// BFS levels by OR-reductions of the frontier's masks. The same rule as
+// k_nd_bisect (R8: components by smallest id, r0 and r1 by (degree, id),
+// order by (level from r1, id), the weighted cut clamped to the subtree
+// capacity), decided with warp votes and reductions instead of CTA barriers.
 constexpr int BW_WARPS = 8;
 
-// (degree << 8 | lane) keys: the lane of the least key among `in`, -1 if none
-__device__ __forceinline__ int32_t warp_argmin_key(bool in, uint32_t key) {
-  const uint32_t k = __reduce_min_sync(0xffffffffu, in ? key : 0xffffffffu);
+// (degree << 8 | local index) keys: the least among `in`, as a local index
+// (-1 if none)
+template <int K>
+__device__ __forceinline__ int32_t warp_argmin_key(const bool (&in)[K], const uint32_t (&key)[K]) {
+  uint32_t best = 0xffffffffu;
+#pragma unroll
+  for (int j = 0; j < K; ++j) best = in[j] && key[j] < best ? key[j] : best;
+  const uint32_t k = __reduce_min_sync(0xffffffffu, best);
   return k == 0xffffffffu ? -1 : (int32_t)(k & 0xffu);
 }
 
-// Level-synchronous BFS from lane src over the lanes with lvl == -1 (src
-// among them); sets their levels and returns the number of levels.
-__device__ __forceinline__ int32_t warp_bfs(uint32_t adj, int32_t& lvl, int32_t src) {
+// Level-synchronous BFS from local index src over the patches with lvl == -1
+// (src among them); sets their levels and returns the number of levels.
+template <int K>
+__device__ __forceinline__ int32_t warp_bfs(const uint32_t (&adj)[K][K], int32_t (&lvl)[K], int32_t src) {
   const int lane = threadIdx.x & 31;
-  uint32_t unvisited = __ballot_sync(0xffffffffu, lvl == -1);
-  if (lane == src) lvl = 0;
-  uint32_t front = 1u << src;
-  unvisited &= ~front;
+  uint32_t unv[K], front[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    unv[j] = __ballot_sync(0xffffffffu, lvl[j] == -1);
+    front[j] = j == (src >> 5) ? 1u << (src & 31) : 0u;
+    if (j == (src >> 5) && lane == (src & 31)) lvl[j] = 0;
+    unv[j] &= ~front[j];
+  }
   int32_t level = 0;
-  while (front) {
-    const uint32_t nxt = __reduce_or_sync(0xffffffffu, (front >> lane & 1u) ? adj : 0u) & unvisited;
+  for (;;) {
+    uint32_t any = 0u;
+#pragma unroll
+    for (int j = 0; j < K; ++j) any |= front[j];
+    if (!any) break;
+    uint32_t nxt[K];
+#pragma unroll
+    for (int w = 0; w < K; ++w) {
+      uint32_t acc = 0u;
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (front[j] >> lane & 1u) acc |= adj[j][w];
+      nxt[w] = __reduce_or_sync(0xffffffffu, acc) & unv[w];
+    }
     ++level;
-    if (nxt >> lane & 1u) lvl = level;
-    unvisited &= ~nxt;
-    front = nxt;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if (nxt[j] >> lane & 1u) lvl[j] = level;
+      unv[j] &= ~nxt[j];
+      front[j] = nxt[j];
+    }
   }
   return level;
 }
 
+template <int K>
 __global__ void __launch_bounds__(BW_WARPS * 32) k_nd_bisect_warp(BisectArgs a) {
   FP_PDL_WAIT();
   constexpr unsigned FULL = 0xffffffffu;
-  __shared__ int32_t s_ids[BW_WARPS][32];
+  constexpr int MAXM = 32 * K;
+  __shared__ int32_t s_ids[BW_WARPS][MAXM];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
   for (int32_t ni = blockIdx.x * BW_WARPS + wid; ni < a.T; ni += gridDim.x * BW_WARPS) {
     const int32_t t = a.t0 + ni;
     const int32_t base = a.npstart[ni];
     const int32_t m = a.npstart[ni + 1] - base;
-    if (m < 2 || m > 32) {
-      // (above 32 patches the subtree capacity was not met: flagged, and the
-      // ordering stage reports it before any result is used)
+    if (m < 2 || m > MAXM) {
+      // (above MAXM patches the subtree capacity was not met: flagged, and
+      // the ordering stage reports it before any result is used)
       if (lane == 0) {
         a.split[ni] = 0;
-        if (m > 32) atomicOr(a.status, ST_NODE_TOO_BIG);
+        if (m > MAXM) atomicOr(a.status, ST_NODE_TOO_BIG);
       }
       continue;
     }
     if (lane == 0) a.split[ni] = 1;
     int32_t* Lg = a.nplist + base;
-    // id order: every lane's rank among the ids, then lane r takes rank r
-    const int32_t myid = lane < m ? Lg[lane] : INT_MAX;
-    int32_t rank = 0;
-    for (int j = 0; j < 32; ++j) rank += __shfl_sync(FULL, myid, j) < myid;
-    if (lane < m) s_ids[wid][rank] = myid;
+    // id order: every id's rank among the node's ids, then local index r
+    // takes rank r
+    int32_t myid[K], rank[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      myid[j] = j * 32 + lane < m ? Lg[j * 32 + lane] : INT_MAX;
+      rank[j] = 0;
+    }
+#pragma unroll
+    for (int jj = 0; jj < K; ++jj)
+      for (int src = 0; src < 32; ++src) {
+        const int32_t o = __shfl_sync(FULL, myid[jj], src);
+#pragma unroll
+        for (int j = 0; j < K; ++j) rank[j] += o < myid[j];
+      }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j * 32 + lane < m) s_ids[wid][rank[j]] = myid[j];
     __syncwarp();
-    const int32_t p = lane < m ? s_ids[wid][lane] : -1;
-    if (lane < m) {
-      Lg[lane] = p;
-      a.loc[p] = lane;
+    int32_t p[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int32_t i = j * 32 + lane;
+      p[j] = i < m ? s_ids[wid][i] : -1;
+      if (i < m) {
+        Lg[i] = p[j];
+        a.loc[p[j]] = i;
+      }
     }
     __syncwarp();
     // neighbours in this node with remaining edge weight, ND_BATCH a round
-    uint32_t adj = 0u;
-    if (lane < m) {
-      const int32_t e0 = a.q_rowptr[p], e1 = a.q_rowptr[p + 1];
-      for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
-        int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
+    uint32_t adj[K][K];
+    int32_t w[K], lvl[K], mark[K], sd[K];
+    uint32_t key[K];
 #pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
-          wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+      for (int x = 0; x < K; ++x) adj[j][x] = 0u;
+      const int32_t i = j * 32 + lane;
+      if (i < m) {
+        const int32_t e0 = a.q_rowptr[p[j]], e1 = a.q_rowptr[p[j] + 1];
+        for (int32_t eb = e0; eb < e1; eb += ND_BATCH) {
+          int32_t q[ND_BATCH], wq[ND_BATCH], nq[ND_BATCH], lq[ND_BATCH];
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k) {
+            q[k] = eb + k < e1 ? a.q_col[eb + k] : -1;
+            wq[k] = eb + k < e1 ? a.q_w[eb + k] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k) {
+            const bool live = q[k] >= 0 && wq[k] > 0;
+            nq[k] = live ? a.patch_node[q[k]] : -1;
+            lq[k] = live ? a.loc[q[k]] : 0;
+          }
+#pragma unroll
+          for (int k = 0; k < ND_BATCH; ++k)
+            if (nq[k] == t) {
+#pragma unroll
+              for (int x = 0; x < K; ++x)
+                if ((lq[k] >> 5) == x) adj[j][x] |= 1u << (lq[k] & 31);
+            }
         }
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k) {
-          const bool live = q[k] >= 0 && wq[k] > 0;
-          nq[k] = live ? a.patch_node[q[k]] : -1;
-          lq[k] = live ? a.loc[q[k]] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < ND_BATCH; ++k)
-          if (nq[k] == t) adj |= 1u << lq[k];
       }
+      int32_t dg = 0;
+#pragma unroll
+      for (int x = 0; x < K; ++x) dg += __popc(adj[j][x]);
+      w[j] = i < m ? a.w[p[j]] : 0;
+      key[j] = ((uint32_t)dg << 8) | (uint32_t)i;
+      lvl[j] = i < m ? -1 : -2;
+      mark[j] = i < m ? 0 : 1;           // 0 untouched, 2 this component, 1 done
+      sd[j] = 0;
     }
-    const int32_t w = lane < m ? a.w[p] : 0;
-    const uint32_t key = ((uint32_t)__popc(adj) << 8) | (uint32_t)lane;
-    int32_t lvl = lane < m ? -1 : -2;
-    int32_t mark = lane < m ? 0 : 1;       // 0 untouched, 2 this component, 1 done
-    int32_t sd = 0;
+    auto lvl_of = [&](int32_t i) -> int32_t {   // the level of local index i (all lanes)
+      int32_t v = 0;
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j == (i >> 5)) v = lvl[j];
+      return __shfl_sync(FULL, v, i & 31);
+    };
     int32_t lo = 1, hi = m - 1;
     if (a.cap_log < 30) {
       const int32_t c = 1 << a.cap_log;
@@ -1057,42 +1125,77 @@ __global__ void __launch_bounds__(BW_WARPS * 32) k_nd_bisect_warp(BisectArgs a) 
     int32_t pos = 0;
     int64_t posw = 0;
     for (;;) {
-      const uint32_t untouched = __ballot_sync(FULL, mark == 0);
-      if (!untouched) break;
-      const int32_t c0 = __ffs(untouched) - 1;
-      const int32_t ra = warp_argmin_key(mark == 0, key);
-      int32_t nl0 = warp_bfs(adj, lvl, ra);
-      if (__shfl_sync(FULL, lvl, c0) >= 0) {
-        if (mark == 0 && lvl >= 0) mark = 2;
-      } else {
-        if (mark == 0 && lvl >= 0) lvl = -1;
-        warp_bfs(adj, lvl, c0);
-        const bool comp = mark == 0 && lvl >= 0;
-        if (comp) {
-          mark = 2;
-          lvl = -1;
-        }
-        nl0 = warp_bfs(adj, lvl, warp_argmin_key(comp, key));
+      int32_t c0 = -1;
+#pragma unroll
+      for (int j = K - 1; j >= 0; --j) {
+        const uint32_t b = __ballot_sync(FULL, mark[j] == 0);
+        if (b) c0 = j * 32 + __ffs(b) - 1;
       }
-      const int32_t r1 = warp_argmin_key(mark == 2 && lvl == nl0 - 1, key);
-      if (mark == 2) lvl = -1;
-      warp_bfs(adj, lvl, r1);
-      const bool cur = mark == 2;
-      const int32_t cs = __popc(__ballot_sync(FULL, cur));
-      const int64_t cw = (int64_t)__reduce_add_sync(FULL, cur ? (uint32_t)w : 0u);
+      if (c0 < 0) break;
+      bool in[K];
+#pragma unroll
+      for (int j = 0; j < K; ++j) in[j] = mark[j] == 0;
+      int32_t nl0 = warp_bfs<K>(adj, lvl, warp_argmin_key<K>(in, key));
+      if (lvl_of(c0) >= 0) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          if (mark[j] == 0 && lvl[j] >= 0) mark[j] = 2;
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          if (mark[j] == 0 && lvl[j] >= 0) lvl[j] = -1;
+        warp_bfs<K>(adj, lvl, c0);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          in[j] = mark[j] == 0 && lvl[j] >= 0;
+          if (in[j]) {
+            mark[j] = 2;
+            lvl[j] = -1;
+          }
+        }
+        nl0 = warp_bfs<K>(adj, lvl, warp_argmin_key<K>(in, key));
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) in[j] = mark[j] == 2 && lvl[j] == nl0 - 1;
+      const int32_t r1 = warp_argmin_key<K>(in, key);
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (mark[j] == 2) lvl[j] = -1;
+      warp_bfs<K>(adj, lvl, r1);
+      bool cur[K];
+      int32_t cs = 0;
+      uint32_t cwl = 0u;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        cur[j] = mark[j] == 2;
+        cs += __popc(__ballot_sync(FULL, cur[j]));
+        cwl += cur[j] ? (uint32_t)w[j] : 0u;
+      }
+      const int64_t cw = (int64_t)__reduce_add_sync(FULL, cwl);
       int32_t d_lstar = -1, d_istar = 0, d_incl = 0;
       if (jstar < 0) {
-        if (W < 0) W = (pos == 0 && cs == m) ? cw : (int64_t)__reduce_add_sync(FULL, (uint32_t)w);
+        if (W < 0) {
+          uint32_t wl = 0u;
+#pragma unroll
+          for (int j = 0; j < K; ++j) wl += (uint32_t)w[j];
+          W = (pos == 0 && cs == m) ? cw : (int64_t)__reduce_add_sync(FULL, wl);
+        }
         if (2 * (posw + cw) >= W) {
           // the crossing lies in this component: levels by weight (and
           // count), then the patches of the crossing level in id order
           const int64_t T2 = W - 2 * posw;
           int64_t cumw = 0;
           int32_t cumc = 0, l = 0, nlev = 0;
-          for (; l < 32; ++l) {                 // levels <= m <= 32
-            const bool at = cur && lvl == l;
-            const int64_t hw = (int64_t)__reduce_add_sync(FULL, at ? (uint32_t)w : 0u);
-            const int32_t hc = __popc(__ballot_sync(FULL, at));
+          for (; l < MAXM; ++l) {                 // levels <= m
+            uint32_t hwl = 0u;
+            int32_t hc = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              const bool at = cur[j] && lvl[j] == l;
+              hwl += at ? (uint32_t)w[j] : 0u;
+              hc += __popc(__ballot_sync(FULL, at));
+            }
+            const int64_t hw = (int64_t)__reduce_add_sync(FULL, hwl);
             if (2 * (cumw + hw) < T2) {
               cumw += hw;
               cumc += hc;
@@ -1102,29 +1205,42 @@ __global__ void __launch_bounds__(BW_WARPS * 32) k_nd_bisect_warp(BisectArgs a) 
             }
           }
           const int32_t lstar = l;
-          const bool at = cur && lvl == lstar;
-          const int32_t wi = at ? w : 0;
-          int32_t inc = wi;
+          // the first patch of the level (in id order) whose prefix weight
+          // reaches half; keep it on the left iff that cut is strictly closer
+          // to the half
+          int32_t istar = -1, incl = 0, carry = 0;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += y;
+          for (int j = 0; j < K; ++j) {
+            const bool at = cur[j] && lvl[j] == lstar;
+            const int32_t wi = at ? w[j] : 0;
+            int32_t inc = wi;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int32_t y = __shfl_up_sync(FULL, inc, o);
+              if (lane >= o) inc += y;
+            }
+            const int32_t exw = carry + inc - wi;
+            const bool hit = at && 2 * (cumw + exw) < T2 && 2 * (cumw + exw + wi) >= T2;
+            int32_t my_incl = 0;
+            if (hit) {
+              const int64_t p1 = posw + cumw + exw + wi;
+              my_incl = (2 * p1 - W) < (W - 2 * (p1 - wi)) ? 1 : 0;
+            }
+            const uint32_t hb = __ballot_sync(FULL, hit);
+            if (istar < 0 && hb) {
+              const int src = __ffs(hb) - 1;
+              istar = j * 32 + src;
+              incl = __shfl_sync(FULL, my_incl, src);
+            }
+            carry += __shfl_sync(FULL, inc, 31);
           }
-          const int32_t exw = inc - wi;
-          const bool hit = at && 2 * (cumw + exw) < T2 && 2 * (cumw + exw + wi) >= T2;
-          const uint32_t hb = __ballot_sync(FULL, hit);
-          const int32_t istar = hb ? __ffs(hb) - 1 : 0;
-          int32_t incl = 0;
-          if (hit) {
-            // keep the crossing patch on the left iff that cut is strictly
-            // closer to the half
-            const int64_t p1 = posw + cumw + exw + wi;
-            incl = (2 * p1 - W) < (W - 2 * (p1 - wi)) ? 1 : 0;
-          }
-          incl = __shfl_sync(FULL, incl, istar);
+          if (istar < 0) istar = 0;
           const int32_t j0lo = pos + cumc, j0hi = pos + cumc + nlev;
           if (j0lo < lo || j0hi > hi) {
-            const int32_t r = __popc(__ballot_sync(FULL, at && lane < istar));
+            int32_t r = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              r += __popc(__ballot_sync(FULL, cur[j] && lvl[j] == lstar && j * 32 + lane < istar));
             const int32_t j0 = pos + cumc + r + incl;
             jstar = j0 < lo ? lo : (j0 > hi ? hi : j0);
             if (jstar == j0) { d_lstar = lstar; d_istar = istar; d_incl = incl; }
@@ -1137,41 +1253,60 @@ __global__ void __launch_bounds__(BW_WARPS * 32) k_nd_bisect_warp(BisectArgs a) 
         }
       }
       if (d_lstar >= 0) {
-        if (cur) {
-          sd = (lvl < d_lstar || (lvl == d_lstar && (lane < d_istar || (d_incl && lane == d_istar)))) ? 0 : 1;
-          mark = 1;
-        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          if (cur[j]) {
+            const int32_t i = j * 32 + lane;
+            sd[j] = (lvl[j] < d_lstar || (lvl[j] == d_lstar && (i < d_istar || (d_incl && i == d_istar)))) ? 0 : 1;
+            mark[j] = 1;
+          }
         if (jstar == INT_MAX) jstar = pos;   // every later component goes right
       } else if (jstar < 0 || pos + cs <= jstar || pos >= jstar) {
-        if (cur) {
-          sd = (jstar >= 0 && pos >= jstar) ? 1 : 0;
-          mark = 1;
-        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+          if (cur[j]) {
+            sd[j] = (jstar >= 0 && pos >= jstar) ? 1 : 0;
+            mark[j] = 1;
+          }
       } else {
         // the cut falls inside the component: its first `need` patches in
         // (level, id) order go left
         const int32_t need = jstar - pos;
         int32_t cum = 0, l = 0;
-        for (; l < 32; ++l) {
-          const int32_t hc = __popc(__ballot_sync(FULL, cur && lvl == l));
+        for (; l < MAXM; ++l) {
+          int32_t hc = 0;
+#pragma unroll
+          for (int j = 0; j < K; ++j) hc += __popc(__ballot_sync(FULL, cur[j] && lvl[j] == l));
           if (cum + hc < need) cum += hc; else break;
         }
-        const uint32_t atm = __ballot_sync(FULL, cur && lvl == l);
-        const int32_t ex = __popc(atm & ((1u << lane) - 1u));
-        if (cur) {
-          sd = (lvl < l || (lvl == l && ex < need - cum)) ? 0 : 1;
-          mark = 1;
+        int32_t before = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const uint32_t atm = __ballot_sync(FULL, cur[j] && lvl[j] == l);
+          const int32_t ex = before + __popc(atm & ltm);
+          if (cur[j]) {
+            sd[j] = (lvl[j] < l || (lvl[j] == l && ex < need - cum)) ? 0 : 1;
+            mark[j] = 1;
+          }
+          before += __popc(atm);
         }
       }
       pos += cs;
       posw += cw;
     }
     // sides, and the crossing patches (a local neighbour on the other side)
-    const uint32_t right = __ballot_sync(FULL, lane < m && sd == 1);
-    if (lane < m) {
-      a.side[p] = sd;
-      a.cross[p] = (int8_t)((adj & (sd ? ~right : right)) != 0u);
-    }
+    uint32_t right[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) right[j] = __ballot_sync(FULL, j * 32 + lane < m && sd[j] == 1);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (j * 32 + lane < m) {
+        uint32_t c = 0u;
+#pragma unroll
+        for (int x = 0; x < K; ++x) c |= adj[j][x] & (sd[j] ? ~right[x] : right[x]);
+        a.side[p[j]] = sd[j];
+        a.cross[p[j]] = (int8_t)(c != 0u);
+      }
   }
 }
 
@@ -1426,10 +1561,13 @@ fp_status run_nested_dissection(fp_handle* h) {
                   lvl, qa, qb, (int8_t*)mark, hist, side, split, cross, mcap, ecap, k, (int32_t)(bsmem / 4),
                   w, Dsplit - d - 1, h->d_status};
     const int GB = T < NUM_SMS_B300 * 8 ? T : NUM_SMS_B300 * 8;
-    if (cap_exact && Dsplit - d <= 5) {
-      // every node holds at most 2^(Dsplit-d) <= 32 patches: one warp a node
-      const int64_t gw = ((int64_t)T + BW_WARPS - 1) / BW_WARPS;
-      FP_LAUNCH(h, k_nd_bisect_warp, (int)std::min<int64_t>(gw, NUM_SMS_B300 * 16), BW_WARPS * 32, 0, ba);
+    if (cap_exact && Dsplit - d <= 7) {
+      // every node holds at most 2^(Dsplit-d) <= 128 patches: one warp a
+      // node, one, two or four of them a lane
+      const int gw = (int)std::min<int64_t>(((int64_t)T + BW_WARPS - 1) / BW_WARPS, NUM_SMS_B300 * 16);
+      if (Dsplit - d <= 5) FP_LAUNCH(h, k_nd_bisect_warp<1>, gw, BW_WARPS * 32, 0, ba);
+      else if (Dsplit - d == 6) FP_LAUNCH(h, k_nd_bisect_warp<2>, gw, BW_WARPS * 32, 0, ba);
+      else FP_LAUNCH(h, k_nd_bisect_warp<4>, gw, BW_WARPS * 32, 0, ba);
     } else {
       // the top levels have a few large nodes, one CTA each: 1024 threads
       // make their gathers of the quotient rows (dependent L2 loads, one
