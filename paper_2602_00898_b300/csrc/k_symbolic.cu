@@ -141,6 +141,64 @@ __device__ __forceinline__ void export_element(const SymArgs& a, const int32_t* 
   }
 }
 
+// export_element with the whole CTA, for the dense tail's last column (a
+// structure of up to thousands of ancestor columns): a word of the structure
+// a thread, offsets by a block scan of the words' popcounts, each thread's
+// entries written eight at a time with their position loads issued first.
+// Called by every thread of the CTA.
+template <class WordOf>
+__device__ void export_element_block(const SymArgs& a, const int32_t* upos, int32_t W, uint32_t cnt, int32_t pf,
+                                     WordOf word_of, int32_t* red) {
+  __shared__ unsigned long long s_eo[2];
+  __shared__ int32_t s_bad;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    s_eo[0] = atomicAdd(&a.elem_ctr[1], (unsigned long long)cnt);
+    s_eo[1] = atomicAdd(&a.elem_ctr[0], 1ull);
+    s_bad = (int64_t)(s_eo[0] + cnt) > a.cap_data || (int64_t)s_eo[1] >= a.cap_hdr;
+    if (s_bad) atomicOr(a.status, ST_POOL_OVERFLOW);
+  }
+  __syncthreads();
+  if (s_bad) return;
+  const unsigned long long off = s_eo[0], hdr = s_eo[1];
+  int32_t carry = 0;
+  for (int32_t w0 = 0; w0 < W; w0 += nthr) {
+    const int32_t w = w0 + tid;
+    uint32_t bits = w < W ? word_of(w) : 0u;
+    int32_t tot;
+    int32_t o = block_excl_scan_i32(__popc(bits), &tot, red) + carry;
+    while (bits) {
+      int32_t q[8];
+      int n = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        q[k] = -1;
+        if (bits) {
+          q[k] = w * 32 + __ffs(bits) - 1;
+          bits &= bits - 1;
+          ++n;
+        }
+      }
+      int32_t v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = q[k] >= 0 ? upos[q[k]] : 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < n) a.elem_data[off + o + k] = v[k];
+      o += n;
+    }
+    carry += tot;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int32_t target = a.node_of[a.perm[pf]];
+    a.elem_hdr[3 * hdr + 1] = (int32_t)off;
+    a.elem_hdr[3 * hdr + 2] = (int32_t)cnt;
+    __threadfence();
+    a.elem_hdr[3 * hdr] = atomicExch(&a.elem_head[target], (int32_t)hdr);
+  }
+}
+
 constexpr int SLAB_ILP = 4;
 
 // Step 1's gather, done once: the upper adjacency entries (column i, position
@@ -536,11 +594,12 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
     }
     run += total;
   }
-  // the last column: its structure is every ancestor column met
+  // the last column: its structure is every ancestor column met; its parent
+  // is the first of them (warp 0), its element goes out with the whole CTA
+  __shared__ int32_t s_pf;
   if (tid < 32) {
-    if (run == 0) {
-      if (lane == 0) a.parent[b + m - 1] = -1;
-    } else if (por) {
+    int32_t pf = -1;
+    if (run != 0 && por) {
       int32_t cmin = 0;
       for (int32_t w0 = 0; w0 < nwa; w0 += 32) {
         const int32_t w = w0 + lane;
@@ -553,11 +612,8 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
           break;
         }
       }
-      const int32_t pf = upos[cmin];
-      if (lane == 0) a.parent[b + m - 1] = pf;
-      if (!a.node_fill)
-        export_element(a, upos, W, (uint32_t)run, pf, [&](int w) -> uint32_t { return w >= wa ? tot[w - wa] : 0u; });
-    } else {
+      pf = upos[cmin];
+    } else if (run != 0) {
       int32_t umin = 0;
       for (int32_t u0 = 0; u0 < nab; u0 += 32) {
         const int32_t u = u0 + lane;
@@ -567,16 +623,27 @@ __device__ void dense_tail(const SymArgs& a, const uint32_t* rows, const int32_t
           break;
         }
       }
-      const int32_t pf = upos[m + umin];
-      if (lane == 0) a.parent[b + m - 1] = pf;
-      const int32_t Wa = (nab + 31) >> 5;
-      if (!a.node_fill) export_element(a, upos + m, Wa, (uint32_t)run, pf, [&](int w) -> uint32_t {
+      pf = upos[m + umin];
+    }
+    if (lane == 0) {
+      a.parent[b + m - 1] = pf;
+      s_pf = pf;
+    }
+  }
+  __syncthreads();
+  const int32_t pf = s_pf;
+  if (run != 0 && !a.node_fill) {
+    if (por) {
+      export_element_block(a, upos, W, (uint32_t)run, pf,
+                           [&](int w) -> uint32_t { return w >= wa ? tot[w - wa] : 0u; }, red);
+    } else {
+      export_element_block(a, upos + m, (nab + 31) >> 5, (uint32_t)run, pf, [&](int w) -> uint32_t {
         const int32_t u = w * 32;
-        uint32_t s = 0u;
+        uint32_t x = 0u;
         for (int k = 0; k < 32; ++k)
-          if (u + k < nab && first[u + k] != NO_ROW) s |= 1u << k;
-        return s;
-      });
+          if (u + k < nab && first[u + k] != NO_ROW) x |= 1u << k;
+        return x;
+      }, red);
     }
   }
 }
