@@ -326,13 +326,20 @@ fp_status fp_batch_permute(fp_handle* h, fp_batch_item* items, int32_t count);
 fp_status fp_batch_symbolic(fp_handle* h, fp_batch_item* items, int32_t count);
 
 /*
- * Autotuner for fp_batch_order: for every size class of the items (vertex
- * counts below 8k, 32k, 128k, 512k, and above) it orders the class's largest
- * item once per candidate cap in {128, 256, 384, 512}, timing create +
- * permute + symbolic with CUDA events (best of two), and keeps the fastest
- * cap whose nnz(L) is within 5% of the smallest nnz(L) seen for that item.
- * The choices are kept process-wide and used by items with patch_cap 0;
- * h_caps (may be NULL) receives the 5 chosen caps (0 for an empty class).
+ * Autotuner for fp_batch_order: one patch cap per size class of the items
+ * (vertex counts below 8k, 32k, 128k, 512k, and above), from the candidates
+ * {128, 256, 384, 512}. When the batch qualifies for the fused form (see
+ * fp_batch_order) the caps are tuned on the fused batch itself: each
+ * candidate for every class at once, keeping the fastest whose total nnz(L)
+ * is within 5% of the least seen, then each class in turn with the other
+ * candidates, a change kept when faster at that fill (best of two runs,
+ * items with their own patch_cap keep it; no output is written). Otherwise
+ * each class's largest item is ordered alone once per candidate, timing
+ * create + permute + symbolic with CUDA events (best of two), and the
+ * fastest cap whose nnz(L) is within 5% of the smallest nnz(L) seen for that
+ * item is kept. The choices are kept process-wide and used by items with
+ * patch_cap 0; h_caps (may be NULL) receives the 5 chosen caps (0 for an
+ * empty class).
  */
 fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t* h_caps);
 

@@ -16,6 +16,7 @@
 // (n_workers > 0) and orders the items one by one when the fused form fails.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -402,12 +403,95 @@ extern "C" fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count,
   return FP_OK;
 }
 
+namespace fp {
+namespace {
+
+// The fused batch's time (best of two, host clock: the call is synchronous)
+// and total nnz(L) with the items of class c at cap caps[c] (items with their
+// own cap keep it); outputs are not written.
+fp_status fused_trial(const fp_batch_item* items, int32_t count, const fp_options& o, cudaStream_t s,
+                      const int32_t* caps, double* ms, int64_t* nnz) {
+  std::vector<fp_batch_item> tr(items, items + count);
+  for (auto& it : tr) {
+    if (it.patch_cap <= 0) it.patch_cap = caps[size_class(it.n_vertices)];
+    it.d_perm = it.d_iperm = it.d_parent = it.d_colcount = nullptr;
+  }
+  *ms = 1e30;
+  for (int r = 0; r < 2; ++r) {
+    const auto t0 = std::chrono::steady_clock::now();
+    FP_TRY(run_fused(tr.data(), count, o, s, nullptr));
+    const double t = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *ms = std::min(*ms, t);
+  }
+  *nnz = 0;
+  for (const auto& it : tr) *nnz += it.nnzL;
+  return FP_OK;
+}
+
+// Tuning for the fused form, on the batch itself: a batch's time is the
+// union's, not a sum of single-mesh pipelines, so the caps are timed where
+// they run. First one cap for every class, the fastest whose total nnz(L) is
+// within 5% of the least seen; then each class in turn tries the other caps
+// with the rest fixed, kept when faster at that fill.
+fp_status autotune_fused(const fp_batch_item* items, int32_t count, const fp_options& o, cudaStream_t s,
+                         int32_t* chosen) {
+  bool present[N_CLASSES] = {false, false, false, false, false};
+  for (int32_t i = 0; i < count; ++i) present[size_class(items[i].n_vertices)] = true;
+  double t[N_CAND];
+  int64_t z[N_CAND];
+  int32_t caps[N_CLASSES];
+  for (int k = 0; k < N_CAND; ++k) {
+    std::fill(caps, caps + N_CLASSES, CAND_CAPS[k]);
+    FP_TRY(fused_trial(items, count, o, s, caps, &t[k], &z[k]));
+  }
+  int64_t minnz = *std::min_element(z, z + N_CAND);
+  int pick = -1;
+  for (int k = 0; k < N_CAND; ++k)
+    if ((double)z[k] <= 1.05 * (double)minnz && (pick < 0 || t[k] < t[pick])) pick = k;
+  std::fill(caps, caps + N_CLASSES, CAND_CAPS[pick]);
+  double best = t[pick];
+  for (int c = 0; c < N_CLASSES; ++c) {
+    if (!present[c]) continue;
+    for (int k = 0; k < N_CAND; ++k) {
+      if (CAND_CAPS[k] == caps[c]) continue;
+      int32_t trial[N_CLASSES];
+      std::copy(caps, caps + N_CLASSES, trial);
+      trial[c] = CAND_CAPS[k];
+      double tk;
+      int64_t zk;
+      FP_TRY(fused_trial(items, count, o, s, trial, &tk, &zk));
+      minnz = std::min(minnz, zk);
+      if ((double)zk <= 1.05 * (double)minnz && tk < best) {
+        best = tk;
+        caps[c] = trial[c];
+      }
+    }
+  }
+  for (int c = 0; c < N_CLASSES; ++c) chosen[c] = present[c] ? caps[c] : 0;
+  return FP_OK;
+}
+
+}  // namespace
+}  // namespace fp
+
 extern "C" fp_status fp_batch_autotune(fp_batch_item* items, int32_t count, const fp_options* opts, int32_t* h_caps) {
   if (count < 0 || (count > 0 && !items) || !opts) return fail(nullptr, FP_ERR_INVALID_ARG, "bad autotune arguments");
   int device = 0;
   cudaGetDevice(&device);
   cudaStream_t s = worker_stream(device);
   if (!s) return fail(nullptr, FP_ERR_CUDA, "autotune stream");
+  if (count > 0 && fused_ok(items, count, *opts)) {
+    int32_t chosen[N_CLASSES];
+    FP_TRY(autotune_fused(items, count, *opts, s, chosen));
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (int c = 0; c < N_CLASSES; ++c)
+        if (chosen[c] > 0) g_tuned_caps[c] = chosen[c];
+    }
+    if (h_caps)
+      for (int c = 0; c < N_CLASSES; ++c) h_caps[c] = chosen[c];
+    return FP_OK;
+  }
   cudaEvent_t a = nullptr, b = nullptr;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
     return fail(nullptr, FP_ERR_CUDA, "autotune events");
