@@ -219,6 +219,7 @@ __device__ __forceinline__ void warp_sort_smem(unsigned long long* buf, int N, i
 // degrees. Each lane gathers two vertices at a time, eight neighbours each,
 // so that their dependent loads (row bounds, neighbours, their node and local
 // index) overlap.
+template <int LEAF_GV>
 __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S, int W, int32_t* verts,
                                         unsigned char* mine, uint32_t* R, uint16_t* deg, int32_t* lv,
                                         int lane) {
@@ -257,7 +258,7 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
   if (by_id) {
     // LEAF_GV vertices a lane per round: their edge ranges, their neighbours
     // (LEAF_GE at a time), then the searches, all independent
-    constexpr int LEAF_GV = 4, LEAF_GE = 8;
+    constexpr int LEAF_GE = 8;
     for (int i0 = lane; i0 < m; i0 += 32 * LEAF_GV) {
       int32_t b[LEAF_GV], e[LEAF_GV], c[LEAF_GV];
 #pragma unroll
@@ -351,9 +352,14 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
   }
 }
 
-// up to LEAF_WARPS warps a CTA, one leaf each (its registers allow 10)
-constexpr int LEAF_WARPS = 10;
-__global__ void __launch_bounds__(LEAF_WARPS * 32) k_md_leaf(MdArgs a) {
+// up to kWarps warps a CTA, one leaf each. Two builds: 10 warps at full
+// registers for launches of about one wave, whose time is the largest leaf's
+// latency, and 20 warps under the register cap that imposes (96 a thread,
+// a few bytes of spill in the setup, slower steps) for launches of many
+// waves, which gain the warps to hide the steps' latency.
+constexpr int LEAF_WARPS = 10, LEAF_WARPS_WIDE = 20;
+template <int kWarps>
+__global__ void __launch_bounds__(kWarps * 32) k_md_leaf(MdArgs a) {
   FP_PDL_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -379,7 +385,7 @@ __global__ void __launch_bounds__(LEAF_WARPS * 32) k_md_leaf(MdArgs a) {
     uint32_t* nzv = (uint32_t*)(nb + ((m + 1) & ~1));  // pivot row's non-zero words
     uint16_t* nzw = (uint16_t*)(nzv + MD_LEAF / 32);   //   and their indices
     // the sorted vertex list, during the setup only (overlaps order and nb)
-    leaf_setup(a, t, m, S, W, verts, mine, R, deg, (int32_t*)order, lane);
+    leaf_setup<kWarps == LEAF_WARPS ? 4 : 2>(a, t, m, S, W, verts, mine, R, deg, (int32_t*)order, lane);
     __syncwarp();
     const uint32_t* deg2 = (const uint32_t*)deg;
     uint32_t* degw = (uint32_t*)deg;
@@ -865,6 +871,38 @@ __global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, in
   }
 }
 
+// Warps of a leaf CTA (one CTA per SM): as many as the slices fit in 220 KB
+// of shared memory, up to wmax. The CTAs are packed rather than spread over
+// every SM: the separators' orderings on the auxiliary streams hold SMs
+// meanwhile, and a leaf CTA, which needs most of an SM's shared memory,
+// waits for one of those to drain.
+int leaf_warps(size_t slice, int wmax) {
+  int64_t nw = (int64_t)(220 * 1024 / slice);
+  if (nw > wmax) nw = wmax;
+  return nw < 1 ? 1 : (int)nw;
+}
+
+// Launches a leaf ordering of `nodes` nodes with slices of `slice` bytes on
+// at most `sms` CTAs: the wide build when `allow_wide`, the nodes fill more
+// than four waves of the 10-warp build and the slices leave room for more
+// warps.
+void launch_leaf(fp_handle* h, cudaStream_t s, const MdArgs& a0, size_t slice, int64_t nodes, int64_t sms,
+                 bool allow_wide) {
+  MdArgs a = a0;
+  int nw = leaf_warps(slice, LEAF_WARPS);
+  const bool wide = allow_wide && nodes > 4 * sms * nw && leaf_warps(slice, LEAF_WARPS_WIDE) > LEAF_WARPS;
+  if (wide) nw = leaf_warps(slice, LEAF_WARPS_WIDE);
+  size_t sm = slice * nw;
+  if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
+  a.slice_bytes = (int64_t)slice;
+  int64_t grid = (nodes + nw - 1) / nw;
+  if (grid > sms) grid = sms;
+  auto k = wide ? k_md_leaf<LEAF_WARPS_WIDE> : k_md_leaf<LEAF_WARPS>;
+  allow_max_dynamic_smem(k);
+  launch_pdl(s, k, (unsigned)grid, 32 * nw, sm, a);
+  h->launches++;
+}
+
 size_t leaf_slice(int m) {
   const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1), m64 = (size_t)((m + 63) & ~63);
   const size_t need = W * S * 4 + m64 * 2 + 2 * m2 * 2 + (MD_LEAF / 32) * 6;
@@ -1128,7 +1166,6 @@ fp_status run_local_order(fp_handle* h) {
     while (cut < nleaf && hs[ls[0][cut]] > LEAF_SPLIT) ++cut;
     if (cut == 0 || cut == nleaf || nleaf <= 2 * warps1) cut = nleaf;
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
-    allow_max_dynamic_smem(k_md_leaf);
     for (int part = 0; part < 2; ++part) {
       const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : (int64_t)ls[0].size();
       if (hi <= lo) continue;
@@ -1136,17 +1173,7 @@ fp_status run_local_order(fp_handle* h) {
       a.nodes = dnodes + lo;
       a.nnodes_launch = (int32_t)(hi - lo);
       a.queue = base.queue + part;
-      const size_t slice = leaf_slice(hs[ls[0][lo]]);
-      int nw = (int)(220 * 1024 / slice);
-      nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
-      size_t sm = slice * nw;
-      if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
-      a.slice_bytes = (int64_t)slice;
-      int64_t grid = (hi - lo + nw - 1) / nw;
-      const int64_t cap = sms - reserved > 1 ? sms - reserved : 1;
-      if (grid > cap) grid = cap;
-      launch_pdl(h->stream, k_md_leaf, (unsigned)grid, 32 * nw, sm, a);
-      h->launches++;
+      launch_leaf(h, h->stream, a, leaf_slice(hs[ls[0][lo]]), hi - lo, cap_sms, true);
     }
   }
   {
@@ -1179,19 +1206,10 @@ fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count,
   fill_i32(h, queue, 0, 1);
   MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->node_begin, vlist, loc, perm_out,
            d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key, queue};
-  const size_t slice = leaf_slice(mmax);
-  int nw = (int)(220 * 1024 / slice);
-  nw = nw < 1 ? 1 : (nw > LEAF_WARPS ? LEAF_WARPS : nw);
-  size_t sm = slice * nw;
-  if (sm < 116 * 1024) sm = 116 * 1024;       // one CTA per SM
-  a.slice_bytes = (int64_t)slice;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  int64_t grid = ((int64_t)count + nw - 1) / nw;
-  if (grid > sms) grid = sms;
-  allow_max_dynamic_smem(k_md_leaf);
   ProfScope ps(FP_PROF_LEARNED, h->stream);
-  FP_LAUNCH(h, k_md_leaf, (int)grid, 32 * nw, sm, a);
+  launch_leaf(h, h->stream, a, leaf_slice(mmax), count, sms, false);
   FP_CHECK_LAUNCH(h, "keyed minimum degree");
   dev_free(h, queue);
   return FP_OK;

@@ -19,6 +19,7 @@
 // patch with the patch's adjacency in shared memory and CTA barriers only.
 #include <cooperative_groups.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "fp_device.cuh"
@@ -46,8 +47,13 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
                                                      unsigned long long* key, int4* fa, int4* fb, int32_t* ctr) {
   FP_PDL_WAIT();
   cg::grid_group grid = cg::this_grid();
+  // the tail's frontiers and counters (CTA 0 only): entries past BFS_TAIL
+  // spill to the global queues at the same index
+  __shared__ int4 s_fr[2][BFS_TAIL];
+  __shared__ int32_t s_ctr[3];
   int4* cur = fa;
   int4* nxt = fb;
+  int sel = 0;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   // one level: every frontier vertex claims its unsettled neighbours. The
@@ -58,15 +64,21 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
   // the claims (atomicMin returns the old key: a vertex settled at an
   // earlier level keeps it, and only the first claim of a vertex moves it to
   // the next frontier); the queue slots, with the claimed vertices' edge
-  // ranges loaded meanwhile.
-  auto sweep = [&](uint32_t level, int32_t ncur, int64_t first, int64_t stride) {
+  // ranges loaded meanwhile. In the tail (kTail) the entries and the
+  // counter are in shared memory, which leaves the label, neighbour, claim
+  // and edge-range round trips.
+  auto sweep = [&](auto tail_tag, uint32_t level, int32_t ncur, int64_t first, int64_t stride) {
+    constexpr bool kTail = decltype(tail_tag)::value;
     const unsigned long long dnext = (unsigned long long)(level + 1) << 32;
-    const bool pre = ncur > BFS_PRECHECK_MIN;
+    const bool pre = !kTail && ncur > BFS_PRECHECK_MIN;
+    int4* scur = s_fr[sel];
+    int4* snxt = s_fr[sel ^ 1];
+    int32_t* cnt = kTail ? s_ctr : ctr;
     for (int64_t i0 = first - lane; i0 < ncur; i0 += stride) {
       const int64_t i = i0 + lane;
       int32_t u = 0, e = 0, e1 = 0;
       if (i < ncur) {
-        const int4 q = __ldcg(&cur[i]);
+        const int4 q = (kTail && i < BFS_TAIL) ? scur[i] : __ldcg(&cur[i]);
         u = q.x;
         e = q.y;
         e1 = q.z;
@@ -106,11 +118,16 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
           tot += __popc(bb) << bp;
         }
         int32_t base = 0;
-        if (lane == 0 && tot) base = atomicAdd(&ctr[(level + 1) % 3], tot);
+        if (lane == 0 && tot) base = atomicAdd(&cnt[(level + 1) % 3], tot);
         base = __shfl_sync(0xffffffffu, base, 0) + ex;
 #pragma unroll
         for (int k = 0; k < BFS_BATCH; ++k)
-          if (claim >> k & 1u) nxt[base++] = make_int4(v[k], rb[k], re[k], 0);
+          if (claim >> k & 1u) {
+            const int4 q = make_int4(v[k], rb[k], re[k], 0);
+            if (kTail && base < BFS_TAIL) snxt[base] = q;
+            else nxt[base] = q;
+            ++base;
+          }
         e += BFS_BATCH;
       }
     }
@@ -118,27 +135,37 @@ __global__ void __launch_bounds__(BFS_THREADS, 2) k_bfs(const int32_t* __restric
   static_assert(BFS_BATCH <= 15, "claim counts must fit four bit planes");
   uint32_t level = 0;
   int32_t nprev = 0;
+  int32_t ncur = 0;
   for (;; ++level) {
-    const int32_t ncur = __ldcg(&ctr[level % 3]);
+    ncur = __ldcg(&ctr[level % 3]);
     if (ncur == 0) return;
     // the frontier grows from the seeds, peaks and dies out: the shrinking
     // tail goes to one CTA (the same decision in every CTA)
     if (ncur <= BFS_TAIL && ncur < nprev) break;
     nprev = ncur;
     if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
-    sweep(level, ncur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+    sweep(std::integral_constant<bool, false>{}, level, ncur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+          (int64_t)gridDim.x * blockDim.x);
     int4* t = cur; cur = nxt; nxt = t;
     grid.sync();
   }
   // small frontiers (the last levels): CTA 0 alone, with CTA barriers instead
-  // of grid barriers
+  // of grid barriers; the frontier (ncur <= BFS_TAIL entries) moves to
+  // shared memory
   if (blockIdx.x != 0) return;
+  for (int32_t i = threadIdx.x; i < ncur; i += blockDim.x) s_fr[0][i] = __ldcg(&cur[i]);
+  if (threadIdx.x == 0) {
+    s_ctr[level % 3] = ncur;
+    s_ctr[(level + 1) % 3] = 0;
+  }
+  __syncthreads();
   for (;; ++level) {
-    const int32_t ncur = __ldcg(&ctr[level % 3]);
+    ncur = s_ctr[level % 3];
     if (ncur == 0) return;
-    if (threadIdx.x == 0) ctr[(level + 2) % 3] = 0;
-    sweep(level, ncur, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) s_ctr[(level + 2) % 3] = 0;
+    sweep(std::integral_constant<bool, true>{}, level, ncur, threadIdx.x, blockDim.x);
     int4* t = cur; cur = nxt; nxt = t;
+    sel ^= 1;
     __syncthreads();
   }
 }
