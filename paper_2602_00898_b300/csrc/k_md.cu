@@ -356,7 +356,9 @@ __device__ __noinline__ void leaf_setup(const MdArgs& a, int32_t t, int m, int S
 // registers for launches of about one wave, whose time is the largest leaf's
 // latency, and 20 warps under the register cap that imposes (96 a thread,
 // a few bytes of spill in the setup, slower steps) for launches of many
-// waves, which gain the warps to hide the steps' latency.
+// waves, which gain the warps to hide the steps' latency. (The bound names
+// no minimum of CTAs per SM: with an explicit 1 the 10-warp build ran its
+// steps about 25% slower at the same register count.)
 constexpr int LEAF_WARPS = 10, LEAF_WARPS_WIDE = 20;
 template <int kWarps>
 __global__ void __launch_bounds__(kWarps * 32) k_md_leaf(MdArgs a) {
@@ -872,10 +874,7 @@ __global__ void k_early_place(const int32_t* __restrict__ node_of, int32_t n, in
 }
 
 // Warps of a leaf CTA (one CTA per SM): as many as the slices fit in 220 KB
-// of shared memory, up to wmax. The CTAs are packed rather than spread over
-// every SM: the separators' orderings on the auxiliary streams hold SMs
-// meanwhile, and a leaf CTA, which needs most of an SM's shared memory,
-// waits for one of those to drain.
+// of shared memory, up to wmax.
 int leaf_warps(size_t slice, int wmax) {
   int64_t nw = (int64_t)(220 * 1024 / slice);
   if (nw > wmax) nw = wmax;
