@@ -238,9 +238,11 @@ struct BisectView {
 // lvl must be -1 on the component. Returns the number of levels. One barrier
 // per level: level l reads its frontier size from scnt[l % 3], appends to
 // scnt[(l + 1) % 3] and clears scnt[(l + 2) % 3], which nobody touches during
-// level l. Each frontier patch claims its neighbours BFS_CLAIM at a time and
-// appends its claims with one shared atomic.
-constexpr int BFS_CLAIM = 8;
+// level l. Eight lanes share a frontier patch, one edge each per round, so a
+// patch's claims go out together instead of one after another; a warp's
+// claims (four patches) are appended with one shared atomic, their offsets
+// from a ballot. The levels do not depend on the order of the claims.
+constexpr int BFS_LANES = 8;
 __device__ int block_bfs(const BisectView& v, int32_t src, int32_t* scnt) {
   int32_t* fa = v.qa;
   int32_t* fb = v.qb;
@@ -252,29 +254,34 @@ __device__ int block_bfs(const BisectView& v, int32_t src, int32_t* scnt) {
     scnt[2] = 0;
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int sub = lane / BFS_LANES, k = lane % BFS_LANES;
+  constexpr int PER_WARP = 32 / BFS_LANES;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int level = 0;
   for (;;) {
     const int32_t nf = scnt[level % 3];
     if (nf == 0) break;
     if (threadIdx.x == 0) scnt[(level + 2) % 3] = 0;
     int32_t* nxt_cnt = &scnt[(level + 1) % 3];
-    for (int32_t i = threadIdx.x; i < nf; i += blockDim.x) {
-      const int32_t u = fa[i];
-      const int32_t e0 = v.rbeg[u], len = v.rlen[u];
-      for (int32_t eb = 0; eb < len; eb += BFS_CLAIM) {
-        int32_t w[BFS_CLAIM];
-        uint32_t got = 0;
-#pragma unroll
-        for (int k = 0; k < BFS_CLAIM; ++k) w[k] = eb + k < len ? v.adj[e0 + eb + k] : -1;
-#pragma unroll
-        for (int k = 0; k < BFS_CLAIM; ++k)
-          if (w[k] >= 0 && atomicCAS(&v.lvl[w[k]], -1, level + 1) == -1) got |= 1u << k;
-        if (got) {
-          int32_t o = atomicAdd(nxt_cnt, __popc(got));
-#pragma unroll
-          for (int k = 0; k < BFS_CLAIM; ++k)
-            if (got >> k & 1u) fb[o++] = w[k];
-        }
+    // warp-uniform sweep: PER_WARP frontier patches a warp per pass
+    for (int32_t i0 = warp * PER_WARP; i0 < nf; i0 += nwarps * PER_WARP) {
+      const int32_t i = i0 + sub;
+      int32_t e0 = 0, len = 0;
+      if (i < nf) {
+        const int32_t u = fa[i];
+        e0 = v.rbeg[u];
+        len = v.rlen[u];
+      }
+      for (int32_t e = k; __any_sync(0xffffffffu, e < len); e += BFS_LANES) {
+        const int32_t w = e < len ? v.adj[e0 + e] : -1;
+        const bool got = w >= 0 && atomicCAS(&v.lvl[w], -1, level + 1) == -1;
+        const unsigned bb = __ballot_sync(0xffffffffu, got);
+        int32_t o = 0;
+        if (lane == 0 && bb) o = atomicAdd(nxt_cnt, __popc(bb));
+        o = __shfl_sync(0xffffffffu, o, 0);
+        if (got) fb[o + __popc(bb & lt)] = w;
       }
     }
     __syncthreads();
