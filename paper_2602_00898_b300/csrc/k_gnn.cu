@@ -163,7 +163,11 @@ constexpr int SC_X = SC_B2 + 32 * 64 * 2;     // feature codes 512 x 8
 constexpr int SC_H = SC_X + GNN_LEAF_MAX * 8;  // layer-1 codes 512 x 32
 constexpr int SC_DEPTH = SC_H + GNN_LEAF_MAX * 32;
 constexpr int SC_DEG = SC_DEPTH + GNN_LEAF_MAX * 4;
-constexpr int SC_BYTES = SC_DEG + GNN_LEAF_MAX * 4;
+constexpr int SC_AOFF = SC_DEG + GNN_LEAF_MAX * 4;   // local adjacency: row starts (uint16)
+constexpr int SC_ECAP = 4096;                         //   and up to 4096 entries (uint16)
+constexpr int SC_ADJ = SC_AOFF + GNN_LEAF_MAX * 2;
+constexpr int SC_BYTES = SC_ADJ + SC_ECAP * 2;
+constexpr int SC_GD = 16;                             // rows gathered on chip: at most 16 entries
 
 // Visits the within-leaf neighbours (local indices) of local vertex i.
 template <class Fn>
@@ -192,11 +196,16 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
   uint8_t* H = sm + SC_H;
   uint32_t* depth = (uint32_t*)(sm + SC_DEPTH);
   int32_t* degh = (int32_t*)(sm + SC_DEG);
+  uint16_t* aoff = (uint16_t*)(sm + SC_AOFF);
+  uint16_t* adj = (uint16_t*)(sm + SC_ADJ);
+  __shared__ int32_t s_ne, s_ovf;
 
   if (warp == 0) tc_alloc32(&s_tmem);
   if (tid == 0) {
     mbar_init(&s_mbar, 1);
     s_dmax = 0;
+    s_ne = 0;
+    s_ovf = 0;
   }
   // weights as BF16 operands: B1 = [w1s | w1n | 0] (32 x 16), B2 = [w2s | w2n] (32 x 64)
   for (int x = tid; x < 32 * 16; x += SC_THREADS) {
@@ -209,13 +218,59 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
     const int32_t c = k < 32 ? a.q[P_W2S + r * 32 + k] : a.q[P_W2N + r * 32 + k - 32];
     put_bf16(sm + SC_B2, kmajor_off(r, k, 64), c);
   }
-  // 1. degrees and the boundary (depth 0)
+  __syncthreads();
+  // 0. the leaf's local adjacency in shared memory, gathered once: a row's
+  // entries (at most SC_GD) and their positions are loaded together, the
+  // within-leaf ones appended to the list by one shared atomic. A row above
+  // SC_GD entries or a list above SC_ECAP leaves every pass on the global
+  // rows instead (the same neighbours; every use below is order-free).
   for (int32_t i = tid; i < m; i += SC_THREADS) {
     const int32_t v = a.perm[b + i];
-    const int32_t dg = a.rowptr[v + 1] - a.rowptr[v];
+    const int32_t e0 = a.rowptr[v], dg = a.rowptr[v + 1] - e0;
+    depth[i] = (uint32_t)dg;                       // the degree, until step 1
+    if (dg > SC_GD) {
+      s_ovf = 1;
+      continue;
+    }
+    int32_t p[SC_GD];
+#pragma unroll
+    for (int k = 0; k < SC_GD; ++k) p[k] = k < dg ? a.col[e0 + k] : -1;
+#pragma unroll
+    for (int k = 0; k < SC_GD; ++k) p[k] = p[k] >= 0 ? a.iperm[p[k]] - b : -1;
     int32_t dh = 0;
-    leaf_neighbours(a, b, m, i, [&](int32_t) { ++dh; });
+#pragma unroll
+    for (int k = 0; k < SC_GD; ++k) dh += (p[k] >= 0 && p[k] < m) ? 1 : 0;
+    int32_t o = atomicAdd(&s_ne, dh);
+    if (o + dh > SC_ECAP) {
+      s_ovf = 1;
+      continue;
+    }
+    aoff[i] = (uint16_t)o;
     degh[i] = dh;
+#pragma unroll
+    for (int k = 0; k < SC_GD; ++k)
+      if (p[k] >= 0 && p[k] < m) adj[o++] = (uint16_t)p[k];
+  }
+  __syncthreads();
+  const bool on_chip = s_ovf == 0;
+  auto nbrs = [&](int32_t i, auto fn) {
+    if (on_chip) {
+      const int32_t o = aoff[i], d = degh[i];
+      for (int32_t k = 0; k < d; ++k) fn((int32_t)adj[o + k]);
+    } else {
+      leaf_neighbours(a, b, m, i, fn);
+    }
+  };
+  // 1. degrees and the boundary (depth 0)
+  for (int32_t i = tid; i < m; i += SC_THREADS) {
+    const int32_t dg = (int32_t)depth[i];
+    int32_t dh = 0;
+    if (on_chip) {
+      dh = degh[i];
+    } else {
+      leaf_neighbours(a, b, m, i, [&](int32_t) { ++dh; });
+      degh[i] = dh;
+    }
     depth[i] = dh < dg ? 0u : INF_DEPTH;
     X[i * 8 + 1] = (uint8_t)min(8 * dg, 255);
     X[i * 8 + 2] = dh < dg ? 64 : 0;
@@ -227,7 +282,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
     __syncthreads();
     for (int32_t i = tid; i < m; i += SC_THREADS) {
       if (depth[i] != d) continue;
-      leaf_neighbours(a, b, m, i, [&](int32_t j) {
+      nbrs(i, [&](int32_t j) {
         if (depth[j] == INF_DEPTH) {
           depth[j] = d + 1;
           s_flag = 1;
@@ -270,7 +325,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
       const int32_t i = tile * 128 + tid;
       if (layer == 1) {
         int32_t sum[6] = {0, 0, 0, 0, 0, 0};
-        if (i < m) leaf_neighbours(a, b, m, i, [&](int32_t j) {
+        if (i < m) nbrs(i, [&](int32_t j) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) sum[k] += X[j * 8 + k];
         });
@@ -288,7 +343,7 @@ __global__ void __launch_bounds__(SC_THREADS) k_gnn_score(ScoreArgs a) {
         int32_t sum[32];
 #pragma unroll
         for (int k = 0; k < 32; ++k) sum[k] = 0;
-        if (i < m) leaf_neighbours(a, b, m, i, [&](int32_t j) {
+        if (i < m) nbrs(i, [&](int32_t j) {
           const uint32_t* hj = (const uint32_t*)(H + j * 32);
 #pragma unroll
           for (int w = 0; w < 8; ++w) {
