@@ -1076,8 +1076,9 @@ fp_status run_local_order(fp_handle* h) {
   MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, nvstart, nvlist, loc, h->perm,
               nullptr, 0, grows, dup + off64, gs, dup + off64 + nsg, 0, nullptr, nullptr, ovf + ls[1].size()};
   // the separators ordered during the dissection are completed on the first
-  // auxiliary stream, the other separators run on the second one (so that
-  // they need not wait for the early ones), the leaves on the handle's stream
+  // auxiliary stream, followed there by those too large for shared memory
+  // (the longest orderings), the other separators run on the second one (so
+  // that they need not wait for either), the leaves on the handle's stream
   // in CTAs that fill whole SMs, leaving `reserved` SMs for separator CTAs
   AuxStream* ax = aux_stream(h->device, 0);
   AuxStream* ax3 = aux_stream(h->device, 1);
@@ -1143,11 +1144,11 @@ fp_status run_local_order(fp_handle* h) {
     const size_t M64 = (size_t)((mmax[2] + 63) & ~63);
     const size_t smsp = M64 * 2 + (size_t)((mmax[2] + 1) & ~1) * 2 + (M64 / 64) * 4;
     allow_max_dynamic_smem(k_md_sparse<true>);
-    ProfScope ps(FP_PROF_MD_LARGE, s3);
-    launch_pdl(s3, k_md_sparse<true>, (unsigned)ls[2].size(), MD_THREADS, smsp, a);
+    ProfScope ps(FP_PROF_MD_LARGE, s2);
+    launch_pdl(s2, k_md_sparse<true>, (unsigned)ls[2].size(), MD_THREADS, smsp, a);
     const size_t smg = (size_t)2 * MD_MAX * sizeof(uint16_t);
     allow_max_dynamic_smem(k_md_global);
-    launch_pdl(s3, k_md_global, (unsigned)ls[2].size(), MD_THREADS, smg, a);
+    launch_pdl(s2, k_md_global, (unsigned)ls[2].size(), MD_THREADS, smg, a);
     h->launches += 2;
   }
   if (!ls[0].empty()) {
