@@ -291,11 +291,16 @@ void early_md_release(fp_handle* h);
 fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops);
 // a10 (k_gnn.cu, k_md.cu, k_symbolic.cu)
 fp_status run_learned(fp_handle* h);
-fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax);
+// lsz (optional) receives the listed leaves' sizes, in list order.
+fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax,
+                    std::vector<int32_t>* lsz = nullptr);
 fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, const int32_t* d_q, uint32_t* d_key,
                            int32_t* d_score, uint8_t* d_x);
+// lsz (optional): the nodes' sizes in list order (largest first), which lets
+// the leaves run in two size classes like the plain leaf orderings.
 fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count, int32_t mmax, int32_t* vlist,
-                            int32_t* loc, const uint32_t* key, int32_t* perm_out);
+                            int32_t* loc, const uint32_t* key, int32_t* perm_out,
+                            const std::vector<int32_t>* lsz = nullptr);
 fp_status run_leaf_fill(fp_handle* h, const int32_t* perm, const int32_t* iperm, const int32_t* d_nodes,
                         int32_t count, int64_t* d_fill);
 // f4: numeric Cholesky of P A P^T over the tree (k_numeric.cu).

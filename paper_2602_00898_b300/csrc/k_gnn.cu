@@ -453,7 +453,7 @@ __global__ void k_scatter_inverse(const int32_t* __restrict__ perm, int32_t n, i
 
 // Leaves of the tree (nodes with vertices and no non-empty descendant) with
 // at most 512 vertices, from the node sizes; returns the list on the device.
-fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax) {
+fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax, std::vector<int32_t>* lsz) {
   const int64_t nn = h->nnodes;
   std::vector<int32_t> sz(nn);
   cudaError_t e = cudaMemcpyAsync(sz.data(), h->node_size, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, h->stream);
@@ -473,6 +473,10 @@ fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, in
     }
   // largest first: the per-leaf kernels that draw leaves from a queue balance better
   std::stable_sort(hl.begin(), hl.end(), [&](int32_t x, int32_t y) { return sz[x] > sz[y]; });
+  if (lsz) {
+    lsz->resize(hl.size());
+    for (size_t i = 0; i < hl.size(); ++i) (*lsz)[i] = sz[hl[i]];
+  }
   *d_list = (int32_t*)dev_alloc(h, sizeof(int32_t) * (hl.size() + 1));
   if (!*d_list) return fail(h, FP_ERR_OUT_OF_MEMORY, "leaf list");
   if (!hl.empty()) {
@@ -500,10 +504,10 @@ fp_status run_learned(fp_handle* h) {
   h->fill_plain = h->fill_chosen = 0;
   if (!h->qnet || n == 0) return FP_OK;
   ProfScope ps(FP_PROF_LEARNED, h->stream);
-  std::vector<int32_t> hl;
+  std::vector<int32_t> hl, lsz;
   int32_t* dl = nullptr;
   int32_t mmax = 0;
-  FP_TRY(leaf_list(h, hl, &dl, &mmax));
+  FP_TRY(leaf_list(h, hl, &dl, &mmax, &lsz));
   const int32_t nl = (int32_t)hl.size();
   const int64_t nn = h->nnodes;
   uint32_t* key = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * n);
@@ -522,7 +526,7 @@ fp_status run_learned(fp_handle* h) {
   FP_TRY(launch_gnn_score(h, dl, nl, h->qnet, key, h->scores, nullptr));
   cudaMemcpyAsync(vlist, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
   cudaMemcpyAsync(perm_l, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
-  FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, key, perm_l));
+  FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, key, perm_l, &lsz));
   const int G = (int)std::min<int64_t>((n + 255) / 256, NUM_SMS_B300 * 8);
   FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, perm_l, n, iperm_l);
   FP_TRY(run_leaf_fill(h, h->perm, h->iperm, dl, nl, fills));

@@ -342,10 +342,10 @@ fp_status gnn_sample(fp_handle* h, int32_t n_seeds, uint8_t* d_x, uint8_t* d_mas
   if (n_seeds < 0 || n_seeds > 64 || !d_x || !d_mask || !d_target || !d_lrowptr || !h_lnnz)
     return fail(h, FP_ERR_INVALID_ARG, "bad sample arguments");
   ProfScope ps(FP_PROF_TRAIN, h->stream);
-  std::vector<int32_t> hl;
+  std::vector<int32_t> hl, lsz;
   int32_t* dl = nullptr;
   int32_t mmax = 0;
-  FP_TRY(leaf_list(h, hl, &dl, &mmax));
+  FP_TRY(leaf_list(h, hl, &dl, &mmax, &lsz));
   const int32_t nl = (int32_t)hl.size();
   const int64_t nn = h->nnodes;
   // within-leaf graph: counts -> scan -> neighbour positions
@@ -387,7 +387,7 @@ fp_status gnn_sample(fp_handle* h, int32_t n_seeds, uint8_t* d_x, uint8_t* d_mas
     FP_LAUNCH(h, k_seed_keys, G, 256, 0, n, (uint64_t)r, key);
     cudaMemcpyAsync(vlist, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync(perm_r, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
-    FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, r == 0 ? nullptr : key, perm_r));
+    FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, r == 0 ? nullptr : key, perm_r, &lsz));
     FP_LAUNCH(h, k_scatter_positions, G, 256, 0, perm_r, n, iperm_r);
     FP_TRY(run_leaf_fill(h, perm_r, iperm_r, dl, nl, fill));
     if (nl) FP_LAUNCH(h, k_keep_best, nl, 128, 0, dl, h->node_begin, h->node_size, fill, r, fill + nn, perm_r, best);

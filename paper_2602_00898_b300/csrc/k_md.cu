@@ -902,6 +902,24 @@ void launch_leaf(fp_handle* h, cudaStream_t s, const MdArgs& a0, size_t slice, i
   h->launches++;
 }
 
+size_t leaf_slice(int m);
+
+// The leaf orderings run in two launches when the leaves span both size
+// classes and are many more than one launch's warps (several waves): those
+// above LEAF_SPLIT vertices with slices for the largest, then the others with
+// slices for at most LEAF_SPLIT, so that more warps fit on an SM. With few
+// leaves one wave holds them all and a second launch would only add its own
+// largest leaf to the time. sz: the sizes, largest first; returns the number
+// of leaves in the first launch (all of them for one launch).
+int64_t leaf_class_cut(const int32_t* sz, int64_t nleaf, int32_t mmax, int64_t sms) {
+  constexpr int LEAF_SPLIT = 256;
+  const int64_t warps1 = sms * std::max(1, std::min<int>(LEAF_WARPS, (int)(220 * 1024 / leaf_slice(mmax))));
+  int64_t cut = 0;
+  while (cut < nleaf && sz[cut] > LEAF_SPLIT) ++cut;
+  if (cut == 0 || cut == nleaf || nleaf <= 2 * warps1) cut = nleaf;
+  return cut;
+}
+
 size_t leaf_slice(int m) {
   const size_t W = (m + 31) >> 5, S = m | 1, m2 = (size_t)((m + 1) & ~1), m64 = (size_t)((m + 63) & ~63);
   const size_t need = W * S * 4 + m64 * 2 + 2 * m2 * 2 + (MD_LEAF / 32) * 6;
@@ -1152,19 +1170,11 @@ fp_status run_local_order(fp_handle* h) {
     h->launches += 2;
   }
   if (!ls[0].empty()) {
-    // two launches when the leaves span both size classes and are many more
-    // than one launch's warps (several waves): those above LEAF_SPLIT
-    // vertices with slices for the largest, then the others with slices for
-    // at most LEAF_SPLIT, so that more warps fit on an SM. With few leaves
-    // one wave holds them all and a second launch would only add its own
-    // largest leaf to the time.
-    constexpr int LEAF_SPLIT = 256;
     const int64_t nleaf = (int64_t)ls[0].size();
     const int64_t cap_sms = sms - reserved > 1 ? sms - reserved : 1;
-    const int64_t warps1 = cap_sms * std::max(1, std::min<int>(LEAF_WARPS, (int)(220 * 1024 / leaf_slice(mmax[0]))));
-    int64_t cut = 0;
-    while (cut < nleaf && hs[ls[0][cut]] > LEAF_SPLIT) ++cut;
-    if (cut == 0 || cut == nleaf || nleaf <= 2 * warps1) cut = nleaf;
+    std::vector<int32_t> lsz(nleaf);
+    for (int64_t i = 0; i < nleaf; ++i) lsz[i] = hs[ls[0][i]];
+    const int64_t cut = leaf_class_cut(lsz.data(), nleaf, mmax[0], cap_sms);
     ProfScope ps(FP_PROF_MD_SMALL, h->stream);
     for (int part = 0; part < 2; ++part) {
       const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : (int64_t)ls[0].size();
@@ -1198,18 +1208,30 @@ fp_status run_local_order(fp_handle* h) {
 }
 
 fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count, int32_t mmax, int32_t* vlist,
-                            int32_t* loc, const uint32_t* key, int32_t* perm_out) {
+                            int32_t* loc, const uint32_t* key, int32_t* perm_out, const std::vector<int32_t>* lsz) {
   if (count == 0) return FP_OK;
   if (mmax > MD_LEAF) return fail(h, FP_ERR_UNSUPPORTED, "keyed ordering of a node above 512 vertices");
-  int32_t* queue = (int32_t*)dev_alloc(h, sizeof(int32_t));
+  if (lsz && (int64_t)lsz->size() != count) return fail(h, FP_ERR_INVALID_ARG, "leaf sizes do not match the list");
+  int32_t* queue = (int32_t*)dev_alloc(h, 2 * sizeof(int32_t));
   if (!queue) return fail(h, FP_ERR_OUT_OF_MEMORY, "node queue");
-  fill_i32(h, queue, 0, 1);
-  MdArgs a{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->node_begin, vlist, loc, perm_out,
-           d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key, queue};
+  fill_i32(h, queue, 0, 2);
+  MdArgs base{h->rowptr, h->col, h->node_of, h->node_begin, h->node_size, h->node_begin, vlist, loc, perm_out,
+              d_nodes, count, nullptr, nullptr, nullptr, nullptr, 0, nullptr, key, queue};
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  // the list is largest first: with the sizes, the same two size classes as
+  // the plain leaf orderings
+  const int64_t cut = lsz ? leaf_class_cut(lsz->data(), count, mmax, sms) : count;
   ProfScope ps(FP_PROF_LEARNED, h->stream);
-  launch_leaf(h, h->stream, a, leaf_slice(mmax), count, sms, false);
+  for (int part = 0; part < 2; ++part) {
+    const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : count;
+    if (hi <= lo) continue;
+    MdArgs a = base;
+    a.nodes = d_nodes + lo;
+    a.nnodes_launch = (int32_t)(hi - lo);
+    a.queue = queue + part;
+    launch_leaf(h, h->stream, a, leaf_slice(part == 0 ? mmax : (*lsz)[lo]), hi - lo, sms, part == 1);
+  }
   FP_CHECK_LAUNCH(h, "keyed minimum degree");
   dev_free(h, queue);
   return FP_OK;
