@@ -141,6 +141,15 @@ struct fp_handle {
   int32_t learned_leaves = 0, learned_kept = 0;
   int64_t fill_plain = 0, fill_chosen = 0;
 
+  // the learned pass runs beside the separator orderings: run_local_order
+  // leaves them on the auxiliary streams (join_pending), with the buffers to
+  // free after the join and the vertex lists by node (positions for the
+  // provisional permutation); finish_orderings joins
+  bool join_pending = false;
+  std::vector<void*> join_frees;
+  const int32_t* pend_nvlist = nullptr;
+  const int32_t* pend_nvstart = nullptr;
+
   // numeric factor (fp_factor), released by fp_permute and fp_destroy
   fp::NumericFactor* numeric = nullptr;
 
@@ -291,11 +300,17 @@ void early_md_release(fp_handle* h);
 fp_status run_symbolic(fp_handle* h, int32_t* d_parent, int32_t* d_colcount, int64_t* nnzL, int64_t* flops);
 // a10 (k_gnn.cu, k_md.cu, k_symbolic.cu)
 fp_status run_learned(fp_handle* h);
+// Joins the separator orderings that run_local_order left running (a no-op
+// unless h->join_pending): the handle's stream waits for both auxiliary
+// streams, then the ordering stage's buffers are freed.
+fp_status finish_orderings(fp_handle* h);
 // lsz (optional) receives the listed leaves' sizes, in list order.
 fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, int32_t* mmax,
                     std::vector<int32_t>* lsz = nullptr);
+// perm/iperm: the positions to read (null: the handle's own).
 fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, const int32_t* d_q, uint32_t* d_key,
-                           int32_t* d_score, uint8_t* d_x);
+                           int32_t* d_score, uint8_t* d_x, const int32_t* perm = nullptr,
+                           const int32_t* iperm = nullptr);
 // lsz (optional): the nodes' sizes in list order (largest first), which lets
 // the leaves run in two size classes like the plain leaf orderings.
 fp_status run_leaf_md_keyed(fp_handle* h, const int32_t* d_nodes, int32_t count, int32_t mmax, int32_t* vlist,

@@ -444,6 +444,28 @@ __global__ void k_choose(const int32_t* __restrict__ leaves, int32_t nl, const i
   }
 }
 
+// A provisional permutation while the separators are still being ordered on
+// the auxiliary streams: every vertex takes a place inside its node's range
+// (its index in the node's vertex list) ...
+__global__ void k_prov_perm(const int32_t* __restrict__ nvlist, const int32_t* __restrict__ nvstart,
+                            const int32_t* __restrict__ node_of, const int32_t* __restrict__ node_begin, int32_t n,
+                            int32_t* __restrict__ perm_p) {
+  FP_PDL_WAIT();
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int32_t v = nvlist[i], t = node_of[v];
+    perm_p[node_begin[t] + (i - nvstart[t])] = v;
+  }
+}
+
+// ... and the listed leaves their final order (one CTA a leaf).
+__global__ void k_leaf_orders(const int32_t* __restrict__ leaves, const int32_t* __restrict__ node_begin,
+                              const int32_t* __restrict__ node_size, const int32_t* __restrict__ perm,
+                              int32_t* __restrict__ perm_p) {
+  FP_PDL_WAIT();
+  const int32_t t = leaves[blockIdx.x], b = node_begin[t], m = node_size[t];
+  for (int32_t i = threadIdx.x; i < m; i += blockDim.x) perm_p[b + i] = perm[b + i];
+}
+
 __global__ void k_scatter_inverse(const int32_t* __restrict__ perm, int32_t n, int32_t* __restrict__ iperm) {
   FP_PDL_WAIT();
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) iperm[perm[i]] = i;
@@ -487,9 +509,10 @@ fp_status leaf_list(fp_handle* h, std::vector<int32_t>& hl, int32_t** d_list, in
 }
 
 fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, const int32_t* d_q, uint32_t* d_key,
-                           int32_t* d_score, uint8_t* d_x) {
+                           int32_t* d_score, uint8_t* d_x, const int32_t* perm, const int32_t* iperm) {
   if (nl == 0) return FP_OK;
-  ScoreArgs sa{h->rowptr, h->col, h->perm, h->iperm, h->node_begin, h->node_size, d_leaves, nl, d_q,
+  ScoreArgs sa{h->rowptr, h->col, perm ? perm : h->perm, iperm ? iperm : h->iperm, h->node_begin, h->node_size,
+               d_leaves, nl, d_q,
                h->opt.patch_cap, d_key, d_score, d_x, h->d_status,
                h->opt.max_spin > 0 ? h->opt.max_spin : SPIN_DEFAULT, h->seg ? h->seg->v : SegView{}};
   allow_max_dynamic_smem(k_gnn_score);
@@ -499,10 +522,16 @@ fp_status launch_gnn_score(fp_handle* h, const int32_t* d_leaves, int32_t nl, co
 }
 
 fp_status run_learned(fp_handle* h) {
+  // the separator orderings left running by run_local_order are joined on
+  // every way out
+  struct JoinGuard {
+    fp_handle* h;
+    ~JoinGuard() { if (h->join_pending) finish_orderings(h); }
+  } jg{h};
   const int32_t n = h->n;
   h->learned_leaves = h->learned_kept = 0;
   h->fill_plain = h->fill_chosen = 0;
-  if (!h->qnet || n == 0) return FP_OK;
+  if (!h->qnet || n == 0) return finish_orderings(h);
   ProfScope ps(FP_PROF_LEARNED, h->stream);
   std::vector<int32_t> hl, lsz;
   int32_t* dl = nullptr;
@@ -523,17 +552,37 @@ fp_status run_learned(fp_handle* h) {
   cudaMemsetAsync(key, 0, sizeof(uint32_t) * n, h->stream);
   cudaMemsetAsync(fills, 0, sizeof(int64_t) * 2 * nn, h->stream);
   cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * nst, h->stream);
-  FP_TRY(launch_gnn_score(h, dl, nl, h->qnet, key, h->scores, nullptr));
-  cudaMemcpyAsync(vlist, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
-  cudaMemcpyAsync(perm_l, h->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
-  FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, key, perm_l, &lsz));
   const int G = (int)std::min<int64_t>((n + 255) / 256, NUM_SMS_B300 * 8);
+  // positions this pass reads: the final ones once the orderings are joined;
+  // while the separators are still being ordered, a provisional permutation
+  // with the leaves' final orders. A leaf's scores and column counts depend
+  // on its own order and on which node each other vertex lies in, not on
+  // the order inside those nodes.
+  const int32_t* pm = h->perm;
+  const int32_t* ipm = h->iperm;
+  int32_t *perm_p = nullptr, *iperm_p = nullptr;
+  if (h->join_pending) {
+    perm_p = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    iperm_p = (int32_t*)dev_alloc(h, sizeof(int32_t) * n);
+    if (!perm_p || !iperm_p) return fail(h, FP_ERR_OUT_OF_MEMORY, "provisional permutation");
+    FP_LAUNCH(h, k_prov_perm, G, 256, 0, h->pend_nvlist, h->pend_nvstart, h->node_of, h->node_begin, n, perm_p);
+    if (nl > 0) FP_LAUNCH(h, k_leaf_orders, nl, 128, 0, dl, h->node_begin, h->node_size, h->perm, perm_p);
+    FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, perm_p, n, iperm_p);
+    pm = perm_p;
+    ipm = iperm_p;
+  }
+  FP_TRY(launch_gnn_score(h, dl, nl, h->qnet, key, h->scores, nullptr, pm, ipm));
+  cudaMemcpyAsync(vlist, pm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
+  cudaMemcpyAsync(perm_l, pm, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, h->stream);
+  FP_TRY(run_leaf_md_keyed(h, dl, nl, mmax, vlist, loc, key, perm_l, &lsz));
   FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, perm_l, n, iperm_l);
-  FP_TRY(run_leaf_fill(h, h->perm, h->iperm, dl, nl, fills));
+  FP_TRY(run_leaf_fill(h, pm, ipm, dl, nl, fills));
   FP_TRY(run_leaf_fill(h, perm_l, iperm_l, dl, nl, fills + nn));
   if (nl > 0)
     FP_LAUNCH(h, k_choose, nl, 128, 0, dl, nl, h->node_begin, h->node_size, fills, fills + nn, perm_l, h->perm, stats,
               h->seg ? h->seg->v : SegView{});
+  ps.end();
+  FP_TRY(finish_orderings(h));
   FP_LAUNCH(h, k_scatter_inverse, G, 256, 0, h->perm, n, h->iperm);
   FP_CHECK_LAUNCH(h, "learned choice");
   std::vector<unsigned long long> hs(nst);
@@ -551,8 +600,8 @@ fp_status run_learned(fp_handle* h) {
   h->fill_plain = (int64_t)tot[1];
   h->fill_chosen = (int64_t)tot[2];
   for (void* p : {(void*)dl, (void*)key, (void*)vlist, (void*)loc, (void*)perm_l, (void*)iperm_l, (void*)fills,
-                  (void*)stats})
-    dev_free(h, p);
+                  (void*)stats, (void*)perm_p, (void*)iperm_p})
+    if (p) dev_free(h, p);
   return FP_OK;
 }
 

@@ -1186,24 +1186,45 @@ fp_status run_local_order(fp_handle* h) {
       launch_leaf(h, h->stream, a, leaf_slice(hs[ls[0][lo]]), hi - lo, cap_sms, true);
     }
   }
-  {
-    // the pair brackets only the wait: it starts when the handle's stream has
-    // finished the leaves and ends when both auxiliary streams have finished
-    ProfScope ps(FP_PROF_JOIN_WAIT, h->stream);
-    cudaEventRecord(ax->join, s2);
-    cudaStreamWaitEvent(h->stream, ax->join, 0);
-    cudaEventRecord(ax3->join, s3);
-    cudaStreamWaitEvent(h->stream, ax3->join, 0);
+  h->join_frees = {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup};
+  h->join_pending = true;
+  if (h->qnet && n > 0) {
+    // the learned pass needs only the leaves' orders (on this stream) and
+    // some position inside each other node: it runs before the join
+    FP_CHECK_LAUNCH(h, "minimum degree");
+    h->pend_nvlist = nvlist;
+    h->pend_nvstart = nvstart;
+    return FP_OK;
   }
-  FP_CHECK_LAUNCH(h, "minimum degree");
-  early_md_release(h);
+  FP_TRY(finish_orderings(h));
   if (n > 0) {
     ProfScope ps(FP_PROF_PERM, h->stream);
     FP_LAUNCH(h, k_iperm, G, 256, 0, h->perm, n, h->iperm);
   }
   FP_CHECK_LAUNCH(h, "iperm");
-  for (void* p : {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup})
-    dev_free(h, p);
+  return FP_OK;
+}
+
+fp_status finish_orderings(fp_handle* h) {
+  if (!h->join_pending) return FP_OK;
+  h->join_pending = false;
+  AuxStream* ax = aux_stream(h->device, 0);
+  AuxStream* ax3 = aux_stream(h->device, 1);
+  if (!ax || !ax3) return fail(h, FP_ERR_CUDA, "auxiliary stream");
+  {
+    // the pair brackets only the wait: it starts when the handle's stream has
+    // finished its own work and ends when both auxiliary streams have
+    ProfScope ps(FP_PROF_JOIN_WAIT, h->stream);
+    cudaEventRecord(ax->join, ax->s);
+    cudaStreamWaitEvent(h->stream, ax->join, 0);
+    cudaEventRecord(ax3->join, ax3->s);
+    cudaStreamWaitEvent(h->stream, ax3->join, 0);
+  }
+  for (void* p : h->join_frees) dev_free(h, p);
+  h->join_frees.clear();
+  h->pend_nvlist = h->pend_nvstart = nullptr;
+  FP_CHECK_LAUNCH(h, "minimum degree");
+  early_md_release(h);
   return FP_OK;
 }
 
