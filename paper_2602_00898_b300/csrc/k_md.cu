@@ -1111,6 +1111,25 @@ fp_status run_local_order(fp_handle* h) {
   const int nbig = (int)(ls[1].size() + ls[2].size() + early.size());
   const int reserved = nbig < 24 ? nbig : 24;
   const int64_t lo1 = (int64_t)ls[0].size(), lo2 = lo1 + (int64_t)ls[1].size(), lo3 = lo2 + (int64_t)ls[2].size();
+  // the leaves first: their launch is on the critical path, the separators'
+  // on the auxiliary streams have time to spare
+  if (!ls[0].empty()) {
+    const int64_t nleaf = (int64_t)ls[0].size();
+    const int64_t cap_sms = sms - reserved > 1 ? sms - reserved : 1;
+    std::vector<int32_t> lsz(nleaf);
+    for (int64_t i = 0; i < nleaf; ++i) lsz[i] = hs[ls[0][i]];
+    const int64_t cut = leaf_class_cut(lsz.data(), nleaf, mmax[0], cap_sms);
+    ProfScope ps(FP_PROF_MD_SMALL, h->stream);
+    for (int part = 0; part < 2; ++part) {
+      const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : (int64_t)ls[0].size();
+      if (hi <= lo) continue;
+      MdArgs a = base;
+      a.nodes = dnodes + lo;
+      a.nnodes_launch = (int32_t)(hi - lo);
+      a.queue = base.queue + part;
+      launch_leaf(h, h->stream, a, leaf_slice(hs[ls[0][lo]]), hi - lo, cap_sms, true);
+    }
+  }
   if (!early.empty()) {
     // separators ordered during the dissection: redo the ones whose adjacency
     // lists overflowed with global rows, then place every other one's ranks
@@ -1168,23 +1187,6 @@ fp_status run_local_order(fp_handle* h) {
     allow_max_dynamic_smem(k_md_global);
     launch_pdl(s2, k_md_global, (unsigned)ls[2].size(), MD_THREADS, smg, a);
     h->launches += 2;
-  }
-  if (!ls[0].empty()) {
-    const int64_t nleaf = (int64_t)ls[0].size();
-    const int64_t cap_sms = sms - reserved > 1 ? sms - reserved : 1;
-    std::vector<int32_t> lsz(nleaf);
-    for (int64_t i = 0; i < nleaf; ++i) lsz[i] = hs[ls[0][i]];
-    const int64_t cut = leaf_class_cut(lsz.data(), nleaf, mmax[0], cap_sms);
-    ProfScope ps(FP_PROF_MD_SMALL, h->stream);
-    for (int part = 0; part < 2; ++part) {
-      const int64_t lo = part == 0 ? 0 : cut, hi = part == 0 ? cut : (int64_t)ls[0].size();
-      if (hi <= lo) continue;
-      MdArgs a = base;
-      a.nodes = dnodes + lo;
-      a.nnodes_launch = (int32_t)(hi - lo);
-      a.queue = base.queue + part;
-      launch_leaf(h, h->stream, a, leaf_slice(hs[ls[0][lo]]), hi - lo, cap_sms, true);
-    }
   }
   h->join_frees = {(void*)sub, (void*)nvstart, (void*)nvfill, (void*)nvlist, (void*)loc, (void*)tmp, (void*)dup};
   h->join_pending = true;
