@@ -619,27 +619,28 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
           const uint4* su = (const uint4*)nu;
           lu.q[0] = su[0]; lu.q[1] = su[1]; lu.q[2] = su[2];
           du = deg[u];
-          // new list: the old entries except p ...
+        }
+        // the loops run to the warp's longest list (a uniform exit, no
+        // divergent branch per lane) with each lane's own entries predicated
+        const int dmax = (int)__reduce_max_sync(0xffffffffu, (uint32_t)du);
+        // new list: the old entries except p ...
 #pragma unroll
-          for (int k = 0; k < SP_CAP; ++k) {
-            if (k >= du) break;
-            if (lu.e[k] != p) nu[pos++] = lu.e[k];
-          }
+        for (int k = 0; k < SP_CAP; ++k) {
+          if (k >= dmax) break;
+          if (k < du && lu.e[k] != p) nu[pos++] = lu.e[k];
         }
         // ... then p's other neighbours not yet present (broadcast one by one)
         for (int j = 0; j < dp; ++j) {
           const int y = __shfl_sync(0xffffffffu, mine_nb, j);
-          if (lane < dp && y != u) {
-            bool found = false;
+          bool found = !(lane < dp && y != u);
 #pragma unroll
-            for (int k = 0; k < SP_CAP; ++k) {
-              if (k >= du) break;
-              found |= lu.e[k] == y;
-            }
-            if (!found) {
-              if (pos < SP_CAP) nu[pos++] = (uint16_t)y;
-              else my_ovf = true;
-            }
+          for (int k = 0; k < SP_CAP; ++k) {
+            if (k >= dmax) break;
+            found |= k < du && lu.e[k] == y;
+          }
+          if (!found) {
+            if (pos < SP_CAP) nu[pos++] = (uint16_t)y;
+            else my_ovf = true;
           }
         }
         // group minima: a neighbour whose key fell lowers its group's
