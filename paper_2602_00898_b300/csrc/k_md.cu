@@ -602,8 +602,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         const int p = (int)(pkey & 0xffffu);
         const int dp = (int)(pkey >> 16);
         // lane j holds the j-th neighbour of p
+        // (p's row is not written during the step, and the previous step's
+        // writes were ordered by its closing warp sync)
         const int mine_nb = lane < dp ? (int)adj[(size_t)p * SP_CAP + lane] : -1;
-        __syncwarp();
         if (lane == 0) {
           order[step] = (uint16_t)p;
           deg[p] = DEG_DEAD;
