@@ -614,12 +614,17 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
         union L24 { uint4 q[3]; uint16_t e[SP_CAP]; };
         L24 lu;
         uint16_t* nu = nullptr;
+        // u's group minimum is read as soon as u is known: the neighbours'
+        // lowerings in this step can only make a rescan it asks for
+        // unnecessary, never a needed one missing (rescans are exact)
+        uint32_t gmin_u = 0xffffffffu;
         if (lane < dp) {
           u = mine_nb;
           nu = adj + (size_t)u * SP_CAP;
           const uint4* su = (const uint4*)nu;
           lu.q[0] = su[0]; lu.q[1] = su[1]; lu.q[2] = su[2];
           du = deg[u];
+          gmin_u = gmin[u >> 6];
         }
         // the loops run to the warp's longest list (a uniform exit, no
         // divergent branch per lane) with each lane's own entries predicated
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_sparse(MdArgs a) {
           const uint32_t kold = ((uint32_t)du << 16) | (uint32_t)u, knew = ((uint32_t)pos << 16) | (uint32_t)u;
           gu = u >> 6;
           if (knew < kold) atomicMin(&gmin[gu], knew);
-          else if (knew > kold && gmin[gu] == kold) resc = true;
+          else if (knew > kold && gmin_u == kold) resc = true;
         }
         __syncwarp();
         ovf = __any_sync(0xffffffffu, my_ovf);
