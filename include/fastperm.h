@@ -298,8 +298,8 @@ fp_status fp_batch_order_learned(fp_batch_item* items, int32_t count, const fp_o
                                  const int32_t* h_codes);
 
 /*
- * The fused batch as a handle (the survey's batch create / permute /
- * symbolic; the paper has no batch form): fp_batch_create builds ONE handle
+ * The fused batch as a handle (batch create / permute / symbolic, in three
+ * calls; the paper has no batch form): fp_batch_create builds ONE handle
  * for the disjoint union of the items' meshes (device faces read on `stream`
  * during the call; patch caps as in fp_batch_order: item->patch_cap, or the
  * autotuned cap of its size class); fp_batch_permute orders it and writes
